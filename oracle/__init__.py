@@ -1,0 +1,18 @@
+"""FP64 CPU oracle for the SD-OCT model-based reconstruction (ISAM forward model,
+its adjoint, the proximal steps and FISTA).
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow, obviously-correct numpy in float64 that
+restates the paper's definitions.  Only the test-suite, the package smoke check
+and the benchmark's CPU-baseline leg may import it; the library itself never
+does, and it shares no code with the CUDA path (inputs come from the seeded
+workload generators, which hold no reconstruction arithmetic).
+
+Modules:
+  isam     -- system operator Phi and its adjoint (Sec. 2.1, Eqs. for_model /
+              back_model), both as a direct non-uniform DFT and as the
+              Kaiser-Bessel NUFFT the paper uses.
+  wavelet  -- orthonormal Daubechies wavelet (4 vanishing moments) built by
+              spectral factorisation, and its periodic 2-D transform.
+  fista    -- penalties, proximal maps, power iteration, ISTA and FISTA
+              (Sec. 2.2-2.3, Eq. alg).
+"""
