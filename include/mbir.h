@@ -1,0 +1,224 @@
+/*
+ * mbir.h -- C ABI of the GB300 model-based iterative reconstruction library for
+ * spectral-domain OCT (Mason et al., "Model-based iterative reconstruction for
+ * spectral-domain optical coherence tomography").
+ *
+ * The library applies the ISAM system operator Phi (Sec. 2.1, Eq. for_model),
+ * its adjoint Phi^H (Sec. 2.1, Eq. back_model, taken as the exact transpose in
+ * the real inner products) and solves
+ *
+ *     x = argmin_x 1/2 ||Phi(x) - y||_2^2 + lambda ||Psi x||_1     (Eqs. obj, ls_obj)
+ *
+ * with FISTA (Sec. 2.3, Eq. alg), Psi = I or an orthonormal Daubechies wavelet
+ * (Sec. 2.2).  Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ *  Image x      complex, row-major [nx][nz]: nx A-scans (lateral pixel dx_um),
+ *               nz depth pixels (dz_um, zero delay at n = 0), depth contiguous.
+ *               Interleaved (re, im) float32 pairs for MBIR_FP32*,
+ *               float64 pairs for MBIR_FP64.
+ *  Measurements y  real, row-major [nx][m]: m spectrometer pixels at the
+ *               wavenumbers k[m] of the geometry.  float32 (MBIR_FP32*) or
+ *               float64 (MBIR_FP64).
+ *  Mask         uint8 [nx][m], 1 = measured, 0 = not measured (diag(s) of
+ *               Eq. for_model); NULL means every sample is measured.  Values of
+ *               y where the mask is 0 are ignored.
+ *  Pointers     x, y, mask are DEVICE pointers owned by the caller.  The plan owns
+ *               its device tables and workspace.  Calls are asynchronous on the
+ *               given cudaStream_t (passed as void*, NULL = legacy default stream)
+ *               unless stated otherwise.
+ *  Errors       every call returns an mbir_status; no call aborts, traps or
+ *               exits.  Arguments are validated on the host before any launch.
+ *               MBIR_ERR_CUDA reports a failed CUDA runtime call (the CUDA error
+ *               text is kept, see mbir_last_error).
+ *  Threads      a plan may be used from one host thread at a time; calls on
+ *               different plans are independent.
+ */
+#ifndef MBIR_H
+#define MBIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbir_plan_s* mbir_plan;
+
+typedef enum {
+  MBIR_OK = 0,
+  MBIR_ERR_INVALID = -1,          /* bad argument (NULL, non-positive size, non-finite value) */
+  MBIR_ERR_UNSUPPORTED_SIZE = -2, /* size outside what the kernels handle (see mbir_plan_create) */
+  MBIR_ERR_OOM = -3,              /* device allocation failed */
+  MBIR_ERR_CUDA = -4,             /* a CUDA runtime call failed */
+  MBIR_ERR_TIMEOUT = -5,          /* a bounded device-side wait gave up */
+  MBIR_ERR_NOT_CONVERGED = -6     /* solver stopped at max_iter before rel_tol was met */
+} mbir_status;
+
+typedef enum { MBIR_FP32 = 0, MBIR_FP32_COMPENSATED = 1, MBIR_FP64 = 2 } mbir_precision;
+
+typedef enum { MBIR_PENALTY_L1 = 0, MBIR_PENALTY_DB4 = 1 } mbir_penalty;
+
+/*
+ * Optical geometry of one B-scan (Sec. 2.1).  Host memory; copied by
+ * mbir_plan_create, so the caller may free it afterwards.
+ *
+ *  nx, nz, m    A-scans, depth pixels, spectrometer pixels.
+ *  k            host [m] wavenumbers (rad/um), strictly monotone.
+ *  source       host [m] source amplitude A(k) >= 0, or NULL for A = 1.
+ *  dx_um        lateral pixel; lateral frequencies q_l = 2 pi l~/(nx dx), l~ the
+ *               signed FFT index (Eq. 4).
+ *  dz_um        depth pixel; 0 selects pi / (2 nz max|dk|), the positive twin-free
+ *               half of the resolved depth range (the role of Q, Eq. for_model).
+ *  na, z_focus_um  Gaussian beam filter G(q,k) = exp(-q^2 / (2 k^2 na^2)) focused
+ *               at depth z_focus (the ISAM filter f^ of Eq. 5); na <= 0 gives G = 1.
+ *  disp_a, disp_b, k0  dispersion phase Omega = a (k-k0)^2 + b (k-k0)^3 (Sec. 2.1).
+ *  falloff_half_um  depth falloff w(z) = exp(-ln2 (z/z_half)^2); <= 0 disables.
+ *  kb_width     Kaiser-Bessel interpolation width J (even, 4..8) of the NUFFT that
+ *               realises the ISAM resampling (Sec. 2.1, "u = Kx").
+ *  kb_oversamp  axial oversampling sigma; K = sigma * nz must be an integer.
+ *               Only 2.0 is supported.
+ *  kb_alpha     KB shape; 0 selects 2.34 * J.
+ *  precision    mbir_precision of x and y for every call on the plan.
+ */
+typedef struct {
+  int32_t nx, nz, m;
+  const double* k;
+  const double* source;
+  double dx_um, dz_um;
+  double na, z_focus_um;
+  double disp_a, disp_b, k0;
+  double falloff_half_um;
+  int32_t kb_width;
+  double kb_oversamp;
+  double kb_alpha;
+  int32_t precision;
+} mbir_geometry;
+
+/*
+ * Solver options (Sec. 2.3).
+ *  penalty            mbir_penalty: l1 on pixels (Psi = I) or on the 3-level periodic
+ *                     orthonormal Daubechies wavelet with 4 vanishing moments.
+ *  lambda             penalty weight; if lambda_is_relative != 0 the weight used is
+ *                     lambda * max|Psi Phi^H(s y)| (one extra adjoint at set-up).
+ *  max_iter           FISTA iterations (>= 1).
+ *  min_iter, rel_tol  if rel_tol > 0 the solve stops after iteration k >= min_iter
+ *                     once |F(z^{k-1}) - F(z^{k-2})| <= rel_tol * F(z^{k-2}); the
+ *                     objective is then read back every iteration (a host sync).
+ *  power_iters        power iterations for L = lambda_max(Phi^H Phi) when step <= 0.
+ *  step               gradient step delta; <= 0 selects 1 / (1.01 L).
+ *  warm_start         != 0: start from the x passed in instead of 0.
+ */
+typedef struct {
+  int32_t penalty;
+  double lambda;
+  int32_t lambda_is_relative;
+  int32_t max_iter;
+  int32_t min_iter;
+  double rel_tol;
+  int32_t power_iters;
+  double step;
+  int32_t warm_start;
+} mbir_solve_opts;
+
+/*
+ * Solver report (host memory, filled by mbir_solve).
+ *  iters             iterations run.
+ *  status            mbir_status of the solve.
+ *  objective         F(z) of the returned iterate (FP64 on the device).
+ *  lipschitz         L used (0 when step was given).
+ *  step, lambda_used the delta and the absolute lambda used.
+ *  objective_trace   optional host array of trace_len doubles; entry k-1 receives
+ *                    F(z^{k-1}) measured during iteration k (NULL: not recorded).
+ */
+typedef struct {
+  int32_t iters;
+  int32_t status;
+  double objective;
+  double lipschitz;
+  double step;
+  double lambda_used;
+  double* objective_trace;
+  int32_t trace_len;
+} mbir_solve_info;
+
+/*
+ * Build a plan for one geometry: validates it, derives the FP64 tables (lateral
+ * frequencies, beta = sqrt(4k^2 - q^2) grid positions, filter, deapodisation,
+ * KB kernel, FFT twiddles) on the host and uploads them, and allocates the
+ * workspace, on the current CUDA device.  Synchronous.
+ * Supported sizes: nx in [2, 4096] and nz in [8, 4096] with every prime factor
+ * <= 7; nx * nz and nx * m below 2^31; m in [1, 65536]; K = 2 nz.
+ * Returns MBIR_ERR_INVALID / MBIR_ERR_UNSUPPORTED_SIZE before touching the GPU.
+ * stream: used for the uploads; *out receives the plan (NULL on failure).
+ */
+int mbir_plan_create(const mbir_geometry* geometry, void* stream, mbir_plan* out);
+
+/* Free a plan and its device memory (synchronises the device).  NULL is a no-op. */
+void mbir_plan_destroy(mbir_plan plan);
+
+/* Geometry sizes of a plan; any output pointer may be NULL. */
+int mbir_plan_dims(mbir_plan plan, int32_t* nx, int32_t* nz, int32_t* m, int32_t* precision);
+
+/*
+ * y = Phi(x) (Eq. for_model): lateral FFT, KB-NUFFT resampling onto
+ * beta = sqrt(4k^2 - q^2) (Eq. 5), filter, dispersion phase, inverse lateral FFT,
+ * real part, mask.  x: device [nx][nz] complex; y: device [nx][m] real, fully
+ * written (0 where the mask is 0).  Uses the plan's workspace: calls on one plan
+ * must be ordered (same stream, or synchronised).
+ */
+int mbir_forward(mbir_plan plan, const void* x, const uint8_t* mask, void* y, void* stream);
+
+/*
+ * x = Phi^H(y) (Eq. back_model as the exact transpose of mbir_forward in the
+ * real inner products <a,b> = Re sum conj(a) b).  y: device [nx][m] real (entries
+ * with mask 0 ignored); x: device [nx][nz] complex, fully written.
+ */
+int mbir_adjoint(mbir_plan plan, const void* y, const uint8_t* mask, void* x, void* stream);
+
+/*
+ * FISTA (Eq. alg) from x^1 = z^0 = 0 (or the x passed in when warm_start),
+ * t^1 = 1, for opts->max_iter iterations (or until rel_tol), writing z^k to x.
+ * Allocates the iteration state on the first call for a given plan and keeps it.
+ * Synchronous when it has to read a device scalar back (step or lambda derived on
+ * the device, rel_tol > 0, or info != NULL); otherwise asynchronous on stream.
+ */
+int mbir_solve(mbir_plan plan, const void* y, const uint8_t* mask, const mbir_solve_opts* opts,
+               void* x, mbir_solve_info* info, void* stream);
+
+/*
+ * lambda_max(Phi^H Phi) for this plan and mask by power iteration from a fixed
+ * pseudo-random start (counter-based hash of the pixel index), FP64 norms
+ * (step-size bound of Sec. 2.3).  Writes the estimate to *out (host).  Synchronous.
+ */
+int mbir_lipschitz(mbir_plan plan, const uint8_t* mask, int32_t iters, double* out, void* stream);
+
+/*
+ * Proximal map of tau * ||Psi x||_1 (Sec. 2.3): z = Psi^T soft(Psi v, tau) with
+ * the complex soft-threshold c max(0, 1 - tau/|c|).  v, z: device [nx][nz]
+ * complex (may alias).  penalty: mbir_penalty.  MBIR_PENALTY_DB4 needs nx and nz
+ * divisible by 8 with nx/8, nz/8 >= 1 and nx/4, nz/4 >= 8.
+ */
+int mbir_prox(mbir_plan plan, int32_t penalty, const void* v, double tau, void* z, void* stream);
+
+/*
+ * Orthonormal 3-level periodic 2-D wavelet analysis c = Psi x (inverse = 0) or
+ * synthesis x = Psi^T c (inverse = 1), Mallat layout in the [nx][nz] array (at each
+ * level the low-low block splits into [[LL, LH], [HL, HH]], first index lateral).
+ * in, out: device [nx][nz] complex, distinct.
+ */
+int mbir_wavelet(mbir_plan plan, int32_t inverse, const void* in, void* out, void* stream);
+
+/* Static description of a status code. */
+const char* mbir_status_string(int status);
+
+/* Text of the last CUDA failure seen by this thread ("" if none). */
+const char* mbir_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBIR_H */

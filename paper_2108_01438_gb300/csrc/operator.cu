@@ -1,0 +1,297 @@
+// The ISAM system operator Phi and its adjoint Phi^H (Sec. 2.1, Eqs. for_model and
+// back_model) as three kernels each:
+//
+//   forward  x[p][n] --lateral FFT over p-->  X[l][n]                    (Eq. 4)
+//            X[l][.] --row kernel: c_n, centred zero-pad to K, K-point FFT,
+//                      J-tap KB interpolation at t_lm, filter f_lm--> S[l][m]   (Eq. 5, "u = Kx")
+//            S[.][m] --inverse lateral FFT, 1/nx, real part, mask-->  y[p][m]  (Re, diag(s))
+//   adjoint  the transpose of each stage in reverse order: masked y embedded as
+//            complex, (1/nx) lateral FFT; per row conj(f), KB spreading (shared-
+//            memory atomics), unnormalised inverse K-point FFT, keep the nz centred
+//            samples, c_n; unnormalised inverse lateral FFT.
+//
+// Lateral stages work on tiles of TC adjacent columns with all nx rows staged in
+// shared memory; row stages give one CTA per lateral frequency l and keep the
+// K-point row (K = 2 nz) in shared memory.
+#include "common.cuh"
+#include "fft.cuh"
+#include "operator.cuh"
+
+namespace mbir {
+
+// --------------------------------------------------------------- lateral FFT
+
+template <class R, int MODE>
+__global__ void __launch_bounds__(kLatThreads)
+lateral_kernel(LatArgs<R> a) {
+  using V = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s = reinterpret_cast<V*>(smem_raw);
+  const int TC = a.tc, nx = a.nx, C = a.cols;
+  const int c0 = blockIdx.x * TC;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int total = nx * TC;
+  for (int e = tid; e < total; e += nthr) {
+    const int p = e / TC, b = e - p * TC;
+    const int c = c0 + b;
+    V v = cmk<V>(R(0), R(0));
+    if (c < C) {
+      const size_t off = (size_t)p * C + c;
+      if constexpr (MODE == LAT_R2C_MASK) {
+        const R r = reinterpret_cast<const R*>(a.in)[off];
+        v.x = (a.mask == nullptr || a.mask[off]) ? r : R(0);
+      } else {
+        v = reinterpret_cast<const V*>(a.in)[off];
+      }
+    }
+    s[p * TC + b] = v;
+  }
+  __syncthreads();
+  constexpr bool INV = (MODE == LAT_C2C_INV || MODE == LAT_C2R_INV_MASK);
+  fft_dif<INV>(s, TC, a.rad, reinterpret_cast<const V*>(a.tw));
+  for (int e = tid; e < total; e += nthr) {
+    const int p = e / TC, b = e - p * TC;
+    const int c = c0 + b;
+    if (c >= C) continue;
+    const size_t off = (size_t)p * C + c;
+    const V v = s[a.perm[p] * TC + b];
+    if constexpr (MODE == LAT_C2R_INV_MASK) {
+      const R r = v.x * a.scale;
+      reinterpret_cast<R*>(a.out)[off] = (a.mask == nullptr || a.mask[off]) ? r : R(0);
+    } else {
+      reinterpret_cast<V*>(a.out)[off] = cscale(v, a.scale);
+    }
+  }
+}
+
+// ------------------------------------------------------------- KB weights
+
+template <class R>
+__device__ __forceinline__ R kb_weight(R u, const float* kb, int J, R alpha, R inv_i0a) {
+  const R au = u < R(0) ? -u : u;
+  if constexpr (sizeof(R) == 4) {
+    const float x = au * float(kKbRes);
+    const int i = (int)x;
+    const float f = x - float(i);
+    const float a0 = kb[i], a1 = kb[i + 1];
+    return fmaf(f, a1 - a0, a0);
+  } else {
+    const double r = 1.0 - (2.0 * au / J) * (2.0 * au / J);
+    if (r < 0.0) return 0.0;
+    return cyl_bessel_i0(alpha * sqrt(r)) * inv_i0a;
+  }
+}
+
+// --------------------------------------------------------- row kernels (NUFFT)
+
+template <class R>
+__global__ void __launch_bounds__(kRowThreads)
+row_forward_kernel(RowArgs<R> a) {
+  using V = cplx_t<R>;
+  using Tab = typename TabOf<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* buf = reinterpret_cast<V*>(smem_raw);
+  float* kb = reinterpret_cast<float*>(buf + a.K);
+  const int l = blockIdx.x;
+  const int lp = l <= a.nx - l ? l : a.nx - l;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int K = a.K, nz = a.nz, n0 = a.n0, J = a.J, M = a.m;
+  if (sizeof(R) == 4)
+    for (int i = tid; i < a.nkb; i += nthr) kb[i] = a.kbtab[i];
+  const V* X = reinterpret_cast<const V*>(a.in) + (size_t)l * nz;
+  const R* cdep = reinterpret_cast<const R*>(a.cdep);
+  // centred zero-padded row, element i = (n - n0) mod K holding c_n X[l][n],
+  // stored digit-reversed for the decimation-in-time transform
+  for (int i = tid; i < K; i += nthr) {
+    int n = i + n0;
+    if (n >= K) n -= K;
+    buf[a.perm[i]] = (n < nz) ? cscale(X[n], cdep[n]) : cmk<V>(R(0), R(0));
+  }
+  __syncthreads();
+  fft_dit<false>(buf, 1, a.rad, reinterpret_cast<const V*>(a.tw));
+  const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
+  V* S = reinterpret_cast<V*>(a.out) + (size_t)l * M;
+  const int h = J / 2;
+  for (int mm = tid; mm < M; mm += nthr) {
+    const Tab e = tab[mm];
+    V acc = cmk<V>(R(0), R(0));
+    for (int j = 0; j < J; ++j) {
+      const R u = R(e.frac) + R(h - 1 - j);
+      const R w = kb_weight<R>(u, kb, J, R(a.alpha), R(a.inv_i0a));
+      int idx = e.i0 - h + 1 + j;
+      if (idx < 0) idx += K;
+      if (idx >= K) idx -= K;
+      const V b = buf[idx];
+      acc.x += w * b.x;
+      acc.y += w * b.y;
+    }
+    S[mm] = cmul(acc, cmk<V>(R(e.fre), R(e.fim)));
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kRowThreads)
+row_adjoint_kernel(RowArgs<R> a) {
+  using V = cplx_t<R>;
+  using Tab = typename TabOf<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* buf = reinterpret_cast<V*>(smem_raw);
+  float* kb = reinterpret_cast<float*>(buf + a.K);
+  const int l = blockIdx.x;
+  const int lp = l <= a.nx - l ? l : a.nx - l;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int K = a.K, nz = a.nz, n0 = a.n0, J = a.J, M = a.m;
+  if (sizeof(R) == 4)
+    for (int i = tid; i < a.nkb; i += nthr) kb[i] = a.kbtab[i];
+  for (int i = tid; i < K; i += nthr) buf[i] = cmk<V>(R(0), R(0));
+  __syncthreads();
+  const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
+  const V* Rh = reinterpret_cast<const V*>(a.in) + (size_t)l * M;
+  const int h = J / 2;
+  R* bufr = reinterpret_cast<R*>(buf);
+  for (int mm = tid; mm < M; mm += nthr) {
+    const Tab e = tab[mm];
+    const V v = cmulc(Rh[mm], cmk<V>(R(e.fre), R(e.fim)));
+    for (int j = 0; j < J; ++j) {
+      const R u = R(e.frac) + R(h - 1 - j);
+      const R w = kb_weight<R>(u, kb, J, R(a.alpha), R(a.inv_i0a));
+      int idx = e.i0 - h + 1 + j;
+      if (idx < 0) idx += K;
+      if (idx >= K) idx -= K;
+      atomicAdd(&bufr[2 * idx], w * v.x);
+      atomicAdd(&bufr[2 * idx + 1], w * v.y);
+    }
+  }
+  __syncthreads();
+  fft_dif<true>(buf, 1, a.rad, reinterpret_cast<const V*>(a.tw));
+  const R* cdep = reinterpret_cast<const R*>(a.cdep);
+  V* Wo = reinterpret_cast<V*>(a.out) + (size_t)l * nz;
+  for (int n = tid; n < nz; n += nthr) {
+    int i = n - n0;
+    if (i < 0) i += K;
+    Wo[n] = cscale(buf[a.perm[i]], cdep[n]);
+  }
+}
+
+// ------------------------------------------------------------------ launch
+
+template <class R, int MODE>
+int launch_lateral(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, R scale,
+                   cudaStream_t st) {
+  LatArgs<R> a;
+  a.in = in;
+  a.out = out;
+  a.mask = mask;
+  a.nx = p->nx;
+  a.cols = cols;
+  a.tc = p->tile_c;
+  a.rad = p->rad_x;
+  a.tw = p->tw_x;
+  a.perm = p->perm_x;
+  a.scale = scale;
+  const int grid = (cols + a.tc - 1) / a.tc;
+  const size_t smem = sizeof(cplx_t<R>) * p->nx * a.tc;
+  lateral_kernel<R, MODE><<<grid, kLatThreads, smem, st>>>(a);
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+template <class R>
+RowArgs<R> row_args(mbir_plan p, const void* in, void* out) {
+  RowArgs<R> a;
+  a.in = in;
+  a.out = out;
+  a.tab = p->tab;
+  a.cdep = p->cdep;
+  a.kbtab = p->kbtab;
+  a.tw = p->tw_k;
+  a.rad = p->rad_k;
+  a.perm = p->perm_k;
+  a.nx = p->nx;
+  a.nz = p->nz;
+  a.m = p->m;
+  a.K = p->K;
+  a.J = p->J;
+  a.n0 = p->n0;
+  a.nkb = kKbRes * p->J / 2 + 2;
+  a.alpha = p->alpha;
+  a.inv_i0a = 1.0 / host_bessel_i0(p->alpha);
+  return a;
+}
+
+template <class R>
+size_t row_smem(mbir_plan p) {
+  return sizeof(cplx_t<R>) * p->K + sizeof(float) * (kKbRes * p->J / 2 + 2);
+}
+
+template <class R>
+int forward_t(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
+  int rc = launch_lateral<R, LAT_C2C_FWD>(p, x, p->wsA, nullptr, p->nz, R(1), st);
+  if (rc) return rc;
+  RowArgs<R> a = row_args<R>(p, p->wsA, p->wsB);
+  row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a);
+  MBIR_LAUNCH_CHECK();
+  return launch_lateral<R, LAT_C2R_INV_MASK>(p, p->wsB, y, mask, p->m, R(1) / R(p->nx), st);
+}
+
+template <class R>
+int adjoint_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
+  int rc = launch_lateral<R, LAT_R2C_MASK>(p, y, p->wsA, mask, p->m, R(1) / R(p->nx), st);
+  if (rc) return rc;
+  RowArgs<R> a = row_args<R>(p, p->wsA, p->wsB);
+  row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a);
+  MBIR_LAUNCH_CHECK();
+  return launch_lateral<R, LAT_C2C_INV>(p, p->wsB, x, nullptr, p->nz, R(1), st);
+}
+
+int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? forward_t<double>(p, x, mask, y, st)
+                                   : forward_t<float>(p, x, mask, y, st);
+}
+
+int adjoint_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? adjoint_t<double>(p, y, mask, x, st)
+                                   : adjoint_t<float>(p, y, mask, x, st);
+}
+
+template <class R>
+static int configure_t(mbir_plan p) {
+  const int lat = (int)(sizeof(cplx_t<R>) * kLatElems);
+  const int row = (int)(sizeof(cplx_t<R>) * kMaxFFT + sizeof(float) * (kKbRes * 4 + 2));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2C_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2C_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_R2C_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2R_INV_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(row_forward_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(row_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
+  return MBIR_OK;
+}
+
+int configure_operator_kernels(mbir_plan p) {
+  return p->precision == MBIR_FP64 ? configure_t<double>(p) : configure_t<float>(p);
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
+extern "C" {
+
+static int check_common(mbir_plan p, const void* a, const void* b) {
+  if (!p || !a || !b) return MBIR_ERR_INVALID;
+  return MBIR_OK;
+}
+
+int mbir_forward(mbir_plan p, const void* x, const uint8_t* mask, void* y, void* stream) {
+  const int rc = check_common(p, x, y);
+  if (rc) return rc;
+  return forward_impl(p, x, mask, y, (cudaStream_t)stream);
+}
+
+int mbir_adjoint(mbir_plan p, const void* y, const uint8_t* mask, void* x, void* stream) {
+  const int rc = check_common(p, y, x);
+  if (rc) return rc;
+  return adjoint_impl(p, y, mask, x, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,424 @@
+// Plan creation: validation of the optical geometry and the FP64 host
+// derivation of every table the kernels read (Sec. 2.1).
+//
+// Per lateral frequency magnitude l' = |l~| (q = 2 pi l'/(nx dx); the tables only
+// depend on q^2) and spectrometer pixel m:
+//   beta  = sqrt(4 k_m^2 - q^2)                         ISAM resampling, Eq. 5
+//   t     = K/(2 pi) (beta dz mod 2 pi)  -> (i0 = floor t, frac = t - i0)
+//   f     = A(k) G(q,k) e^{j [Omega(k) - 2 k z_f + beta (z_f - n0 dz)]}
+// where G = exp(-q^2/(2 k^2 NA^2)) is the focused Gaussian beam filter (the
+// paper's f^, Eq. 5), Omega the dispersion phase and the last term moves the
+// phase reference of the depth sum from the NUFFT centre n0 dz to the focus.
+// Per depth pixel n:  c_n = w(z_n) / Psi((n - n0)/K)  (falloff x deapodisation).
+// All phases are reduced in FP64 before rounding to the kernel precision.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace mbir {
+
+static thread_local std::string g_last_error;
+
+int set_cuda_error(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return MBIR_ERR_OOM;
+  return MBIR_ERR_CUDA;
+}
+
+void set_error_text(const std::string& s) { g_last_error = s; }
+
+// Modified Bessel function I0 by its power series sum ((x/2)^k / k!)^2.
+static double bessel_i0(double x) {
+  const double h = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 500; ++k) {
+    term *= h / (double(k) * double(k));
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+double host_bessel_i0(double x) { return bessel_i0(x); }
+
+// Kaiser-Bessel kernel psi(u) = I0(alpha sqrt(1 - (2u/J)^2)) / I0(alpha), |u| <= J/2.
+static double kb_psi(double u, int J, double alpha) {
+  const double r = 1.0 - (2.0 * u / J) * (2.0 * u / J);
+  if (r < 0.0) return 0.0;
+  return bessel_i0(alpha * sqrt(r)) / bessel_i0(alpha);
+}
+
+// Its Fourier transform at nu cycles per cell:
+// J sinh(sqrt(alpha^2 - (pi J nu)^2)) / sqrt(...) / I0(alpha)  (sin form beyond alpha).
+static double kb_hat(double nu, int J, double alpha) {
+  const double s2 = alpha * alpha - (M_PI * J * nu) * (M_PI * J * nu);
+  double v;
+  if (s2 > 1e-30) {
+    const double s = sqrt(s2);
+    v = sinh(s) / s;
+  } else if (s2 < -1e-30) {
+    const double s = sqrt(-s2);
+    v = sin(s) / s;
+  } else {
+    v = 1.0;
+  }
+  return J * v / bessel_i0(alpha);
+}
+
+static bool factor_radix(int n, Radix* r) {
+  r->n = n;
+  r->npass = 0;
+  int rem = n;
+  const int order[] = {8, 4, 2, 3, 5, 7};
+  for (int f : order) {
+    while (rem % f == 0) {
+      if (r->npass >= kMaxPasses) return false;
+      r->r[r->npass++] = f;
+      rem /= f;
+    }
+  }
+  if (rem != 1) return false;
+  // a lone radix-2 pass next to a radix-8 pass: 8 * 2 becomes 4 * 4
+  for (int i = 0; i < r->npass; ++i) {
+    if (r->r[i] != 2) continue;
+    for (int j = 0; j < r->npass; ++j) {
+      if (r->r[j] == 8) {
+        r->r[j] = 4;
+        r->r[i] = 4;
+        break;
+      }
+    }
+    break;
+  }
+  return true;
+}
+
+template <class V>
+static void make_twiddles(int n, std::vector<V>& out) {
+  out.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const double a = -2.0 * M_PI * double(i) / double(n);
+    out[i].x = cos(a);
+    out[i].y = sin(a);
+  }
+}
+
+static int validate(const mbir_geometry* g) {
+  if (!g || !g->k) return MBIR_ERR_INVALID;
+  if (g->nx <= 0 || g->nz <= 0 || g->m <= 0) return MBIR_ERR_INVALID;
+  if (!(g->dx_um > 0) || !(g->dz_um >= 0) || !isfinite(g->dx_um) || !isfinite(g->dz_um))
+    return MBIR_ERR_INVALID;
+  if (!isfinite(g->na) || !isfinite(g->z_focus_um) || !isfinite(g->disp_a) || !isfinite(g->disp_b) ||
+      !isfinite(g->k0) || !isfinite(g->falloff_half_um) || !isfinite(g->kb_alpha) || g->kb_alpha < 0)
+    return MBIR_ERR_INVALID;
+  if (g->precision < MBIR_FP32 || g->precision > MBIR_FP64) return MBIR_ERR_INVALID;
+  for (int i = 0; i < g->m; ++i) {
+    if (!isfinite(g->k[i]) || g->k[i] <= 0) return MBIR_ERR_INVALID;
+    if (g->source && (!isfinite(g->source[i]) || g->source[i] < 0)) return MBIR_ERR_INVALID;
+  }
+  if (g->m > 1) {
+    const bool inc = g->k[1] > g->k[0];
+    for (int i = 1; i < g->m; ++i) {
+      if (inc ? !(g->k[i] > g->k[i - 1]) : !(g->k[i] < g->k[i - 1])) return MBIR_ERR_INVALID;
+    }
+  } else if (g->dz_um == 0) {
+    return MBIR_ERR_INVALID;   // the default dz needs a wavenumber step
+  }
+  if (g->kb_width < 4 || g->kb_width > 8 || (g->kb_width & 1)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  if (g->kb_oversamp != 2.0) return MBIR_ERR_UNSUPPORTED_SIZE;
+  if (g->nx < 2 || g->nx > 4096 || g->nz < 8 || g->nz > 4096 || g->m > 65536)
+    return MBIR_ERR_UNSUPPORTED_SIZE;
+  if ((int64_t)g->nx * g->nz >= (int64_t(1) << 31) || (int64_t)g->nx * g->m >= (int64_t(1) << 31))
+    return MBIR_ERR_UNSUPPORTED_SIZE;
+  Radix r;
+  if (!factor_radix(g->nx, &r) || !factor_radix(2 * g->nz, &r)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  return MBIR_OK;
+}
+
+template <class R>
+static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
+  using V = cplx_t<R>;
+  using Tab = typename TabOf<R>::T;
+  const int nx = p->nx, nz = p->nz, m = p->m, K = p->K, J = p->J;
+  std::vector<V> twx, twk;
+  make_twiddles(nx, twx);
+  make_twiddles(K, twk);
+  std::vector<R> cdep(nz);
+  for (int n = 0; n < nz; ++n) {
+    const double z = n * p->dz;
+    double w = 1.0;
+    if (g->falloff_half_um > 0) w = exp(-M_LN2 * (z / g->falloff_half_um) * (z / g->falloff_half_um));
+    cdep[n] = R(w / kb_hat(double(n - p->n0) / K, J, p->alpha));
+  }
+  std::vector<Tab> tab((size_t)p->nlh * m);
+  for (int lp = 0; lp < p->nlh; ++lp) {
+    const double q = 2.0 * M_PI * lp / (nx * p->dx);
+    for (int mm = 0; mm < m; ++mm) {
+      const double k = g->k[mm];
+      const double b2 = 4.0 * k * k - q * q;
+      Tab e;
+      memset(&e, 0, sizeof(e));
+      if (b2 > 0) {
+        const double beta = sqrt(b2);
+        double t = (K / (2.0 * M_PI)) * fmod(beta * p->dz, 2.0 * M_PI);
+        double i0 = floor(t);
+        double frac = t - i0;
+        int ii = (int)i0;
+        if (ii >= K) ii -= K;
+        if (ii < 0) ii += K;
+        const double A = g->source ? g->source[mm] : 1.0;
+        const double G = g->na > 0 ? exp(-q * q / (2.0 * k * k * g->na * g->na)) : 1.0;
+        const double dk = k - g->k0;
+        const double omega = g->disp_a * dk * dk + g->disp_b * dk * dk * dk;
+        const double phase = fmod(omega - 2.0 * k * g->z_focus_um, 2.0 * M_PI) +
+                             fmod(beta * (g->z_focus_um - p->n0 * p->dz), 2.0 * M_PI);
+        e.i0 = ii;
+        e.frac = (decltype(e.frac))frac;
+        e.fre = (decltype(e.fre))(A * G * cos(phase));
+        e.fim = (decltype(e.fim))(A * G * sin(phase));
+      }
+      tab[(size_t)lp * m + mm] = e;
+    }
+  }
+  MBIR_CUDA_TRY(cudaMalloc(&p->tw_x, sizeof(V) * nx));
+  MBIR_CUDA_TRY(cudaMalloc(&p->tw_k, sizeof(V) * K));
+  MBIR_CUDA_TRY(cudaMalloc(&p->cdep, sizeof(R) * nz));
+  MBIR_CUDA_TRY(cudaMalloc(&p->tab, sizeof(Tab) * tab.size()));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_x, twx.data(), sizeof(V) * nx, cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_k, twk.data(), sizeof(V) * K, cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->cdep, cdep.data(), sizeof(R) * nz, cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tab, tab.data(), sizeof(Tab) * tab.size(), cudaMemcpyHostToDevice, st));
+  std::vector<int> px(nx), pk(K);
+  for (int i = 0; i < nx; ++i) px[i] = digit_reverse(i, p->rad_x);
+  for (int i = 0; i < K; ++i) pk[i] = digit_reverse(i, p->rad_k);
+  MBIR_CUDA_TRY(cudaMalloc(&p->perm_x, sizeof(int) * nx));
+  MBIR_CUDA_TRY(cudaMalloc(&p->perm_k, sizeof(int) * K));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->perm_x, px.data(), sizeof(int) * nx, cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->perm_k, pk.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+  return MBIR_OK;
+}
+
+// Daubechies low-pass filter with 4 vanishing moments, derived by spectral
+// factorisation: z^3 P((2 - z - 1/z)/4), P(u) = 1 + 4u + 10u^2 + 20u^3, has three
+// reciprocal root pairs; the roots inside the unit circle (found by Durand-Kerner
+// iteration) together with four roots at z = -1 give the minimum-phase filter,
+// scaled to sum sqrt(2).
+static void daubechies8(double h[8]) {
+  // polynomial coefficients, highest power first, of z^3 P(u(z))
+  // u z = (-z^2 + 2z - 1)/4
+  double poly[7] = {0, 0, 0, 0, 0, 0, 0};
+  const double binom[4] = {1, 4, 10, 20};
+  for (int kk = 0; kk < 4; ++kk) {
+    double term[7] = {1, 0, 0, 0, 0, 0, 0};
+    int deg = 0;
+    for (int r = 0; r < kk; ++r) {
+      double nt[7] = {0, 0, 0, 0, 0, 0, 0};
+      const double uz[3] = {-0.25, 0.5, -0.25};
+      for (int a = 0; a <= deg; ++a)
+        for (int b = 0; b < 3; ++b) nt[a + b] += term[a] * uz[b];
+      deg += 2;
+      for (int a = 0; a <= deg; ++a) term[a] = nt[a];
+    }
+    // term (degree 2kk) times z^(3-kk), aligned in a degree-6 array
+    const int lead = 3 - kk;
+    for (int a = 0; a <= deg; ++a) poly[lead + a] += binom[kk] * term[a];
+  }
+  // Durand-Kerner on the monic version
+  double re[6], im[6];
+  for (int i = 0; i < 6; ++i) {
+    const double ang = 0.4 + 2.0 * M_PI * i / 6.0;
+    re[i] = 0.9 * cos(ang);
+    im[i] = 0.9 * sin(ang);
+  }
+  for (int it = 0; it < 2000; ++it) {
+    double maxd = 0;
+    for (int i = 0; i < 6; ++i) {
+      // p(z_i)
+      double pr = 1.0, pi = 0.0;
+      for (int a = 1; a <= 6; ++a) {
+        const double nr = pr * re[i] - pi * im[i] + poly[a] / poly[0];
+        const double ni = pr * im[i] + pi * re[i];
+        pr = nr; pi = ni;
+      }
+      double dr = 1.0, di = 0.0;
+      for (int j = 0; j < 6; ++j) {
+        if (j == i) continue;
+        const double xr = re[i] - re[j], xi = im[i] - im[j];
+        const double nr = dr * xr - di * xi, ni = dr * xi + di * xr;
+        dr = nr; di = ni;
+      }
+      const double den = dr * dr + di * di;
+      const double qr = (pr * dr + pi * di) / den, qi = (pi * dr - pr * di) / den;
+      re[i] -= qr;
+      im[i] -= qi;
+      maxd = fmax(maxd, fabs(qr) + fabs(qi));
+    }
+    if (maxd < 1e-16) break;
+  }
+  // product (z+1)^4 * prod_{|r|<1} (z - r), highest power first
+  double cr[8] = {1, 0, 0, 0, 0, 0, 0, 0}, ci[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int deg = 0;
+  auto mul_root = [&](double rr, double ri) {
+    double nr[8] = {0}, ni[8] = {0};
+    for (int a = 0; a <= deg; ++a) {
+      nr[a] += cr[a];
+      ni[a] += ci[a];
+      nr[a + 1] -= cr[a] * rr - ci[a] * ri;
+      ni[a + 1] -= cr[a] * ri + ci[a] * rr;
+    }
+    ++deg;
+    for (int a = 0; a <= deg; ++a) { cr[a] = nr[a]; ci[a] = ni[a]; }
+  };
+  for (int i = 0; i < 4; ++i) mul_root(-1.0, 0.0);
+  for (int i = 0; i < 6; ++i)
+    if (re[i] * re[i] + im[i] * im[i] < 1.0) mul_root(re[i], im[i]);
+  double s = 0;
+  for (int a = 0; a < 8; ++a) s += cr[a];
+  for (int a = 0; a < 8; ++a) h[a] = cr[a] * (M_SQRT2 / s);
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
+extern "C" {
+
+const char* mbir_status_string(int s) {
+  switch (s) {
+    case MBIR_OK: return "ok";
+    case MBIR_ERR_INVALID: return "invalid argument";
+    case MBIR_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case MBIR_ERR_OOM: return "out of device memory";
+    case MBIR_ERR_CUDA: return "CUDA error";
+    case MBIR_ERR_TIMEOUT: return "device wait timed out";
+    case MBIR_ERR_NOT_CONVERGED: return "not converged";
+    default: return "unknown status";
+  }
+}
+
+const char* mbir_last_error(void) { return g_last_error.c_str(); }
+
+void mbir_plan_destroy(mbir_plan p) {
+  if (!p) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != p->device) cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  destroy_solve_state(p);
+  cudaFree(p->tw_x);
+  cudaFree(p->tw_k);
+  cudaFree(p->perm_x);
+  cudaFree(p->perm_k);
+  cudaFree(p->cdep);
+  cudaFree(p->tab);
+  cudaFree(p->kbtab);
+  cudaFree(p->h_db4);
+  cudaFree(p->h_db4f);
+  cudaFree(p->wsA);
+  cudaFree(p->wsB);
+  cudaFree(p->red);
+  if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+  delete p;
+}
+
+int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
+  if (!out) return MBIR_ERR_INVALID;
+  *out = nullptr;
+  const int v = validate(g);
+  if (v != MBIR_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  mbir_plan p = new (std::nothrow) mbir_plan_s;
+  if (!p) return MBIR_ERR_OOM;
+  memset(p, 0, sizeof(*p));
+  p->nx = g->nx;
+  p->nz = g->nz;
+  p->m = g->m;
+  p->K = 2 * g->nz;
+  p->J = g->kb_width;
+  p->n0 = g->nz / 2;
+  p->nlh = g->nx / 2 + 1;
+  p->precision = g->precision;
+  p->dx = g->dx_um;
+  if (g->dz_um > 0) {
+    p->dz = g->dz_um;
+  } else {
+    double dkmax = 0;
+    for (int i = 1; i < g->m; ++i) dkmax = fmax(dkmax, fabs(g->k[i] - g->k[i - 1]));
+    p->dz = M_PI / (2.0 * g->nz * dkmax);
+  }
+  p->alpha = g->kb_alpha > 0 ? g->kb_alpha : 2.34 * g->kb_width;
+  factor_radix(p->nx, &p->rad_x);
+  factor_radix(p->K, &p->rad_k);
+  // lateral tile: keep nx * tile_c <= 8192 elements, at most 16 columns
+  int tc = 8192 / p->nx;
+  if (tc > 16) tc = 16;
+  int pw = 1;
+  while (pw * 2 <= tc) pw *= 2;
+  p->tile_c = pw;
+
+  int rc = MBIR_OK;
+  auto fail = [&](int code) { mbir_plan_destroy(p); return code; };
+  if (cudaGetDevice(&p->device) != cudaSuccess) return fail(set_cuda_error(cudaGetLastError(), "cudaGetDevice"));
+
+  rc = (p->precision == MBIR_FP64) ? upload_tables<double>(p, g, st) : upload_tables<float>(p, g, st);
+  if (rc != MBIR_OK) return fail(rc);
+
+  // KB kernel samples for the FP32 path: psi(i / kKbRes), i = 0 .. kKbRes*J/2 + 1
+  {
+    const int nkb = kKbRes * p->J / 2 + 2;
+    std::vector<float> kb(nkb);
+    for (int i = 0; i < nkb; ++i) {
+      const double u = double(i) / kKbRes;
+      kb[i] = (u <= 0.5 * p->J) ? (float)kb_psi(u, p->J, p->alpha) : 0.0f;
+    }
+    cudaError_t e = cudaMalloc(&p->kbtab, sizeof(float) * nkb);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMalloc kbtab"));
+    e = cudaMemcpy(p->kbtab, kb.data(), sizeof(float) * nkb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpy kbtab"));
+  }
+  {
+    double h[8];
+    daubechies8(h);
+    float hf[8];
+    for (int i = 0; i < 8; ++i) hf[i] = (float)h[i];
+    cudaError_t e = cudaMalloc(&p->h_db4, sizeof(h));
+    if (e == cudaSuccess) e = cudaMalloc(&p->h_db4f, sizeof(hf));
+    if (e == cudaSuccess) e = cudaMemcpy(p->h_db4, h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->h_db4f, hf, sizeof(hf), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "wavelet filter upload"));
+  }
+  {
+    const size_t cols = (size_t)(p->nz > p->m ? p->nz : p->m);
+    p->ws_elems = (size_t)p->nx * cols;
+    const size_t esz = (p->precision == MBIR_FP64) ? sizeof(double2) : sizeof(float2);
+    cudaError_t e = cudaMalloc(&p->wsA, esz * p->ws_elems);
+    if (e == cudaSuccess) e = cudaMalloc(&p->wsB, esz * p->ws_elems);
+    if (e == cudaSuccess) e = cudaMalloc(&p->red, sizeof(double) * kRedSlots);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "workspace allocation"));
+  }
+  rc = configure_operator_kernels(p);
+  if (rc != MBIR_OK) return fail(rc);
+  *out = p;
+  return MBIR_OK;
+}
+
+int mbir_plan_dims(mbir_plan p, int32_t* nx, int32_t* nz, int32_t* m, int32_t* precision) {
+  if (!p) return MBIR_ERR_INVALID;
+  if (nx) *nx = p->nx;
+  if (nz) *nz = p->nz;
+  if (m) *m = p->m;
+  if (precision) *precision = p->precision;
+  return MBIR_OK;
+}
+
+}  // extern "C"

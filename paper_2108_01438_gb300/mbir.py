@@ -1,0 +1,281 @@
+"""Thin ctypes binding of ``include/mbir.h``: argument marshalling only.
+
+Every computation runs in the CUDA library ``libmbir.so``; torch supplies device
+memory and streams.  There is no CPU fallback: if the library was not built,
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmbir.so")
+
+FP32, FP32_COMPENSATED, FP64 = 0, 1, 2
+PENALTY_L1, PENALTY_DB4 = 0, 1
+PENALTIES = {"l1": PENALTY_L1, "db4": PENALTY_DB4}
+
+STATUS = {0: "MBIR_OK", -1: "MBIR_ERR_INVALID", -2: "MBIR_ERR_UNSUPPORTED_SIZE",
+          -3: "MBIR_ERR_OOM", -4: "MBIR_ERR_CUDA", -5: "MBIR_ERR_TIMEOUT",
+          -6: "MBIR_ERR_NOT_CONVERGED"}
+
+
+class MbirError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class Geometry(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("nz", C.c_int32), ("m", C.c_int32),
+        ("k", C.POINTER(C.c_double)), ("source", C.POINTER(C.c_double)),
+        ("dx_um", C.c_double), ("dz_um", C.c_double),
+        ("na", C.c_double), ("z_focus_um", C.c_double),
+        ("disp_a", C.c_double), ("disp_b", C.c_double), ("k0", C.c_double),
+        ("falloff_half_um", C.c_double),
+        ("kb_width", C.c_int32), ("kb_oversamp", C.c_double), ("kb_alpha", C.c_double),
+        ("precision", C.c_int32),
+    ]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [
+        ("penalty", C.c_int32), ("lam", C.c_double), ("lambda_is_relative", C.c_int32),
+        ("max_iter", C.c_int32), ("min_iter", C.c_int32), ("rel_tol", C.c_double),
+        ("power_iters", C.c_int32), ("step", C.c_double), ("warm_start", C.c_int32),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32), ("status", C.c_int32), ("objective", C.c_double),
+        ("lipschitz", C.c_double), ("step", C.c_double), ("lambda_used", C.c_double),
+        ("objective_trace", C.POINTER(C.c_double)), ("trace_len", C.c_int32),
+    ]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGNATURES = {
+    "mbir_plan_create": (C.c_int, [C.POINTER(Geometry), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mbir_plan_destroy": (None, [C.c_void_p]),
+    "mbir_plan_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mbir_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveOpts), C.c_void_p,
+                             C.POINTER(SolveInfo), C.c_void_p]),
+    "mbir_lipschitz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
+    "mbir_prox": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    "mbir_wavelet": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_status_string": (C.c_char_p, [C.c_int]),
+    "mbir_last_error": (C.c_char_p, []),
+}
+
+
+def lib() -> C.CDLL:
+    """Load libmbir.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        detail = lib().mbir_last_error().decode() if rc == -4 or rc == -3 else ""
+        raise MbirError(rc, where, detail)
+
+
+def _stream_handle(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class _HostArrays:
+    k: np.ndarray
+    source: np.ndarray | None
+
+
+def make_geometry(d: dict, precision: int = FP32) -> tuple[Geometry, _HostArrays]:
+    """C geometry from a workload's plain-number description (keeps the host arrays alive)."""
+    k = np.ascontiguousarray(d["k"], dtype=np.float64)
+    src = d.get("source")
+    src = None if src is None else np.ascontiguousarray(src, dtype=np.float64)
+    g = Geometry()
+    g.nx, g.nz, g.m = int(d["nx"]), int(d["nz"]), int(d["m"])
+    g.k = k.ctypes.data_as(C.POINTER(C.c_double))
+    g.source = src.ctypes.data_as(C.POINTER(C.c_double)) if src is not None else None
+    g.dx_um = float(d["dx_um"])
+    g.dz_um = float(d.get("dz_um", 0.0))
+    g.na = float(d.get("na", 0.0))
+    g.z_focus_um = float(d.get("z_focus_um", 0.0))
+    g.disp_a = float(d.get("disp_a", 0.0))
+    g.disp_b = float(d.get("disp_b", 0.0))
+    g.k0 = float(d.get("k0", 0.0))
+    g.falloff_half_um = float(d.get("falloff_half_um", 0.0))
+    g.kb_width = int(d.get("kb_width", 6))
+    g.kb_oversamp = float(d.get("kb_oversamp", 2.0))
+    g.kb_alpha = float(d.get("kb_alpha", 0.0))
+    g.precision = int(precision)
+    return g, _HostArrays(k, src)
+
+
+class Plan:
+    """One B-scan geometry on the current CUDA device (mbir_plan_create)."""
+
+    def __init__(self, geometry: dict, precision: int = FP32, stream=None):
+        import torch
+        self.geometry = geometry
+        self.precision = precision
+        self.nx, self.nz, self.m = int(geometry["nx"]), int(geometry["nz"]), int(geometry["m"])
+        self.real_dtype = torch.float64 if precision == FP64 else torch.float32
+        self.complex_dtype = torch.complex128 if precision == FP64 else torch.complex64
+        g, keep = make_geometry(geometry, precision)
+        h = C.c_void_p()
+        _check(lib().mbir_plan_create(C.byref(g), _stream_handle(stream), C.byref(h)), "mbir_plan_create")
+        self._h = h
+        del keep
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mbir_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- argument checks -------------------------------------------------
+    def _image(self, t, name):
+        if t.dtype != self.complex_dtype or tuple(t.shape) != (self.nx, self.nz) or not t.is_cuda \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {self.complex_dtype} tensor "
+                             f"of shape ({self.nx}, {self.nz})")
+
+    def _meas(self, t, name):
+        if t.dtype != self.real_dtype or tuple(t.shape) != (self.nx, self.m) or not t.is_cuda \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {self.real_dtype} tensor "
+                             f"of shape ({self.nx}, {self.m})")
+
+    def _mask(self, t):
+        import torch
+        if t is None:
+            return None
+        if t.dtype != torch.uint8 or tuple(t.shape) != (self.nx, self.m) or not t.is_cuda \
+                or not t.is_contiguous():
+            raise ValueError(f"mask must be a contiguous CUDA uint8 tensor of shape ({self.nx}, {self.m})")
+        return t
+
+    # -- operators -------------------------------------------------------
+    def forward(self, x, mask=None, out=None, stream=None):
+        import torch
+        self._image(x, "x")
+        mask = self._mask(mask)
+        if out is None:
+            out = torch.empty((self.nx, self.m), dtype=self.real_dtype, device=x.device)
+        self._meas(out, "out")
+        _check(lib().mbir_forward(self._h, _ptr(x), _ptr(mask), _ptr(out), _stream_handle(stream)),
+               "mbir_forward")
+        return out
+
+    def adjoint(self, y, mask=None, out=None, stream=None):
+        import torch
+        self._meas(y, "y")
+        mask = self._mask(mask)
+        if out is None:
+            out = torch.empty((self.nx, self.nz), dtype=self.complex_dtype, device=y.device)
+        self._image(out, "out")
+        _check(lib().mbir_adjoint(self._h, _ptr(y), _ptr(mask), _ptr(out), _stream_handle(stream)),
+               "mbir_adjoint")
+        return out
+
+    def lipschitz(self, mask=None, iters: int = 30, stream=None) -> float:
+        mask = self._mask(mask)
+        v = C.c_double()
+        _check(lib().mbir_lipschitz(self._h, _ptr(mask), int(iters), C.byref(v), _stream_handle(stream)),
+               "mbir_lipschitz")
+        return v.value
+
+    def prox(self, v, tau: float, penalty: str = "l1", out=None, stream=None):
+        import torch
+        self._image(v, "v")
+        if out is None:
+            out = torch.empty_like(v)
+        self._image(out, "out")
+        _check(lib().mbir_prox(self._h, PENALTIES[penalty], _ptr(v), float(tau), _ptr(out),
+                               _stream_handle(stream)), "mbir_prox")
+        return out
+
+    def wavelet(self, x, inverse: bool = False, out=None, stream=None):
+        import torch
+        self._image(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        self._image(out, "out")
+        _check(lib().mbir_wavelet(self._h, int(bool(inverse)), _ptr(x), _ptr(out), _stream_handle(stream)),
+               "mbir_wavelet")
+        return out
+
+    def solve(self, y, mask=None, *, penalty: str = "l1", lam: float = 0.01, relative: bool = True,
+              iters: int = 100, min_iter: int = 0, rel_tol: float = 0.0, power_iters: int = 30,
+              step: float = 0.0, x0=None, out=None, trace: bool = False, stream=None):
+        """FISTA (mbir_solve).  Returns (x, info dict)."""
+        import torch
+        self._meas(y, "y")
+        mask = self._mask(mask)
+        if out is None:
+            out = torch.zeros((self.nx, self.nz), dtype=self.complex_dtype, device=y.device) \
+                if x0 is None else x0.clone()
+        elif x0 is not None:
+            out.copy_(x0)
+        self._image(out, "out")
+        o = SolveOpts(PENALTIES[penalty], float(lam), int(bool(relative)), int(iters), int(min_iter),
+                      float(rel_tol), int(power_iters), float(step), int(x0 is not None))
+        info = SolveInfo()
+        tr = None
+        if trace:
+            tr = (C.c_double * iters)()
+            info.objective_trace = C.cast(tr, C.POINTER(C.c_double))
+            info.trace_len = iters
+        rc = lib().mbir_solve(self._h, _ptr(y), _ptr(mask), C.byref(o), _ptr(out), C.byref(info),
+                              _stream_handle(stream))
+        if rc not in (0, -6):
+            _check(rc, "mbir_solve")
+        d = dict(iters=info.iters, status=info.status, objective=info.objective,
+                 lipschitz=info.lipschitz, step=info.step, lambda_used=info.lambda_used)
+        if trace:
+            d["trace"] = np.array(tr[: info.iters])
+        return out, d
