@@ -83,6 +83,10 @@ struct mbir_plan_s {
   void* wsA;
   void* wsB;
   size_t ws_elems;
+  // wavelet scratch (lazily allocated): level-1/2 low-low blocks, coefficients
+  void* wv_b1;
+  void* wv_b2;
+  void* wv_coef;
   // reductions: partial sums
   double* red;                // kRedSlots doubles
   mbir::SolveState* solve;    // lazily created
@@ -91,6 +95,7 @@ struct mbir_plan_s {
 namespace mbir {
 
 constexpr int kRedSlots = 4096;
+constexpr int kSoftGrid = 1024;
 
 int set_cuda_error(cudaError_t e, const char* where);
 void set_error_text(const std::string& s);
@@ -111,11 +116,18 @@ void set_error_text(const std::string& s);
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st);
 int adjoint_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st);
 int configure_operator_kernels(mbir_plan p);
+int forward_solve_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
+                       double mu, double* partial, cudaStream_t st);
+// vout == nullptr: l1 prox fused (z^k written over z2); else v written to vout
+int adjoint_solve_impl(mbir_plan p, const void* r, const void* z1, void* z2, void* vout, double mu,
+                       double delta, double tau, double* partial, cudaStream_t st);
+int lateral_grid(mbir_plan p, int cols);
 
 // wavelet.cu
 int wavelet_impl(mbir_plan p, int inverse, const void* in, void* out, cudaStream_t st);
 int prox_impl(mbir_plan p, int penalty, const void* v, double tau, void* z, cudaStream_t st);
 bool wavelet_supported(int nx, int nz);
+int configure_wavelet_kernels(mbir_plan p);
 
 // solve.cu
 void destroy_solve_state(mbir_plan p);

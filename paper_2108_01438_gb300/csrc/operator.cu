@@ -21,6 +21,24 @@ namespace mbir {
 
 // --------------------------------------------------------------- lateral FFT
 
+// Deterministic block sum of one double per thread (fixed shuffle tree).
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double wsum[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;   // valid in thread 0
+}
+
 template <class R, int MODE>
 __global__ void __launch_bounds__(kLatThreads)
 lateral_kernel(LatArgs<R> a) {
@@ -47,8 +65,9 @@ lateral_kernel(LatArgs<R> a) {
     s[p * TC + b] = v;
   }
   __syncthreads();
-  constexpr bool INV = (MODE == LAT_C2C_INV || MODE == LAT_C2R_INV_MASK);
+  constexpr bool INV = (MODE != LAT_C2C_FWD && MODE != LAT_R2C_MASK);
   fft_dif<INV>(s, TC, a.rad, reinterpret_cast<const V*>(a.tw));
+  double part = 0.0;
   for (int e = tid; e < total; e += nthr) {
     const int p = e / TC, b = e - p * TC;
     const int c = c0 + b;
@@ -58,9 +77,38 @@ lateral_kernel(LatArgs<R> a) {
     if constexpr (MODE == LAT_C2R_INV_MASK) {
       const R r = v.x * a.scale;
       reinterpret_cast<R*>(a.out)[off] = (a.mask == nullptr || a.mask[off]) ? r : R(0);
+    } else if constexpr (MODE == LAT_SOLVE_FWD) {
+      const bool meas = (a.mask == nullptr || a.mask[off]);
+      const R pz = meas ? v.x * a.scale : R(0);
+      const R yv = meas ? a.y[off] : R(0);
+      const R prev = a.pz[off];
+      const R d = pz - yv;
+      part += double(d) * double(d);
+      a.pz[off] = pz;
+      a.r[off] = (R(1) + a.mu) * pz - a.mu * prev - yv;
+    } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
+      const V z1 = reinterpret_cast<const V*>(a.z1)[off];
+      const V z2 = reinterpret_cast<const V*>(a.z2)[off];
+      V xv;
+      xv.x = z1.x + a.mu * (z1.x - z2.x) - a.delta * v.x;
+      xv.y = z1.y + a.mu * (z1.y - z2.y) - a.delta * v.y;
+      if constexpr (MODE == LAT_SOLVE_ADJ_L1) {
+        const R mag = sqrt(xv.x * xv.x + xv.y * xv.y);
+        const R sh = mag > a.tau ? R(1) - a.tau / mag : R(0);
+        xv.x *= sh;
+        xv.y *= sh;
+        part += mag > a.tau ? double(mag - a.tau) : 0.0;
+        reinterpret_cast<V*>(a.z2)[off] = xv;
+      } else {
+        reinterpret_cast<V*>(a.vout)[off] = xv;
+      }
     } else {
       reinterpret_cast<V*>(a.out)[off] = cscale(v, a.scale);
     }
+  }
+  if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_ADJ_L1) {
+    const double t = block_sum(part);
+    if (tid == 0) a.partial[blockIdx.x] = t;
   }
 }
 
@@ -175,9 +223,10 @@ row_adjoint_kernel(RowArgs<R> a) {
 
 // ------------------------------------------------------------------ launch
 
-template <class R, int MODE>
-int launch_lateral(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, R scale,
-                   cudaStream_t st) {
+int lateral_grid(mbir_plan p, int cols);
+
+template <class R>
+LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, R scale) {
   LatArgs<R> a;
   a.in = in;
   a.out = out;
@@ -189,9 +238,27 @@ int launch_lateral(mbir_plan p, const void* in, void* out, const uint8_t* mask, 
   a.tw = p->tw_x;
   a.perm = p->perm_x;
   a.scale = scale;
-  const int grid = (cols + a.tc - 1) / a.tc;
-  const size_t smem = sizeof(cplx_t<R>) * p->nx * a.tc;
-  lateral_kernel<R, MODE><<<grid, kLatThreads, smem, st>>>(a);
+  a.y = nullptr;
+  a.pz = nullptr;
+  a.r = nullptr;
+  a.z1 = nullptr;
+  a.z2 = nullptr;
+  a.vout = nullptr;
+  a.mu = a.delta = a.tau = R(0);
+  a.partial = nullptr;
+  return a;
+}
+
+template <class R>
+size_t lat_smem(mbir_plan p) {
+  return sizeof(cplx_t<R>) * p->nx * p->tile_c;
+}
+
+template <class R, int MODE>
+int launch_lateral(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, R scale,
+                   cudaStream_t st) {
+  LatArgs<R> a = lat_args<R>(p, in, out, mask, cols, scale);
+  lateral_kernel<R, MODE><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a);
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
 }
@@ -244,6 +311,65 @@ int adjoint_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStre
   return launch_lateral<R, LAT_C2C_INV>(p, p->wsB, x, nullptr, p->nz, R(1), st);
 }
 
+template <class R>
+int forward_solve_t(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
+                    double mu, double* partial, cudaStream_t st) {
+  int rc = launch_lateral<R, LAT_C2C_FWD>(p, z1, p->wsA, nullptr, p->nz, R(1), st);
+  if (rc) return rc;
+  RowArgs<R> ra = row_args<R>(p, p->wsA, p->wsB);
+  row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra);
+  MBIR_LAUNCH_CHECK();
+  LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, mask, p->m, R(1) / R(p->nx));
+  a.y = reinterpret_cast<const R*>(y);
+  a.pz = reinterpret_cast<R*>(pz);
+  a.r = reinterpret_cast<R*>(r);
+  a.mu = R(mu);
+  a.partial = partial;
+  lateral_kernel<R, LAT_SOLVE_FWD><<<lateral_grid(p, p->m), kLatThreads, lat_smem<R>(p), st>>>(a);
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+template <class R>
+int adjoint_solve_t(mbir_plan p, const void* r, const void* z1, void* z2, void* vout, double mu,
+                    double delta, double tau, double* partial, cudaStream_t st) {
+  // r is already zero where the mask is zero
+  int rc = launch_lateral<R, LAT_R2C_MASK>(p, r, p->wsA, nullptr, p->m, R(1) / R(p->nx), st);
+  if (rc) return rc;
+  RowArgs<R> ra = row_args<R>(p, p->wsA, p->wsB);
+  row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra);
+  MBIR_LAUNCH_CHECK();
+  LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, nullptr, p->nz, R(1));
+  a.z1 = z1;
+  a.z2 = z2;
+  a.vout = vout;
+  a.mu = R(mu);
+  a.delta = R(delta);
+  a.tau = R(tau);
+  a.partial = partial;
+  if (vout)
+    lateral_kernel<R, LAT_SOLVE_ADJ_V><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a);
+  else
+    lateral_kernel<R, LAT_SOLVE_ADJ_L1><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a);
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+int forward_solve_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
+                       double mu, double* partial, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? forward_solve_t<double>(p, z1, mask, y, pz, r, mu, partial, st)
+                                   : forward_solve_t<float>(p, z1, mask, y, pz, r, mu, partial, st);
+}
+
+int adjoint_solve_impl(mbir_plan p, const void* r, const void* z1, void* z2, void* vout, double mu,
+                       double delta, double tau, double* partial, cudaStream_t st) {
+  return p->precision == MBIR_FP64
+             ? adjoint_solve_t<double>(p, r, z1, z2, vout, mu, delta, tau, partial, st)
+             : adjoint_solve_t<float>(p, r, z1, z2, vout, mu, delta, tau, partial, st);
+}
+
+int lateral_grid(mbir_plan p, int cols) { return (cols + p->tile_c - 1) / p->tile_c; }
+
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
   return p->precision == MBIR_FP64 ? forward_t<double>(p, x, mask, y, st)
                                    : forward_t<float>(p, x, mask, y, st);
@@ -262,6 +388,9 @@ static int configure_t(mbir_plan p) {
   MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2C_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
   MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_R2C_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
   MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2R_INV_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_SOLVE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_SOLVE_ADJ_L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_SOLVE_ADJ_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
   MBIR_CUDA_TRY(cudaFuncSetAttribute(row_forward_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   MBIR_CUDA_TRY(cudaFuncSetAttribute(row_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   return MBIR_OK;

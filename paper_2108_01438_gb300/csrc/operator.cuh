@@ -9,7 +9,16 @@ constexpr int kLatThreads = 256;    // lateral FFT block size
 constexpr int kLatElems = 8192;     // nx * columns staged per lateral CTA
 constexpr int kRowThreads = 512;    // row (NUFFT) block size
 
-enum LatMode { LAT_C2C_FWD = 0, LAT_C2C_INV = 1, LAT_R2C_MASK = 2, LAT_C2R_INV_MASK = 3 };
+enum LatMode {
+  LAT_C2C_FWD = 0,        // X = lateral FFT of x
+  LAT_C2C_INV = 1,        // x = unnormalised inverse lateral FFT of W
+  LAT_R2C_MASK = 2,       // R = (1/nx) lateral FFT of (s * y)
+  LAT_C2R_INV_MASK = 3,   // y = s * Re{(1/nx) inverse lateral FFT of S}
+  // FISTA epilogues (Eq. alg), fused into the last stage of Phi / Phi^H:
+  LAT_SOLVE_FWD = 4,      // pz = Phi z^{k-1}; r = (1+mu) pz - mu pz_prev - s y; data term
+  LAT_SOLVE_ADJ_L1 = 5,   // g = Phi^H r; z^k = soft(z1 + mu (z1 - z2) - delta g, tau); |z^k| sum
+  LAT_SOLVE_ADJ_V = 6     // g = Phi^H r; v = z1 + mu (z1 - z2) - delta g (wavelet prox follows)
+};
 
 template <class R>
 struct LatArgs {
@@ -21,6 +30,15 @@ struct LatArgs {
   const void* tw;
   const int* perm;   // digit reversal of the nx-point transform
   R scale;
+  // solver epilogue operands (LAT_SOLVE_*)
+  const R* y;          // measurements [nx][m]
+  R* pz;               // in: Phi z^{k-2}, out: Phi z^{k-1}   [nx][m]
+  R* r;                // residual out [nx][m]
+  const void* z1;      // z^{k-1} [nx][nz]
+  void* z2;            // in: z^{k-2}; out: z^k (ADJ_L1) -- may be read before written
+  void* vout;          // v out (ADJ_V)
+  R mu, delta, tau;
+  double* partial;     // one FP64 partial sum per CTA
 };
 
 template <class R>

@@ -323,6 +323,9 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaFree(p->kbtab);
   cudaFree(p->h_db4);
   cudaFree(p->h_db4f);
+  cudaFree(p->wv_b1);
+  cudaFree(p->wv_b2);
+  cudaFree(p->wv_coef);
   cudaFree(p->wsA);
   cudaFree(p->wsB);
   cudaFree(p->red);
@@ -407,6 +410,8 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
     if (e != cudaSuccess) return fail(set_cuda_error(e, "workspace allocation"));
   }
   rc = configure_operator_kernels(p);
+  if (rc != MBIR_OK) return fail(rc);
+  rc = configure_wavelet_kernels(p);
   if (rc != MBIR_OK) return fail(rc);
   *out = p;
   return MBIR_OK;

@@ -1,10 +1,465 @@
+// FISTA (Sec. 2.3, Eq. alg) around the fused operator passes, the power-iteration
+// step-size bound, the relative lambda rule and the FP64 objective (Eqs. obj,
+// ls_obj).
+//
+// One iteration k (x^1 = z^0 = 0, t^1 = 1, mu_{k-1} = (t^{k-1} - 1)/t^k, mu_0 = 0):
+//   forward pass on z^{k-1}, epilogue: pz = Phi z^{k-1} (kept for the next
+//     iteration), r = Phi x^k - s y = (1 + mu) pz - mu Phi z^{k-2} - s y
+//     (Phi is real-linear and x^k = z^{k-1} + mu (z^{k-1} - z^{k-2})), and the FP64
+//     partial sums of 1/2 ||pz - s y||^2, the data term of F(z^{k-1});
+//   adjoint pass on r, epilogue: z^k = prox_{tau}(x^k - delta Phi^H r) with
+//     tau = lambda delta (l1 fused; the wavelet prox follows as its own kernels),
+//     and the partial sums of ||Psi z^k||_1.
+// F(z^{k-1}) = data + lambda * reg is reduced on the device in a fixed order, so
+// the objective trace is deterministic.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
 #include "common.cuh"
+
 namespace mbir {
-void destroy_solve_state(mbir_plan) {}
+
+int prox_partial_impl(mbir_plan p, int penalty, const void* v, double tau, void* z, double* partial,
+                      cudaStream_t st);
+int wavelet_partial_count(int nx, int nz);
+int ensure_wavelet_scratch(mbir_plan p);
+
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+struct SolveState {
+  size_t nimg = 0, nmeas = 0;
+  void* zA = nullptr;
+  void* zB = nullptr;
+  void* v = nullptr;
+  void* pz = nullptr;
+  void* r = nullptr;
+  double* part_data = nullptr;
+  double* part_reg = nullptr;
+  double* part_tmp = nullptr;
+  double* scal = nullptr;
+  double* objtrace = nullptr;
+  int n_data = 0, n_reg = 0, trace_cap = 0;
+};
+
+// ------------------------------------------------------------------ kernels
+
+__device__ __forceinline__ double block_sum_s(double v) {
+  __shared__ double wsum[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
 }
+
+__device__ __forceinline__ double block_max_s(double v) {
+  __shared__ double wmax[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wmax[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? wmax[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+  }
+  __syncthreads();
+  return t;
+}
+
+// out = wa * sum(a[0..na)) + wb * sum(b[0..nb)), one block, fixed order.
+__global__ void combine_kernel(const double* a, int na, double wa, const double* b, int nb, double wb,
+                               double* out) {
+  double s = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < na; i += blockDim.x) s += a[i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) t += b[i];
+  const double S = block_sum_s(s);
+  const double T = block_sum_s(t);
+  if (threadIdx.x == 0) *out = wa * S + (nb > 0 ? wb * T : 0.0);
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// Pseudo-random start vector of the power iteration: uniform in [-1, 1) from a
+// counter-based hash (SplitMix64) of the element index.
+template <class R>
+__global__ void fill_hash_kernel(cplx_t<R>* v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(2 * i), b = splitmix64(2 * i + 1);
+    v[i] = cmk<cplx_t<R>>(R((a >> 11) * 0x1.0p-53 * 2.0 - 1.0), R((b >> 11) * 0x1.0p-53 * 2.0 - 1.0));
+  }
+}
+
+// part[2 blk] = sum Re(conj(v) w), part[2 blk + 1] = sum |w|^2
+template <class R>
+__global__ void dot_norm_kernel(const cplx_t<R>* v, const cplx_t<R>* w, size_t n, double* part) {
+  double d = 0.0, q = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx_t<R> a = v[i], b = w[i];
+    d += double(a.x) * double(b.x) + double(a.y) * double(b.y);
+    q += double(b.x) * double(b.x) + double(b.y) * double(b.y);
+  }
+  const double D = block_sum_s(d), Q = block_sum_s(q);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = D;
+    part[2 * blockIdx.x + 1] = Q;
+  }
+}
+
+// scal[0] = <v, w>, scal[1] = 1/||w||, scal[2] = ||w||^2
+__global__ void power_finalize_kernel(const double* part, int nb, double* scal) {
+  double d = 0.0, q = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    d += part[2 * i];
+    q += part[2 * i + 1];
+  }
+  const double D = block_sum_s(d), Q = block_sum_s(q);
+  if (threadIdx.x == 0) {
+    scal[0] = D;
+    scal[1] = Q > 0 ? 1.0 / sqrt(Q) : 0.0;
+    scal[2] = Q;
+  }
+}
+
+template <class R>
+__global__ void scale_kernel(cplx_t<R>* v, const cplx_t<R>* w, size_t n, const double* scal) {
+  const R s = R(scal[1]);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    v[i] = cscale(w[i], s);
+}
+
+template <class R>
+__global__ void maxabs_kernel(const cplx_t<R>* v, size_t n, double* part) {
+  double m = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx_t<R> a = v[i];
+    m = fmax(m, sqrt(double(a.x) * double(a.x) + double(a.y) * double(a.y)));
+  }
+  const double M = block_max_s(m);
+  if (threadIdx.x == 0) part[blockIdx.x] = M;
+}
+
+__global__ void max_finalize_kernel(const double* part, int nb, double* out) {
+  double m = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, part[i]);
+  const double M = block_max_s(m);
+  if (threadIdx.x == 0) *out = M;
+}
+
+template <class R>
+__global__ void abs_sum_kernel(const cplx_t<R>* v, size_t n, double* part) {
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx_t<R> a = v[i];
+    s += sqrt(double(a.x) * double(a.x) + double(a.y) * double(a.y));
+  }
+  const double S = block_sum_s(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = S;
+}
+
+template <class R>
+__global__ void resid_kernel(const R* pz, const R* y, const uint8_t* mask, size_t n, double* part) {
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (mask && !mask[i]) continue;
+    const double d = double(pz[i]) - double(y[i]);
+    s += d * d;
+  }
+  const double S = block_sum_s(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = S;
+}
+
+// ------------------------------------------------------------------ state
+
+static size_t elem_size(mbir_plan p) { return p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2); }
+static size_t real_size(mbir_plan p) { return p->precision == MBIR_FP64 ? sizeof(double) : sizeof(float); }
+
+void destroy_solve_state(mbir_plan p) {
+  SolveState* s = p->solve;
+  if (!s) return;
+  cudaFree(s->zA);
+  cudaFree(s->zB);
+  cudaFree(s->v);
+  cudaFree(s->pz);
+  cudaFree(s->r);
+  cudaFree(s->part_data);
+  cudaFree(s->part_reg);
+  cudaFree(s->part_tmp);
+  cudaFree(s->scal);
+  cudaFree(s->objtrace);
+  delete s;
+  p->solve = nullptr;
+}
+
+static int ensure_state(mbir_plan p, int trace_cap) {
+  if (p->solve && p->solve->trace_cap >= trace_cap) return MBIR_OK;
+  if (p->solve) {
+    cudaFree(p->solve->objtrace);
+    p->solve->objtrace = nullptr;
+    MBIR_CUDA_TRY(cudaMalloc(&p->solve->objtrace, sizeof(double) * trace_cap));
+    p->solve->trace_cap = trace_cap;
+    return MBIR_OK;
+  }
+  SolveState* s = new (std::nothrow) SolveState;
+  if (!s) return MBIR_ERR_OOM;
+  p->solve = s;
+  s->nimg = (size_t)p->nx * p->nz;
+  s->nmeas = (size_t)p->nx * p->m;
+  s->n_data = lateral_grid(p, p->m);
+  int nr = lateral_grid(p, p->nz);
+  if (wavelet_supported(p->nx, p->nz)) {
+    const int w = wavelet_partial_count(p->nx, p->nz);
+    if (w > nr) nr = w;
+  }
+  s->n_reg = nr;
+  s->trace_cap = trace_cap;
+  MBIR_CUDA_TRY(cudaMalloc(&s->zA, elem_size(p) * s->nimg));
+  MBIR_CUDA_TRY(cudaMalloc(&s->zB, elem_size(p) * s->nimg));
+  MBIR_CUDA_TRY(cudaMalloc(&s->v, elem_size(p) * s->nimg));
+  MBIR_CUDA_TRY(cudaMalloc(&s->pz, real_size(p) * s->nmeas));
+  MBIR_CUDA_TRY(cudaMalloc(&s->r, real_size(p) * s->nmeas));
+  MBIR_CUDA_TRY(cudaMalloc(&s->part_data, sizeof(double) * s->n_data));
+  MBIR_CUDA_TRY(cudaMalloc(&s->part_reg, sizeof(double) * s->n_reg));
+  MBIR_CUDA_TRY(cudaMalloc(&s->part_tmp, sizeof(double) * 2 * kRedBlocks));
+  MBIR_CUDA_TRY(cudaMalloc(&s->scal, sizeof(double) * 16));
+  MBIR_CUDA_TRY(cudaMalloc(&s->objtrace, sizeof(double) * trace_cap));
+  return MBIR_OK;
+}
+
+static int grid_for(size_t n) {
+  size_t g = (n + kRedThreads - 1) / kRedThreads;
+  return (int)(g < (size_t)kRedBlocks ? (g ? g : 1) : kRedBlocks);
+}
+
+// ------------------------------------------------------------------ pieces
+
+template <class R>
+static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out, cudaStream_t st) {
+  using V = cplx_t<R>;
+  SolveState* s = p->solve;
+  const size_t n = s->nimg;
+  const int gb = grid_for(n);
+  V* v = (V*)s->v;
+  V* w = (V*)s->zA;
+  fill_hash_kernel<R><<<gb, kRedThreads, 0, st>>>(v, n);
+  dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->part_tmp);
+  power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal);
+  scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->scal);
+  MBIR_LAUNCH_CHECK();
+  for (int it = 0; it < iters; ++it) {
+    int rc = forward_impl(p, v, mask, s->r, st);
+    if (rc) return rc;
+    rc = adjoint_impl(p, s->r, mask, w, st);
+    if (rc) return rc;
+    dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->part_tmp);
+    power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal);
+    scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->scal);
+    MBIR_LAUNCH_CHECK();
+  }
+  MBIR_CUDA_TRY(cudaMemcpyAsync(out, s->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+  return MBIR_OK;
+}
+
+// max |Psi Phi^H (s y)|
+template <class R>
+static int lambda_scale_t(mbir_plan p, const void* y, const uint8_t* mask, int penalty, double* out,
+                          cudaStream_t st) {
+  using V = cplx_t<R>;
+  SolveState* s = p->solve;
+  const size_t n = s->nimg;
+  int rc = adjoint_impl(p, y, mask, s->zA, st);
+  if (rc) return rc;
+  const V* src = (const V*)s->zA;
+  if (penalty == MBIR_PENALTY_DB4) {
+    rc = wavelet_impl(p, 0, s->zA, s->v, st);
+    if (rc) return rc;
+    src = (const V*)s->v;
+  }
+  const int gb = grid_for(n);
+  maxabs_kernel<R><<<gb, kRedThreads, 0, st>>>(src, n, s->part_tmp);
+  max_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal + 4);
+  MBIR_LAUNCH_CHECK();
+  MBIR_CUDA_TRY(cudaMemcpyAsync(out, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+  return MBIR_OK;
+}
+
+// reg partials of z for the penalty, written as solve iterations would
+template <class R>
+static int reg_partials_t(mbir_plan p, int penalty, const void* z, cudaStream_t st) {
+  SolveState* s = p->solve;
+  if (penalty == MBIR_PENALTY_L1) {
+    const int gb = lateral_grid(p, p->nz);
+    abs_sum_kernel<R><<<gb, kRedThreads, 0, st>>>((const cplx_t<R>*)z, s->nimg, s->part_reg);
+    MBIR_LAUNCH_CHECK();
+    return MBIR_OK;
+  }
+  return prox_partial_impl(p, penalty, z, 0.0, s->v, s->part_reg, st);
+}
+
+static int reg_count(mbir_plan p, int penalty) {
+  return penalty == MBIR_PENALTY_L1 ? lateral_grid(p, p->nz) : wavelet_partial_count(p->nx, p->nz);
+}
+
+template <class R>
+static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
+                   mbir_solve_info* info, cudaStream_t st) {
+  SolveState* s = p->solve;
+  const size_t es = elem_size(p);
+  double L = 0.0, delta = o->step;
+  if (!(delta > 0)) {
+    const int pit = o->power_iters > 0 ? o->power_iters : 30;
+    int rc = lipschitz_t<R>(p, mask, pit, &L, st);
+    if (rc) return rc;
+    if (!(L > 0) || !isfinite(L)) return MBIR_ERR_INVALID;
+    delta = 1.0 / (1.01 * L);
+  }
+  double lam = o->lambda;
+  if (o->lambda_is_relative) {
+    double m = 0.0;
+    int rc = lambda_scale_t<R>(p, y, mask, o->penalty, &m, st);
+    if (rc) return rc;
+    lam *= m;
+  }
+  const double tau = lam * delta;
+  // momentum sequence mu_k = (t^k - 1)/t^{k+1}
+  std::vector<double> mu(o->max_iter + 1, 0.0);
+  {
+    double t = 1.0;
+    for (int k = 0; k <= o->max_iter; ++k) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      mu[k] = (t - 1.0) / tn;
+      t = tn;
+    }
+  }
+  void* z1 = s->zA;
+  void* z2 = s->zB;
+  const int nreg = reg_count(p, o->penalty);
+  MBIR_CUDA_TRY(cudaMemsetAsync(s->pz, 0, real_size(p) * s->nmeas, st));
+  if (o->warm_start) {
+    MBIR_CUDA_TRY(cudaMemcpyAsync(z1, x, es * s->nimg, cudaMemcpyDeviceToDevice, st));
+    MBIR_CUDA_TRY(cudaMemcpyAsync(z2, x, es * s->nimg, cudaMemcpyDeviceToDevice, st));
+    int rc = reg_partials_t<R>(p, o->penalty, z1, st);
+    if (rc) return rc;
+  } else {
+    MBIR_CUDA_TRY(cudaMemsetAsync(z1, 0, es * s->nimg, st));
+    MBIR_CUDA_TRY(cudaMemsetAsync(z2, 0, es * s->nimg, st));
+    MBIR_CUDA_TRY(cudaMemsetAsync(s->part_reg, 0, sizeof(double) * s->n_reg, st));
+  }
+  int k = 0, status = MBIR_OK;
+  const bool check = o->rel_tol > 0;
+  if (check) status = MBIR_ERR_NOT_CONVERGED;
+  for (k = 1; k <= o->max_iter; ++k) {
+    const double m = k >= 2 ? mu[k - 2] : 0.0;
+    int rc = forward_solve_impl(p, z1, mask, y, s->pz, s->r, m, s->part_data, st);
+    if (rc) return rc;
+    combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_data, s->n_data, 0.5, s->part_reg, nreg, lam,
+                                              s->objtrace + (k - 1));
+    MBIR_LAUNCH_CHECK();
+    if (o->penalty == MBIR_PENALTY_L1) {
+      rc = adjoint_solve_impl(p, s->r, z1, z2, nullptr, m, delta, tau, s->part_reg, st);
+      if (rc) return rc;
+    } else {
+      rc = adjoint_solve_impl(p, s->r, z1, z2, s->v, m, delta, tau, nullptr, st);
+      if (rc) return rc;
+      rc = prox_partial_impl(p, o->penalty, s->v, tau, z2, s->part_reg, st);
+      if (rc) return rc;
+    }
+    void* t = z1;
+    z1 = z2;
+    z2 = t;
+    if (check && k >= 3 && k >= o->min_iter) {
+      double f[2];
+      MBIR_CUDA_TRY(cudaMemcpyAsync(f, s->objtrace + (k - 2), 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+      if (fabs(f[1] - f[0]) <= o->rel_tol * fabs(f[0])) {
+        status = MBIR_OK;
+        break;
+      }
+    }
+  }
+  const int iters = k > o->max_iter ? o->max_iter : k;
+  MBIR_CUDA_TRY(cudaMemcpyAsync(x, z1, es * s->nimg, cudaMemcpyDeviceToDevice, st));
+  if (info) {
+    // F(z^iters): one more forward pass for the data term
+    int rc = forward_impl(p, z1, mask, s->r, st);
+    if (rc) return rc;
+    const int gb = grid_for(s->nmeas);
+    resid_kernel<R><<<gb, kRedThreads, 0, st>>>((const R*)s->r, (const R*)y, mask, s->nmeas, s->part_tmp);
+    combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, 0.5, s->part_reg, nreg, lam, s->scal + 6);
+    MBIR_LAUNCH_CHECK();
+    double fin = 0.0;
+    MBIR_CUDA_TRY(cudaMemcpyAsync(&fin, s->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (info->objective_trace && info->trace_len > 0) {
+      const int n = info->trace_len < iters ? info->trace_len : iters;
+      MBIR_CUDA_TRY(cudaMemcpyAsync(info->objective_trace, s->objtrace, sizeof(double) * n,
+                                    cudaMemcpyDeviceToHost, st));
+    }
+    MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+    info->iters = iters;
+    info->status = status;
+    info->objective = fin;
+    info->lipschitz = L;
+    info->step = delta;
+    info->lambda_used = lam;
+  }
+  return status;
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
 extern "C" {
-int mbir_solve(mbir_plan, const void*, const uint8_t*, const mbir_solve_opts*, void*, mbir_solve_info*, void*) {
-  return MBIR_ERR_UNSUPPORTED_SIZE;
+
+int mbir_lipschitz(mbir_plan p, const uint8_t* mask, int32_t iters, double* out, void* stream) {
+  if (!p || !out || iters < 1) return MBIR_ERR_INVALID;
+  int rc = ensure_state(p, 1);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  return p->precision == MBIR_FP64 ? lipschitz_t<double>(p, mask, iters, out, st)
+                                   : lipschitz_t<float>(p, mask, iters, out, st);
 }
-int mbir_lipschitz(mbir_plan, const uint8_t*, int32_t, double*, void*) { return MBIR_ERR_UNSUPPORTED_SIZE; }
+
+int mbir_solve(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
+               mbir_solve_info* info, void* stream) {
+  if (!p || !y || !o || !x) return MBIR_ERR_INVALID;
+  if (o->max_iter < 1 || o->min_iter < 0) return MBIR_ERR_INVALID;
+  if (o->penalty != MBIR_PENALTY_L1 && o->penalty != MBIR_PENALTY_DB4) return MBIR_ERR_INVALID;
+  if (!(o->lambda >= 0) || !isfinite(o->lambda) || !isfinite(o->step) || !(o->rel_tol >= 0))
+    return MBIR_ERR_INVALID;
+  if (o->penalty == MBIR_PENALTY_DB4 && !wavelet_supported(p->nx, p->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  int rc = ensure_state(p, o->max_iter);
+  if (rc) return rc;
+  if (o->penalty == MBIR_PENALTY_DB4) {
+    rc = ensure_wavelet_scratch(p);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  return p->precision == MBIR_FP64 ? solve_t<double>(p, y, mask, o, x, info, st)
+                                   : solve_t<float>(p, y, mask, o, x, info, st);
 }
+
+}  // extern "C"

@@ -1,8 +1,367 @@
+// Orthonormal wavelet penalty transform Psi (Sec. 2.2): 3-level periodic 2-D
+// Daubechies wavelet with 4 vanishing moments (8 taps), applied to the real and
+// imaginary parts alike, and its proximal map Psi^T soft(Psi v, tau) (Sec. 2.3).
+//
+// Layout (Mallat): at each level the current low-low block of size P x N, stored
+// at the top-left of an [nx][nz] array, becomes [[LL, LH], [HL, HH]] with blocks
+// of P/2 x N/2; the first letter is the filter along the lateral axis p, the
+// second along depth n.  One analysis level:
+//   lo_n / hi_n[i][b] = sum_t h_t / g_t  x[i][(2b + t) mod N]
+//   LL / HL[a][b]     = sum_t h_t / g_t  lo_n[(2a + t) mod P][b]
+//   LH / HH[a][b]     = sum_t h_t / g_t  hi_n[(2a + t) mod P][b]
+// with g_t = (-1)^t h_{7-t}.  Synthesis is the transpose, written as a gather:
+// output index X receives from coefficient (X - t)/2 for the four t of X's parity.
+#include <math.h>
+
 #include "common.cuh"
+
 namespace mbir {
-bool wavelet_supported(int nx, int nz) { return nx % 8 == 0 && nz % 8 == 0 && nx / 4 >= 8 && nz / 4 >= 8; }
+
+constexpr int kFwdTA = 16, kFwdTB = 32;   // analysis: output coefficient tile (a x b)
+constexpr int kInvTR = 32, kInvTC = 64;   // synthesis: output pixel tile (rows x cols)
+constexpr int kWavThreads = 256;
+constexpr int kFwdRows = 2 * kFwdTA + 6, kFwdCols = 2 * kFwdTB + 6;
+constexpr int kInvRows = kInvTR / 2 + 3, kInvCols = kInvTC / 2 + 3;
+
+template <class R>
+struct WArgs {
+  const void* in;
+  int istride;      // analysis: input block; synthesis: LL block
+  void* out;
+  int ostride;      // analysis: LL output; synthesis: output block
+  void* coef;
+  int cstride;      // detail bands at their Mallat positions (level block at the origin)
+  int P, N;         // level block size (analysis input / synthesis output)
+  const R* h;       // 8 low-pass taps
+  R tau;
+  int thresh;       // analysis: 0 none, 1 details, 2 details and LL
+  double* partial;  // analysis with thresh: sum |soft(c)| per CTA
+};
+
+template <class R>
+__device__ __forceinline__ cplx_t<R> soft_c(cplx_t<R> c, R tau, double& acc) {
+  const R mag = sqrt(c.x * c.x + c.y * c.y);
+  const R s = mag > tau ? R(1) - tau / mag : R(0);
+  if (mag > tau) acc += double(mag - tau);
+  return cmk<cplx_t<R>>(c.x * s, c.y * s);
 }
+
+__device__ __forceinline__ double block_sum_w(double v) {
+  __shared__ double wsum[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kWavThreads) dwt_fwd_kernel(WArgs<R> a) {
+  using V = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tin = reinterpret_cast<V*>(smem_raw);              // [kFwdRows][kFwdCols]
+  V* tL = tin + kFwdRows * kFwdCols;                    // [kFwdRows][kFwdTB]
+  V* tH = tL + kFwdRows * kFwdTB;
+  __shared__ R h[8], g[8];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid < 8) {
+    h[tid] = a.h[tid];
+    g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
+  }
+  const int P = a.P, N = a.N;
+  const int a0 = blockIdx.y * kFwdTA, b0 = blockIdx.x * kFwdTB;
+  const V* in = reinterpret_cast<const V*>(a.in);
+  for (int e = tid; e < kFwdRows * kFwdCols; e += nthr) {
+    const int i = e / kFwdCols, j = e - i * kFwdCols;
+    const int row = (2 * a0 + i) % P, col = (2 * b0 + j) % N;
+    tin[e] = in[(size_t)row * a.istride + col];
+  }
+  __syncthreads();
+  for (int e = tid; e < kFwdRows * kFwdTB; e += nthr) {
+    const int i = e / kFwdTB, b = e - i * kFwdTB;
+    const V* src = tin + i * kFwdCols + 2 * b;
+    V lo = cmk<V>(R(0), R(0)), hi = lo;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const V x = src[t];
+      lo.x += h[t] * x.x; lo.y += h[t] * x.y;
+      hi.x += g[t] * x.x; hi.y += g[t] * x.y;
+    }
+    tL[e] = lo;
+    tH[e] = hi;
+  }
+  __syncthreads();
+  const int Ph = P / 2, Nh = N / 2;
+  V* coef = reinterpret_cast<V*>(a.coef);
+  V* llo = reinterpret_cast<V*>(a.out);
+  double acc = 0.0;
+  for (int e = tid; e < kFwdTA * kFwdTB; e += nthr) {
+    const int ai = e / kFwdTB, b = e - ai * kFwdTB;
+    const int A = a0 + ai, B = b0 + b;
+    if (A >= Ph || B >= Nh) continue;
+    V ll = cmk<V>(R(0), R(0)), hl = ll, lh = ll, hh = ll;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const V xl = tL[(2 * ai + t) * kFwdTB + b];
+      const V xh = tH[(2 * ai + t) * kFwdTB + b];
+      ll.x += h[t] * xl.x; ll.y += h[t] * xl.y;
+      hl.x += g[t] * xl.x; hl.y += g[t] * xl.y;
+      lh.x += h[t] * xh.x; lh.y += h[t] * xh.y;
+      hh.x += g[t] * xh.x; hh.y += g[t] * xh.y;
+    }
+    if (a.thresh >= 1) {
+      lh = soft_c<R>(lh, a.tau, acc);
+      hl = soft_c<R>(hl, a.tau, acc);
+      hh = soft_c<R>(hh, a.tau, acc);
+    }
+    if (a.thresh == 2) ll = soft_c<R>(ll, a.tau, acc);
+    llo[(size_t)A * a.ostride + B] = ll;
+    coef[(size_t)A * a.cstride + Nh + B] = lh;
+    coef[(size_t)(Ph + A) * a.cstride + B] = hl;
+    coef[(size_t)(Ph + A) * a.cstride + Nh + B] = hh;
+  }
+  if (a.partial) {
+    const double t = block_sum_w(acc);
+    if (tid == 0) a.partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kWavThreads) dwt_inv_kernel(WArgs<R> a) {
+  using V = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* cLL = reinterpret_cast<V*>(smem_raw);              // [kInvRows][kInvCols] each
+  V* cLH = cLL + kInvRows * kInvCols;
+  V* cHL = cLH + kInvRows * kInvCols;
+  V* cHH = cHL + kInvRows * kInvCols;
+  V* tlo = cHH + kInvRows * kInvCols;                   // [kInvTR][kInvCols]
+  V* thi = tlo + kInvTR * kInvCols;
+  __shared__ R h[8], g[8];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid < 8) {
+    h[tid] = a.h[tid];
+    g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
+  }
+  const int P = a.P, N = a.N, Ph = P / 2, Nh = N / 2;
+  const int r0 = blockIdx.y * kInvTR, c0 = blockIdx.x * kInvTC;
+  const V* ll = reinterpret_cast<const V*>(a.in);
+  const V* coef = reinterpret_cast<const V*>(a.coef);
+  for (int e = tid; e < kInvRows * kInvCols; e += nthr) {
+    const int ia = e / kInvCols, ib = e - ia * kInvCols;
+    const int A = ((r0 / 2 - 3 + ia) % Ph + Ph) % Ph;
+    const int B = ((c0 / 2 - 3 + ib) % Nh + Nh) % Nh;
+    cLL[e] = ll[(size_t)A * a.istride + B];
+    cLH[e] = coef[(size_t)A * a.cstride + Nh + B];
+    cHL[e] = coef[(size_t)(Ph + A) * a.cstride + B];
+    cHH[e] = coef[(size_t)(Ph + A) * a.cstride + Nh + B];
+  }
+  __syncthreads();
+  for (int e = tid; e < kInvTR * kInvCols; e += nthr) {
+    const int r = e / kInvCols, ib = e - r * kInvCols;
+    V lo = cmk<V>(R(0), R(0)), hi = lo;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = (r & 1) + 2 * q;
+      const int ia = (r - t) / 2 + 3;
+      const V vll = cLL[ia * kInvCols + ib], vhl = cHL[ia * kInvCols + ib];
+      const V vlh = cLH[ia * kInvCols + ib], vhh = cHH[ia * kInvCols + ib];
+      lo.x += h[t] * vll.x + g[t] * vhl.x; lo.y += h[t] * vll.y + g[t] * vhl.y;
+      hi.x += h[t] * vlh.x + g[t] * vhh.x; hi.y += h[t] * vlh.y + g[t] * vhh.y;
+    }
+    tlo[e] = lo;
+    thi[e] = hi;
+  }
+  __syncthreads();
+  V* out = reinterpret_cast<V*>(a.out);
+  for (int e = tid; e < kInvTR * kInvTC; e += nthr) {
+    const int r = e / kInvTC, c = e - r * kInvTC;
+    if (r0 + r >= P || c0 + c >= N) continue;
+    V x = cmk<V>(R(0), R(0));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = (c & 1) + 2 * q;
+      const int ib = (c - t) / 2 + 3;
+      const V lo = tlo[r * kInvCols + ib], hi = thi[r * kInvCols + ib];
+      x.x += h[t] * lo.x + g[t] * hi.x;
+      x.y += h[t] * lo.y + g[t] * hi.y;
+    }
+    out[(size_t)(r0 + r) * a.ostride + c0 + c] = x;
+  }
+}
+
+template <class R>
+__global__ void soft_kernel(const cplx_t<R>* v, cplx_t<R>* z, size_t n, R tau, double* partial) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    z[i] = soft_c<R>(v[i], tau, acc);
+  if (partial) {
+    const double t = block_sum_w(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+static size_t fwd_smem(size_t vs) { return vs * (kFwdRows * kFwdCols + 2 * kFwdRows * kFwdTB); }
+static size_t inv_smem(size_t vs) { return vs * (4 * kInvRows * kInvCols + 2 * kInvTR * kInvCols); }
+
+int wavelet_partial_count(int nx, int nz) {
+  int total = 0, P = nx, N = nz;
+  for (int lev = 0; lev < 3; ++lev) {
+    total += ((N / 2 + kFwdTB - 1) / kFwdTB) * ((P / 2 + kFwdTA - 1) / kFwdTA);
+    P /= 2;
+    N /= 2;
+  }
+  return total;
+}
+
+int ensure_wavelet_scratch(mbir_plan p) {
+  if (p->wv_b1) return MBIR_OK;
+  const size_t es = p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t n = (size_t)p->nx * p->nz;
+  MBIR_CUDA_TRY(cudaMalloc(&p->wv_b1, es * (n / 4)));
+  MBIR_CUDA_TRY(cudaMalloc(&p->wv_b2, es * (n / 16)));
+  MBIR_CUDA_TRY(cudaMalloc(&p->wv_coef, es * n));
+  return MBIR_OK;
+}
+
+template <class R>
+static int analysis_t(mbir_plan p, const void* in, void* coef, bool thresh, R tau, double* partial,
+                      cudaStream_t st) {
+  const int nx = p->nx, nz = p->nz;
+  const void* src = in;
+  int sstride = nz;
+  int P = nx, N = nz;
+  double* part = partial;
+  void* lls[3] = {p->wv_b1, p->wv_b2, coef};
+  int lstr[3] = {nz / 2, nz / 4, nz};
+  for (int lev = 0; lev < 3; ++lev) {
+    WArgs<R> a;
+    a.in = src;
+    a.istride = sstride;
+    a.out = lls[lev];
+    a.ostride = lstr[lev];
+    a.coef = coef;
+    a.cstride = nz;
+    a.P = P;
+    a.N = N;
+    a.h = p->precision == MBIR_FP64 ? reinterpret_cast<const R*>(p->h_db4) : reinterpret_cast<const R*>(p->h_db4f);
+    a.tau = tau;
+    a.thresh = thresh ? (lev == 2 ? 2 : 1) : 0;
+    a.partial = thresh ? part : nullptr;
+    dim3 grid((N / 2 + kFwdTB - 1) / kFwdTB, (P / 2 + kFwdTA - 1) / kFwdTA);
+    dwt_fwd_kernel<R><<<grid, kWavThreads, fwd_smem(sizeof(cplx_t<R>)), st>>>(a);
+    MBIR_LAUNCH_CHECK();
+    if (part) part += grid.x * grid.y;
+    src = lls[lev];
+    sstride = lstr[lev];
+    P /= 2;
+    N /= 2;
+  }
+  return MBIR_OK;
+}
+
+template <class R>
+static int synthesis_t(mbir_plan p, const void* coef, void* out, cudaStream_t st) {
+  const int nx = p->nx, nz = p->nz;
+  const void* lls[3] = {p->wv_b1, p->wv_b2, coef};
+  const int lstr[3] = {nz / 2, nz / 4, nz};
+  void* outs[3] = {out, p->wv_b1, p->wv_b2};
+  const int ostr[3] = {nz, nz / 2, nz / 4};
+  for (int lev = 2; lev >= 0; --lev) {
+    WArgs<R> a;
+    a.in = lls[lev];
+    a.istride = lstr[lev];
+    a.out = outs[lev];
+    a.ostride = ostr[lev];
+    a.coef = const_cast<void*>(coef);
+    a.cstride = nz;
+    a.P = nx >> lev;
+    a.N = nz >> lev;
+    a.h = p->precision == MBIR_FP64 ? reinterpret_cast<const R*>(p->h_db4) : reinterpret_cast<const R*>(p->h_db4f);
+    a.tau = R(0);
+    a.thresh = 0;
+    a.partial = nullptr;
+    dim3 grid((a.N + kInvTC - 1) / kInvTC, (a.P + kInvTR - 1) / kInvTR);
+    dwt_inv_kernel<R><<<grid, kWavThreads, inv_smem(sizeof(cplx_t<R>)), st>>>(a);
+    MBIR_LAUNCH_CHECK();
+  }
+  return MBIR_OK;
+}
+
+bool wavelet_supported(int nx, int nz) { return nx % 8 == 0 && nz % 8 == 0 && nx >= 32 && nz >= 32; }
+
+template <class R>
+static int configure_wavelet_t() {
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fwd_smem(sizeof(cplx_t<R>))));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)inv_smem(sizeof(cplx_t<R>))));
+  return MBIR_OK;
+}
+
+int configure_wavelet_kernels(mbir_plan p) {
+  return p->precision == MBIR_FP64 ? configure_wavelet_t<double>() : configure_wavelet_t<float>();
+}
+
+int wavelet_impl(mbir_plan p, int inverse, const void* in, void* out, cudaStream_t st) {
+  if (!wavelet_supported(p->nx, p->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  int rc = ensure_wavelet_scratch(p);
+  if (rc) return rc;
+  if (p->precision == MBIR_FP64)
+    return inverse ? synthesis_t<double>(p, in, out, st) : analysis_t<double>(p, in, out, false, 0.0, nullptr, st);
+  return inverse ? synthesis_t<float>(p, in, out, st) : analysis_t<float>(p, in, out, false, 0.0f, nullptr, st);
+}
+
+// z = prox of tau ||Psi .||_1 at v; partial (may be null) receives per-CTA sums of
+// |Psi z| (wavelet_partial_count entries for DB4, soft_grid entries for L1).
+int prox_partial_impl(mbir_plan p, int penalty, const void* v, double tau, void* z, double* partial,
+                      cudaStream_t st) {
+  const bool f64 = p->precision == MBIR_FP64;
+  if (penalty == MBIR_PENALTY_L1) {
+    const size_t n = (size_t)p->nx * p->nz;
+    if (f64)
+      soft_kernel<double><<<kSoftGrid, 256, 0, st>>>((const double2*)v, (double2*)z, n, tau, partial);
+    else
+      soft_kernel<float><<<kSoftGrid, 256, 0, st>>>((const float2*)v, (float2*)z, n, (float)tau, partial);
+    MBIR_LAUNCH_CHECK();
+    return MBIR_OK;
+  }
+  if (penalty != MBIR_PENALTY_DB4) return MBIR_ERR_INVALID;
+  if (!wavelet_supported(p->nx, p->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  int rc = ensure_wavelet_scratch(p);
+  if (rc) return rc;
+  if (f64) {
+    rc = analysis_t<double>(p, v, p->wv_coef, true, tau, partial, st);
+    if (rc) return rc;
+    return synthesis_t<double>(p, p->wv_coef, z, st);
+  }
+  rc = analysis_t<float>(p, v, p->wv_coef, true, (float)tau, partial, st);
+  if (rc) return rc;
+  return synthesis_t<float>(p, p->wv_coef, z, st);
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
 extern "C" {
-int mbir_prox(mbir_plan, int32_t, const void*, double, void*, void*) { return MBIR_ERR_UNSUPPORTED_SIZE; }
-int mbir_wavelet(mbir_plan, int32_t, const void*, void*, void*) { return MBIR_ERR_UNSUPPORTED_SIZE; }
+
+int mbir_prox(mbir_plan p, int32_t penalty, const void* v, double tau, void* z, void* stream) {
+  if (!p || !v || !z || !(tau >= 0) || !isfinite(tau)) return MBIR_ERR_INVALID;
+  if (penalty != MBIR_PENALTY_L1 && penalty != MBIR_PENALTY_DB4) return MBIR_ERR_INVALID;
+  return prox_partial_impl(p, penalty, v, tau, z, nullptr, (cudaStream_t)stream);
 }
+
+int mbir_wavelet(mbir_plan p, int32_t inverse, const void* in, void* out, void* stream) {
+  if (!p || !in || !out || in == out) return MBIR_ERR_INVALID;
+  return wavelet_impl(p, inverse, in, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
