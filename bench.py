@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 MBIR hot path.
+
+One step = one complete reconstruction of the full-size synthetic B-scan
+(1024 A-scans x 2048 spectral pixels, complex64 image 1024 x 2048, 500 seeded
+beads, half the A-scans measured, 25 dB noise): power iteration for the step
+size, the relative lambda rule and 100 FISTA iterations with the 3-level db4
+wavelet penalty, all through the C ABI (mbir_solve).  The metric is B-scans per
+second for the whole job; Phi+Phi^H pairs per second are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank reconstructs its own
+B-scans (independent problems, no data-path collective): weak scaling.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "bscan-1024x2048-db4-100it-half-ascans"
+METRIC = "fista_bscans_per_sec"
+UNIT = "B-scans/s"
+ITERS = 100
+POWER_ITERS = 30
+LAMBDA_FRAC = 0.01
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def oracle_timing(sample_iters: int = 2):
+    """Time the FP64 oracle on a bounded sample of the workload: one Phi+Phi^H pair
+    and `sample_iters` FISTA iterations (db4) of the full-size B-scan, then
+    extrapolate to one full reconstruction (30 power-iteration pairs, the lambda
+    rule and 100 iterations)."""
+    import numpy as np
+    from oracle import fista, isam, wavelet
+    from paper_2108_01438_gb300 import workloads
+
+    wl = workloads.full_workload()
+    g = isam.make_geom(wl["geom"])
+    mask = wl["mask"]
+    h = wavelet.daubechies_lowpass(4)
+    phi = lambda v: isam.phi_nufft(v, mask, g)
+    phi_adj = lambda r: isam.phi_adj_nufft(r, mask, g)
+    y = phi(wl["x_true"])
+    t0 = time.perf_counter()
+    a = phi_adj(phi(wl["x_true"]))
+    t_pair = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lam = LAMBDA_FRAC * float(np.max(np.abs(wavelet.dwt2(phi_adj(y * mask), h, 3))))
+    t_lambda = time.perf_counter() - t0
+    delta = 1e-4
+    t0 = time.perf_counter()
+    fista.fista(phi, phi_adj, y, mask, lambda v, t: fista.prox_wavelet(v, t, h), lam, delta,
+                sample_iters, (g.nx, g.nz))
+    t_iter = (time.perf_counter() - t0) / sample_iters
+    del a
+    t_solve = POWER_ITERS * t_pair + t_lambda + ITERS * t_iter
+    return dict(t_pair=t_pair, t_iter=t_iter, t_lambda=t_lambda, t_solve=t_solve)
+
+
+def cores_used() -> int:
+    # numpy's FFT (pocketfft) and the elementwise ufuncs run single-threaded
+    return 1
+
+
+def run_reference(args, rank: int, ws: int) -> None:
+    if rank != 0:
+        return
+    from oracle import isam  # noqa: F401  (the oracle is the reference arm)
+    times = []
+    for step in range(args.warmup + args.steps):
+        t = oracle_timing(sample_iters=1)
+        if step >= args.warmup:
+            times.append(t["t_solve"])
+    mean = statistics.mean(times)
+    value = 1.0 / mean
+    sample = ("per step: one FP64 Phi+Phi^H pair, the lambda rule and 1 FISTA db4 iteration of the "
+              "1024x2048 B-scan, extrapolated to 30 power-iteration pairs + lambda + 100 iterations")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "nx": 1024, "nz": 2048, "m": 2048,
+                                        "penalty": "db4", "iters": ITERS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ clocks sampler
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int | None):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.index is not None:
+            cmd += ["-i", str(self.index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smi_index(local_rank: int) -> int | None:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+        return None
+    return local_rank
+
+
+# ------------------------------------------------------------ roofline helpers
+
+def algorithmic_bytes(cls: str, nx: int, nz: int, m: int) -> float | None:
+    """Bytes one launch of a kernel class must move (FP32 path), from its operands."""
+    nlh = nx // 2 + 1
+    img, meas = nx * nz, nx * m
+    table = nlh * m * 16
+    return {
+        "lateral_forward": 16.0 * img,                       # read x, write X
+        "row_forward": 8.0 * img + table + 8.0 * meas,       # read X, table, write S
+        "lateral_inverse_real": 25.0 * meas,                 # read S, mask, y, pz; write pz, r
+        "lateral_residual": 12.0 * meas,                     # read r, write R
+        "row_adjoint": 8.0 * meas + table + 8.0 * img,       # read R, table, write W
+        "lateral_adjoint": 32.0 * img,                       # read W, z1, z2; write v or z
+    }.get(cls)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2108_01438_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_for(cls: str) -> float | None:
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get(cls)
+    if not e or e.get("source_hash") != source_hash() or e.get("workload") != WORKLOAD:
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+# ------------------------------------------------------------ our arm
+
+def run_ours(args, rank: int, ws: int, local: int) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2108_01438_gb300 import mbir, workloads
+
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        from paper_2108_01438_gb300 import build
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    mbir.lib()
+
+    wl = workloads.full_workload(seed_offset=1 + rank)
+    d = wl["geom"]
+    nx, nz, m = d["nx"], d["nz"], d["m"]
+    plan = mbir.Plan(d)
+    stream = torch.cuda.current_stream()
+    x_true = torch.from_numpy(wl["x_true"].astype(np.complex64)).to(dev)
+    mask = torch.from_numpy(wl["mask"]).to(dev)
+    clean = plan.forward(x_true, mask)
+    sig = torch.sqrt(torch.mean(clean[mask == 1].double() ** 2)).item()
+    noise = torch.from_numpy(wl["noise"].astype(np.float32)).to(dev)
+    y = (clean + float(sig * 10 ** (-wl["snr_db"] / 20)) * noise * mask).contiguous()
+    out = torch.empty((nx, nz), dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        plan.solve(y, mask, penalty="db4", lam=LAMBDA_FRAC, relative=True, iters=ITERS,
+                   power_iters=POWER_ITERS, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(smi_index(local))
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    plan.profile_begin(1 << 17)
+    for i in range(args.steps):
+        flush.zero_()                       # evict the previous step's data from L2
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof = plan.profile_end()
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = ws * args.steps / total_max
+
+    # Phi + Phi^H pairs per second on the same B-scan (operators alone)
+    xa = torch.empty_like(out)
+    for _ in range(3):
+        plan.forward(out, mask, out=y.new_empty(y.shape))
+    pairs = 200
+    yb = torch.empty_like(y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(pairs):
+        plan.forward(out, mask, out=yb)
+        plan.adjoint(yb, mask, out=xa)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pair_ms = e0.elapsed_time(e1) / pairs
+
+    # end to end through host buffers: pinned inputs in, reconstruction out, each step
+    y_host = y.cpu().pin_memory()
+    m_host = mask.cpu().pin_memory()
+    x_host = torch.empty((nx, nz), dtype=torch.complex64).pin_memory()
+    y_dev, m_dev = torch.empty_like(y), torch.empty_like(mask)
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        e_ev[i][0].record(stream)
+        y_dev.copy_(y_host, non_blocking=True)
+        m_dev.copy_(m_host, non_blocking=True)
+        plan.solve(y_dev, m_dev, penalty="db4", lam=LAMBDA_FRAC, relative=True, iters=ITERS,
+                   power_iters=POWER_ITERS, out=out)
+        x_host.copy_(out, non_blocking=True)
+        e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in e_ev) / 1e3
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * args.steps / float(t.item())
+
+    launches = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_cls, (dom_n, dom_ms) = dom
+    avg_ms = dom_ms / dom_n
+    alg = algorithmic_bytes(dom_cls, nx, nz, m)
+    peak, peak_kind = measured_peak()
+    roofline = None
+    if alg is not None:
+        achieved = alg / (avg_ms * 1e-3) / 1e9
+        traffic = traffic_for(dom_cls)
+        roofline = {"bound": "hbm", "kernel": dom_cls, "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "alg_bytes": alg, "avg_launch_ms": avg_ms}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ot = oracle_timing(sample_iters=2)
+        cpu = {"value": 1.0 / ot["t_solve"], "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+               "sample": ("one FP64 Phi+Phi^H pair, the lambda rule and 2 FISTA db4 iterations of the "
+                          "1024x2048 B-scan (%.1f s), extrapolated to 30 pairs + lambda + 100 iterations"
+                          % (ot["t_pair"] + ot["t_lambda"] + 2 * ot["t_iter"])),
+               "pairs_per_sec": 1.0 / ot["t_pair"]}
+
+    if rank == 0:
+        step_sorted = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_max * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": nx, "nz": nz, "m": m, "penalty": "db4",
+                       "iters": ITERS, "power_iters": POWER_ITERS, "mask": "50% of A-scans",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "pairs_per_sec": ws * 1e3 / pair_ms,
+            "latency_ms": {"p50": statistics.median(step_ms),
+                           "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
+            "kernels_ms_per_launch": {k: v[1] / v[0] for k, v in prof.items()},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),
+                    "d2h_bytes_per_step": out.numel() * 8},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        return
+    run_ours(args, rank, ws, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -211,6 +211,22 @@ int mbir_prox(mbir_plan plan, int32_t penalty, const void* v, double tau, void* 
  */
 int mbir_wavelet(mbir_plan plan, int32_t inverse, const void* in, void* out, void* stream);
 
+/*
+ * Kernel timing (tracing).  mbir_profile_begin makes every later launch on the plan
+ * record a CUDA event pair on its stream (up to `capacity` launches; further
+ * launches run unrecorded).  mbir_profile_end waits for the recorded events, fills
+ * up to max_entries entries, one per kernel class that ran (static names), stops
+ * recording and frees the events.  *n_entries receives the entry count.
+ */
+typedef struct {
+  const char* name;      /* kernel class, e.g. "row_forward" */
+  int64_t launches;      /* recorded launches */
+  double total_ms;       /* summed event time */
+} mbir_profile_entry;
+
+int mbir_profile_begin(mbir_plan plan, int32_t capacity);
+int mbir_profile_end(mbir_plan plan, mbir_profile_entry* out, int32_t max_entries, int32_t* n_entries);
+
 /* Static description of a status code. */
 const char* mbir_status_string(int status);
 

@@ -59,6 +59,29 @@ template <> struct TabOf<float> { using T = TabF; };
 template <> struct TabOf<double> { using T = TabD; };
 
 struct SolveState;   // defined in solve.cu
+
+// Kernel classes for the event profiler (mbir_profile_begin / _end).
+enum ProfClass {
+  PC_LAT_FWD = 0,     // lateral FFT of the image (first stage of Phi)
+  PC_ROW_FWD,         // row NUFFT forward
+  PC_LAT_INV,         // inverse lateral FFT + real part (+ FISTA measurement epilogue)
+  PC_LAT_R2C,         // lateral FFT of the masked residual (first stage of Phi^H)
+  PC_ROW_ADJ,         // row NUFFT adjoint
+  PC_LAT_ADJ,         // inverse lateral FFT of the adjoint (+ FISTA image epilogue)
+  PC_DWT_FWD,         // wavelet analysis level (+ soft-threshold)
+  PC_DWT_INV,         // wavelet synthesis level
+  PC_SOFT,            // elementwise soft-threshold
+  PC_REDUCE,          // reductions, scalars, power-iteration helpers
+  PC_COUNT
+};
+
+struct Profiler {
+  int cap = 0, n = 0;
+  cudaEvent_t* ev = nullptr;   // 2 * cap
+  int* cls = nullptr;          // cap
+};
+
+const char* prof_class_name(int c);
 struct BatchCache;
 
 }  // namespace mbir
@@ -90,6 +113,7 @@ struct mbir_plan_s {
   // reductions: partial sums
   double* red;                // kRedSlots doubles
   mbir::SolveState* solve;    // lazily created
+  mbir::Profiler* prof;       // non-null while profiling
 };
 
 namespace mbir {
@@ -111,6 +135,27 @@ void set_error_text(const std::string& s);
     cudaError_t e_ = cudaGetLastError();                                        \
     if (e_ != cudaSuccess) return ::mbir::set_cuda_error(e_, "kernel launch");   \
   } while (0)
+
+// Event profiler: prof_begin returns a slot (or -1 when not recording).
+inline int prof_begin(mbir_plan p, int cls, cudaStream_t st) {
+  Profiler* pr = p->prof;
+  if (!pr || pr->n >= pr->cap) return -1;
+  const int i = pr->n++;
+  pr->cls[i] = cls;
+  cudaEventRecord(pr->ev[2 * i], st);
+  return i;
+}
+inline void prof_end(mbir_plan p, int slot, cudaStream_t st) {
+  if (slot >= 0) cudaEventRecord(p->prof->ev[2 * slot + 1], st);
+}
+struct ProfScope {
+  mbir_plan p;
+  cudaStream_t st;
+  int slot;
+  ProfScope(mbir_plan p_, int cls, cudaStream_t st_) : p(p_), st(st_), slot(prof_begin(p_, cls, st_)) {}
+  ~ProfScope() { prof_end(p, slot, st); }
+};
+void destroy_profiler(mbir_plan p);
 
 // operator.cu
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st);

@@ -249,6 +249,13 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
   return a;
 }
 
+constexpr int lat_class(int mode) {
+  return mode == LAT_C2C_FWD ? PC_LAT_FWD
+         : mode == LAT_R2C_MASK ? PC_LAT_R2C
+         : (mode == LAT_C2R_INV_MASK || mode == LAT_SOLVE_FWD) ? PC_LAT_INV
+                                                               : PC_LAT_ADJ;
+}
+
 template <class R>
 size_t lat_smem(mbir_plan p) {
   return sizeof(cplx_t<R>) * p->nx * p->tile_c;
@@ -258,7 +265,7 @@ template <class R, int MODE>
 int launch_lateral(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, R scale,
                    cudaStream_t st) {
   LatArgs<R> a = lat_args<R>(p, in, out, mask, cols, scale);
-  lateral_kernel<R, MODE><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a);
+  { ProfScope ps_(p, lat_class(MODE), st); lateral_kernel<R, MODE><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a); }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
 }
@@ -296,7 +303,7 @@ int forward_t(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStre
   int rc = launch_lateral<R, LAT_C2C_FWD>(p, x, p->wsA, nullptr, p->nz, R(1), st);
   if (rc) return rc;
   RowArgs<R> a = row_args<R>(p, p->wsA, p->wsB);
-  row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a);
+  { ProfScope ps_(p, PC_ROW_FWD, st); row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a); }
   MBIR_LAUNCH_CHECK();
   return launch_lateral<R, LAT_C2R_INV_MASK>(p, p->wsB, y, mask, p->m, R(1) / R(p->nx), st);
 }
@@ -306,7 +313,7 @@ int adjoint_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStre
   int rc = launch_lateral<R, LAT_R2C_MASK>(p, y, p->wsA, mask, p->m, R(1) / R(p->nx), st);
   if (rc) return rc;
   RowArgs<R> a = row_args<R>(p, p->wsA, p->wsB);
-  row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a);
+  { ProfScope ps_(p, PC_ROW_ADJ, st); row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a); }
   MBIR_LAUNCH_CHECK();
   return launch_lateral<R, LAT_C2C_INV>(p, p->wsB, x, nullptr, p->nz, R(1), st);
 }
@@ -317,7 +324,7 @@ int forward_solve_t(mbir_plan p, const void* z1, const uint8_t* mask, const void
   int rc = launch_lateral<R, LAT_C2C_FWD>(p, z1, p->wsA, nullptr, p->nz, R(1), st);
   if (rc) return rc;
   RowArgs<R> ra = row_args<R>(p, p->wsA, p->wsB);
-  row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra);
+  { ProfScope ps_(p, PC_ROW_FWD, st); row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra); }
   MBIR_LAUNCH_CHECK();
   LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, mask, p->m, R(1) / R(p->nx));
   a.y = reinterpret_cast<const R*>(y);
@@ -325,7 +332,7 @@ int forward_solve_t(mbir_plan p, const void* z1, const uint8_t* mask, const void
   a.r = reinterpret_cast<R*>(r);
   a.mu = R(mu);
   a.partial = partial;
-  lateral_kernel<R, LAT_SOLVE_FWD><<<lateral_grid(p, p->m), kLatThreads, lat_smem<R>(p), st>>>(a);
+  { ProfScope ps_(p, PC_LAT_INV, st); lateral_kernel<R, LAT_SOLVE_FWD><<<lateral_grid(p, p->m), kLatThreads, lat_smem<R>(p), st>>>(a); }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
 }
@@ -337,7 +344,7 @@ int adjoint_solve_t(mbir_plan p, const void* r, const void* z1, void* z2, void* 
   int rc = launch_lateral<R, LAT_R2C_MASK>(p, r, p->wsA, nullptr, p->m, R(1) / R(p->nx), st);
   if (rc) return rc;
   RowArgs<R> ra = row_args<R>(p, p->wsA, p->wsB);
-  row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra);
+  { ProfScope ps_(p, PC_ROW_ADJ, st); row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra); }
   MBIR_LAUNCH_CHECK();
   LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, nullptr, p->nz, R(1));
   a.z1 = z1;
@@ -348,9 +355,9 @@ int adjoint_solve_t(mbir_plan p, const void* r, const void* z1, void* z2, void* 
   a.tau = R(tau);
   a.partial = partial;
   if (vout)
-    lateral_kernel<R, LAT_SOLVE_ADJ_V><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a);
+    { ProfScope ps_(p, PC_LAT_ADJ, st); lateral_kernel<R, LAT_SOLVE_ADJ_V><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a); }
   else
-    lateral_kernel<R, LAT_SOLVE_ADJ_L1><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a);
+    { ProfScope ps_(p, PC_LAT_ADJ, st); lateral_kernel<R, LAT_SOLVE_ADJ_L1><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a); }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
 }

@@ -286,11 +286,90 @@ static void daubechies8(double h[8]) {
   for (int a = 0; a < 8; ++a) h[a] = cr[a] * (M_SQRT2 / s);
 }
 
+const char* prof_class_name(int c) {
+  static const char* names[PC_COUNT] = {"lateral_forward", "row_forward", "lateral_inverse_real",
+                                        "lateral_residual", "row_adjoint", "lateral_adjoint",
+                                        "dwt_analysis", "dwt_synthesis", "soft_threshold", "reduce"};
+  return (c >= 0 && c < PC_COUNT) ? names[c] : "unknown";
+}
+
+void destroy_profiler(mbir_plan p) {
+  Profiler* pr = p->prof;
+  if (!pr) return;
+  for (int i = 0; i < 2 * pr->cap; ++i) cudaEventDestroy(pr->ev[i]);
+  delete[] pr->ev;
+  delete[] pr->cls;
+  delete pr;
+  p->prof = nullptr;
+}
+
 }  // namespace mbir
 
 using namespace mbir;
 
 extern "C" {
+
+int mbir_profile_begin(mbir_plan p, int32_t capacity) {
+  if (!p || capacity < 1 || capacity > (1 << 22)) return MBIR_ERR_INVALID;
+  destroy_profiler(p);
+  Profiler* pr = new (std::nothrow) Profiler;
+  if (!pr) return MBIR_ERR_OOM;
+  pr->ev = new (std::nothrow) cudaEvent_t[2 * (size_t)capacity];
+  pr->cls = new (std::nothrow) int[capacity];
+  if (!pr->ev || !pr->cls) {
+    delete[] pr->ev;
+    delete[] pr->cls;
+    delete pr;
+    return MBIR_ERR_OOM;
+  }
+  int made = 0;
+  for (; made < 2 * capacity; ++made) {
+    if (cudaEventCreate(&pr->ev[made]) != cudaSuccess) break;
+  }
+  if (made < 2 * capacity) {
+    for (int i = 0; i < made; ++i) cudaEventDestroy(pr->ev[i]);
+    delete[] pr->ev;
+    delete[] pr->cls;
+    delete pr;
+    return set_cuda_error(cudaGetLastError(), "cudaEventCreate");
+  }
+  pr->cap = capacity;
+  pr->n = 0;
+  p->prof = pr;
+  return MBIR_OK;
+}
+
+int mbir_profile_end(mbir_plan p, mbir_profile_entry* out, int32_t max_entries, int32_t* n_entries) {
+  if (!p || !p->prof) return MBIR_ERR_INVALID;
+  Profiler* pr = p->prof;
+  int64_t launches[PC_COUNT] = {0};
+  double total[PC_COUNT] = {0};
+  int rc = MBIR_OK;
+  for (int i = 0; i < pr->n; ++i) {
+    cudaError_t e = cudaEventSynchronize(pr->ev[2 * i + 1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr->ev[2 * i], pr->ev[2 * i + 1]);
+    if (e != cudaSuccess) {
+      rc = set_cuda_error(e, "profile events");
+      break;
+    }
+    launches[pr->cls[i]] += 1;
+    total[pr->cls[i]] += ms;
+  }
+  int n = 0;
+  for (int c = 0; c < PC_COUNT; ++c) {
+    if (!launches[c]) continue;
+    if (out && n < max_entries) {
+      out[n].name = prof_class_name(c);
+      out[n].launches = launches[c];
+      out[n].total_ms = total[c];
+    }
+    ++n;
+  }
+  if (n_entries) *n_entries = n;
+  destroy_profiler(p);
+  return rc;
+}
 
 const char* mbir_status_string(int s) {
   switch (s) {
@@ -313,6 +392,7 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaGetDevice(&cur);
   if (cur != p->device) cudaSetDevice(p->device);
   cudaDeviceSynchronize();
+  destroy_profiler(p);
   destroy_solve_state(p);
   cudaFree(p->tw_x);
   cudaFree(p->tw_k);

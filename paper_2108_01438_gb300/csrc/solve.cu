@@ -262,19 +262,19 @@ static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out,
   const int gb = grid_for(n);
   V* v = (V*)s->v;
   V* w = (V*)s->zA;
-  fill_hash_kernel<R><<<gb, kRedThreads, 0, st>>>(v, n);
-  dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->part_tmp);
-  power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal);
-  scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->scal);
+  { ProfScope ps_(p, PC_REDUCE, st); fill_hash_kernel<R><<<gb, kRedThreads, 0, st>>>(v, n); }
+  { ProfScope ps_(p, PC_REDUCE, st); dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->part_tmp); }
+  { ProfScope ps_(p, PC_REDUCE, st); power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal); }
+  { ProfScope ps_(p, PC_REDUCE, st); scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->scal); }
   MBIR_LAUNCH_CHECK();
   for (int it = 0; it < iters; ++it) {
     int rc = forward_impl(p, v, mask, s->r, st);
     if (rc) return rc;
     rc = adjoint_impl(p, s->r, mask, w, st);
     if (rc) return rc;
-    dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->part_tmp);
-    power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal);
-    scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->scal);
+    { ProfScope ps_(p, PC_REDUCE, st); dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->part_tmp); }
+    { ProfScope ps_(p, PC_REDUCE, st); power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal); }
+    { ProfScope ps_(p, PC_REDUCE, st); scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->scal); }
     MBIR_LAUNCH_CHECK();
   }
   MBIR_CUDA_TRY(cudaMemcpyAsync(out, s->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -298,8 +298,8 @@ static int lambda_scale_t(mbir_plan p, const void* y, const uint8_t* mask, int p
     src = (const V*)s->v;
   }
   const int gb = grid_for(n);
-  maxabs_kernel<R><<<gb, kRedThreads, 0, st>>>(src, n, s->part_tmp);
-  max_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal + 4);
+  { ProfScope ps_(p, PC_REDUCE, st); maxabs_kernel<R><<<gb, kRedThreads, 0, st>>>(src, n, s->part_tmp); }
+  { ProfScope ps_(p, PC_REDUCE, st); max_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal + 4); }
   MBIR_LAUNCH_CHECK();
   MBIR_CUDA_TRY(cudaMemcpyAsync(out, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
   MBIR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -312,7 +312,7 @@ static int reg_partials_t(mbir_plan p, int penalty, const void* z, cudaStream_t 
   SolveState* s = p->solve;
   if (penalty == MBIR_PENALTY_L1) {
     const int gb = lateral_grid(p, p->nz);
-    abs_sum_kernel<R><<<gb, kRedThreads, 0, st>>>((const cplx_t<R>*)z, s->nimg, s->part_reg);
+    { ProfScope ps_(p, PC_REDUCE, st); abs_sum_kernel<R><<<gb, kRedThreads, 0, st>>>((const cplx_t<R>*)z, s->nimg, s->part_reg); }
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }
@@ -375,8 +375,11 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
     const double m = k >= 2 ? mu[k - 2] : 0.0;
     int rc = forward_solve_impl(p, z1, mask, y, s->pz, s->r, m, s->part_data, st);
     if (rc) return rc;
-    combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_data, s->n_data, 0.5, s->part_reg, nreg, lam,
-                                              s->objtrace + (k - 1));
+    {
+      ProfScope ps_(p, PC_REDUCE, st);
+      combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_data, s->n_data, 0.5, s->part_reg, nreg, lam,
+                                                s->objtrace + (k - 1));
+    }
     MBIR_LAUNCH_CHECK();
     if (o->penalty == MBIR_PENALTY_L1) {
       rc = adjoint_solve_impl(p, s->r, z1, z2, nullptr, m, delta, tau, s->part_reg, st);
@@ -407,8 +410,8 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
     int rc = forward_impl(p, z1, mask, s->r, st);
     if (rc) return rc;
     const int gb = grid_for(s->nmeas);
-    resid_kernel<R><<<gb, kRedThreads, 0, st>>>((const R*)s->r, (const R*)y, mask, s->nmeas, s->part_tmp);
-    combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, 0.5, s->part_reg, nreg, lam, s->scal + 6);
+    { ProfScope ps_(p, PC_REDUCE, st); resid_kernel<R><<<gb, kRedThreads, 0, st>>>((const R*)s->r, (const R*)y, mask, s->nmeas, s->part_tmp); }
+    { ProfScope ps_(p, PC_REDUCE, st); combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, 0.5, s->part_reg, nreg, lam, s->scal + 6); }
     MBIR_LAUNCH_CHECK();
     double fin = 0.0;
     MBIR_CUDA_TRY(cudaMemcpyAsync(&fin, s->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -256,7 +256,7 @@ static int analysis_t(mbir_plan p, const void* in, void* coef, bool thresh, R ta
     a.thresh = thresh ? (lev == 2 ? 2 : 1) : 0;
     a.partial = thresh ? part : nullptr;
     dim3 grid((N / 2 + kFwdTB - 1) / kFwdTB, (P / 2 + kFwdTA - 1) / kFwdTA);
-    dwt_fwd_kernel<R><<<grid, kWavThreads, fwd_smem(sizeof(cplx_t<R>)), st>>>(a);
+    { ProfScope ps_(p, PC_DWT_FWD, st); dwt_fwd_kernel<R><<<grid, kWavThreads, fwd_smem(sizeof(cplx_t<R>)), st>>>(a); }
     MBIR_LAUNCH_CHECK();
     if (part) part += grid.x * grid.y;
     src = lls[lev];
@@ -289,7 +289,7 @@ static int synthesis_t(mbir_plan p, const void* coef, void* out, cudaStream_t st
     a.thresh = 0;
     a.partial = nullptr;
     dim3 grid((a.N + kInvTC - 1) / kInvTC, (a.P + kInvTR - 1) / kInvTR);
-    dwt_inv_kernel<R><<<grid, kWavThreads, inv_smem(sizeof(cplx_t<R>)), st>>>(a);
+    { ProfScope ps_(p, PC_DWT_INV, st); dwt_inv_kernel<R><<<grid, kWavThreads, inv_smem(sizeof(cplx_t<R>)), st>>>(a); }
     MBIR_LAUNCH_CHECK();
   }
   return MBIR_OK;
@@ -327,9 +327,9 @@ int prox_partial_impl(mbir_plan p, int penalty, const void* v, double tau, void*
   if (penalty == MBIR_PENALTY_L1) {
     const size_t n = (size_t)p->nx * p->nz;
     if (f64)
-      soft_kernel<double><<<kSoftGrid, 256, 0, st>>>((const double2*)v, (double2*)z, n, tau, partial);
+      { ProfScope ps_(p, PC_SOFT, st); soft_kernel<double><<<kSoftGrid, 256, 0, st>>>((const double2*)v, (double2*)z, n, tau, partial); }
     else
-      soft_kernel<float><<<kSoftGrid, 256, 0, st>>>((const float2*)v, (float2*)z, n, (float)tau, partial);
+      { ProfScope ps_(p, PC_SOFT, st); soft_kernel<float><<<kSoftGrid, 256, 0, st>>>((const float2*)v, (float2*)z, n, (float)tau, partial); }
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }

@@ -59,6 +59,10 @@ class SolveInfo(C.Structure):
     ]
 
 
+class ProfileEntry(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -74,6 +78,8 @@ _SIGNATURES = {
     "mbir_lipschitz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
     "mbir_prox": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "mbir_wavelet": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_profile_begin": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mbir_profile_end": (C.c_int, [C.c_void_p, C.POINTER(ProfileEntry), C.c_int32, C.POINTER(C.c_int32)]),
     "mbir_status_string": (C.c_char_p, [C.c_int]),
     "mbir_last_error": (C.c_char_p, []),
 }
@@ -228,6 +234,18 @@ class Plan:
         _check(lib().mbir_lipschitz(self._h, _ptr(mask), int(iters), C.byref(v), _stream_handle(stream)),
                "mbir_lipschitz")
         return v.value
+
+    def profile_begin(self, capacity: int = 1 << 16) -> None:
+        """Record a CUDA event pair around every later kernel launch on this plan."""
+        _check(lib().mbir_profile_begin(self._h, int(capacity)), "mbir_profile_begin")
+
+    def profile_end(self) -> dict:
+        """Stop recording; returns {kernel class: (launches, total_ms)}."""
+        buf = (ProfileEntry * 32)()
+        n = C.c_int32()
+        _check(lib().mbir_profile_end(self._h, buf, 32, C.byref(n)), "mbir_profile_end")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+                for i in range(min(n.value, 32))}
 
     def prox(self, v, tau: float, penalty: str = "l1", out=None, stream=None):
         import torch
