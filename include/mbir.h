@@ -212,6 +212,27 @@ int mbir_prox(mbir_plan plan, int32_t penalty, const void* v, double tau, void* 
 int mbir_wavelet(mbir_plan plan, int32_t inverse, const void* in, void* out, void* stream);
 
 /*
+ * mbir_wavelet without a plan and without allocating: for callers that cannot
+ * call cudaMalloc -- a real-time loop that must not allocate once running, an
+ * embedding that hands the library only pre-sized buffers, or a process whose
+ * device memory is owned by another allocator.  The paper has no counterpart;
+ * this is a deployment convenience.
+ *  nx, nz     image size; both divisible by 8 and >= 32, nx * nz <= 2^21
+ *             (2097152 pixels, e.g. 1024 x 2048).  Larger sizes return
+ *             MBIR_ERR_UNSUPPORTED_SIZE (see mbir_last_error).
+ *  inverse    0: analysis c = Psi x; 1: synthesis x = Psi^T c (layout as mbir_wavelet).
+ *  in, out    device [nx][nz] complex64, distinct, owned by the caller.
+ * Scratch: a file-scope device array of 5 MiB + 256 bytes (the filter taps and
+ * the level-1/2 low-low blocks) that every GPU loading the library holds until
+ * exit; nothing in it needs to start at zero, since a call writes every element it
+ * reads.  All calls on a device share it, so calls that overlap on the GPU (other
+ * streams, other threads) race: order them.  The first call on a device sets up
+ * (looks up the array's device address and uploads the taps, synchronously); make
+ * that first call before any stream capture.  Allocates nothing, ever.
+ */
+int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in, void* out, void* stream);
+
+/*
  * Kernel timing (tracing).  mbir_profile_begin makes every later launch on the plan
  * record a CUDA event pair on its stream (up to `capacity` launches; further
  * launches run unrecorded).  mbir_profile_end waits for the recorded events, fills

@@ -286,6 +286,8 @@ static void daubechies8(double h[8]) {
   for (int a = 0; a < 8; ++a) h[a] = cr[a] * (M_SQRT2 / s);
 }
 
+void daubechies8_taps(double h[8]) { daubechies8(h); }
+
 const char* prof_class_name(int c) {
   static const char* names[PC_COUNT] = {"lateral_forward", "row_forward", "lateral_inverse_real",
                                         "lateral_residual", "row_adjoint", "lateral_adjoint",

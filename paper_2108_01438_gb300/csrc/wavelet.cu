@@ -12,6 +12,9 @@
 // with g_t = (-1)^t h_{7-t}.  Synthesis is the transpose, written as a gather:
 // output index X receives from coefficient (X - t)/2 for the four t of X's parity.
 #include <math.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "common.cuh"
 
@@ -347,11 +350,81 @@ int prox_partial_impl(mbir_plan p, int penalty, const void* v, double tau, void*
   return synthesis_t<float>(p, p->wv_coef, z, st);
 }
 
+// ------------------------------------------------- allocation-free variant
+//
+// The wavelet transform without a plan, for callers that must not allocate
+// device memory at all (see mbir_wavelet_static in mbir.h).  Its scratch -- the
+// filter taps and the level-1 and level-2 low-low blocks -- lives in one
+// file-scope device array that every GPU loading the library keeps until exit.
+
+void daubechies8_taps(double h[8]);
+
+constexpr size_t kStaticMaxPixels = size_t(1) << 21;          // nx * nz limit
+constexpr size_t kStaticTapSlots = 32;                         // 256 bytes for the 8 taps
+constexpr size_t kStaticElems = kStaticTapSlots + kStaticMaxPixels / 4 + kStaticMaxPixels / 16;
+static __device__ __align__(256) float2 g_static_scratch[kStaticElems];
+
+constexpr int kStaticMaxDevices = 64;
+static std::mutex g_static_mutex;
+static float2* g_static_base[kStaticMaxDevices];   // device address of g_static_scratch, per device
+
+// Once per device, with that device current: the array's device address (its
+// name in host code is only a host-side stand-in) and the filter taps.
+static int static_scratch_setup(int dev, float2** base) {
+  if (dev < 0 || dev >= kStaticMaxDevices) return MBIR_ERR_UNSUPPORTED_SIZE;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_base[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaGetSymbolAddress(static wavelet scratch)");
+    double h[8];
+    daubechies8_taps(h);
+    float hf[8];
+    for (int i = 0; i < 8; ++i) hf[i] = (float)h[i];
+    e = cudaMemcpy(ptr, hf, sizeof(hf), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_cuda_error(e, "static wavelet taps upload");
+    g_static_base[dev] = static_cast<float2*>(ptr);
+  }
+  *base = g_static_base[dev];
+  return MBIR_OK;
+}
+
+int wavelet_static_impl(int nx, int nz, int inverse, const void* in, void* out, cudaStream_t st) {
+  if (!in || !out || in == out || nx <= 0 || nz <= 0) return MBIR_ERR_INVALID;
+  if (!wavelet_supported(nx, nz)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  if ((size_t)nx * (size_t)nz > kStaticMaxPixels) {
+    set_error_text("mbir_wavelet_static: nx * nz exceeds the static scratch limit of 2^21 pixels");
+    return MBIR_ERR_UNSUPPORTED_SIZE;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
+  float2* base = nullptr;
+  int rc = static_scratch_setup(dev, &base);
+  if (rc) return rc;
+  // a plan-shaped view onto the static scratch: no tables, no allocation
+  mbir_plan_s view;
+  memset(&view, 0, sizeof(view));
+  view.nx = nx;
+  view.nz = nz;
+  view.precision = MBIR_FP32;
+  view.device = dev;
+  view.h_db4f = reinterpret_cast<float*>(base);
+  view.wv_b1 = base + kStaticTapSlots;
+  view.wv_b2 = base + kStaticTapSlots + (size_t)nx * nz / 4;
+  return inverse ? synthesis_t<float>(&view, in, out, st)
+                 : analysis_t<float>(&view, in, out, false, 0.0f, nullptr, st);
+}
+
 }  // namespace mbir
 
 using namespace mbir;
 
 extern "C" {
+
+int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in, void* out, void* stream) {
+  return wavelet_static_impl(nx, nz, inverse, in, out, (cudaStream_t)stream);
+}
 
 int mbir_prox(mbir_plan p, int32_t penalty, const void* v, double tau, void* z, void* stream) {
   if (!p || !v || !z || !(tau >= 0) || !isfinite(tau)) return MBIR_ERR_INVALID;

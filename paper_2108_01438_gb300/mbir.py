@@ -78,6 +78,7 @@ _SIGNATURES = {
     "mbir_lipschitz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
     "mbir_prox": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "mbir_wavelet": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_wavelet_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_profile_begin": (C.c_int, [C.c_void_p, C.c_int32]),
     "mbir_profile_end": (C.c_int, [C.c_void_p, C.POINTER(ProfileEntry), C.c_int32, C.POINTER(C.c_int32)]),
     "mbir_status_string": (C.c_char_p, [C.c_int]),
