@@ -131,7 +131,8 @@ typedef struct {
  *  lipschitz         L used (0 when step was given).
  *  step, lambda_used the delta and the absolute lambda used.
  *  objective_trace   optional host array of trace_len doubles; entry k-1 receives
- *                    F(z^{k-1}) measured during iteration k (NULL: not recorded).
+ *                    F(z^{k-1}) measured during iteration k (NULL: not recorded; the
+ *                    per-iteration objective is then only reduced when rel_tol > 0).
  */
 typedef struct {
   int32_t iters;

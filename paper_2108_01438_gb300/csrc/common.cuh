@@ -40,13 +40,19 @@ template <bool INV, class V> __device__ __forceinline__ V mul_mj(V a) {
 // ------------------------------------------------------------------ plan
 
 constexpr int kMaxPasses = 16;
-constexpr int kKbRes = 1024;          // KB table samples per grid cell
 constexpr int kMaxFFT = 8192;         // largest transform length (K = 2 nz)
+constexpr int kMaxJ = 8;              // largest KB width
+constexpr int kKbDeg = 9;             // degree of the per-tap KB weight polynomials
 
 struct Radix {
   int n;                  // transform length
   int npass;
   int r[kMaxPasses];      // radix of each pass, in decimation-in-frequency order
+  int lg[kMaxPasses];     // log2 of each radix when pow2
+  int pow2;               // every radix a power of two
+  int log2n;
+  int tw_shift;           // twiddles: w^e = hi[e >> tw_shift] * lo[e & (tw_lo - 1)]
+  int tw_lo, tw_hi;       // table lengths
 };
 
 // One entry of the per-(|l~|, m) resampling table: integer grid cell of
@@ -93,13 +99,13 @@ struct mbir_plan_s {
   mbir::Radix rad_x, rad_k;
   int tile_c;                 // lateral FFT columns per CTA
   // device tables (one precision, per plan)
-  void* tw_x;                 // nx twiddles e^{-2 pi j i / nx}
-  void* tw_k;                 // K twiddles
+  void* tw_x;                 // nx-point twiddle tables [lo | hi]
+  void* tw_k;                 // K-point twiddle tables [lo | hi]
   int* perm_x;                // digit reversal of the nx-point transform
   int* perm_k;                // digit reversal of the K-point transform
   void* cdep;                 // [nz] falloff / KB deapodisation
   void* tab;                  // [nlh][m] TabF or TabD
-  float* kbtab;               // KB kernel samples (FP32 path)
+  float kbpoly[mbir::kMaxJ][mbir::kKbDeg + 1];   // FP32 KB weight polynomials per tap
   double* h_db4;              // 8 wavelet taps (device, double)
   float* h_db4f;              // same, float
   // workspace: two [nx][max(nz, m)] complex buffers

@@ -1,20 +1,23 @@
-// Shared-memory mixed-radix (2,3,4,5,7,8) in-place Cooley-Tukey FFT used by
+// Shared-memory mixed-radix (2,3,4,5,7,8,16) in-place Cooley-Tukey FFT used by
 // every transform of the operator: the lateral FFTs over A-scans (Eq. 4) and
 // the oversampled axial FFT inside the NUFFT (Sec. 2.1).
 //
 // Data: `batch` interleaved sequences of length N in shared memory, element i of
-// sequence b at s[i * batch + b].  With the radices R_1..R_P of the plan:
+// sequence b at s[sw(i) * batch + b], where sw is either the identity or, for
+// batch = 1 and N divisible by 16, the XOR swizzle i ^ ((i >> 4) & 15) that keeps
+// the unit-stride last passes free of bank conflicts.  With radices R_1..R_P:
 //   decimation in frequency (dif): natural-order input; pass p works on blocks of
 //     length L = N / (R_1 ... R_{p-1}): for j < M = L/R the R points
 //     j + r M of a block go through an R-point DFT, output q is multiplied by
 //     w_L^{q j}, and each point is written back where it was read.  The result
-//     X[k] ends at position digit_reverse(k) (see digit_reverse below).
+//     X[k] ends at position digit_reverse(k).
 //   decimation in time (dit): the transpose, input x[k] placed at
 //     digit_reverse(k), passes in reverse radix order, twiddles before the DFT,
 //     natural-order output.
 // Each butterfly owns its R slots, so threads run butterflies one at a time and
-// only a barrier between passes is needed.  The twiddle table holds
-// w_N^i = e^{-2 pi j i / N}; inverse transforms use its conjugate, unnormalised.
+// only a barrier between passes is needed.  Twiddles w_N^e = e^{-2 pi j e / N}
+// come from two small shared-memory tables, w_N^e = hi[e >> s] * lo[e & (2^s-1)];
+// inverse transforms use the conjugate and are unnormalised.
 #pragma once
 
 #include "common.cuh"
@@ -35,8 +38,40 @@ __host__ __device__ inline int digit_reverse(int k, const Radix& rad) {
   return pos;
 }
 
+// Same, by shifts, when every radix is a power of two (rad.pow2).
+__device__ __forceinline__ int digit_reverse_pow2(int k, const Radix& rad) {
+  int pos = 0, rem_bits = rad.log2n;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    if (p < rad.npass) {
+      const int b = rad.lg[p];
+      rem_bits -= b;
+      pos |= (k & ((1 << b) - 1)) << rem_bits;
+      k >>= b;
+    }
+  }
+#pragma unroll 1
+  for (int p = 4; p < rad.npass; ++p) {
+    const int b = rad.lg[p];
+    rem_bits -= b;
+    pos |= (k & ((1 << b) - 1)) << rem_bits;
+    k >>= b;
+  }
+  return pos;
+}
+
+template <class V>
+struct Tw2 {
+  const V* lo;   // w_N^i, i < 2^shift
+  const V* hi;   // w_N^{i 2^shift}
+  int shift, mask;
+  __device__ __forceinline__ V operator()(int e) const { return cmul(hi[e >> shift], lo[e & mask]); }
+};
+
+__device__ __forceinline__ int swz(int i, bool on) { return on ? (i ^ ((i >> 4) & 15)) : i; }
+
 template <int R, bool INV, class V>
-__device__ __forceinline__ void dft_small(V (&v)[R], const V* __restrict__ tw, int N) {
+__device__ __forceinline__ void dft_small(V (&v)[R], const Tw2<V>& tw, int N) {
   using S = decltype(V{}.x);
   if constexpr (R == 2) {
     V a = v[0], b = v[1];
@@ -66,8 +101,41 @@ __device__ __forceinline__ void dft_small(V (&v)[R], const V* __restrict__ tw, i
     v[1] = cadd(E1, O1w); v[5] = csub(E1, O1w);
     v[2] = cadd(E2, O2w); v[6] = csub(E2, O2w);
     v[3] = cadd(E3, O3w); v[7] = csub(E3, O3w);
+  } else if constexpr (R == 16) {
+    // 16 = 4 x 4: radix-4 DFTs over n1 of x[4 n1 + n2], twiddle w_16^{n2 k1},
+    // radix-4 DFTs over n2; output k1 + 4 k2
+    V y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      V a[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+      dft_small<4, INV>(a, tw, N);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = a[k1];
+    }
+    const S c1 = S(0.92387953251128675612818318939679);   // cos(pi/8)
+    const S s1 = S(0.38268343236508977172845998403040);   // sin(pi/8)
+    const S h = S(0.70710678118654752440084436210485);
+    // w_16^e for e = n2 k1 in {1, 2, 3, 4, 6, 9}; forward sign -, inverse +
+    const S sg = INV ? S(1) : S(-1);
+    auto rot = [&](V a, S c, S s) { return cmk<V>(a.x * c - a.y * s, a.x * s + a.y * c); };
+    y[1][1] = rot(y[1][1], c1, sg * s1);                 // e = 1
+    y[1][2] = rot(y[1][2], h, sg * h);                   // e = 2
+    y[1][3] = rot(y[1][3], s1, sg * c1);                 // e = 3
+    y[2][1] = rot(y[2][1], h, sg * h);                   // e = 2
+    y[2][2] = mul_mj<INV>(y[2][2]);                      // e = 4
+    y[2][3] = rot(y[2][3], -h, sg * h);                  // e = 6
+    y[3][1] = rot(y[3][1], s1, sg * c1);                 // e = 3
+    y[3][2] = rot(y[3][2], -h, sg * h);                  // e = 6
+    y[3][3] = rot(y[3][3], -c1, -sg * s1);               // e = 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      V a[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      dft_small<4, INV>(a, tw, N);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = a[k2];
+    }
   } else {
-    // direct R-point DFT, roots of unity taken from the N-point table
+    // direct R-point DFT, roots of unity from the N-point twiddles
     V out[R];
     const int stride = N / R;
 #pragma unroll
@@ -75,7 +143,7 @@ __device__ __forceinline__ void dft_small(V (&v)[R], const V* __restrict__ tw, i
       V acc = v[0];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        V w = tw[((r * q) % R) * stride];
+        V w = tw(((r * q) % R) * stride);
         if (INV) w = cconj(w);
         acc = cadd(acc, cmul(v[r], w));
       }
@@ -102,8 +170,8 @@ __device__ __forceinline__ int log2_if_pow2(int d) {
 }
 
 template <int R, bool INV, bool DIT, class V>
-__device__ __forceinline__ void ct_pass(V* s, int N, int batch, int bshift, int L,
-                                        const V* __restrict__ tw, int tid, int nthr) {
+__device__ __forceinline__ void ct_pass(V* s, int N, int batch, int bshift, int L, const Tw2<V>& tw,
+                                        bool sw, int tid, int nthr) {
   const int M = L / R;
   const int mshift = log2_if_pow2(M);
   const int nb = batch * (N / R);
@@ -115,11 +183,11 @@ __device__ __forceinline__ void ct_pass(V* s, int N, int batch, int bshift, int 
     const int base = blk * L + j;
     V v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[(base + r * M) * batch + b];
+    for (int r = 0; r < R; ++r) v[r] = s[swz(base + r * M, sw) * batch + b];
     if (DIT && j != 0) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        V w = tw[r * j * tstep];
+        V w = tw(r * j * tstep);
         if (INV) w = cconj(w);
         v[r] = cmul(v[r], w);
       }
@@ -128,27 +196,28 @@ __device__ __forceinline__ void ct_pass(V* s, int N, int batch, int bshift, int 
     if (!DIT && j != 0) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        V w = tw[q * j * tstep];
+        V w = tw(q * j * tstep);
         if (INV) w = cconj(w);
         v[q] = cmul(v[q], w);
       }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) s[(base + r * M) * batch + b] = v[r];
+    for (int r = 0; r < R; ++r) s[swz(base + r * M, sw) * batch + b] = v[r];
   }
   __syncthreads();
 }
 
 template <bool INV, bool DIT, class V>
 __device__ __forceinline__ void ct_dispatch(int R, V* s, int N, int batch, int bshift, int L,
-                                            const V* __restrict__ tw, int tid, int nthr) {
+                                            const Tw2<V>& tw, bool sw, int tid, int nthr) {
   switch (R) {
-    case 8: ct_pass<8, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 4: ct_pass<4, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 2: ct_pass<2, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 3: ct_pass<3, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 5: ct_pass<5, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 7: ct_pass<7, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 16: ct_pass<16, INV, DIT>(s, N, batch, bshift, L, tw, sw, tid, nthr); break;
+    case 8: ct_pass<8, INV, DIT>(s, N, batch, bshift, L, tw, sw, tid, nthr); break;
+    case 4: ct_pass<4, INV, DIT>(s, N, batch, bshift, L, tw, sw, tid, nthr); break;
+    case 2: ct_pass<2, INV, DIT>(s, N, batch, bshift, L, tw, sw, tid, nthr); break;
+    case 3: ct_pass<3, INV, DIT>(s, N, batch, bshift, L, tw, sw, tid, nthr); break;
+    case 5: ct_pass<5, INV, DIT>(s, N, batch, bshift, L, tw, sw, tid, nthr); break;
+    case 7: ct_pass<7, INV, DIT>(s, N, batch, bshift, L, tw, sw, tid, nthr); break;
     default: break;
   }
 }
@@ -156,28 +225,42 @@ __device__ __forceinline__ void ct_dispatch(int R, V* s, int N, int batch, int b
 // Decimation in frequency: natural order in, digit-reversed order out.
 // Caller must __syncthreads() between filling s and this call.
 template <bool INV, class V>
-__device__ void fft_dif(V* s, int batch, const Radix& rad, const V* __restrict__ tw) {
+__device__ void fft_dif(V* s, int batch, const Radix& rad, const Tw2<V>& tw, bool sw) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int bshift = log2_if_pow2(batch);
   int L = rad.n;
   for (int p = 0; p < rad.npass; ++p) {
     const int R = rad.r[p];
-    ct_dispatch<INV, false>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
+    ct_dispatch<INV, false>(R, s, rad.n, batch, bshift, L, tw, sw, tid, nthr);
     L /= R;
   }
 }
 
 // Decimation in time: digit-reversed order in, natural order out.
 template <bool INV, class V>
-__device__ void fft_dit(V* s, int batch, const Radix& rad, const V* __restrict__ tw) {
+__device__ void fft_dit(V* s, int batch, const Radix& rad, const Tw2<V>& tw, bool sw) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int bshift = log2_if_pow2(batch);
   int L = 1;
   for (int p = rad.npass - 1; p >= 0; --p) {
     const int R = rad.r[p];
     L *= R;
-    ct_dispatch<INV, true>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
+    ct_dispatch<INV, true>(R, s, rad.n, batch, bshift, L, tw, sw, tid, nthr);
   }
+}
+
+// Copy the two twiddle tables of a transform (tw2 = [lo | hi] in global memory)
+// into shared memory and return the accessor.  No barrier inside.
+template <class V>
+__device__ __forceinline__ Tw2<V> load_twiddles(V* smem, const V* __restrict__ g, const Radix& rad) {
+  const int n = rad.tw_lo + rad.tw_hi;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) smem[i] = g[i];
+  Tw2<V> t;
+  t.lo = smem;
+  t.hi = smem + rad.tw_lo;
+  t.shift = rad.tw_shift;
+  t.mask = rad.tw_lo - 1;
+  return t;
 }
 
 }  // namespace mbir

@@ -12,14 +12,14 @@
 //
 // Lateral stages work on tiles of TC adjacent columns with all nx rows staged in
 // shared memory; row stages give one CTA per lateral frequency l and keep the
-// K-point row (K = 2 nz) in shared memory.
+// K-point row (K = 2 nz) in shared memory.  FP32 KB weights come from per-tap
+// degree-9 polynomials in the fractional grid position (fitted in FP64 per plan);
+// FP64 plans evaluate the Bessel function directly.
 #include "common.cuh"
 #include "fft.cuh"
 #include "operator.cuh"
 
 namespace mbir {
-
-// --------------------------------------------------------------- lateral FFT
 
 // Deterministic block sum of one double per thread (fixed shuffle tree).
 __device__ __forceinline__ double block_sum(double v) {
@@ -39,71 +39,145 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;   // valid in thread 0
 }
 
+// --------------------------------------------------------------- lateral FFT
+
+// Load element (p, c) of the lateral input as complex.
 template <class R, int MODE>
-__global__ void __launch_bounds__(kLatThreads)
+__device__ __forceinline__ cplx_t<R> lat_load(const LatArgs<R>& a, size_t off) {
+  using V = cplx_t<R>;
+  if constexpr (MODE == LAT_R2C_MASK) {
+    const R r = reinterpret_cast<const R*>(a.in)[off];
+    return cmk<V>((a.mask == nullptr || a.mask[off]) ? r : R(0), R(0));
+  } else {
+    return reinterpret_cast<const V*>(a.in)[off];
+  }
+}
+
+// Operands an epilogue reads besides the transform output, fetched ahead of use
+// so that several elements' loads are in flight at once.
+template <class R>
+struct EpOps {
+  R y, prev;
+  cplx_t<R> z1, z2;
+  bool meas;
+};
+
+template <class R, int MODE>
+__device__ __forceinline__ EpOps<R> lat_prefetch(const LatArgs<R>& a, size_t off) {
+  using V = cplx_t<R>;
+  EpOps<R> o;
+  if constexpr (MODE == LAT_C2R_INV_MASK) {
+    o.meas = (a.mask == nullptr || a.mask[off]);
+  } else if constexpr (MODE == LAT_SOLVE_FWD) {
+    o.meas = (a.mask == nullptr || a.mask[off]);
+    o.y = a.y[off];
+    o.prev = a.pz[off];
+  } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
+    o.z1 = reinterpret_cast<const V*>(a.z1)[off];
+    o.z2 = reinterpret_cast<const V*>(a.z2)[off];
+  }
+  return o;
+}
+
+template <class R, int MODE>
+__device__ __forceinline__ void lat_store(const LatArgs<R>& a, size_t off, cplx_t<R> v, const EpOps<R>& o,
+                                          double& part) {
+  using V = cplx_t<R>;
+  if constexpr (MODE == LAT_C2R_INV_MASK) {
+    reinterpret_cast<R*>(a.out)[off] = o.meas ? v.x * a.scale : R(0);
+  } else if constexpr (MODE == LAT_SOLVE_FWD) {
+    const R pz = o.meas ? v.x * a.scale : R(0);
+    const R yv = o.meas ? o.y : R(0);
+    const R d = pz - yv;
+    part += double(d) * double(d);
+    a.pz[off] = pz;
+    a.r[off] = (R(1) + a.mu) * pz - a.mu * o.prev - yv;
+  } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
+    V xv;
+    xv.x = o.z1.x + a.mu * (o.z1.x - o.z2.x) - a.delta * v.x;
+    xv.y = o.z1.y + a.mu * (o.z1.y - o.z2.y) - a.delta * v.y;
+    if constexpr (MODE == LAT_SOLVE_ADJ_L1) {
+      const R mag = sqrt(xv.x * xv.x + xv.y * xv.y);
+      const R sh = mag > a.tau ? R(1) - a.tau / mag : R(0);
+      xv.x *= sh;
+      xv.y *= sh;
+      part += mag > a.tau ? double(mag - a.tau) : 0.0;
+      reinterpret_cast<V*>(a.z2)[off] = xv;
+    } else {
+      reinterpret_cast<V*>(a.vout)[off] = xv;
+    }
+  } else {
+    reinterpret_cast<V*>(a.out)[off] = cscale(v, a.scale);
+  }
+}
+
+template <class R, int MODE>
+__global__ void __launch_bounds__(kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
 lateral_kernel(LatArgs<R> a) {
   using V = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s = reinterpret_cast<V*>(smem_raw);
+  V* tws = s + a.nx * a.tc;
   const int TC = a.tc, nx = a.nx, C = a.cols;
   const int c0 = blockIdx.x * TC;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int total = nx * TC;
-  for (int e = tid; e < total; e += nthr) {
-    const int p = e / TC, b = e - p * TC;
-    const int c = c0 + b;
-    V v = cmk<V>(R(0), R(0));
-    if (c < C) {
-      const size_t off = (size_t)p * C + c;
-      if constexpr (MODE == LAT_R2C_MASK) {
-        const R r = reinterpret_cast<const R*>(a.in)[off];
-        v.x = (a.mask == nullptr || a.mask[off]) ? r : R(0);
-      } else {
-        v = reinterpret_cast<const V*>(a.in)[off];
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
+  // stage the tile: column pairs (b, b+1), four pairs in flight per thread
+  const int half = TC >> 1;
+  const int npairs = nx * half;
+  constexpr int U = 4;
+  for (int e0 = tid; e0 < npairs; e0 += U * nthr) {
+    V va[U], vb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nthr;
+      va[u] = vb[u] = cmk<V>(R(0), R(0));
+      if (e < npairs) {
+        const int p = e / half, b = 2 * (e - p * half);
+        const int c = c0 + b;
+        const size_t off = (size_t)p * C + c;
+        if (c < C) va[u] = lat_load<R, MODE>(a, off);
+        if (c + 1 < C) vb[u] = lat_load<R, MODE>(a, off + 1);
       }
     }
-    s[p * TC + b] = v;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nthr;
+      if (e < npairs) {
+        const int p = e / half, b = 2 * (e - p * half);
+        s[p * TC + b] = va[u];
+        s[p * TC + b + 1] = vb[u];
+      }
+    }
   }
   __syncthreads();
   constexpr bool INV = (MODE != LAT_C2C_FWD && MODE != LAT_R2C_MASK);
-  fft_dif<INV>(s, TC, a.rad, reinterpret_cast<const V*>(a.tw));
+  fft_dif<INV>(s, TC, a.rad, tw, false);
   double part = 0.0;
-  for (int e = tid; e < total; e += nthr) {
-    const int p = e / TC, b = e - p * TC;
-    const int c = c0 + b;
-    if (c >= C) continue;
-    const size_t off = (size_t)p * C + c;
-    const V v = s[a.perm[p] * TC + b];
-    if constexpr (MODE == LAT_C2R_INV_MASK) {
-      const R r = v.x * a.scale;
-      reinterpret_cast<R*>(a.out)[off] = (a.mask == nullptr || a.mask[off]) ? r : R(0);
-    } else if constexpr (MODE == LAT_SOLVE_FWD) {
-      const bool meas = (a.mask == nullptr || a.mask[off]);
-      const R pz = meas ? v.x * a.scale : R(0);
-      const R yv = meas ? a.y[off] : R(0);
-      const R prev = a.pz[off];
-      const R d = pz - yv;
-      part += double(d) * double(d);
-      a.pz[off] = pz;
-      a.r[off] = (R(1) + a.mu) * pz - a.mu * prev - yv;
-    } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
-      const V z1 = reinterpret_cast<const V*>(a.z1)[off];
-      const V z2 = reinterpret_cast<const V*>(a.z2)[off];
-      V xv;
-      xv.x = z1.x + a.mu * (z1.x - z2.x) - a.delta * v.x;
-      xv.y = z1.y + a.mu * (z1.y - z2.y) - a.delta * v.y;
-      if constexpr (MODE == LAT_SOLVE_ADJ_L1) {
-        const R mag = sqrt(xv.x * xv.x + xv.y * xv.y);
-        const R sh = mag > a.tau ? R(1) - a.tau / mag : R(0);
-        xv.x *= sh;
-        xv.y *= sh;
-        part += mag > a.tau ? double(mag - a.tau) : 0.0;
-        reinterpret_cast<V*>(a.z2)[off] = xv;
-      } else {
-        reinterpret_cast<V*>(a.vout)[off] = xv;
+  for (int e0 = tid; e0 < npairs; e0 += U * nthr) {
+    EpOps<R> oa[U], ob[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nthr;
+      if (e < npairs) {
+        const int p = e / half, b = 2 * (e - p * half);
+        const int c = c0 + b;
+        const size_t off = (size_t)p * C + c;
+        if (c < C) oa[u] = lat_prefetch<R, MODE>(a, off);
+        if (c + 1 < C) ob[u] = lat_prefetch<R, MODE>(a, off + 1);
       }
-    } else {
-      reinterpret_cast<V*>(a.out)[off] = cscale(v, a.scale);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nthr;
+      if (e < npairs) {
+        const int p = e / half, b = 2 * (e - p * half);
+        const int c = c0 + b;
+        const size_t off = (size_t)p * C + c;
+        const int src = a.perm[p] * TC + b;
+        if (c < C) lat_store<R, MODE>(a, off, s[src], oa[u], part);
+        if (c + 1 < C) lat_store<R, MODE>(a, off + 1, s[src + 1], ob[u], part);
+      }
     }
   }
   if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_ADJ_L1) {
@@ -114,116 +188,175 @@ lateral_kernel(LatArgs<R> a) {
 
 // ------------------------------------------------------------- KB weights
 
-template <class R>
-__device__ __forceinline__ R kb_weight(R u, const float* kb, int J, R alpha, R inv_i0a) {
-  const R au = u < R(0) ? -u : u;
+// Weights of the J taps at fractional grid position frac (tap j at offset
+// J/2 - 1 - j + frac from the point).
+template <class R, int J>
+__device__ __forceinline__ void kb_weights(R frac, const RowArgs<R>& a, R (&w)[J]) {
   if constexpr (sizeof(R) == 4) {
-    const float x = au * float(kKbRes);
-    const int i = (int)x;
-    const float f = x - float(i);
-    const float a0 = kb[i], a1 = kb[i + 1];
-    return fmaf(f, a1 - a0, a0);
+    const float x = frac - 0.5f;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      float acc = a.kbpoly[j][kKbDeg];
+#pragma unroll
+      for (int d = kKbDeg - 1; d >= 0; --d) acc = fmaf(acc, x, a.kbpoly[j][d]);
+      w[j] = acc;
+    }
   } else {
-    const double r = 1.0 - (2.0 * au / J) * (2.0 * au / J);
-    if (r < 0.0) return 0.0;
-    return cyl_bessel_i0(alpha * sqrt(r)) * inv_i0a;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const double u = frac + double(J / 2 - 1 - j);
+      const double r = 1.0 - (2.0 * u / J) * (2.0 * u / J);
+      w[j] = r < 0.0 ? 0.0 : cyl_bessel_i0(a.alpha * sqrt(r)) * a.inv_i0a;
+    }
   }
+}
+
+template <class R>
+__device__ __forceinline__ int row_pos(int i, const RowArgs<R>& a) {
+  return a.rad.pow2 ? digit_reverse_pow2(i, a.rad) : a.perm[i];
 }
 
 // --------------------------------------------------------- row kernels (NUFFT)
 
-template <class R>
-__global__ void __launch_bounds__(kRowThreads)
+template <class R, int J>
+__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
 row_forward_kernel(RowArgs<R> a) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
-  float* kb = reinterpret_cast<float*>(buf + a.K);
+  V* tws = buf + a.K;
   const int l = blockIdx.x;
   const int lp = l <= a.nx - l ? l : a.nx - l;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int K = a.K, nz = a.nz, n0 = a.n0, J = a.J, M = a.m;
-  if (sizeof(R) == 4)
-    for (int i = tid; i < a.nkb; i += nthr) kb[i] = a.kbtab[i];
+  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  const bool sw = (K & 15) == 0;
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
   const V* X = reinterpret_cast<const V*>(a.in) + (size_t)l * nz;
   const R* cdep = reinterpret_cast<const R*>(a.cdep);
   // centred zero-padded row, element i = (n - n0) mod K holding c_n X[l][n],
-  // stored digit-reversed for the decimation-in-time transform
-  for (int i = tid; i < K; i += nthr) {
-    int n = i + n0;
-    if (n >= K) n -= K;
-    buf[a.perm[i]] = (n < nz) ? cscale(X[n], cdep[n]) : cmk<V>(R(0), R(0));
+  // placed digit-reversed for the decimation-in-time transform
+  constexpr int U = 4;
+  for (int i0 = tid; i0 < K; i0 += U * nthr) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      int n = i + n0;
+      if (n >= K) n -= K;
+      v[u] = (i < K && n < nz) ? cscale(X[n], cdep[n]) : cmk<V>(R(0), R(0));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      if (i < K) buf[swz(row_pos(i, a), sw)] = v[u];
+    }
   }
   __syncthreads();
-  fft_dit<false>(buf, 1, a.rad, reinterpret_cast<const V*>(a.tw));
+  fft_dit<false>(buf, 1, a.rad, tw, sw);
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
   V* S = reinterpret_cast<V*>(a.out) + (size_t)l * M;
-  const int h = J / 2;
-  for (int mm = tid; mm < M; mm += nthr) {
-    const Tab e = tab[mm];
-    V acc = cmk<V>(R(0), R(0));
-    for (int j = 0; j < J; ++j) {
-      const R u = R(e.frac) + R(h - 1 - j);
-      const R w = kb_weight<R>(u, kb, J, R(a.alpha), R(a.inv_i0a));
-      int idx = e.i0 - h + 1 + j;
-      if (idx < 0) idx += K;
-      if (idx >= K) idx -= K;
-      const V b = buf[idx];
-      acc.x += w * b.x;
-      acc.y += w * b.y;
+  constexpr int h = J / 2;
+  constexpr int UM = 2;
+  for (int m0 = tid; m0 < M; m0 += UM * nthr) {
+    Tab e[UM];
+#pragma unroll
+    for (int u = 0; u < UM; ++u) {
+      const int mm = m0 + u * nthr;
+      if (mm < M) e[u] = tab[mm];
     }
-    S[mm] = cmul(acc, cmk<V>(R(e.fre), R(e.fim)));
+#pragma unroll
+    for (int u = 0; u < UM; ++u) {
+      const int mm = m0 + u * nthr;
+      if (mm >= M) continue;
+      R w[J];
+      kb_weights<R, J>(R(e[u].frac), a, w);
+      V acc = cmk<V>(R(0), R(0));
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        int idx = e[u].i0 - h + 1 + j;
+        if (idx < 0) idx += K;
+        if (idx >= K) idx -= K;
+        const V b = buf[swz(idx, sw)];
+        acc.x += w[j] * b.x;
+        acc.y += w[j] * b.y;
+      }
+      S[mm] = cmul(acc, cmk<V>(R(e[u].fre), R(e[u].fim)));
+    }
   }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kRowThreads)
+template <class R, int J>
+__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
 row_adjoint_kernel(RowArgs<R> a) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
-  float* kb = reinterpret_cast<float*>(buf + a.K);
+  V* tws = buf + a.K;
   const int l = blockIdx.x;
   const int lp = l <= a.nx - l ? l : a.nx - l;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int K = a.K, nz = a.nz, n0 = a.n0, J = a.J, M = a.m;
-  if (sizeof(R) == 4)
-    for (int i = tid; i < a.nkb; i += nthr) kb[i] = a.kbtab[i];
+  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  const bool sw = (K & 15) == 0;
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
   for (int i = tid; i < K; i += nthr) buf[i] = cmk<V>(R(0), R(0));
   __syncthreads();
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
   const V* Rh = reinterpret_cast<const V*>(a.in) + (size_t)l * M;
-  const int h = J / 2;
+  constexpr int h = J / 2;
   R* bufr = reinterpret_cast<R*>(buf);
-  for (int mm = tid; mm < M; mm += nthr) {
-    const Tab e = tab[mm];
-    const V v = cmulc(Rh[mm], cmk<V>(R(e.fre), R(e.fim)));
-    for (int j = 0; j < J; ++j) {
-      const R u = R(e.frac) + R(h - 1 - j);
-      const R w = kb_weight<R>(u, kb, J, R(a.alpha), R(a.inv_i0a));
-      int idx = e.i0 - h + 1 + j;
-      if (idx < 0) idx += K;
-      if (idx >= K) idx -= K;
-      atomicAdd(&bufr[2 * idx], w * v.x);
-      atomicAdd(&bufr[2 * idx + 1], w * v.y);
+  constexpr int UM = 2;
+  for (int m0 = tid; m0 < M; m0 += UM * nthr) {
+    Tab e[UM];
+    V r[UM];
+#pragma unroll
+    for (int u = 0; u < UM; ++u) {
+      const int mm = m0 + u * nthr;
+      if (mm < M) {
+        e[u] = tab[mm];
+        r[u] = Rh[mm];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UM; ++u) {
+      const int mm = m0 + u * nthr;
+      if (mm >= M) continue;
+      const V v = cmulc(r[u], cmk<V>(R(e[u].fre), R(e[u].fim)));
+      R w[J];
+      kb_weights<R, J>(R(e[u].frac), a, w);
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        int idx = e[u].i0 - h + 1 + j;
+        if (idx < 0) idx += K;
+        if (idx >= K) idx -= K;
+        const int q = swz(idx, sw);
+        atomicAdd(&bufr[2 * q], w[j] * v.x);
+        atomicAdd(&bufr[2 * q + 1], w[j] * v.y);
+      }
     }
   }
   __syncthreads();
-  fft_dif<true>(buf, 1, a.rad, reinterpret_cast<const V*>(a.tw));
+  fft_dif<true>(buf, 1, a.rad, tw, sw);
   const R* cdep = reinterpret_cast<const R*>(a.cdep);
   V* Wo = reinterpret_cast<V*>(a.out) + (size_t)l * nz;
   for (int n = tid; n < nz; n += nthr) {
     int i = n - n0;
     if (i < 0) i += K;
-    Wo[n] = cscale(buf[a.perm[i]], cdep[n]);
+    Wo[n] = cscale(buf[swz(row_pos(i, a), sw)], cdep[n]);
   }
 }
 
 // ------------------------------------------------------------------ launch
 
-int lateral_grid(mbir_plan p, int cols);
+int lateral_grid(mbir_plan p, int cols) { return (cols + p->tile_c - 1) / p->tile_c; }
+
+constexpr int lat_class(int mode) {
+  return mode == LAT_C2C_FWD ? PC_LAT_FWD
+         : mode == LAT_R2C_MASK ? PC_LAT_R2C
+         : (mode == LAT_C2R_INV_MASK || mode == LAT_SOLVE_FWD) ? PC_LAT_INV
+                                                               : PC_LAT_ADJ;
+}
 
 template <class R>
 LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, R scale) {
@@ -249,25 +382,25 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
   return a;
 }
 
-constexpr int lat_class(int mode) {
-  return mode == LAT_C2C_FWD ? PC_LAT_FWD
-         : mode == LAT_R2C_MASK ? PC_LAT_R2C
-         : (mode == LAT_C2R_INV_MASK || mode == LAT_SOLVE_FWD) ? PC_LAT_INV
-                                                               : PC_LAT_ADJ;
-}
-
 template <class R>
 size_t lat_smem(mbir_plan p) {
-  return sizeof(cplx_t<R>) * p->nx * p->tile_c;
+  return sizeof(cplx_t<R>) * ((size_t)p->nx * p->tile_c + p->rad_x.tw_lo + p->rad_x.tw_hi);
+}
+
+template <class R, int MODE>
+int launch_lateral_args(mbir_plan p, const LatArgs<R>& a, int cols, cudaStream_t st) {
+  {
+    ProfScope ps_(p, lat_class(MODE), st);
+    lateral_kernel<R, MODE><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a);
+  }
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
 }
 
 template <class R, int MODE>
 int launch_lateral(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, R scale,
                    cudaStream_t st) {
-  LatArgs<R> a = lat_args<R>(p, in, out, mask, cols, scale);
-  { ProfScope ps_(p, lat_class(MODE), st); lateral_kernel<R, MODE><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a); }
-  MBIR_LAUNCH_CHECK();
-  return MBIR_OK;
+  return launch_lateral_args<R, MODE>(p, lat_args<R>(p, in, out, mask, cols, scale), cols, st);
 }
 
 template <class R>
@@ -277,34 +410,57 @@ RowArgs<R> row_args(mbir_plan p, const void* in, void* out) {
   a.out = out;
   a.tab = p->tab;
   a.cdep = p->cdep;
-  a.kbtab = p->kbtab;
   a.tw = p->tw_k;
-  a.rad = p->rad_k;
   a.perm = p->perm_k;
+  a.rad = p->rad_k;
   a.nx = p->nx;
   a.nz = p->nz;
   a.m = p->m;
   a.K = p->K;
-  a.J = p->J;
   a.n0 = p->n0;
-  a.nkb = kKbRes * p->J / 2 + 2;
   a.alpha = p->alpha;
   a.inv_i0a = 1.0 / host_bessel_i0(p->alpha);
+  for (int j = 0; j < kMaxJ; ++j)
+    for (int d = 0; d <= kKbDeg; ++d) a.kbpoly[j][d] = p->kbpoly[j][d];
   return a;
 }
 
 template <class R>
 size_t row_smem(mbir_plan p) {
-  return sizeof(cplx_t<R>) * p->K + sizeof(float) * (kKbRes * p->J / 2 + 2);
+  return sizeof(cplx_t<R>) * ((size_t)p->K + p->rad_k.tw_lo + p->rad_k.tw_hi);
+}
+
+template <class R>
+int launch_row(mbir_plan p, bool adjoint, const void* in, void* out, cudaStream_t st) {
+  RowArgs<R> a = row_args<R>(p, in, out);
+  const size_t smem = row_smem<R>(p);
+  {
+    ProfScope ps_(p, adjoint ? PC_ROW_ADJ : PC_ROW_FWD, st);
+    switch (p->J) {
+      case 4:
+        if (adjoint) row_adjoint_kernel<R, 4><<<p->nx, kRowThreads, smem, st>>>(a);
+        else row_forward_kernel<R, 4><<<p->nx, kRowThreads, smem, st>>>(a);
+        break;
+      case 6:
+        if (adjoint) row_adjoint_kernel<R, 6><<<p->nx, kRowThreads, smem, st>>>(a);
+        else row_forward_kernel<R, 6><<<p->nx, kRowThreads, smem, st>>>(a);
+        break;
+      default:
+        if (adjoint) row_adjoint_kernel<R, 8><<<p->nx, kRowThreads, smem, st>>>(a);
+        else row_forward_kernel<R, 8><<<p->nx, kRowThreads, smem, st>>>(a);
+        break;
+    }
+  }
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
 }
 
 template <class R>
 int forward_t(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
   int rc = launch_lateral<R, LAT_C2C_FWD>(p, x, p->wsA, nullptr, p->nz, R(1), st);
   if (rc) return rc;
-  RowArgs<R> a = row_args<R>(p, p->wsA, p->wsB);
-  { ProfScope ps_(p, PC_ROW_FWD, st); row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a); }
-  MBIR_LAUNCH_CHECK();
+  rc = launch_row<R>(p, false, p->wsA, p->wsB, st);
+  if (rc) return rc;
   return launch_lateral<R, LAT_C2R_INV_MASK>(p, p->wsB, y, mask, p->m, R(1) / R(p->nx), st);
 }
 
@@ -312,9 +468,8 @@ template <class R>
 int adjoint_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
   int rc = launch_lateral<R, LAT_R2C_MASK>(p, y, p->wsA, mask, p->m, R(1) / R(p->nx), st);
   if (rc) return rc;
-  RowArgs<R> a = row_args<R>(p, p->wsA, p->wsB);
-  { ProfScope ps_(p, PC_ROW_ADJ, st); row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(a); }
-  MBIR_LAUNCH_CHECK();
+  rc = launch_row<R>(p, true, p->wsA, p->wsB, st);
+  if (rc) return rc;
   return launch_lateral<R, LAT_C2C_INV>(p, p->wsB, x, nullptr, p->nz, R(1), st);
 }
 
@@ -323,18 +478,15 @@ int forward_solve_t(mbir_plan p, const void* z1, const uint8_t* mask, const void
                     double mu, double* partial, cudaStream_t st) {
   int rc = launch_lateral<R, LAT_C2C_FWD>(p, z1, p->wsA, nullptr, p->nz, R(1), st);
   if (rc) return rc;
-  RowArgs<R> ra = row_args<R>(p, p->wsA, p->wsB);
-  { ProfScope ps_(p, PC_ROW_FWD, st); row_forward_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra); }
-  MBIR_LAUNCH_CHECK();
+  rc = launch_row<R>(p, false, p->wsA, p->wsB, st);
+  if (rc) return rc;
   LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, mask, p->m, R(1) / R(p->nx));
   a.y = reinterpret_cast<const R*>(y);
   a.pz = reinterpret_cast<R*>(pz);
   a.r = reinterpret_cast<R*>(r);
   a.mu = R(mu);
   a.partial = partial;
-  { ProfScope ps_(p, PC_LAT_INV, st); lateral_kernel<R, LAT_SOLVE_FWD><<<lateral_grid(p, p->m), kLatThreads, lat_smem<R>(p), st>>>(a); }
-  MBIR_LAUNCH_CHECK();
-  return MBIR_OK;
+  return launch_lateral_args<R, LAT_SOLVE_FWD>(p, a, p->m, st);
 }
 
 template <class R>
@@ -343,9 +495,8 @@ int adjoint_solve_t(mbir_plan p, const void* r, const void* z1, void* z2, void* 
   // r is already zero where the mask is zero
   int rc = launch_lateral<R, LAT_R2C_MASK>(p, r, p->wsA, nullptr, p->m, R(1) / R(p->nx), st);
   if (rc) return rc;
-  RowArgs<R> ra = row_args<R>(p, p->wsA, p->wsB);
-  { ProfScope ps_(p, PC_ROW_ADJ, st); row_adjoint_kernel<R><<<p->nx, kRowThreads, row_smem<R>(p), st>>>(ra); }
-  MBIR_LAUNCH_CHECK();
+  rc = launch_row<R>(p, true, p->wsA, p->wsB, st);
+  if (rc) return rc;
   LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, nullptr, p->nz, R(1));
   a.z1 = z1;
   a.z2 = z2;
@@ -354,12 +505,18 @@ int adjoint_solve_t(mbir_plan p, const void* r, const void* z1, void* z2, void* 
   a.delta = R(delta);
   a.tau = R(tau);
   a.partial = partial;
-  if (vout)
-    { ProfScope ps_(p, PC_LAT_ADJ, st); lateral_kernel<R, LAT_SOLVE_ADJ_V><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a); }
-  else
-    { ProfScope ps_(p, PC_LAT_ADJ, st); lateral_kernel<R, LAT_SOLVE_ADJ_L1><<<lateral_grid(p, p->nz), kLatThreads, lat_smem<R>(p), st>>>(a); }
-  MBIR_LAUNCH_CHECK();
-  return MBIR_OK;
+  if (vout) return launch_lateral_args<R, LAT_SOLVE_ADJ_V>(p, a, p->nz, st);
+  return launch_lateral_args<R, LAT_SOLVE_ADJ_L1>(p, a, p->nz, st);
+}
+
+int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? forward_t<double>(p, x, mask, y, st)
+                                   : forward_t<float>(p, x, mask, y, st);
+}
+
+int adjoint_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? adjoint_t<double>(p, y, mask, x, st)
+                                   : adjoint_t<float>(p, y, mask, x, st);
 }
 
 int forward_solve_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
@@ -375,36 +532,32 @@ int adjoint_solve_impl(mbir_plan p, const void* r, const void* z1, void* z2, voi
              : adjoint_solve_t<float>(p, r, z1, z2, vout, mu, delta, tau, partial, st);
 }
 
-int lateral_grid(mbir_plan p, int cols) { return (cols + p->tile_c - 1) / p->tile_c; }
-
-int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
-  return p->precision == MBIR_FP64 ? forward_t<double>(p, x, mask, y, st)
-                                   : forward_t<float>(p, x, mask, y, st);
-}
-
-int adjoint_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
-  return p->precision == MBIR_FP64 ? adjoint_t<double>(p, y, mask, x, st)
-                                   : adjoint_t<float>(p, y, mask, x, st);
-}
-
 template <class R>
-static int configure_t(mbir_plan p) {
-  const int lat = (int)(sizeof(cplx_t<R>) * kLatElems);
-  const int row = (int)(sizeof(cplx_t<R>) * kMaxFFT + sizeof(float) * (kKbRes * 4 + 2));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2C_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2C_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_R2C_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_C2R_INV_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_SOLVE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_SOLVE_ADJ_L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(lateral_kernel<R, LAT_SOLVE_ADJ_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(row_forward_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(row_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
+static int configure_t() {
+  const int lat = (int)(sizeof(cplx_t<R>) * (kLatElems + 512));
+  const int row = (int)(sizeof(cplx_t<R>) * (kMaxFFT + 512));
+#define MBIR_SMEM_ATTR(fn, bytes)                                                                  \
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));    \
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_FWD>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_INV>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_R2C_MASK>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2R_INV_MASK>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_FWD>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_L1>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V>), lat);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 4>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 6>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 8>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 4>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 6>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 8>), row);
+#undef MBIR_SMEM_ATTR
   return MBIR_OK;
 }
 
 int configure_operator_kernels(mbir_plan p) {
-  return p->precision == MBIR_FP64 ? configure_t<double>(p) : configure_t<float>(p);
+  return p->precision == MBIR_FP64 ? configure_t<double>() : configure_t<float>();
 }
 
 }  // namespace mbir

@@ -5,9 +5,27 @@
 
 namespace mbir {
 
-constexpr int kLatThreads = 256;    // lateral FFT block size
-constexpr int kLatElems = 8192;     // nx * columns staged per lateral CTA
-constexpr int kRowThreads = 512;    // row (NUFFT) block size
+// Launch shapes (overridable at build time for tuning sweeps).
+#ifndef MBIR_LAT_THREADS
+#define MBIR_LAT_THREADS 512
+#endif
+#ifndef MBIR_LAT_ELEMS
+#define MBIR_LAT_ELEMS 8192
+#endif
+#ifndef MBIR_ROW_THREADS
+#define MBIR_ROW_THREADS 256
+#endif
+#ifndef MBIR_ROW_MINB
+#define MBIR_ROW_MINB 4
+#endif
+#ifndef MBIR_LAT_MINB
+#define MBIR_LAT_MINB 2
+#endif
+constexpr int kLatThreads = MBIR_LAT_THREADS;   // lateral FFT block size
+constexpr int kLatElems = MBIR_LAT_ELEMS;       // nx * columns staged per lateral CTA (max)
+constexpr int kRowThreads = MBIR_ROW_THREADS;   // row (NUFFT) block size
+constexpr int kRowMinBlocks = MBIR_ROW_MINB;    // resident CTAs per SM the register budget targets
+constexpr int kLatMinBlocks = MBIR_LAT_MINB;
 
 enum LatMode {
   LAT_C2C_FWD = 0,        // X = lateral FFT of x
@@ -47,12 +65,12 @@ struct RowArgs {
   void* out;
   const void* tab;
   const void* cdep;
-  const float* kbtab;
   const void* tw;
-  const int* perm;   // digit reversal of the K-point transform
+  const int* perm;   // digit reversal of the K-point transform (non power-of-two K)
   Radix rad;
-  int nx, nz, m, K, J, n0, nkb;
+  int nx, nz, m, K, n0;
   double alpha, inv_i0a;
+  float kbpoly[kMaxJ][kKbDeg + 1];   // FP32 KB weight of tap j: polynomial in (frac - 1/2)
 };
 
 double host_bessel_i0(double x);

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "operator.cuh"
 
 namespace mbir {
 
@@ -74,10 +75,10 @@ static double kb_hat(double nu, int J, double alpha) {
 }
 
 static bool factor_radix(int n, Radix* r) {
+  memset(r, 0, sizeof(*r));
   r->n = n;
-  r->npass = 0;
   int rem = n;
-  const int order[] = {8, 4, 2, 3, 5, 7};
+  const int order[] = {16, 8, 4, 2, 3, 5, 7};
   for (int f : order) {
     while (rem % f == 0) {
       if (r->npass >= kMaxPasses) return false;
@@ -86,28 +87,87 @@ static bool factor_radix(int n, Radix* r) {
     }
   }
   if (rem != 1) return false;
-  // a lone radix-2 pass next to a radix-8 pass: 8 * 2 becomes 4 * 4
+  // a lone radix-2 pass next to a radix-16 or radix-8 pass: 16*2 -> 8*4, 8*2 -> 4*4
   for (int i = 0; i < r->npass; ++i) {
     if (r->r[i] != 2) continue;
     for (int j = 0; j < r->npass; ++j) {
-      if (r->r[j] == 8) {
-        r->r[j] = 4;
-        r->r[i] = 4;
-        break;
-      }
+      if (r->r[j] == 16) { r->r[j] = 8; r->r[i] = 4; break; }
+      if (r->r[j] == 8) { r->r[j] = 4; r->r[i] = 4; break; }
     }
     break;
   }
+  r->pow2 = (n & (n - 1)) == 0;
+  r->log2n = 0;
+  while ((1 << r->log2n) < n) ++r->log2n;
+  for (int i = 0; i < r->npass; ++i) {
+    int b = 0;
+    while ((1 << b) < r->r[i]) ++b;
+    r->lg[i] = b;
+  }
+  // two-level twiddle tables: lo = w^i (i < 2^s), hi = w^{i 2^s}
+  int s = (r->log2n + 1) / 2;
+  if (s < 1) s = 1;
+  r->tw_shift = s;
+  r->tw_lo = 1 << s;
+  r->tw_hi = (n + r->tw_lo - 1) / r->tw_lo;
   return true;
 }
 
+// [lo | hi] twiddle tables of an n-point transform, w = e^{-2 pi j / n}, in FP64.
 template <class V>
-static void make_twiddles(int n, std::vector<V>& out) {
-  out.resize(n);
-  for (int i = 0; i < n; ++i) {
-    const double a = -2.0 * M_PI * double(i) / double(n);
+static void make_twiddles(const Radix& rad, std::vector<V>& out) {
+  const int n = rad.n;
+  out.resize(rad.tw_lo + rad.tw_hi);
+  for (int i = 0; i < rad.tw_lo; ++i) {
+    const double a = -2.0 * M_PI * double(i % n) / double(n);
     out[i].x = cos(a);
     out[i].y = sin(a);
+  }
+  for (int i = 0; i < rad.tw_hi; ++i) {
+    const double a = -2.0 * M_PI * double(((int64_t)i * rad.tw_lo) % n) / double(n);
+    out[rad.tw_lo + i].x = cos(a);
+    out[rad.tw_lo + i].y = sin(a);
+  }
+}
+
+// FP64 fit of the KB weight of each tap j as a degree-kKbDeg polynomial in
+// x = frac - 1/2 (tap offset J/2 - 1 - j + frac), interpolating at Chebyshev
+// nodes on [-1/2, 1/2] (Vandermonde system by Gaussian elimination).
+static void fit_kb_polynomials(int J, double alpha, float out[kMaxJ][kKbDeg + 1]) {
+  constexpr int D = kKbDeg + 1;
+  memset(out, 0, sizeof(float) * kMaxJ * D);
+  for (int j = 0; j < J; ++j) {
+    double A[D][D + 1];
+    for (int q = 0; q < D; ++q) {
+      const double x = 0.5 * cos(M_PI * (q + 0.5) / D);
+      double pw = 1.0;
+      for (int d = 0; d < D; ++d) {
+        A[q][d] = pw;
+        pw *= x;
+      }
+      A[q][D] = kb_psi(x + 0.5 + (J / 2 - 1 - j), J, alpha);
+    }
+    for (int c = 0; c < D; ++c) {
+      int piv = c;
+      for (int q = c + 1; q < D; ++q)
+        if (fabs(A[q][c]) > fabs(A[piv][c])) piv = q;
+      for (int d = 0; d <= D; ++d) {
+        const double t = A[c][d];
+        A[c][d] = A[piv][d];
+        A[piv][d] = t;
+      }
+      for (int q = c + 1; q < D; ++q) {
+        const double f = A[q][c] / A[c][c];
+        for (int d = c; d <= D; ++d) A[q][d] -= f * A[c][d];
+      }
+    }
+    double coef[D];
+    for (int c = D - 1; c >= 0; --c) {
+      double acc = A[c][D];
+      for (int d = c + 1; d < D; ++d) acc -= A[c][d] * coef[d];
+      coef[c] = acc / A[c][c];
+    }
+    for (int d = 0; d < D; ++d) out[j][d] = (float)coef[d];
   }
 }
 
@@ -149,8 +209,8 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
   using Tab = typename TabOf<R>::T;
   const int nx = p->nx, nz = p->nz, m = p->m, K = p->K, J = p->J;
   std::vector<V> twx, twk;
-  make_twiddles(nx, twx);
-  make_twiddles(K, twk);
+  make_twiddles(p->rad_x, twx);
+  make_twiddles(p->rad_k, twk);
   std::vector<R> cdep(nz);
   for (int n = 0; n < nz; ++n) {
     const double z = n * p->dz;
@@ -188,12 +248,12 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
       tab[(size_t)lp * m + mm] = e;
     }
   }
-  MBIR_CUDA_TRY(cudaMalloc(&p->tw_x, sizeof(V) * nx));
-  MBIR_CUDA_TRY(cudaMalloc(&p->tw_k, sizeof(V) * K));
+  MBIR_CUDA_TRY(cudaMalloc(&p->tw_x, sizeof(V) * twx.size()));
+  MBIR_CUDA_TRY(cudaMalloc(&p->tw_k, sizeof(V) * twk.size()));
   MBIR_CUDA_TRY(cudaMalloc(&p->cdep, sizeof(R) * nz));
   MBIR_CUDA_TRY(cudaMalloc(&p->tab, sizeof(Tab) * tab.size()));
-  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_x, twx.data(), sizeof(V) * nx, cudaMemcpyHostToDevice, st));
-  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_k, twk.data(), sizeof(V) * K, cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_x, twx.data(), sizeof(V) * twx.size(), cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_k, twk.data(), sizeof(V) * twk.size(), cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->cdep, cdep.data(), sizeof(R) * nz, cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->tab, tab.data(), sizeof(Tab) * tab.size(), cudaMemcpyHostToDevice, st));
   std::vector<int> px(nx), pk(K);
@@ -402,7 +462,6 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaFree(p->perm_k);
   cudaFree(p->cdep);
   cudaFree(p->tab);
-  cudaFree(p->kbtab);
   cudaFree(p->h_db4);
   cudaFree(p->h_db4f);
   cudaFree(p->wv_b1);
@@ -444,8 +503,8 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   p->alpha = g->kb_alpha > 0 ? g->kb_alpha : 2.34 * g->kb_width;
   factor_radix(p->nx, &p->rad_x);
   factor_radix(p->K, &p->rad_k);
-  // lateral tile: keep nx * tile_c <= 8192 elements, at most 16 columns
-  int tc = 8192 / p->nx;
+  // lateral tile: keep nx * tile_c <= kLatElems elements, at most 16 columns
+  int tc = kLatElems / p->nx;
   if (tc > 16) tc = 16;
   int pw = 1;
   while (pw * 2 <= tc) pw *= 2;
@@ -458,19 +517,7 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   rc = (p->precision == MBIR_FP64) ? upload_tables<double>(p, g, st) : upload_tables<float>(p, g, st);
   if (rc != MBIR_OK) return fail(rc);
 
-  // KB kernel samples for the FP32 path: psi(i / kKbRes), i = 0 .. kKbRes*J/2 + 1
-  {
-    const int nkb = kKbRes * p->J / 2 + 2;
-    std::vector<float> kb(nkb);
-    for (int i = 0; i < nkb; ++i) {
-      const double u = double(i) / kKbRes;
-      kb[i] = (u <= 0.5 * p->J) ? (float)kb_psi(u, p->J, p->alpha) : 0.0f;
-    }
-    cudaError_t e = cudaMalloc(&p->kbtab, sizeof(float) * nkb);
-    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMalloc kbtab"));
-    e = cudaMemcpy(p->kbtab, kb.data(), sizeof(float) * nkb, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpy kbtab"));
-  }
+  fit_kb_polynomials(p->J, p->alpha, p->kbpoly);
   {
     double h[8];
     daubechies8(h);

@@ -370,12 +370,14 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
   }
   int k = 0, status = MBIR_OK;
   const bool check = o->rel_tol > 0;
+  // the objective of every iterate is reduced only when something reads it
+  const bool want_trace = check || (info && info->objective_trace && info->trace_len > 0);
   if (check) status = MBIR_ERR_NOT_CONVERGED;
   for (k = 1; k <= o->max_iter; ++k) {
     const double m = k >= 2 ? mu[k - 2] : 0.0;
     int rc = forward_solve_impl(p, z1, mask, y, s->pz, s->r, m, s->part_data, st);
     if (rc) return rc;
-    {
+    if (want_trace) {
       ProfScope ps_(p, PC_REDUCE, st);
       combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_data, s->n_data, 0.5, s->part_reg, nreg, lam,
                                                 s->objtrace + (k - 1));

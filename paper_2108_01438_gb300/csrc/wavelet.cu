@@ -82,10 +82,24 @@ __global__ void __launch_bounds__(kWavThreads) dwt_fwd_kernel(WArgs<R> a) {
   const int P = a.P, N = a.N;
   const int a0 = blockIdx.y * kFwdTA, b0 = blockIdx.x * kFwdTB;
   const V* in = reinterpret_cast<const V*>(a.in);
-  for (int e = tid; e < kFwdRows * kFwdCols; e += nthr) {
-    const int i = e / kFwdCols, j = e - i * kFwdCols;
-    const int row = (2 * a0 + i) % P, col = (2 * b0 + j) % N;
-    tin[e] = in[(size_t)row * a.istride + col];
+  // stage the input tile with every load of a thread in flight at once
+  constexpr int kFwdPer = (kFwdRows * kFwdCols + kWavThreads - 1) / kWavThreads;
+  {
+    V vv[kFwdPer];
+#pragma unroll
+    for (int q = 0; q < kFwdPer; ++q) {
+      const int e = tid + q * nthr;
+      if (e < kFwdRows * kFwdCols) {
+        const int i = e / kFwdCols, j = e - i * kFwdCols;
+        const int row = (2 * a0 + i) % P, col = (2 * b0 + j) % N;
+        vv[q] = in[(size_t)row * a.istride + col];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kFwdPer; ++q) {
+      const int e = tid + q * nthr;
+      if (e < kFwdRows * kFwdCols) tin[e] = vv[q];
+    }
   }
   __syncthreads();
   for (int e = tid; e < kFwdRows * kFwdTB; e += nthr) {
@@ -157,14 +171,32 @@ __global__ void __launch_bounds__(kWavThreads) dwt_inv_kernel(WArgs<R> a) {
   const int r0 = blockIdx.y * kInvTR, c0 = blockIdx.x * kInvTC;
   const V* ll = reinterpret_cast<const V*>(a.in);
   const V* coef = reinterpret_cast<const V*>(a.coef);
-  for (int e = tid; e < kInvRows * kInvCols; e += nthr) {
-    const int ia = e / kInvCols, ib = e - ia * kInvCols;
-    const int A = ((r0 / 2 - 3 + ia) % Ph + Ph) % Ph;
-    const int B = ((c0 / 2 - 3 + ib) % Nh + Nh) % Nh;
-    cLL[e] = ll[(size_t)A * a.istride + B];
-    cLH[e] = coef[(size_t)A * a.cstride + Nh + B];
-    cHL[e] = coef[(size_t)(Ph + A) * a.cstride + B];
-    cHH[e] = coef[(size_t)(Ph + A) * a.cstride + Nh + B];
+  constexpr int kInvPer = (kInvRows * kInvCols + kWavThreads - 1) / kWavThreads;
+  {
+    V v0[kInvPer], v1[kInvPer], v2[kInvPer], v3[kInvPer];
+#pragma unroll
+    for (int q = 0; q < kInvPer; ++q) {
+      const int e = tid + q * nthr;
+      if (e < kInvRows * kInvCols) {
+        const int ia = e / kInvCols, ib = e - ia * kInvCols;
+        const int A = ((r0 / 2 - 3 + ia) % Ph + Ph) % Ph;
+        const int B = ((c0 / 2 - 3 + ib) % Nh + Nh) % Nh;
+        v0[q] = ll[(size_t)A * a.istride + B];
+        v1[q] = coef[(size_t)A * a.cstride + Nh + B];
+        v2[q] = coef[(size_t)(Ph + A) * a.cstride + B];
+        v3[q] = coef[(size_t)(Ph + A) * a.cstride + Nh + B];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kInvPer; ++q) {
+      const int e = tid + q * nthr;
+      if (e < kInvRows * kInvCols) {
+        cLL[e] = v0[q];
+        cLH[e] = v1[q];
+        cHL[e] = v2[q];
+        cHH[e] = v3[q];
+      }
+    }
   }
   __syncthreads();
   for (int e = tid; e < kInvTR * kInvCols; e += nthr) {

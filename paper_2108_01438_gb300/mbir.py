@@ -13,7 +13,8 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmbir.so")
+# MBIR_LIBRARY selects another build of the library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("MBIR_LIBRARY") or os.path.join(HERE, "libmbir.so")
 
 FP32, FP32_COMPENSATED, FP64 = 0, 1, 2
 PENALTY_L1, PENALTY_DB4 = 0, 1
