@@ -55,10 +55,12 @@ struct Radix {
   int tw_lo, tw_hi;       // table lengths
 };
 
-// One entry of the per-(|l~|, m) resampling table: integer grid cell of
-// t = K/(2 pi) (beta dz mod 2 pi), its fractional part and the complex filter.
-struct TabF { int i0; float frac; float fre, fim; };
-struct TabD { int i0; int pad; double frac; double fre, fim; };
+// One entry of the per-(|l~|, m) resampling table for t = K/(2 pi) (beta dz mod 2 pi):
+// cell = (u << 16) | pc, pc = floor(t) - J/2 + 1 (mod K) the first tap's grid cell
+// and u its unwrapped offset within the row (see the plan), the fractional part
+// of t and the complex filter.
+struct TabF { int cell; float frac; float fre, fim; };
+struct TabD { int cell; int pad; double frac; double fre, fim; };
 
 template <class R> struct TabOf;
 template <> struct TabOf<float> { using T = TabF; };
@@ -105,6 +107,8 @@ struct mbir_plan_s {
   int* perm_k;                // digit reversal of the K-point transform
   void* cdep;                 // [nz] falloff / KB deapodisation
   void* tab;                  // [nlh][m] TabF or TabD
+  int4* rowmeta;              // [nlh] {base cell of u = 0, span of u + J, direction, 0}
+  int gather_ok;              // every row monotone with span <= K: deterministic adjoint gather
   float kbpoly[mbir::kMaxJ][mbir::kKbDeg + 1];   // FP32 KB weight polynomials per tap
   double* h_db4;              // 8 wavelet taps (device, double)
   float* h_db4f;              // same, float

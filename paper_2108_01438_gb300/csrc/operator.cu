@@ -256,7 +256,6 @@ row_forward_kernel(RowArgs<R> a) {
   fft_dit<false>(buf, 1, a.rad, tw, sw);
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
   V* S = reinterpret_cast<V*>(a.out) + (size_t)l * M;
-  constexpr int h = J / 2;
   constexpr int UM = 2;
   for (int m0 = tid; m0 < M; m0 += UM * nthr) {
     Tab e[UM];
@@ -272,10 +271,10 @@ row_forward_kernel(RowArgs<R> a) {
       R w[J];
       kb_weights<R, J>(R(e[u].frac), a, w);
       V acc = cmk<V>(R(0), R(0));
+      const int pc = e[u].cell & 0xFFFF;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        int idx = e[u].i0 - h + 1 + j;
-        if (idx < 0) idx += K;
+        int idx = pc + j;
         if (idx >= K) idx -= K;
         const V b = buf[swz(idx, sw)];
         acc.x += w[j] * b.x;
@@ -304,7 +303,6 @@ row_adjoint_kernel(RowArgs<R> a) {
   __syncthreads();
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
   const V* Rh = reinterpret_cast<const V*>(a.in) + (size_t)l * M;
-  constexpr int h = J / 2;
   R* bufr = reinterpret_cast<R*>(buf);
   constexpr int UM = 2;
   for (int m0 = tid; m0 < M; m0 += UM * nthr) {
@@ -325,16 +323,135 @@ row_adjoint_kernel(RowArgs<R> a) {
       const V v = cmulc(r[u], cmk<V>(R(e[u].fre), R(e[u].fim)));
       R w[J];
       kb_weights<R, J>(R(e[u].frac), a, w);
+      const int pc = e[u].cell & 0xFFFF;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        int idx = e[u].i0 - h + 1 + j;
-        if (idx < 0) idx += K;
+        int idx = pc + j;
         if (idx >= K) idx -= K;
         const int q = swz(idx, sw);
         atomicAdd(&bufr[2 * q], w[j] * v.x);
         atomicAdd(&bufr[2 * q + 1], w[j] * v.y);
       }
     }
+  }
+  __syncthreads();
+  fft_dif<true>(buf, 1, a.rad, tw, sw);
+  const R* cdep = reinterpret_cast<const R*>(a.cdep);
+  V* Wo = reinterpret_cast<V*>(a.out) + (size_t)l * nz;
+  for (int n = tid; n < nz; n += nthr) {
+    int i = n - n0;
+    if (i < 0) i += K;
+    Wo[n] = cscale(buf[swz(row_pos(i, a), sw)], cdep[n]);
+  }
+}
+
+// Adjoint row kernel without atomics: the transpose of the J-tap interpolation
+// as a segmented gather.  Within a row the first-tap cells of the pixels,
+// unwrapped to u (plan table), are monotone in m, so the pixels reaching grid
+// cell c (those with c - J + 1 <= u <= c) form a contiguous run once the row is
+// staged in increasing-u order.  first[c] = min{s : u_s >= c} is built by a
+// conflict-free scatter (each cell written once); cell c then sums its run in a
+// fixed order, so the result is deterministic.
+template <class R, int J>
+__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
+row_adjoint_gather_kernel(RowArgs<R> a) {
+  using V = cplx_t<R>;
+  using Tab = typename TabOf<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  V* buf = reinterpret_cast<V*>(smem_raw);
+  V* tws = buf + K;
+  V* sv = tws + a.rad.tw_lo + a.rad.tw_hi;                          // [M] conj(f) R
+  // FP32 with kGatherPrecomp: the J weights of every pixel [M][J]; otherwise frac [M]
+  R* sfrac = reinterpret_cast<R*>(sv + M);
+  constexpr bool kPre = kGatherPrecomp && sizeof(R) == 4;
+  float* spoly = reinterpret_cast<float*>(sfrac + (kPre ? M * J : M));   // [J][kKbDeg + 1]
+  uint16_t* su = reinterpret_cast<uint16_t*>(spoly + J * (kKbDeg + 1));   // [M]
+  uint16_t* sfirst = su + M + (M & 1);                              // [span + 1]
+  const int l = blockIdx.x;
+  const int lp = l <= a.nx - l ? l : a.nx - l;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool sw = (K & 15) == 0;
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
+  if (sizeof(R) == 4)
+    for (int i = tid; i < J * (kKbDeg + 1); i += nthr) spoly[i] = a.kbpoly[i / (kKbDeg + 1)][i % (kKbDeg + 1)];
+  const int4 meta = a.rowmeta[lp];
+  const int base = meta.x, span = meta.y, dir = meta.z;
+  const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
+  const V* Rh = reinterpret_cast<const V*>(a.in) + (size_t)l * M;
+  // stage the row in increasing-u order
+  constexpr int UM = 4;
+  for (int m0 = tid; m0 < M; m0 += UM * nthr) {
+    Tab e[UM];
+    V r[UM];
+#pragma unroll
+    for (int q = 0; q < UM; ++q) {
+      const int mm = m0 + q * nthr;
+      if (mm < M) {
+        e[q] = tab[mm];
+        r[q] = Rh[mm];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < UM; ++q) {
+      const int mm = m0 + q * nthr;
+      if (mm < M) {
+        const int sidx = dir > 0 ? mm : M - 1 - mm;
+        sv[sidx] = cmulc(r[q], cmk<V>(R(e[q].fre), R(e[q].fim)));
+        if constexpr (kPre) {
+          R w[J];
+          kb_weights<R, J>(R(e[q].frac), a, w);
+#pragma unroll
+          for (int j = 0; j < J; ++j) sfrac[sidx * J + j] = w[j];
+        } else {
+          sfrac[sidx] = R(e[q].frac);
+        }
+        su[sidx] = (uint16_t)((unsigned)e[q].cell >> 16);
+      }
+    }
+  }
+  __syncthreads();
+  // first[c] = min{s : u_s >= c} for c in [0, span]: pixel s owns the cells
+  // (u_{s-1}, u_s] (u_{-1} = -1); the last pixel also owns (u_{M-1}, span] -> M
+  for (int sidx = tid; sidx < M; sidx += nthr) {
+    const int lo = sidx == 0 ? 0 : int(su[sidx - 1]) + 1;
+    const int hi = su[sidx];
+    for (int c = lo; c <= hi; ++c) sfirst[c] = (uint16_t)sidx;
+    if (sidx == M - 1)
+      for (int c = hi + 1; c <= span; ++c) sfirst[c] = (uint16_t)M;
+  }
+  __syncthreads();
+  // each physical cell i: unwrapped c = (i - base) mod K; sum its run of pixels
+  for (int i = tid; i < K; i += nthr) {
+    int c = i - base;
+    if (c < 0) c += K;
+    V acc = cmk<V>(R(0), R(0));
+    if (c < span) {
+      const int slo = c - J + 1 <= 0 ? 0 : int(sfirst[c - J + 1]);
+      const int shi = int(sfirst[c + 1]) - 1;
+      for (int sidx = slo; sidx <= shi; ++sidx) {
+        const int j = c - int(su[sidx]);
+        R w;
+        if constexpr (kPre) {
+          w = sfrac[sidx * J + j];
+        } else if constexpr (sizeof(R) == 4) {
+          const float x = sfrac[sidx] - 0.5f;
+          const float* cf = spoly + j * (kKbDeg + 1);
+          float t = cf[kKbDeg];
+#pragma unroll
+          for (int d = kKbDeg - 1; d >= 0; --d) t = fmaf(t, x, cf[d]);
+          w = t;
+        } else {
+          const double uu = sfrac[sidx] + double(J / 2 - 1 - j);
+          const double rr = 1.0 - (2.0 * uu / J) * (2.0 * uu / J);
+          w = rr < 0.0 ? 0.0 : cyl_bessel_i0(a.alpha * sqrt(rr)) * a.inv_i0a;
+        }
+        const V v = sv[sidx];
+        acc.x += w * v.x;
+        acc.y += w * v.y;
+      }
+    }
+    buf[swz(i, sw)] = acc;
   }
   __syncthreads();
   fft_dif<true>(buf, 1, a.rad, tw, sw);
@@ -418,6 +535,7 @@ RowArgs<R> row_args(mbir_plan p, const void* in, void* out) {
   a.m = p->m;
   a.K = p->K;
   a.n0 = p->n0;
+  a.rowmeta = p->rowmeta;
   a.alpha = p->alpha;
   a.inv_i0a = 1.0 / host_bessel_i0(p->alpha);
   for (int j = 0; j < kMaxJ; ++j)
@@ -431,8 +549,29 @@ size_t row_smem(mbir_plan p) {
 }
 
 template <class R>
+size_t row_gather_smem(mbir_plan p) {
+  const size_t M = p->m;
+  const size_t nw = (kGatherPrecomp && sizeof(R) == 4) ? M * p->J : M;
+  return sizeof(cplx_t<R>) * ((size_t)p->K + p->rad_k.tw_lo + p->rad_k.tw_hi + M) + sizeof(R) * nw +
+         sizeof(float) * p->J * (kKbDeg + 1) + sizeof(uint16_t) * (M + (M & 1) + p->K + 2);
+}
+
+template <class R>
 int launch_row(mbir_plan p, bool adjoint, const void* in, void* out, cudaStream_t st) {
   RowArgs<R> a = row_args<R>(p, in, out);
+  const size_t gsmem = row_gather_smem<R>(p);
+  if (adjoint && !kAdjAtomic && p->gather_ok && gsmem <= (size_t)227 * 1024) {
+    {
+      ProfScope ps_(p, PC_ROW_ADJ, st);
+      switch (p->J) {
+        case 4: row_adjoint_gather_kernel<R, 4><<<p->nx, kRowThreads, gsmem, st>>>(a); break;
+        case 6: row_adjoint_gather_kernel<R, 6><<<p->nx, kRowThreads, gsmem, st>>>(a); break;
+        default: row_adjoint_gather_kernel<R, 8><<<p->nx, kRowThreads, gsmem, st>>>(a); break;
+      }
+    }
+    MBIR_LAUNCH_CHECK();
+    return MBIR_OK;
+  }
   const size_t smem = row_smem<R>(p);
   {
     ProfScope ps_(p, adjoint ? PC_ROW_ADJ : PC_ROW_FWD, st);
@@ -536,6 +675,7 @@ template <class R>
 static int configure_t() {
   const int lat = (int)(sizeof(cplx_t<R>) * (kLatElems + 512));
   const int row = (int)(sizeof(cplx_t<R>) * (kMaxFFT + 512));
+  const int gat = 227 * 1024;
 #define MBIR_SMEM_ATTR(fn, bytes)                                                                  \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));    \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
@@ -552,6 +692,9 @@ static int configure_t() {
   MBIR_SMEM_ATTR((row_adjoint_kernel<R, 4>), row);
   MBIR_SMEM_ATTR((row_adjoint_kernel<R, 6>), row);
   MBIR_SMEM_ATTR((row_adjoint_kernel<R, 8>), row);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 4>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8>), gat);
 #undef MBIR_SMEM_ATTR
   return MBIR_OK;
 }

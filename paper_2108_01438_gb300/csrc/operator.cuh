@@ -18,6 +18,12 @@ namespace mbir {
 #ifndef MBIR_ROW_MINB
 #define MBIR_ROW_MINB 4
 #endif
+#ifndef MBIR_GATHER_PRECOMP
+#define MBIR_GATHER_PRECOMP 1
+#endif
+#ifndef MBIR_ADJ_ATOMIC
+#define MBIR_ADJ_ATOMIC 0
+#endif
 #ifndef MBIR_LAT_MINB
 #define MBIR_LAT_MINB 2
 #endif
@@ -26,6 +32,8 @@ constexpr int kLatElems = MBIR_LAT_ELEMS;       // nx * columns staged per later
 constexpr int kRowThreads = MBIR_ROW_THREADS;   // row (NUFFT) block size
 constexpr int kRowMinBlocks = MBIR_ROW_MINB;    // resident CTAs per SM the register budget targets
 constexpr int kLatMinBlocks = MBIR_LAT_MINB;
+constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
+constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics
 
 enum LatMode {
   LAT_C2C_FWD = 0,        // X = lateral FFT of x
@@ -67,6 +75,7 @@ struct RowArgs {
   const void* cdep;
   const void* tw;
   const int* perm;   // digit reversal of the K-point transform (non power-of-two K)
+  const int4* rowmeta;   // per row {base, span, direction, 0} of the unwrapped tap cells
   Radix rad;
   int nx, nz, m, K, n0;
   double alpha, inv_i0a;

@@ -218,7 +218,19 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
     if (g->falloff_half_um > 0) w = exp(-M_LN2 * (z / g->falloff_half_um) * (z / g->falloff_half_um));
     cdep[n] = R(w / kb_hat(double(n - p->n0) / K, J, p->alpha));
   }
+  // Resampling table.  Per row l' and pixel m: the first tap cell pc = floor(t) -
+  // J/2 + 1 (mod K), frac, and the filter.  For the adjoint's segmented gather the
+  // first-tap cells of a row are also unwrapped into a monotone sequence U_m (the
+  // beta mapping is monotone in k); u = U_m - min U is packed above pc.  Rows whose
+  // unwrapped cells are not monotone or span more than K cells make the plan use
+  // shared-memory atomics in the adjoint instead.
   std::vector<Tab> tab((size_t)p->nlh * m);
+  std::vector<int4> meta(p->nlh);
+  const int h = J / 2;
+  bool gather_ok = m <= 65535 && K <= 32768;
+  std::vector<int> pc(m), valid(m);
+  std::vector<double> fr(m);
+  std::vector<long long> U(m);
   for (int lp = 0; lp < p->nlh; ++lp) {
     const double q = 2.0 * M_PI * lp / (nx * p->dx);
     for (int mm = 0; mm < m; ++mm) {
@@ -226,28 +238,81 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
       const double b2 = 4.0 * k * k - q * q;
       Tab e;
       memset(&e, 0, sizeof(e));
+      valid[mm] = b2 > 0;
+      pc[mm] = 0;
+      fr[mm] = 0.0;
       if (b2 > 0) {
         const double beta = sqrt(b2);
         double t = (K / (2.0 * M_PI)) * fmod(beta * p->dz, 2.0 * M_PI);
         double i0 = floor(t);
-        double frac = t - i0;
-        int ii = (int)i0;
-        if (ii >= K) ii -= K;
-        if (ii < 0) ii += K;
+        fr[mm] = t - i0;
+        long long first = (long long)i0 - h + 1;
+        first %= K;
+        if (first < 0) first += K;
+        pc[mm] = (int)first;
         const double A = g->source ? g->source[mm] : 1.0;
         const double G = g->na > 0 ? exp(-q * q / (2.0 * k * k * g->na * g->na)) : 1.0;
         const double dk = k - g->k0;
         const double omega = g->disp_a * dk * dk + g->disp_b * dk * dk * dk;
         const double phase = fmod(omega - 2.0 * k * g->z_focus_um, 2.0 * M_PI) +
                              fmod(beta * (g->z_focus_um - p->n0 * p->dz), 2.0 * M_PI);
-        e.i0 = ii;
-        e.frac = (decltype(e.frac))frac;
         e.fre = (decltype(e.fre))(A * G * cos(phase));
         e.fim = (decltype(e.fim))(A * G * sin(phase));
       }
       tab[(size_t)lp * m + mm] = e;
     }
+    // evanescent pixels (filter 0) borrow a neighbour's position to keep the row monotone
+    int first_valid = -1, last = -1;
+    for (int mm = 0; mm < m; ++mm) {
+      if (valid[mm]) {
+        if (first_valid < 0) first_valid = mm;
+        last = mm;
+      } else if (last >= 0) {
+        pc[mm] = pc[last];
+        fr[mm] = fr[last];
+      }
+    }
+    for (int mm = 0; mm < first_valid; ++mm) {
+      pc[mm] = pc[first_valid];
+      fr[mm] = fr[first_valid];
+    }
+    // unwrap and check monotonicity / span
+    U[0] = pc[0];
+    int dir = 0;
+    bool mono = true;
+    for (int mm = 1; mm < m; ++mm) {
+      long long d = (long long)pc[mm] - pc[mm - 1];
+      if (d > K / 2) d -= K;
+      if (d <= -(K + 1) / 2) d += K;
+      U[mm] = U[mm - 1] + d;
+      if (d > 0) {
+        if (dir < 0) mono = false;
+        dir = 1;
+      } else if (d < 0) {
+        if (dir > 0) mono = false;
+        dir = -1;
+      }
+    }
+    long long umin = U[0], umax = U[0];
+    for (int mm = 1; mm < m; ++mm) {
+      umin = U[mm] < umin ? U[mm] : umin;
+      umax = U[mm] > umax ? U[mm] : umax;
+    }
+    const long long span = umax - umin + J;
+    if (!mono || span > K) gather_ok = false;
+    long long base = umin % K;
+    if (base < 0) base += K;
+    meta[lp] = make_int4((int)base, (int)span, dir >= 0 ? 1 : -1, 0);
+    for (int mm = 0; mm < m; ++mm) {
+      Tab& e = tab[(size_t)lp * m + mm];
+      const long long u = (mono && span <= K) ? U[mm] - umin : 0;
+      e.cell = (int)((u << 16) | (long long)pc[mm]);
+      e.frac = (decltype(e.frac))fr[mm];
+    }
   }
+  p->gather_ok = gather_ok ? 1 : 0;
+  MBIR_CUDA_TRY(cudaMalloc(&p->rowmeta, sizeof(int4) * meta.size()));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(p->rowmeta, meta.data(), sizeof(int4) * meta.size(), cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMalloc(&p->tw_x, sizeof(V) * twx.size()));
   MBIR_CUDA_TRY(cudaMalloc(&p->tw_k, sizeof(V) * twk.size()));
   MBIR_CUDA_TRY(cudaMalloc(&p->cdep, sizeof(R) * nz));
@@ -459,6 +524,7 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaFree(p->tw_x);
   cudaFree(p->tw_k);
   cudaFree(p->perm_x);
+  cudaFree(p->rowmeta);
   cudaFree(p->perm_k);
   cudaFree(p->cdep);
   cudaFree(p->tab);
