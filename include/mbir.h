@@ -190,6 +190,22 @@ int mbir_solve(mbir_plan plan, const void* y, const uint8_t* mask, const mbir_so
                void* x, mbir_solve_info* info, void* stream);
 
 /*
+ * FISTA on n B-scans at once (the uneven-size batch): plans[i] (each plan at most
+ * once, all with the same precision, KB width and shape), y[i], mask[i] (mask may
+ * be NULL, or mask[i] NULL), opts[i] and x[i] as for mbir_solve.  Every stage of
+ * the path -- power iteration, lambda rule, the operator passes, the FISTA
+ * epilogues and the wavelet levels -- is one launch over all scans; the iteration
+ * loop is captured into a CUDA graph and replayed when `stream` is a created
+ * stream (not the legacy or per-thread default).  Each scan's result does not
+ * depend on what it is batched with.  All opts[i].max_iter must be equal and
+ * rel_tol must be 0 (fixed iteration count).  info (NULL or n entries) receives
+ * iters, lipschitz, step and lambda_used; objective is not evaluated (NaN).
+ * Synchronous at set-up (one read-back for the whole batch) and when info != NULL.
+ */
+int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const uint8_t* const* mask,
+                     const mbir_solve_opts* opts, void* const* x, mbir_solve_info* info, void* stream);
+
+/*
  * lambda_max(Phi^H Phi) for this plan and mask by power iteration from a fixed
  * pseudo-random start (counter-based hash of the pixel index), FP64 norms
  * (step-size bound of Sec. 2.3).  Writes the estimate to *out (host).  Synchronous.

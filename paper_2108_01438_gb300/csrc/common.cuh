@@ -68,6 +68,30 @@ template <> struct TabOf<double> { using T = TabD; };
 
 struct SolveState;   // defined in solve.cu
 
+// Batched launches: one grid covers several B-scans.  args[s] is scan s's
+// argument block (device memory) and off[s] .. off[s+1]-1 its CTAs; a null args
+// means a single scan whose block is passed by value.  mu (when set_mu) replaces
+// the momentum of every block, the one value that changes per FISTA iteration.
+template <class Args>
+struct BatchRef {
+  const Args* args;
+  const int* off;
+  int n;
+  int set_mu;
+  double mu;
+};
+
+template <class Args>
+inline BatchRef<Args> no_batch() {
+  BatchRef<Args> b;
+  b.args = nullptr;
+  b.off = nullptr;
+  b.n = 0;
+  b.set_mu = 0;
+  b.mu = 0.0;
+  return b;
+}
+
 // Kernel classes for the event profiler (mbir_profile_begin / _end).
 enum ProfClass {
   PC_LAT_FWD = 0,     // lateral FFT of the image (first stage of Phi)
@@ -166,6 +190,55 @@ struct ProfScope {
   ~ProfScope() { prof_end(p, slot, st); }
 };
 void destroy_profiler(mbir_plan p);
+
+// Batched launch descriptor: device array of per-scan argument blocks, CTA
+// prefix offsets (n + 1 entries), total CTAs, dynamic shared memory (the
+// maximum over the scans), the by-value block (uniform fields) and the momentum.
+struct BatchLaunch {
+  const void* dargs;
+  const int* doff;
+  int n, total;
+  size_t smem;
+  const void* host0;
+  int set_mu;
+  double mu;
+};
+
+// Operands of one lateral stage for one scan (batch.cu fills these).
+struct LatFill {
+  const void* in;
+  void* out;
+  const uint8_t* mask;
+  int cols;
+  double scale;
+  const void* y;
+  void* pz;
+  void* r;
+  const void* z1;
+  void* z2;
+  void* vout;
+  double delta, tau;
+  double* partial;
+};
+
+// operator.cu (batch helpers)
+size_t lat_args_bytes(int precision);
+size_t row_args_bytes(int precision);
+size_t lat_smem_bytes(mbir_plan p);
+size_t row_smem_bytes(mbir_plan p, int adjoint_gather);
+bool plan_uses_gather(mbir_plan p);
+void fill_lat_args(mbir_plan p, const LatFill& f, void* dst);
+void fill_row_args(mbir_plan p, const void* in, void* out, void* dst);
+int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st);
+int batch_row(int kind, int precision, int J, const BatchLaunch& L, cudaStream_t st);
+
+// wavelet.cu (batch helpers)
+size_t dwt_args_bytes(int precision);
+int dwt_level_ctas(int P, int N, int inverse);
+size_t dwt_smem_bytes(int precision, int inverse);
+void fill_dwt_args(mbir_plan p, int level, int inverse, const void* in, void* out, void* coef, double tau,
+                   int thresh, double* partial, void* dst);
+int batch_dwt(int inverse, int precision, const BatchLaunch& L, cudaStream_t st);
 
 // operator.cu
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st);

@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "operator.cuh"
+#include <string.h>
 
 namespace mbir {
 
@@ -39,11 +40,49 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;   // valid in thread 0
 }
 
+// This CTA's argument block (the by-value one, or its scan's block in a batch)
+// and its index within its scan's grid.
+template <class Args>
+__device__ __forceinline__ const Args* resolve_args(const Args* a0, const BatchRef<Args>& B, int& blk) {
+  blk = blockIdx.x;
+  if (B.args == nullptr) return a0;
+  int lo = 0, hi = B.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.off[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  blk -= B.off[lo];
+  return B.args + lo;
+}
+
+// Copy a radix plan into shared memory (no barrier inside).
+__device__ __forceinline__ void copy_radix(Radix* dst, const Radix* src) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(Radix) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+}
+
+// Operands of the lateral load/store phases, held in registers.
+template <class R>
+struct LatEp {
+  const void* in;
+  void* out;
+  const uint8_t* mask;
+  const R* y;
+  R* pz;
+  R* r;
+  const void* z1;
+  void* z2;
+  void* vout;
+  R scale, mu, delta, tau;
+};
+
 // --------------------------------------------------------------- lateral FFT
 
 // Load element (p, c) of the lateral input as complex.
-template <class R, int MODE>
-__device__ __forceinline__ cplx_t<R> lat_load(const LatArgs<R>& a, size_t off) {
+template <class R, int MODE, class A>
+__device__ __forceinline__ cplx_t<R> lat_load(const A& a, size_t off) {
   using V = cplx_t<R>;
   if constexpr (MODE == LAT_R2C_MASK) {
     const R r = reinterpret_cast<const R*>(a.in)[off];
@@ -62,8 +101,8 @@ struct EpOps {
   bool meas;
 };
 
-template <class R, int MODE>
-__device__ __forceinline__ EpOps<R> lat_prefetch(const LatArgs<R>& a, size_t off) {
+template <class R, int MODE, class A>
+__device__ __forceinline__ EpOps<R> lat_prefetch(const A& a, size_t off) {
   using V = cplx_t<R>;
   EpOps<R> o;
   if constexpr (MODE == LAT_C2R_INV_MASK) {
@@ -79,8 +118,8 @@ __device__ __forceinline__ EpOps<R> lat_prefetch(const LatArgs<R>& a, size_t off
   return o;
 }
 
-template <class R, int MODE>
-__device__ __forceinline__ void lat_store(const LatArgs<R>& a, size_t off, cplx_t<R> v, const EpOps<R>& o,
+template <class R, int MODE, class A>
+__device__ __forceinline__ void lat_store(const A& a, size_t off, cplx_t<R> v, const EpOps<R>& o,
                                           double& part) {
   using V = cplx_t<R>;
   if constexpr (MODE == LAT_C2R_INV_MASK) {
@@ -111,17 +150,18 @@ __device__ __forceinline__ void lat_store(const LatArgs<R>& a, size_t off, cplx_
   }
 }
 
-template <class R, int MODE>
-__global__ void __launch_bounds__(kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
-lateral_kernel(LatArgs<R> a) {
+// One lateral tile: `a` supplies the operands (the launch's argument block, or a
+// register copy of a batched scan's block), `rad` the nx-point radix plan.
+template <class R, int MODE, class A>
+__device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int nx, int TC, int C, int blk,
+                                             const void* twg, const int* perm, double* partial) {
   using V = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s = reinterpret_cast<V*>(smem_raw);
-  V* tws = s + a.nx * a.tc;
-  const int TC = a.tc, nx = a.nx, C = a.cols;
-  const int c0 = blockIdx.x * TC;
+  V* tws = s + nx * TC;
+  const int c0 = blk * TC;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(twg), rad);
   // stage the tile: column pairs (b, b+1), four pairs in flight per thread
   const int half = TC >> 1;
   const int npairs = nx * half;
@@ -152,7 +192,7 @@ lateral_kernel(LatArgs<R> a) {
   }
   __syncthreads();
   constexpr bool INV = (MODE != LAT_C2C_FWD && MODE != LAT_R2C_MASK);
-  fft_dif<INV>(s, TC, a.rad, tw, false);
+  fft_dif<INV>(s, TC, rad, tw, false);
   double part = 0.0;
   for (int e0 = tid; e0 < npairs; e0 += U * nthr) {
     EpOps<R> oa[U], ob[U];
@@ -174,7 +214,7 @@ lateral_kernel(LatArgs<R> a) {
         const int p = e / half, b = 2 * (e - p * half);
         const int c = c0 + b;
         const size_t off = (size_t)p * C + c;
-        const int src = a.perm[p] * TC + b;
+        const int src = perm[p] * TC + b;
         if (c < C) lat_store<R, MODE>(a, off, s[src], oa[u], part);
         if (c + 1 < C) lat_store<R, MODE>(a, off + 1, s[src + 1], ob[u], part);
       }
@@ -182,7 +222,36 @@ lateral_kernel(LatArgs<R> a) {
   }
   if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_ADJ_L1) {
     const double t = block_sum(part);
-    if (tid == 0) a.partial[blockIdx.x] = t;
+    if (tid == 0) partial[blk] = t;
+  }
+}
+
+template <class R, int MODE, bool BAT>
+__global__ void __launch_bounds__(kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
+lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>> B) {
+  if constexpr (!BAT) {
+    lateral_body<R, MODE>(a0, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, a0.partial);
+  } else {
+    int blk;
+    const LatArgs<R>& A = *resolve_args(&a0, B, blk);
+    __shared__ Radix rad;
+    copy_radix(&rad, &A.rad);
+    LatEp<R> e;
+    e.in = A.in;
+    e.out = A.out;
+    e.mask = A.mask;
+    e.y = A.y;
+    e.pz = A.pz;
+    e.r = A.r;
+    e.z1 = A.z1;
+    e.z2 = A.z2;
+    e.vout = A.vout;
+    e.scale = A.scale;
+    e.mu = B.set_mu ? R(B.mu) : A.mu;
+    e.delta = A.delta;
+    e.tau = A.tau;
+    __syncthreads();
+    lateral_body<R, MODE>(e, rad, A.nx, A.tc, A.cols, blk, A.tw, A.perm, A.partial);
   }
 }
 
@@ -211,27 +280,26 @@ __device__ __forceinline__ void kb_weights(R frac, const RowArgs<R>& a, R (&w)[J
   }
 }
 
-template <class R>
-__device__ __forceinline__ int row_pos(int i, const RowArgs<R>& a) {
-  return a.rad.pow2 ? digit_reverse_pow2(i, a.rad) : a.perm[i];
+__device__ __forceinline__ int row_pos(int i, const Radix& rad, const int* perm) {
+  return rad.pow2 ? digit_reverse_pow2(i, rad) : perm[i];
 }
 
 // --------------------------------------------------------- row kernels (NUFFT)
 
 template <class R, int J>
-__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
-row_forward_kernel(RowArgs<R> a) {
+__device__ __forceinline__ void row_forward_body(const RowArgs<R>& a, const Radix& rad, int blk, const RowArgs<R>& a0) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
   V* tws = buf + a.K;
-  const int l = blockIdx.x;
+  const int l = blk;
   const int lp = l <= a.nx - l ? l : a.nx - l;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
   const bool sw = (K & 15) == 0;
-  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
+  const int* perm = a.perm;
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), rad);
   const V* X = reinterpret_cast<const V*>(a.in) + (size_t)l * nz;
   const R* cdep = reinterpret_cast<const R*>(a.cdep);
   // centred zero-padded row, element i = (n - n0) mod K holding c_n X[l][n],
@@ -249,11 +317,11 @@ row_forward_kernel(RowArgs<R> a) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * nthr;
-      if (i < K) buf[swz(row_pos(i, a), sw)] = v[u];
+      if (i < K) buf[swz(row_pos(i, rad, perm), sw)] = v[u];
     }
   }
   __syncthreads();
-  fft_dit<false>(buf, 1, a.rad, tw, sw);
+  fft_dit<false>(buf, 1, rad, tw, sw);
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
   V* S = reinterpret_cast<V*>(a.out) + (size_t)l * M;
   constexpr int UM = 2;
@@ -269,7 +337,7 @@ row_forward_kernel(RowArgs<R> a) {
       const int mm = m0 + u * nthr;
       if (mm >= M) continue;
       R w[J];
-      kb_weights<R, J>(R(e[u].frac), a, w);
+      kb_weights<R, J>(R(e[u].frac), a0, w);
       V acc = cmk<V>(R(0), R(0));
       const int pc = e[u].cell & 0xFFFF;
 #pragma unroll
@@ -285,20 +353,35 @@ row_forward_kernel(RowArgs<R> a) {
   }
 }
 
-template <class R, int J>
+template <class R, int J, bool BAT>
 __global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
-row_adjoint_kernel(RowArgs<R> a) {
+row_forward_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<RowArgs<R>> B) {
+  if constexpr (!BAT) {
+    row_forward_body<R, J>(a0, a0.rad, (int)blockIdx.x, a0);
+  } else {
+    int blk;
+    const RowArgs<R>& A = *resolve_args(&a0, B, blk);
+    __shared__ Radix rad;
+    copy_radix(&rad, &A.rad);
+    __syncthreads();
+    row_forward_body<R, J>(A, rad, blk, a0);
+  }
+}
+
+template <class R, int J>
+__device__ __forceinline__ void row_adjoint_body(const RowArgs<R>& a, const Radix& rad, int blk, const RowArgs<R>& a0) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
   V* tws = buf + a.K;
-  const int l = blockIdx.x;
+  const int l = blk;
   const int lp = l <= a.nx - l ? l : a.nx - l;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
   const bool sw = (K & 15) == 0;
-  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
+  const int* perm = a.perm;
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), rad);
   for (int i = tid; i < K; i += nthr) buf[i] = cmk<V>(R(0), R(0));
   __syncthreads();
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
@@ -322,7 +405,7 @@ row_adjoint_kernel(RowArgs<R> a) {
       if (mm >= M) continue;
       const V v = cmulc(r[u], cmk<V>(R(e[u].fre), R(e[u].fim)));
       R w[J];
-      kb_weights<R, J>(R(e[u].frac), a, w);
+      kb_weights<R, J>(R(e[u].frac), a0, w);
       const int pc = e[u].cell & 0xFFFF;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
@@ -335,13 +418,28 @@ row_adjoint_kernel(RowArgs<R> a) {
     }
   }
   __syncthreads();
-  fft_dif<true>(buf, 1, a.rad, tw, sw);
+  fft_dif<true>(buf, 1, rad, tw, sw);
   const R* cdep = reinterpret_cast<const R*>(a.cdep);
   V* Wo = reinterpret_cast<V*>(a.out) + (size_t)l * nz;
   for (int n = tid; n < nz; n += nthr) {
     int i = n - n0;
     if (i < 0) i += K;
-    Wo[n] = cscale(buf[swz(row_pos(i, a), sw)], cdep[n]);
+    Wo[n] = cscale(buf[swz(row_pos(i, rad, perm), sw)], cdep[n]);
+  }
+}
+
+template <class R, int J, bool BAT>
+__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
+row_adjoint_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<RowArgs<R>> B) {
+  if constexpr (!BAT) {
+    row_adjoint_body<R, J>(a0, a0.rad, (int)blockIdx.x, a0);
+  } else {
+    int blk;
+    const RowArgs<R>& A = *resolve_args(&a0, B, blk);
+    __shared__ Radix rad;
+    copy_radix(&rad, &A.rad);
+    __syncthreads();
+    row_adjoint_body<R, J>(A, rad, blk, a0);
   }
 }
 
@@ -353,28 +451,28 @@ row_adjoint_kernel(RowArgs<R> a) {
 // conflict-free scatter (each cell written once); cell c then sums its run in a
 // fixed order, so the result is deterministic.
 template <class R, int J>
-__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
-row_adjoint_gather_kernel(RowArgs<R> a) {
+__device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, const Radix& rad, int blk, const RowArgs<R>& a0) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
   V* buf = reinterpret_cast<V*>(smem_raw);
   V* tws = buf + K;
-  V* sv = tws + a.rad.tw_lo + a.rad.tw_hi;                          // [M] conj(f) R
+  V* sv = tws + rad.tw_lo + rad.tw_hi;                          // [M] conj(f) R
   // FP32 with kGatherPrecomp: the J weights of every pixel [M][J]; otherwise frac [M]
   R* sfrac = reinterpret_cast<R*>(sv + M);
   constexpr bool kPre = kGatherPrecomp && sizeof(R) == 4;
   float* spoly = reinterpret_cast<float*>(sfrac + (kPre ? M * J : M));   // [J][kKbDeg + 1]
   uint16_t* su = reinterpret_cast<uint16_t*>(spoly + J * (kKbDeg + 1));   // [M]
   uint16_t* sfirst = su + M + (M & 1);                              // [span + 1]
-  const int l = blockIdx.x;
+  const int l = blk;
   const int lp = l <= a.nx - l ? l : a.nx - l;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool sw = (K & 15) == 0;
-  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), a.rad);
+  const int* perm = a.perm;
+  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), rad);
   if (sizeof(R) == 4)
-    for (int i = tid; i < J * (kKbDeg + 1); i += nthr) spoly[i] = a.kbpoly[i / (kKbDeg + 1)][i % (kKbDeg + 1)];
+    for (int i = tid; i < J * (kKbDeg + 1); i += nthr) spoly[i] = a0.kbpoly[i / (kKbDeg + 1)][i % (kKbDeg + 1)];
   const int4 meta = a.rowmeta[lp];
   const int base = meta.x, span = meta.y, dir = meta.z;
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
@@ -400,7 +498,7 @@ row_adjoint_gather_kernel(RowArgs<R> a) {
         sv[sidx] = cmulc(r[q], cmk<V>(R(e[q].fre), R(e[q].fim)));
         if constexpr (kPre) {
           R w[J];
-          kb_weights<R, J>(R(e[q].frac), a, w);
+          kb_weights<R, J>(R(e[q].frac), a0, w);
 #pragma unroll
           for (int j = 0; j < J; ++j) sfrac[sidx * J + j] = w[j];
         } else {
@@ -444,7 +542,7 @@ row_adjoint_gather_kernel(RowArgs<R> a) {
         } else {
           const double uu = sfrac[sidx] + double(J / 2 - 1 - j);
           const double rr = 1.0 - (2.0 * uu / J) * (2.0 * uu / J);
-          w = rr < 0.0 ? 0.0 : cyl_bessel_i0(a.alpha * sqrt(rr)) * a.inv_i0a;
+          w = rr < 0.0 ? 0.0 : cyl_bessel_i0(a0.alpha * sqrt(rr)) * a0.inv_i0a;
         }
         const V v = sv[sidx];
         acc.x += w * v.x;
@@ -454,13 +552,28 @@ row_adjoint_gather_kernel(RowArgs<R> a) {
     buf[swz(i, sw)] = acc;
   }
   __syncthreads();
-  fft_dif<true>(buf, 1, a.rad, tw, sw);
+  fft_dif<true>(buf, 1, rad, tw, sw);
   const R* cdep = reinterpret_cast<const R*>(a.cdep);
   V* Wo = reinterpret_cast<V*>(a.out) + (size_t)l * nz;
   for (int n = tid; n < nz; n += nthr) {
     int i = n - n0;
     if (i < 0) i += K;
-    Wo[n] = cscale(buf[swz(row_pos(i, a), sw)], cdep[n]);
+    Wo[n] = cscale(buf[swz(row_pos(i, rad, perm), sw)], cdep[n]);
+  }
+}
+
+template <class R, int J, bool BAT>
+__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
+row_adjoint_gather_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<RowArgs<R>> B) {
+  if constexpr (!BAT) {
+    row_adjoint_gather_body<R, J>(a0, a0.rad, (int)blockIdx.x, a0);
+  } else {
+    int blk;
+    const RowArgs<R>& A = *resolve_args(&a0, B, blk);
+    __shared__ Radix rad;
+    copy_radix(&rad, &A.rad);
+    __syncthreads();
+    row_adjoint_gather_body<R, J>(A, rad, blk, a0);
   }
 }
 
@@ -508,7 +621,7 @@ template <class R, int MODE>
 int launch_lateral_args(mbir_plan p, const LatArgs<R>& a, int cols, cudaStream_t st) {
   {
     ProfScope ps_(p, lat_class(MODE), st);
-    lateral_kernel<R, MODE><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a);
+    lateral_kernel<R, MODE, false><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a, no_batch<LatArgs<R>>());
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -560,13 +673,13 @@ template <class R>
 int launch_row(mbir_plan p, bool adjoint, const void* in, void* out, cudaStream_t st) {
   RowArgs<R> a = row_args<R>(p, in, out);
   const size_t gsmem = row_gather_smem<R>(p);
-  if (adjoint && !kAdjAtomic && p->gather_ok && gsmem <= (size_t)227 * 1024) {
+  if (adjoint && !kAdjAtomic && p->gather_ok && gsmem <= (size_t)kMaxDynSmem) {
     {
       ProfScope ps_(p, PC_ROW_ADJ, st);
       switch (p->J) {
-        case 4: row_adjoint_gather_kernel<R, 4><<<p->nx, kRowThreads, gsmem, st>>>(a); break;
-        case 6: row_adjoint_gather_kernel<R, 6><<<p->nx, kRowThreads, gsmem, st>>>(a); break;
-        default: row_adjoint_gather_kernel<R, 8><<<p->nx, kRowThreads, gsmem, st>>>(a); break;
+        case 4: row_adjoint_gather_kernel<R, 4, false><<<p->nx, kRowThreads, gsmem, st>>>(a, no_batch<RowArgs<R>>()); break;
+        case 6: row_adjoint_gather_kernel<R, 6, false><<<p->nx, kRowThreads, gsmem, st>>>(a, no_batch<RowArgs<R>>()); break;
+        default: row_adjoint_gather_kernel<R, 8, false><<<p->nx, kRowThreads, gsmem, st>>>(a, no_batch<RowArgs<R>>()); break;
       }
     }
     MBIR_LAUNCH_CHECK();
@@ -577,16 +690,16 @@ int launch_row(mbir_plan p, bool adjoint, const void* in, void* out, cudaStream_
     ProfScope ps_(p, adjoint ? PC_ROW_ADJ : PC_ROW_FWD, st);
     switch (p->J) {
       case 4:
-        if (adjoint) row_adjoint_kernel<R, 4><<<p->nx, kRowThreads, smem, st>>>(a);
-        else row_forward_kernel<R, 4><<<p->nx, kRowThreads, smem, st>>>(a);
+        if (adjoint) row_adjoint_kernel<R, 4, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
+        else row_forward_kernel<R, 4, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
         break;
       case 6:
-        if (adjoint) row_adjoint_kernel<R, 6><<<p->nx, kRowThreads, smem, st>>>(a);
-        else row_forward_kernel<R, 6><<<p->nx, kRowThreads, smem, st>>>(a);
+        if (adjoint) row_adjoint_kernel<R, 6, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
+        else row_forward_kernel<R, 6, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
         break;
       default:
-        if (adjoint) row_adjoint_kernel<R, 8><<<p->nx, kRowThreads, smem, st>>>(a);
-        else row_forward_kernel<R, 8><<<p->nx, kRowThreads, smem, st>>>(a);
+        if (adjoint) row_adjoint_kernel<R, 8, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
+        else row_forward_kernel<R, 8, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
         break;
     }
   }
@@ -675,26 +788,42 @@ template <class R>
 static int configure_t() {
   const int lat = (int)(sizeof(cplx_t<R>) * (kLatElems + 512));
   const int row = (int)(sizeof(cplx_t<R>) * (kMaxFFT + 512));
-  const int gat = 227 * 1024;
+  const int gat = kMaxDynSmem;
 #define MBIR_SMEM_ATTR(fn, bytes)                                                                  \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));    \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_FWD>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_INV>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_R2C_MASK>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2R_INV_MASK>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_FWD>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_L1>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V>), lat);
-  MBIR_SMEM_ATTR((row_forward_kernel<R, 4>), row);
-  MBIR_SMEM_ATTR((row_forward_kernel<R, 6>), row);
-  MBIR_SMEM_ATTR((row_forward_kernel<R, 8>), row);
-  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 4>), row);
-  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 6>), row);
-  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 8>), row);
-  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 4>), gat);
-  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6>), gat);
-  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8>), gat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_FWD, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_FWD, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_INV, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_INV, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_R2C_MASK, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_R2C_MASK, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2R_INV_MASK, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2R_INV_MASK, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_FWD, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_FWD, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_L1, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_L1, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V, true>), lat);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 4, false>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 4, true>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 6, false>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 6, true>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 8, false>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 8, true>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 4, false>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 4, true>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 6, false>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 6, true>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 8, false>), row);
+  MBIR_SMEM_ATTR((row_adjoint_kernel<R, 8, true>), row);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 4, false>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 4, true>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6, false>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6, true>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, false>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, true>), gat);
 #undef MBIR_SMEM_ATTR
   return MBIR_OK;
 }
@@ -727,3 +856,123 @@ int mbir_adjoint(mbir_plan p, const void* y, const uint8_t* mask, void* x, void*
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ batched launches
+//
+// Helpers for the batch engine (batch.cu): build a scan's argument block into
+// host memory and launch one stage over a device array of such blocks.
+
+namespace mbir {
+
+size_t lat_args_bytes(int precision) {
+  return precision == MBIR_FP64 ? sizeof(LatArgs<double>) : sizeof(LatArgs<float>);
+}
+size_t row_args_bytes(int precision) {
+  return precision == MBIR_FP64 ? sizeof(RowArgs<double>) : sizeof(RowArgs<float>);
+}
+size_t lat_smem_bytes(mbir_plan p) {
+  return p->precision == MBIR_FP64 ? lat_smem<double>(p) : lat_smem<float>(p);
+}
+size_t row_smem_bytes(mbir_plan p, int adjoint_gather) {
+  if (p->precision == MBIR_FP64) return adjoint_gather ? row_gather_smem<double>(p) : row_smem<double>(p);
+  return adjoint_gather ? row_gather_smem<float>(p) : row_smem<float>(p);
+}
+bool plan_uses_gather(mbir_plan p) {
+  return !kAdjAtomic && p->gather_ok && row_smem_bytes(p, 1) <= (size_t)kMaxDynSmem;
+}
+
+template <class R>
+static void fill_lat_t(mbir_plan p, const LatFill& f, void* dst) {
+  LatArgs<R> a = lat_args<R>(p, f.in, f.out, f.mask, f.cols, R(f.scale));
+  a.y = reinterpret_cast<const R*>(f.y);
+  a.pz = reinterpret_cast<R*>(f.pz);
+  a.r = reinterpret_cast<R*>(f.r);
+  a.z1 = f.z1;
+  a.z2 = f.z2;
+  a.vout = f.vout;
+  a.mu = R(0);
+  a.delta = R(f.delta);
+  a.tau = R(f.tau);
+  a.partial = f.partial;
+  memcpy(dst, &a, sizeof(a));
+}
+
+void fill_lat_args(mbir_plan p, const LatFill& f, void* dst) {
+  if (p->precision == MBIR_FP64) fill_lat_t<double>(p, f, dst);
+  else fill_lat_t<float>(p, f, dst);
+}
+
+void fill_row_args(mbir_plan p, const void* in, void* out, void* dst) {
+  if (p->precision == MBIR_FP64) {
+    RowArgs<double> a = row_args<double>(p, in, out);
+    memcpy(dst, &a, sizeof(a));
+  } else {
+    RowArgs<float> a = row_args<float>(p, in, out);
+    memcpy(dst, &a, sizeof(a));
+  }
+}
+
+template <class R, int MODE>
+static void lat_batch_t(const BatchLaunch& L, cudaStream_t st) {
+  BatchRef<LatArgs<R>> B;
+  B.args = reinterpret_cast<const LatArgs<R>*>(L.dargs);
+  B.off = L.doff;
+  B.n = L.n;
+  B.set_mu = L.set_mu;
+  B.mu = L.mu;
+  LatArgs<R> a0;
+  memcpy(&a0, L.host0, sizeof(a0));
+  lateral_kernel<R, MODE, true><<<L.total, kLatThreads, L.smem, st>>>(a0, B);
+}
+
+int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st) {
+  if (L.total <= 0) return MBIR_OK;
+#define MBIR_LAT_CASE(M)                                                         \
+  case M:                                                                        \
+    if (precision == MBIR_FP64) lat_batch_t<double, M>(L, st);                   \
+    else lat_batch_t<float, M>(L, st);                                           \
+    break;
+  switch (mode) {
+    MBIR_LAT_CASE(LAT_C2C_FWD)
+    MBIR_LAT_CASE(LAT_C2C_INV)
+    MBIR_LAT_CASE(LAT_R2C_MASK)
+    MBIR_LAT_CASE(LAT_C2R_INV_MASK)
+    MBIR_LAT_CASE(LAT_SOLVE_FWD)
+    MBIR_LAT_CASE(LAT_SOLVE_ADJ_L1)
+    MBIR_LAT_CASE(LAT_SOLVE_ADJ_V)
+    default: return MBIR_ERR_INVALID;
+  }
+#undef MBIR_LAT_CASE
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+template <class R, int J>
+static void row_batch_t(int kind, const BatchLaunch& L, cudaStream_t st) {
+  BatchRef<RowArgs<R>> B;
+  B.args = reinterpret_cast<const RowArgs<R>*>(L.dargs);
+  B.off = L.doff;
+  B.n = L.n;
+  B.set_mu = 0;
+  B.mu = 0.0;
+  RowArgs<R> a0;
+  memcpy(&a0, L.host0, sizeof(a0));
+  if (kind == 0) row_forward_kernel<R, J, true><<<L.total, kRowThreads, L.smem, st>>>(a0, B);
+  else if (kind == 1) row_adjoint_gather_kernel<R, J, true><<<L.total, kRowThreads, L.smem, st>>>(a0, B);
+  else row_adjoint_kernel<R, J, true><<<L.total, kRowThreads, L.smem, st>>>(a0, B);
+}
+
+// kind: 0 forward, 1 adjoint gather, 2 adjoint with atomics
+int batch_row(int kind, int precision, int J, const BatchLaunch& L, cudaStream_t st) {
+  if (L.total <= 0) return MBIR_OK;
+  const bool f64 = precision == MBIR_FP64;
+  switch (J) {
+    case 4: f64 ? row_batch_t<double, 4>(kind, L, st) : row_batch_t<float, 4>(kind, L, st); break;
+    case 6: f64 ? row_batch_t<double, 6>(kind, L, st) : row_batch_t<float, 6>(kind, L, st); break;
+    default: f64 ? row_batch_t<double, 8>(kind, L, st) : row_batch_t<float, 8>(kind, L, st); break;
+  }
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+}  // namespace mbir

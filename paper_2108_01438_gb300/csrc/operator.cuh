@@ -32,6 +32,7 @@ constexpr int kLatElems = MBIR_LAT_ELEMS;       // nx * columns staged per later
 constexpr int kRowThreads = MBIR_ROW_THREADS;   // row (NUFFT) block size
 constexpr int kRowMinBlocks = MBIR_ROW_MINB;    // resident CTAs per SM the register budget targets
 constexpr int kLatMinBlocks = MBIR_LAT_MINB;
+constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
 constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics
 

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "solve_state.cuh"
 
 namespace mbir {
 
@@ -29,21 +30,6 @@ int ensure_wavelet_scratch(mbir_plan p);
 
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
-
-struct SolveState {
-  size_t nimg = 0, nmeas = 0;
-  void* zA = nullptr;
-  void* zB = nullptr;
-  void* v = nullptr;
-  void* pz = nullptr;
-  void* r = nullptr;
-  double* part_data = nullptr;
-  double* part_reg = nullptr;
-  double* part_tmp = nullptr;
-  double* scal = nullptr;
-  double* objtrace = nullptr;
-  int n_data = 0, n_reg = 0, trace_cap = 0;
-};
 
 // ------------------------------------------------------------------ kernels
 
@@ -212,7 +198,7 @@ void destroy_solve_state(mbir_plan p) {
   p->solve = nullptr;
 }
 
-static int ensure_state(mbir_plan p, int trace_cap) {
+int ensure_state(mbir_plan p, int trace_cap) {
   if (p->solve && p->solve->trace_cap >= trace_cap) return MBIR_OK;
   if (p->solve) {
     cudaFree(p->solve->objtrace);

@@ -39,7 +39,22 @@ struct WArgs {
   R tau;
   int thresh;       // analysis: 0 none, 1 details, 2 details and LL
   double* partial;  // analysis with thresh: sum |soft(c)| per CTA
+  int gx;           // CTAs along the columns (the grid is flattened row-major)
 };
+
+template <class Args>
+__device__ __forceinline__ Args resolve_wargs(const Args& a0, const BatchRef<Args>& B, int& blk) {
+  blk = blockIdx.x;
+  if (B.args == nullptr) return a0;
+  int lo = 0, hi = B.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.off[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  blk -= B.off[lo];
+  return B.args[lo];
+}
 
 template <class R>
 __device__ __forceinline__ cplx_t<R> soft_c(cplx_t<R> c, R tau, double& acc) {
@@ -67,8 +82,12 @@ __device__ __forceinline__ double block_sum_w(double v) {
 }
 
 template <class R>
-__global__ void __launch_bounds__(kWavThreads) dwt_fwd_kernel(WArgs<R> a) {
+__global__ void __launch_bounds__(kWavThreads)
+dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B) {
   using V = cplx_t<R>;
+  int blk;
+  const WArgs<R> a = resolve_wargs(arg0, B, blk);
+  const int bx = blk % a.gx, by = blk / a.gx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tin = reinterpret_cast<V*>(smem_raw);              // [kFwdRows][kFwdCols]
   V* tL = tin + kFwdRows * kFwdCols;                    // [kFwdRows][kFwdTB]
@@ -80,7 +99,7 @@ __global__ void __launch_bounds__(kWavThreads) dwt_fwd_kernel(WArgs<R> a) {
     g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
   }
   const int P = a.P, N = a.N;
-  const int a0 = blockIdx.y * kFwdTA, b0 = blockIdx.x * kFwdTB;
+  const int a0 = by * kFwdTA, b0 = bx * kFwdTB;
   const V* in = reinterpret_cast<const V*>(a.in);
   // stage the input tile with every load of a thread in flight at once
   constexpr int kFwdPer = (kFwdRows * kFwdCols + kWavThreads - 1) / kWavThreads;
@@ -147,13 +166,17 @@ __global__ void __launch_bounds__(kWavThreads) dwt_fwd_kernel(WArgs<R> a) {
   }
   if (a.partial) {
     const double t = block_sum_w(acc);
-    if (tid == 0) a.partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    if (tid == 0) a.partial[blk] = t;
   }
 }
 
 template <class R>
-__global__ void __launch_bounds__(kWavThreads) dwt_inv_kernel(WArgs<R> a) {
+__global__ void __launch_bounds__(kWavThreads)
+dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B) {
   using V = cplx_t<R>;
+  int blk;
+  const WArgs<R> a = resolve_wargs(arg0, B, blk);
+  const int bx = blk % a.gx, by = blk / a.gx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* cLL = reinterpret_cast<V*>(smem_raw);              // [kInvRows][kInvCols] each
   V* cLH = cLL + kInvRows * kInvCols;
@@ -168,7 +191,7 @@ __global__ void __launch_bounds__(kWavThreads) dwt_inv_kernel(WArgs<R> a) {
     g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
   }
   const int P = a.P, N = a.N, Ph = P / 2, Nh = N / 2;
-  const int r0 = blockIdx.y * kInvTR, c0 = blockIdx.x * kInvTC;
+  const int r0 = by * kInvTR, c0 = bx * kInvTC;
   const V* ll = reinterpret_cast<const V*>(a.in);
   const V* coef = reinterpret_cast<const V*>(a.coef);
   constexpr int kInvPer = (kInvRows * kInvCols + kWavThreads - 1) / kWavThreads;
@@ -290,10 +313,11 @@ static int analysis_t(mbir_plan p, const void* in, void* coef, bool thresh, R ta
     a.tau = tau;
     a.thresh = thresh ? (lev == 2 ? 2 : 1) : 0;
     a.partial = thresh ? part : nullptr;
-    dim3 grid((N / 2 + kFwdTB - 1) / kFwdTB, (P / 2 + kFwdTA - 1) / kFwdTA);
-    { ProfScope ps_(p, PC_DWT_FWD, st); dwt_fwd_kernel<R><<<grid, kWavThreads, fwd_smem(sizeof(cplx_t<R>)), st>>>(a); }
+    const int gx = (N / 2 + kFwdTB - 1) / kFwdTB, gy = (P / 2 + kFwdTA - 1) / kFwdTA;
+    a.gx = gx;
+    { ProfScope ps_(p, PC_DWT_FWD, st); dwt_fwd_kernel<R><<<gx * gy, kWavThreads, fwd_smem(sizeof(cplx_t<R>)), st>>>(a, no_batch<WArgs<R>>()); }
     MBIR_LAUNCH_CHECK();
-    if (part) part += grid.x * grid.y;
+    if (part) part += gx * gy;
     src = lls[lev];
     sstride = lstr[lev];
     P /= 2;
@@ -323,8 +347,9 @@ static int synthesis_t(mbir_plan p, const void* coef, void* out, cudaStream_t st
     a.tau = R(0);
     a.thresh = 0;
     a.partial = nullptr;
-    dim3 grid((a.N + kInvTC - 1) / kInvTC, (a.P + kInvTR - 1) / kInvTR);
-    { ProfScope ps_(p, PC_DWT_INV, st); dwt_inv_kernel<R><<<grid, kWavThreads, inv_smem(sizeof(cplx_t<R>)), st>>>(a); }
+    const int gx = (a.N + kInvTC - 1) / kInvTC, gy = (a.P + kInvTR - 1) / kInvTR;
+    a.gx = gx;
+    { ProfScope ps_(p, PC_DWT_INV, st); dwt_inv_kernel<R><<<gx * gy, kWavThreads, inv_smem(sizeof(cplx_t<R>)), st>>>(a, no_batch<WArgs<R>>()); }
     MBIR_LAUNCH_CHECK();
   }
   return MBIR_OK;
@@ -470,3 +495,88 @@ int mbir_wavelet(mbir_plan p, int32_t inverse, const void* in, void* out, void* 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ batched launches
+
+namespace mbir {
+
+size_t dwt_args_bytes(int precision) {
+  return precision == MBIR_FP64 ? sizeof(WArgs<double>) : sizeof(WArgs<float>);
+}
+
+int dwt_level_ctas(int P, int N, int inverse) {
+  if (inverse) return ((N + kInvTC - 1) / kInvTC) * ((P + kInvTR - 1) / kInvTR);
+  return ((N / 2 + kFwdTB - 1) / kFwdTB) * ((P / 2 + kFwdTA - 1) / kFwdTA);
+}
+
+size_t dwt_smem_bytes(int precision, int inverse) {
+  const size_t vs = precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
+  return inverse ? inv_smem(vs) : fwd_smem(vs);
+}
+
+// Argument block of analysis (inverse = 0) or synthesis level `level` (0 = finest)
+// for plan p, laid out like the plan-path launches: analysis reads `in` at level
+// 0 and the plan's low-low scratch above, synthesis writes `out` at level 0.
+template <class R>
+static void fill_dwt_t(mbir_plan p, int level, int inverse, const void* in, void* out, void* coef, double tau,
+                       int thresh, double* partial, void* dst) {
+  const int nx = p->nx, nz = p->nz;
+  void* lls[3] = {p->wv_b1, p->wv_b2, coef};
+  const int lstr[3] = {nz / 2, nz / 4, nz};
+  WArgs<R> a;
+  memset(&a, 0, sizeof(a));
+  a.P = nx >> level;
+  a.N = nz >> level;
+  a.coef = coef;
+  a.cstride = nz;
+  a.h = p->precision == MBIR_FP64 ? reinterpret_cast<const R*>(p->h_db4) : reinterpret_cast<const R*>(p->h_db4f);
+  a.tau = R(tau);
+  a.partial = partial;
+  if (!inverse) {
+    a.in = level == 0 ? in : lls[level - 1];
+    a.istride = level == 0 ? nz : lstr[level - 1];
+    a.out = lls[level];
+    a.ostride = lstr[level];
+    a.thresh = thresh;
+    a.gx = (a.N / 2 + kFwdTB - 1) / kFwdTB;
+  } else {
+    a.in = lls[level];
+    a.istride = lstr[level];
+    a.out = level == 0 ? out : lls[level - 1];
+    a.ostride = level == 0 ? nz : lstr[level - 1];
+    a.thresh = 0;
+    a.partial = nullptr;
+    a.gx = (a.N + kInvTC - 1) / kInvTC;
+  }
+  memcpy(dst, &a, sizeof(a));
+}
+
+void fill_dwt_args(mbir_plan p, int level, int inverse, const void* in, void* out, void* coef, double tau,
+                   int thresh, double* partial, void* dst) {
+  if (p->precision == MBIR_FP64) fill_dwt_t<double>(p, level, inverse, in, out, coef, tau, thresh, partial, dst);
+  else fill_dwt_t<float>(p, level, inverse, in, out, coef, tau, thresh, partial, dst);
+}
+
+template <class R>
+static void dwt_batch_t(int inverse, const BatchLaunch& L, cudaStream_t st) {
+  BatchRef<WArgs<R>> B;
+  B.args = reinterpret_cast<const WArgs<R>*>(L.dargs);
+  B.off = L.doff;
+  B.n = L.n;
+  B.set_mu = 0;
+  B.mu = 0.0;
+  WArgs<R> a0;
+  memcpy(&a0, L.host0, sizeof(a0));
+  if (inverse) dwt_inv_kernel<R><<<L.total, kWavThreads, L.smem, st>>>(a0, B);
+  else dwt_fwd_kernel<R><<<L.total, kWavThreads, L.smem, st>>>(a0, B);
+}
+
+int batch_dwt(int inverse, int precision, const BatchLaunch& L, cudaStream_t st) {
+  if (L.total <= 0) return MBIR_OK;
+  if (precision == MBIR_FP64) dwt_batch_t<double>(inverse, L, st);
+  else dwt_batch_t<float>(inverse, L, st);
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+}  // namespace mbir

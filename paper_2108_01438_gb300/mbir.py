@@ -76,6 +76,8 @@ _SIGNATURES = {
     "mbir_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveOpts), C.c_void_p,
                              C.POINTER(SolveInfo), C.c_void_p]),
+    "mbir_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                   C.POINTER(SolveOpts), C.POINTER(C.c_void_p), C.POINTER(SolveInfo), C.c_void_p]),
     "mbir_lipschitz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
     "mbir_prox": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "mbir_wavelet": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -299,3 +301,34 @@ class Plan:
         if trace:
             d["trace"] = np.array(tr[: info.iters])
         return out, d
+
+
+def solve_batch(plans, ys, masks=None, *, penalties="l1", lams=0.01, relative=True, iters=100,
+                power_iters=30, steps=0.0, outs=None, stream=None):
+    """FISTA on several B-scans in one batched, graph-captured run (mbir_solve_batch).
+
+    plans, ys, masks, outs: sequences (masks entries may be None); penalties, lams and
+    steps: one value for all or one per scan.  Returns (xs, infos)."""
+    import torch
+    n = len(plans)
+    as_list = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * n
+    penalties, lams, steps = as_list(penalties), as_list(lams), as_list(steps)
+    masks = [None] * n if masks is None else list(masks)
+    if outs is None:
+        outs = [torch.zeros((p.nx, p.nz), dtype=p.complex_dtype, device=y.device) for p, y in zip(plans, ys)]
+    for p, y, m, o in zip(plans, ys, masks, outs):
+        p._meas(y, "y")
+        p._mask(m)
+        p._image(o, "out")
+    H = (C.c_void_p * n)(*[p.handle.value for p in plans])
+    Y = (C.c_void_p * n)(*[y.data_ptr() for y in ys])
+    M = (C.c_void_p * n)(*[(m.data_ptr() if m is not None else None) for m in masks])
+    X = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    O = (SolveOpts * n)(*[SolveOpts(PENALTIES[pen], float(lam), int(bool(relative)), int(iters), 0, 0.0,
+                                    int(power_iters), float(st), 0)
+                          for pen, lam, st in zip(penalties, lams, steps)])
+    I = (SolveInfo * n)()
+    _check(lib().mbir_solve_batch(H, n, Y, M, O, X, I, _stream_handle(stream)), "mbir_solve_batch")
+    infos = [dict(iters=I[i].iters, status=I[i].status, lipschitz=I[i].lipschitz, step=I[i].step,
+                  lambda_used=I[i].lambda_used) for i in range(n)]
+    return outs, infos
