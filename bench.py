@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch comparison")
     return ap.parse_args()
 
 
@@ -235,6 +236,62 @@ def traffic_for(cls: str) -> float | None:
     return float(e["dram_bytes_per_launch"])
 
 
+# ------------------------------------------------------------ uneven batch
+
+def batch_comparison(dev, stream, count: int = 64, repeats: int = 2) -> dict:
+    """The uneven-batch workload (64 B-scans, widths 256-2048, depths 1024/2048,
+    l1, 100 iterations, power iteration and relative lambda per scan): one batched,
+    graph-captured solve (mbir_solve_batch) against the same scans solved one at a
+    time with mbir_solve.  B-scans per second for both."""
+    import numpy as np
+    import torch
+
+    from paper_2108_01438_gb300 import mbir, workloads
+
+    wls = workloads.batch_workload(count)
+    plans, ys, ms = [], [], []
+    for wl in wls:
+        p = mbir.Plan(wl["geom"])
+        x = torch.from_numpy(wl["x_true"].astype(np.complex64)).to(dev)
+        m = torch.from_numpy(wl["mask"]).to(dev)
+        clean = p.forward(x, m)
+        sig = torch.sqrt(torch.mean(clean[m == 1].double() ** 2)).item()
+        noise = torch.from_numpy(wl["noise"].astype(np.float32)).to(dev)
+        ys.append((clean + float(sig * 10 ** (-wl["snr_db"] / 20)) * noise * m).contiguous())
+        plans.append(p)
+        ms.append(m)
+    outs = [torch.empty((p.nx, p.nz), dtype=torch.complex64, device=dev) for p in plans]
+    kw = dict(penalties="l1", lams=LAMBDA_FRAC, relative=True, iters=ITERS, power_iters=POWER_ITERS)
+
+    def batched():
+        with torch.cuda.stream(stream):
+            mbir.solve_batch(plans, ys, ms, outs=outs, stream=stream, **kw)
+
+    def sequential():
+        with torch.cuda.stream(stream):
+            for p, y, m, o in zip(plans, ys, ms, outs):
+                p.solve(y, m, penalty="l1", lam=LAMBDA_FRAC, relative=True, iters=ITERS,
+                        power_iters=POWER_ITERS, out=o, stream=stream)
+
+    res = {}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(repeats):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        res[name] = count * repeats / (e0.elapsed_time(e1) / 1e3)
+    for p in plans:
+        p.close()
+    pix = sum(w["geom"]["nx"] * w["geom"]["nz"] for w in wls)
+    return {"workload": f"{count} uneven B-scans, widths 256-2048, depths 1024/2048, l1, {ITERS} iterations",
+            "image_megapixels": round(pix / 1e6, 2), "batched_bscans_per_sec": res["batched"],
+            "sequential_bscans_per_sec": res["sequential"], "speedup": res["batched"] / res["sequential"]}
+
+
 # ------------------------------------------------------------ our arm
 
 def run_ours(args, rank: int, ws: int, local: int) -> None:
@@ -356,6 +413,10 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic, "alg_bytes": alg, "avg_launch_ms": avg_ms}
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_comparison(dev, torch.cuda.Stream(device=dev))
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ot = oracle_timing(sample_iters=2)
@@ -379,6 +440,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
             "kernels_ms_per_launch": {k: v[1] / v[0] for k, v in prof.items()},
+            "batch": batch,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),

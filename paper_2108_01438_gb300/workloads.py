@@ -22,7 +22,7 @@ __all__ = [
     "BASE_SEED", "spectrometer_k", "geometry", "point_scatterers", "beads",
     "mask_full", "mask_ascans", "mask_bernoulli", "mask_equispaced",
     "mask_partial", "unit_noise", "tiny_workload", "full_workload",
-    "smooth_widths",
+    "smooth_widths", "batch_workload",
 ]
 
 
@@ -174,3 +174,33 @@ def full_workload(seed_offset: int = 1) -> dict:
         mask=mask_ascans(nx, m, 0.5, seed + 7), noise=unit_noise(nx, m, seed + 1000), snr_db=25.0,
         penalty="db4", lambda_frac=0.01, iters=100,
     )
+
+
+def batch_workload(count: int = 64, seed_offset: int = 2, widths: tuple[int, int] = (256, 2048),
+                   depths: tuple[int, ...] = (1024, 2048), scatterers: int = 200) -> list[dict]:
+    """Uneven batch: widths drawn uniformly from the 7-smooth multiples of 8 in
+    ``widths``, depth (= spectral pixels) from ``depths``, per-scan focus depth
+    U[0.25, 0.75] of the imaged depth and dispersion up to 30 rad at the band edge,
+    per-element Bernoulli sub-sampling keeping U[0.25, 0.75] of the samples,
+    point-scatterer phantoms, l1, 100 iterations."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    choices = smooth_widths(*widths)
+    out = []
+    for i in range(count):
+        nx = int(rng.choice(choices))
+        nz = int(rng.choice(depths))
+        m = nz
+        focus = float(rng.uniform(0.25, 0.75))
+        a_edge = float(rng.uniform(-30.0, 30.0))
+        b_edge = float(rng.uniform(-10.0, 10.0))
+        keep = float(rng.uniform(0.25, 0.75))
+        d = geometry(nx, nz, m, focus_frac=focus, disp_edge_rad=a_edge)
+        edge = float(np.max(np.abs(d["k"] - d["k0"])))
+        d["disp_b"] = b_edge / edge ** 3
+        s = int(rng.integers(1 << 30))
+        out.append(dict(
+            name=f"batch-{i}-{nx}x{nz}", geom=d, x_true=point_scatterers(nx, nz, scatterers, s),
+            mask=mask_bernoulli(nx, m, keep, s + 1), noise=unit_noise(nx, m, s + 2), snr_db=30.0,
+            penalty="l1", lambda_frac=0.01, iters=100,
+        ))
+    return out
