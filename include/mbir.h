@@ -206,6 +206,51 @@ int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const ui
                      const mbir_solve_opts* opts, void* const* x, mbir_solve_info* info, void* stream);
 
 /*
+ * Serving with continuous batching.  Requests (one B-scan solve each, on any plan
+ * of one precision) are submitted at any time; each mbir_server_step is one tick:
+ * pending requests are admitted in arrival order while the device state they
+ * need (mbir_server_request_bytes) fits the HBM budget (a request larger than the
+ * whole budget fails with MBIR_ERR_OOM), the newly admitted ones run their set-up
+ * (power iteration, lambda rule) as one batch, every active request advances one
+ * FISTA iteration in one batched pass, and requests that reached max_iter or
+ * their relative-objective tolerance (rel_tol, after min_iter) are retired: z is
+ * copied to their x and their state freed.  Iterates, momentum, step size and the
+ * objective history stay on the device.  A request's result does not depend on
+ * the other requests it shared ticks with.  y, mask and x of a request must stay
+ * valid until it is done.  Synchronous (each step waits for its work).
+ */
+typedef struct mbir_server_s* mbir_server;
+
+int mbir_server_create(size_t hbm_budget_bytes, void* stream, mbir_server* out);
+void mbir_server_destroy(mbir_server srv);
+/* *ticket identifies the request in mbir_server_poll. */
+int mbir_server_submit(mbir_server srv, mbir_plan plan, const void* y, const uint8_t* mask,
+                       const mbir_solve_opts* opts, void* x, int64_t* ticket);
+/* One tick; any output pointer may be NULL. */
+int mbir_server_step(mbir_server srv, int32_t* n_active, int32_t* n_pending, int32_t* n_completed);
+/*
+ * *done = 1 once the request finished (its info then filled: iters, status --
+ * MBIR_ERR_NOT_CONVERGED when rel_tol was not met by max_iter, MBIR_ERR_OOM when it
+ * could never fit -- objective F(z^{k-1}) when rel_tol > 0, lipschitz, step,
+ * lambda_used); *latency_s = seconds from submission to completion (or so far).
+ * A finished ticket is released by the poll that reports it.
+ */
+int mbir_server_poll(mbir_server srv, int64_t ticket, int32_t* done, mbir_solve_info* info, double* latency_s);
+int mbir_server_stats(mbir_server srv, size_t* bytes_in_use, size_t* peak_bytes, int64_t* completed);
+/* Device bytes a request on `plan` holds while active. */
+int mbir_server_request_bytes(mbir_plan plan, int32_t penalty, int32_t max_iter, size_t* bytes);
+
+/*
+ * Host-only replay of the server's admission rule (no GPU): request i arrives at
+ * tick arrive_tick[i] (non-decreasing), needs bytes[i] and stays service_ticks[i]
+ * ticks once admitted.  Fills admit_tick / done_tick (-1 for requests larger than
+ * the budget) and the peak bytes held.
+ */
+int mbir_admission_simulate(size_t budget, int32_t n, const int64_t* bytes, const int32_t* arrive_tick,
+                            const int32_t* service_ticks, int32_t* admit_tick, int32_t* done_tick,
+                            int64_t* peak_bytes);
+
+/*
  * lambda_max(Phi^H Phi) for this plan and mask by power iteration from a fixed
  * pseudo-random start (counter-based hash of the pixel index), FP64 norms
  * (step-size bound of Sec. 2.3).  Writes the estimate to *out (host).  Synchronous.

@@ -2,19 +2,20 @@
 // every stage of the path -- the operator passes, the FISTA epilogues, the
 // wavelet levels, the power iteration and the lambda rule -- runs as ONE launch
 // over all scans, each CTA finding its scan from a prefix table of CTA offsets.
-// The FISTA loop (Sec. 2.3, Eq. alg) is captured once into a CUDA graph and
-// replayed.  A scan runs exactly the same kernel code whatever it is batched
-// with (the adjoint gather is deterministic), so its result does not depend on
-// the mix.
+// A fixed-count FISTA loop (Sec. 2.3, Eq. alg) is captured once into a CUDA graph
+// and replayed; the serving loop instead advances scans that sit at different
+// iteration counts one batched iteration at a time.  A scan runs exactly the
+// same kernel code whatever it is batched with (the adjoint gather is
+// deterministic), so its result does not depend on the mix.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "operator.cuh"
-#include "solve_state.cuh"
 
 namespace mbir {
 
@@ -151,482 +152,628 @@ __global__ void b_max_finalize(const ScanVec* sv, int nb) {
   if (threadIdx.x == 0) s.scal[4] = M;
 }
 
-// ------------------------------------------------------------------ engine
 
-struct BScan {
-  mbir_plan p;
-  const void* y;
-  const uint8_t* mask;
-  void* x;
-  mbir_solve_opts o;
-  double L, lam, delta, tau;
+// Objective of each scan: out = 1/2 sum(part_data) + lam * sum(part_reg), written to
+// the scan's trace entry and to the engine's per-slot array.
+struct ObjArgs {
+  const double* part_data;
+  int n_data;
+  const double* part_reg;
+  int n_reg;
+  double lam;
+  double* trace_out;
+  double* slot_out;
 };
 
-class Engine {
- public:
-  Engine(std::vector<BScan>& scans, cudaStream_t st) : sc_(scans), st_(st) {}
-  ~Engine() {
-    cudaFree(dbuf_);
-    cudaFreeHost(hbuf_);
+__global__ void b_objective(const ObjArgs* oa) {
+  const ObjArgs o = oa[blockIdx.x];
+  double s = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < o.n_data; i += blockDim.x) s += o.part_data[i];
+  for (int i = threadIdx.x; i < o.n_reg; i += blockDim.x) t += o.part_reg[i];
+  const double S = bsum(s), T = bsum(t);
+  if (threadIdx.x == 0) {
+    const double f = 0.5 * S + o.lam * T;
+    if (o.trace_out) *o.trace_out = f;
+    *o.slot_out = f;
   }
+}
 
-  int prepare() {
-    prec_ = sc_[0].p->precision;
-    J_ = sc_[0].p->J;
-    gather_ = true;
-    for (auto& s : sc_) {
-      if (s.p->precision != prec_ || s.p->J != J_ || s.p->alpha != sc_[0].p->alpha) return MBIR_ERR_INVALID;
-      if (s.p->device != sc_[0].p->device) return MBIR_ERR_INVALID;
-      gather_ = gather_ && plan_uses_gather(s.p);
-      int rc = ensure_state(s.p, s.o.max_iter);
-      if (rc) return rc;
-      if (s.o.penalty == MBIR_PENALTY_DB4) {
-        if (!wavelet_supported(s.p->nx, s.p->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;
-        rc = ensure_wavelet_scratch(s.p);
-        if (rc) return rc;
-      }
-    }
-    esz_ = prec_ == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
-    rsz_ = prec_ == MBIR_FP64 ? sizeof(double) : sizeof(float);
-    return MBIR_OK;
+// ------------------------------------------------------------------ contexts
+
+int plan_ctx(mbir_plan p, int penalty, int trace_cap, Ctx* out) {
+  int rc = ensure_state(p, trace_cap);
+  if (rc) return rc;
+  if (penalty == MBIR_PENALTY_DB4) {
+    if (!wavelet_supported(p->nx, p->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;
+    rc = ensure_wavelet_scratch(p);
+    if (rc) return rc;
   }
+  SolveState* S = p->solve;
+  Ctx c;
+  c.wsA = p->wsA;
+  c.wsB = p->wsB;
+  c.zA = S->zA;
+  c.zB = S->zB;
+  c.v = S->v;
+  c.pz = S->pz;
+  c.r = S->r;
+  c.wv_b1 = p->wv_b1;
+  c.wv_b2 = p->wv_b2;
+  c.wv_coef = p->wv_coef;
+  c.part_data = S->part_data;
+  c.part_reg = S->part_reg;
+  c.part_tmp = S->part_tmp;
+  c.scal = S->scal;
+  c.objtrace = S->objtrace;
+  c.n_data = S->n_data;
+  c.n_reg = S->n_reg;
+  c.trace_cap = S->trace_cap;
+  c.nimg = S->nimg;
+  c.nmeas = S->nmeas;
+  c.owned = false;
+  *out = c;
+  return MBIR_OK;
+}
 
-  // ---- stage recording: argument blocks are appended to a host staging buffer,
-  // uploaded once, then launched from the device copy.
-  struct Stage {
-    int kind;   // 0 lateral, 1 row, 2 dwt analysis, 3 dwt synthesis
-    int mode;   // lateral mode / row kind
-    size_t arg_off, off_off;
-    int n, total;
-    size_t smem;
-    int uses_mu;
+static int reg_partials(mbir_plan p) {
+  int nr = lateral_grid(p, p->nz);
+  if (wavelet_supported(p->nx, p->nz)) nr = std::max(nr, wavelet_partial_count(p->nx, p->nz));
+  return nr;
+}
+
+size_t ctx_bytes(mbir_plan p, int penalty, int trace_cap) {
+  const size_t es = p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t rs = p->precision == MBIR_FP64 ? sizeof(double) : sizeof(float);
+  const size_t img = (size_t)p->nx * p->nz, meas = (size_t)p->nx * p->m;
+  size_t b = 2 * es * p->ws_elems + 3 * es * img + 2 * rs * meas;
+  if (penalty == MBIR_PENALTY_DB4) b += es * (img / 4 + img / 16 + img);
+  b += sizeof(double) * ((size_t)lateral_grid(p, p->m) + reg_partials(p) + 2 * 1024 + 16 + trace_cap);
+  return b;
+}
+
+void ctx_free(Ctx* c) {
+  if (!c->owned) return;
+  void* ptrs[] = {c->wsA, c->wsB, c->zA, c->zB, c->v, c->pz, c->r, c->wv_b1, c->wv_b2, c->wv_coef,
+                  c->part_data, c->part_reg, c->part_tmp, c->scal, c->objtrace};
+  for (void* q : ptrs) cudaFree(q);
+  *c = Ctx();
+}
+
+int ctx_alloc(mbir_plan p, int penalty, int trace_cap, Ctx* out) {
+  Ctx c;
+  c.owned = true;
+  const size_t es = p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t rs = p->precision == MBIR_FP64 ? sizeof(double) : sizeof(float);
+  c.nimg = (size_t)p->nx * p->nz;
+  c.nmeas = (size_t)p->nx * p->m;
+  c.n_data = lateral_grid(p, p->m);
+  c.n_reg = reg_partials(p);
+  c.trace_cap = trace_cap;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** q, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(q, bytes);
   };
-
-  size_t push(const void* data, size_t bytes) {
-    const size_t at = (hlen_ + 15) & ~size_t(15);
-    if (at + bytes > hcap_) grow(at + bytes);
-    if (grow_failed_ || at + bytes > hcap_) {
-      grow_failed_ = true;
-      return 0;
-    }
-    memcpy(hbuf_ + at, data, bytes);
-    hlen_ = at + bytes;
-    return at;
+  A(&c.wsA, es * p->ws_elems);
+  A(&c.wsB, es * p->ws_elems);
+  A(&c.zA, es * c.nimg);
+  A(&c.zB, es * c.nimg);
+  A(&c.v, es * c.nimg);
+  A(&c.pz, rs * c.nmeas);
+  A(&c.r, rs * c.nmeas);
+  if (penalty == MBIR_PENALTY_DB4) {
+    A(&c.wv_b1, es * (c.nimg / 4));
+    A(&c.wv_b2, es * (c.nimg / 16));
+    A(&c.wv_coef, es * c.nimg);
   }
-
-  void grow(size_t need) {
-    size_t cap = hcap_ ? hcap_ : (1 << 16);
-    while (cap < need) cap *= 2;
-    unsigned char* nb = nullptr;
-    if (cudaMallocHost(&nb, cap) != cudaSuccess) {
-      nb = nullptr;
-      grow_failed_ = true;
-      return;
-    }
-    if (hbuf_) {
-      memcpy(nb, hbuf_, hlen_);
-      cudaFreeHost(hbuf_);
-    }
-    hbuf_ = nb;
-    hcap_ = cap;
+  A((void**)&c.part_data, sizeof(double) * c.n_data);
+  A((void**)&c.part_reg, sizeof(double) * c.n_reg);
+  A((void**)&c.part_tmp, sizeof(double) * 2 * 1024);
+  A((void**)&c.scal, sizeof(double) * 16);
+  A((void**)&c.objtrace, sizeof(double) * std::max(trace_cap, 1));
+  if (e != cudaSuccess) {
+    ctx_free(&c);
+    return set_cuda_error(e, "request context allocation");
   }
+  *out = c;
+  return MBIR_OK;
+}
 
-  // lateral stage over the scans `idx`
-  template <class F>
-  int add_lateral(std::vector<Stage>& out, int mode, const std::vector<int>& idx, F make, bool uses_mu) {
-    if (idx.empty()) return MBIR_OK;
-    const size_t ab = lat_args_bytes(prec_);
-    std::vector<unsigned char> blocks(ab * idx.size());
-    std::vector<int> off(idx.size() + 1, 0);
-    size_t smem = 0;
-    for (size_t i = 0; i < idx.size(); ++i) {
-      BScan& s = sc_[idx[i]];
-      LatFill f = make(s);
-      fill_lat_args(s.p, f, blocks.data() + i * ab);
-      off[i + 1] = off[i] + lateral_grid(s.p, f.cols);
-      smem = std::max(smem, lat_smem_bytes(s.p));
-    }
-    Stage g{0, mode, 0, 0, (int)idx.size(), off.back(), smem, uses_mu ? 1 : 0};
-    g.arg_off = push(blocks.data(), blocks.size());
-    g.off_off = push(off.data(), off.size() * sizeof(int));
-    out.push_back(g);
-    return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
+// ------------------------------------------------------------------ engine
+
+Engine::~Engine() {
+  cudaStreamSynchronize(st_);
+  cudaFree(dbuf_);
+  cudaFree(dobj_);
+  for (Staging& r : ring_) {
+    cudaFreeHost(r.h);
+    if (r.ev) cudaEventDestroy(r.ev);
   }
+}
 
-  int add_row(std::vector<Stage>& out, bool adjoint, const std::vector<int>& idx, int in_ws /*0: A->B*/) {
-    if (idx.empty()) return MBIR_OK;
-    const size_t ab = row_args_bytes(prec_);
-    std::vector<unsigned char> blocks(ab * idx.size());
-    std::vector<int> off(idx.size() + 1, 0);
-    size_t smem = 0;
-    const int kind = adjoint ? (gather_ ? 1 : 2) : 0;
-    for (size_t i = 0; i < idx.size(); ++i) {
-      BScan& s = sc_[idx[i]];
-      fill_row_args(s.p, in_ws == 0 ? s.p->wsA : s.p->wsB, in_ws == 0 ? s.p->wsB : s.p->wsA,
-                    blocks.data() + i * ab);
-      off[i + 1] = off[i] + s.p->nx;
-      smem = std::max(smem, row_smem_bytes(s.p, kind == 1));
-    }
-    Stage g{1, kind, 0, 0, (int)idx.size(), off.back(), smem, 0};
-    g.arg_off = push(blocks.data(), blocks.size());
-    g.off_off = push(off.data(), off.size() * sizeof(int));
-    out.push_back(g);
-    return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
+int Engine::begin_build() {
+  cur_ = (cur_ + 1) % kRing;
+  Staging& r = ring_[cur_];
+  if (r.pending) {
+    MBIR_CUDA_TRY(cudaEventSynchronize(r.ev));
+    r.pending = false;
   }
+  hbuf_ = r.h;
+  hcap_ = r.cap;
+  hlen_ = 0;
+  return MBIR_OK;
+}
 
-  // one wavelet level over the scans `idx`
-  int add_dwt(std::vector<Stage>& out, int inverse, int level, const std::vector<int>& idx,
-              const void* const* in, void* const* outp, double* const* partial, bool thresh) {
-    if (idx.empty()) return MBIR_OK;
-    const size_t ab = dwt_args_bytes(prec_);
-    std::vector<unsigned char> blocks(ab * idx.size());
-    std::vector<int> off(idx.size() + 1, 0);
-    for (size_t i = 0; i < idx.size(); ++i) {
-      BScan& s = sc_[idx[i]];
-      const int th = thresh ? (level == 2 ? 2 : 1) : 0;
-      fill_dwt_args(s.p, level, inverse, in ? in[i] : nullptr, outp ? outp[i] : nullptr, s.p->wv_coef,
-                    thresh ? s.tau : 0.0, th, partial ? partial[i] : nullptr, blocks.data() + i * ab);
-      off[i + 1] = off[i] + dwt_level_ctas(s.p->nx >> level, s.p->nz >> level, inverse);
+int Engine::check(const std::vector<BScan*>& scans) {
+  for (BScan* s : scans) {
+    if (prec_ < 0) {
+      prec_ = s->p->precision;
+      J_ = s->p->J;
+      alpha_ = s->p->alpha;
+      esz_ = prec_ == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
+      rsz_ = prec_ == MBIR_FP64 ? sizeof(double) : sizeof(float);
     }
-    Stage g{inverse ? 3 : 2, 0, 0, 0, (int)idx.size(), off.back(), dwt_smem_bytes(prec_, inverse), 0};
-    g.arg_off = push(blocks.data(), blocks.size());
-    g.off_off = push(off.data(), off.size() * sizeof(int));
-    out.push_back(g);
-    return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
+    if (s->p->precision != prec_ || s->p->J != J_ || s->p->alpha != alpha_) return MBIR_ERR_INVALID;
+    if (s->o.penalty == MBIR_PENALTY_DB4 && !s->c.wv_coef) return MBIR_ERR_INVALID;
   }
+  return MBIR_OK;
+}
 
-  int upload() {
-    if (hlen_ > dcap_) {
-      cudaFree(dbuf_);
-      dbuf_ = nullptr;
-      MBIR_CUDA_TRY(cudaMalloc(&dbuf_, hlen_));
-      dcap_ = hlen_;
-    }
-    MBIR_CUDA_TRY(cudaMemcpyAsync(dbuf_, hbuf_, hlen_, cudaMemcpyHostToDevice, st_));
-    return MBIR_OK;
+size_t Engine::push(const void* data, size_t bytes) {
+  const size_t at = (hlen_ + 15) & ~size_t(15);
+  if (at + bytes > hcap_) grow(at + bytes);
+  if (grow_failed_ || at + bytes > hcap_) {
+    grow_failed_ = true;
+    return 0;
   }
+  memcpy(hbuf_ + at, data, bytes);
+  hlen_ = at + bytes;
+  return at;
+}
 
-  int run(const Stage& g, double mu) {
-    BatchLaunch L;
-    L.dargs = static_cast<unsigned char*>(dbuf_) + g.arg_off;
-    L.doff = reinterpret_cast<const int*>(static_cast<unsigned char*>(dbuf_) + g.off_off);
-    L.n = g.n;
-    L.total = g.total;
-    L.smem = g.smem;
-    L.host0 = hbuf_ + g.arg_off;
-    L.set_mu = g.uses_mu;
-    L.mu = mu;
-    switch (g.kind) {
-      case 0: return batch_lateral(g.mode, prec_, L, st_);
-      case 1: return batch_row(g.mode, prec_, J_, L, st_);
-      case 2: return batch_dwt(0, prec_, L, st_);
-      default: return batch_dwt(1, prec_, L, st_);
-    }
+void Engine::grow(size_t need) {
+  size_t cap = hcap_ ? hcap_ : (1 << 16);
+  while (cap < need) cap *= 2;
+  unsigned char* nb = nullptr;
+  if (cudaMallocHost(&nb, cap) != cudaSuccess) {
+    grow_failed_ = true;
+    return;
   }
-
-  size_t push_scanvec(const std::vector<ScanVec>& v) { return push(v.data(), v.size() * sizeof(ScanVec)); }
-  const ScanVec* dvec(size_t off) const {
-    return reinterpret_cast<const ScanVec*>(static_cast<unsigned char*>(dbuf_) + off);
+  if (hbuf_) {
+    memcpy(nb, hbuf_, hlen_);
+    cudaFreeHost(hbuf_);   // not pending: begin_build waited for its last upload
   }
+  hbuf_ = nb;
+  hcap_ = cap;
+  ring_[cur_].h = nb;
+  ring_[cur_].cap = cap;
+}
 
-  int vec_kernel(int which, size_t off, int n) {
-    dim3 grid(kBBlocks, n);
-    const ScanVec* d = dvec(off);
-    const bool f64 = prec_ == MBIR_FP64;
-    switch (which) {
-      case 0: f64 ? b_fill_hash<double><<<grid, kBThreads, 0, st_>>>(d) : b_fill_hash<float><<<grid, kBThreads, 0, st_>>>(d); break;
-      case 1: f64 ? b_dot_norm<double><<<grid, kBThreads, 0, st_>>>(d) : b_dot_norm<float><<<grid, kBThreads, 0, st_>>>(d); break;
-      case 2: b_power_finalize<<<dim3(1, n), kBThreads, 0, st_>>>(d, kBBlocks); break;
-      case 3: f64 ? b_scale<double><<<grid, kBThreads, 0, st_>>>(d) : b_scale<float><<<grid, kBThreads, 0, st_>>>(d); break;
-      case 4: f64 ? b_maxabs<double><<<grid, kBThreads, 0, st_>>>(d) : b_maxabs<float><<<grid, kBThreads, 0, st_>>>(d); break;
-      default: b_max_finalize<<<dim3(1, n), kBThreads, 0, st_>>>(d, kBBlocks); break;
-    }
+int Engine::upload() {
+  if (grow_failed_) return MBIR_ERR_OOM;
+  if (hlen_ > dcap_) {
+    // previous launches reading dbuf_ must be done before it is released
+    MBIR_CUDA_TRY(cudaStreamSynchronize(st_));
+    cudaFree(dbuf_);
+    dbuf_ = nullptr;
+    const size_t cap = std::max(hlen_, 2 * dcap_);
+    MBIR_CUDA_TRY(cudaMalloc(&dbuf_, cap));
+    dcap_ = cap;
+  }
+  MBIR_CUDA_TRY(cudaMemcpyAsync(dbuf_, hbuf_, hlen_, cudaMemcpyHostToDevice, st_));
+  Staging& r = ring_[cur_];
+  if (!r.ev) MBIR_CUDA_TRY(cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming));
+  MBIR_CUDA_TRY(cudaEventRecord(r.ev, st_));
+  r.pending = true;
+  return MBIR_OK;
+}
+
+static LatFill lfill(const void* in, void* out, const uint8_t* mask, int cols, double scale) {
+  LatFill f;
+  memset(&f, 0, sizeof(f));
+  f.in = in;
+  f.out = out;
+  f.mask = mask;
+  f.cols = cols;
+  f.scale = scale;
+  return f;
+}
+
+template <class F>
+int Engine::add_lateral(std::vector<Stage>& out, int mode, const std::vector<BScan*>& idx, F make, bool uses_mu) {
+  if (idx.empty()) return MBIR_OK;
+  const size_t ab = lat_args_bytes(prec_);
+  std::vector<unsigned char> blocks(ab * idx.size());
+  std::vector<int> off(idx.size() + 1, 0);
+  size_t smem = 0;
+  for (size_t i = 0; i < idx.size(); ++i) {
+    BScan& s = *idx[i];
+    LatFill f = make(s);
+    fill_lat_args(s.p, f, blocks.data() + i * ab);
+    off[i + 1] = off[i] + lateral_grid(s.p, f.cols);
+    smem = std::max(smem, lat_smem_bytes(s.p));
+  }
+  Stage g{0, mode, 0, 0, (int)idx.size(), off.back(), smem, uses_mu ? 1 : 0};
+  g.arg_off = push(blocks.data(), blocks.size());
+  g.off_off = push(off.data(), off.size() * sizeof(int));
+  out.push_back(g);
+  return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
+}
+
+int Engine::add_row(std::vector<Stage>& out, bool adjoint, const std::vector<BScan*>& idx) {
+  if (idx.empty()) return MBIR_OK;
+  const size_t ab = row_args_bytes(prec_);
+  std::vector<unsigned char> blocks(ab * idx.size());
+  std::vector<int> off(idx.size() + 1, 0);
+  size_t smem = 0;
+  bool gather = true;
+  for (BScan* s : idx) gather = gather && plan_uses_gather(s->p);
+  const int kind = adjoint ? (gather ? 1 : 2) : 0;
+  for (size_t i = 0; i < idx.size(); ++i) {
+    BScan& s = *idx[i];
+    fill_row_args(s.p, s.c.wsA, s.c.wsB, blocks.data() + i * ab);
+    off[i + 1] = off[i] + s.p->nx;
+    smem = std::max(smem, row_smem_bytes(s.p, kind == 1));
+  }
+  Stage g{1, kind, 0, 0, (int)idx.size(), off.back(), smem, 0};
+  g.arg_off = push(blocks.data(), blocks.size());
+  g.off_off = push(off.data(), off.size() * sizeof(int));
+  out.push_back(g);
+  return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
+}
+
+int Engine::add_dwt(std::vector<Stage>& out, int inverse, int level, const std::vector<BScan*>& idx,
+                    const std::vector<const void*>& in, const std::vector<void*>& outp,
+                    const std::vector<void*>& coefs, const std::vector<double*>& partial, bool thresh) {
+  if (idx.empty()) return MBIR_OK;
+  const size_t ab = dwt_args_bytes(prec_);
+  std::vector<unsigned char> blocks(ab * idx.size());
+  std::vector<int> off(idx.size() + 1, 0);
+  for (size_t i = 0; i < idx.size(); ++i) {
+    BScan& s = *idx[i];
+    const int th = thresh ? (level == 2 ? 2 : 1) : 0;
+    fill_dwt_args(s.p, level, inverse, in.empty() ? nullptr : in[i], outp.empty() ? nullptr : outp[i], coefs[i],
+                  thresh ? s.tau : 0.0, th, partial.empty() ? nullptr : partial[i], s.c.wv_b1, s.c.wv_b2,
+                  blocks.data() + i * ab);
+    off[i + 1] = off[i] + dwt_level_ctas(s.p->nx >> level, s.p->nz >> level, inverse);
+  }
+  Stage g{inverse ? 3 : 2, 0, 0, 0, (int)idx.size(), off.back(), dwt_smem_bytes(prec_, inverse), 0};
+  g.arg_off = push(blocks.data(), blocks.size());
+  g.off_off = push(off.data(), off.size() * sizeof(int));
+  out.push_back(g);
+  return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
+}
+
+int Engine::run(const Stage& g, double mu) {
+  if (g.kind == 4) {
+    const ObjArgs* d = reinterpret_cast<const ObjArgs*>(static_cast<unsigned char*>(dbuf_) + g.arg_off);
+    b_objective<<<g.n, kBThreads, 0, st_>>>(d);
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }
+  BatchLaunch L;
+  L.dargs = static_cast<unsigned char*>(dbuf_) + g.arg_off;
+  L.doff = reinterpret_cast<const int*>(static_cast<unsigned char*>(dbuf_) + g.off_off);
+  L.n = g.n;
+  L.total = g.total;
+  L.smem = g.smem;
+  L.host0 = hbuf_ + g.arg_off;
+  L.set_mu = g.uses_mu;
+  L.mu = mu;
+  switch (g.kind) {
+    case 0: return batch_lateral(g.mode, prec_, L, st_);
+    case 1: return batch_row(g.mode, prec_, J_, L, st_);
+    case 2: return batch_dwt(0, prec_, L, st_);
+    default: return batch_dwt(1, prec_, L, st_);
+  }
+}
 
-  // ---- the solve
-  int solve() {
-    const int n = (int)sc_.size();
-    std::vector<int> all(n), pow_idx, lam_idx, l1_idx, db4_idx;
-    for (int i = 0; i < n; ++i) {
-      all[i] = i;
-      if (!(sc_[i].o.step > 0)) pow_idx.push_back(i);
-      if (sc_[i].o.lambda_is_relative) lam_idx.push_back(i);
-      (sc_[i].o.penalty == MBIR_PENALTY_L1 ? l1_idx : db4_idx).push_back(i);
+int Engine::vec_kernel(int which, size_t off, int n) {
+  dim3 grid(kBBlocks, n);
+  const ScanVec* d = reinterpret_cast<const ScanVec*>(static_cast<unsigned char*>(dbuf_) + off);
+  const bool f64 = prec_ == MBIR_FP64;
+  switch (which) {
+    case 0: f64 ? b_fill_hash<double><<<grid, kBThreads, 0, st_>>>(d) : b_fill_hash<float><<<grid, kBThreads, 0, st_>>>(d); break;
+    case 1: f64 ? b_dot_norm<double><<<grid, kBThreads, 0, st_>>>(d) : b_dot_norm<float><<<grid, kBThreads, 0, st_>>>(d); break;
+    case 2: b_power_finalize<<<dim3(1, n), kBThreads, 0, st_>>>(d, kBBlocks); break;
+    case 3: f64 ? b_scale<double><<<grid, kBThreads, 0, st_>>>(d) : b_scale<float><<<grid, kBThreads, 0, st_>>>(d); break;
+    case 4: f64 ? b_maxabs<double><<<grid, kBThreads, 0, st_>>>(d) : b_maxabs<float><<<grid, kBThreads, 0, st_>>>(d); break;
+    default: b_max_finalize<<<dim3(1, n), kBThreads, 0, st_>>>(d, kBBlocks); break;
+  }
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+int Engine::setup(const std::vector<BScan*>& scans) {
+  if (scans.empty()) return MBIR_OK;
+  int rc = check(scans);
+  if (rc) return rc;
+  std::vector<BScan*> pw, lm, lm_db4;
+  for (BScan* s : scans) {
+    if (!(s->o.step > 0)) pw.push_back(s);
+    if (s->o.lambda_is_relative) {
+      lm.push_back(s);
+      if (s->o.penalty == MBIR_PENALTY_DB4) lm_db4.push_back(s);
     }
-    int rc;
-    // ---------------- set-up: power iteration and lambda, batched
-    std::vector<Stage> pw, lm;
-    size_t pw_vec = 0, lm_vec = 0, lm_vec2 = 0;
-    if (!pow_idx.empty()) {
-      rc = add_lateral(pw, LAT_C2C_FWD, pow_idx, [&](BScan& s) {
-        return fill(s.p, s.p->solve->v, s.p->wsA, nullptr, s.p->nz, 1.0); }, false);
-      if (rc) return rc;
-      if ((rc = add_row(pw, false, pow_idx, 0))) return rc;
-      rc = add_lateral(pw, LAT_C2R_INV_MASK, pow_idx, [&](BScan& s) {
-        return fill(s.p, s.p->wsB, s.p->solve->r, s.mask, s.p->m, 1.0 / s.p->nx); }, false);
-      if (rc) return rc;
-      rc = add_lateral(pw, LAT_R2C_MASK, pow_idx, [&](BScan& s) {
-        return fill(s.p, s.p->solve->r, s.p->wsA, s.mask, s.p->m, 1.0 / s.p->nx); }, false);
-      if (rc) return rc;
-      if ((rc = add_row(pw, true, pow_idx, 0))) return rc;
-      rc = add_lateral(pw, LAT_C2C_INV, pow_idx, [&](BScan& s) {
-        return fill(s.p, s.p->wsB, s.p->solve->zA, nullptr, s.p->nz, 1.0); }, false);
-      if (rc) return rc;
-      std::vector<ScanVec> vv, vw;
-      for (int i : pow_idx) {
-        SolveState* S = sc_[i].p->solve;
-        vv.push_back({S->v, S->v, S->nimg, S->part_tmp, S->scal});
-        vw.push_back({S->v, S->zA, S->nimg, S->part_tmp, S->scal});
-      }
-      pw_vec = push_scanvec(vv);
-      lm_vec2 = push_scanvec(vw);   // (v, w) pairs
+  }
+  if ((rc = begin_build())) return rc;
+  std::vector<Stage> pst, lst;
+  size_t v_self = 0, v_pair = 0, v_lam = 0;
+  if (!pw.empty()) {
+    if ((rc = add_lateral(pst, LAT_C2C_FWD, pw, [](BScan& s) { return lfill(s.c.v, s.c.wsA, nullptr, s.p->nz, 1.0); }, false))) return rc;
+    if ((rc = add_row(pst, false, pw))) return rc;
+    if ((rc = add_lateral(pst, LAT_C2R_INV_MASK, pw, [](BScan& s) { return lfill(s.c.wsB, s.c.r, s.mask, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
+    if ((rc = add_lateral(pst, LAT_R2C_MASK, pw, [](BScan& s) { return lfill(s.c.r, s.c.wsA, s.mask, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
+    if ((rc = add_row(pst, true, pw))) return rc;
+    if ((rc = add_lateral(pst, LAT_C2C_INV, pw, [](BScan& s) { return lfill(s.c.wsB, s.c.zA, nullptr, s.p->nz, 1.0); }, false))) return rc;
+    std::vector<ScanVec> a, b;
+    for (BScan* s : pw) {
+      a.push_back({s->c.v, s->c.v, s->c.nimg, s->c.part_tmp, s->c.scal});
+      b.push_back({s->c.v, s->c.zA, s->c.nimg, s->c.part_tmp, s->c.scal});
     }
-    if (!lam_idx.empty()) {
-      rc = add_lateral(lm, LAT_R2C_MASK, lam_idx, [&](BScan& s) {
-        return fill(s.p, s.y, s.p->wsA, s.mask, s.p->m, 1.0 / s.p->nx); }, false);
-      if (rc) return rc;
-      if ((rc = add_row(lm, true, lam_idx, 0))) return rc;
-      rc = add_lateral(lm, LAT_C2C_INV, lam_idx, [&](BScan& s) {
-        return fill(s.p, s.p->wsB, s.p->solve->zA, nullptr, s.p->nz, 1.0); }, false);
-      if (rc) return rc;
-      std::vector<int> lam_db4;
-      for (int i : lam_idx)
-        if (sc_[i].o.penalty == MBIR_PENALTY_DB4) lam_db4.push_back(i);
-      std::vector<const void*> ins;
-      std::vector<void*> outs;
-      for (int i : lam_db4) {
-        ins.push_back(sc_[i].p->solve->zA);
-        outs.push_back(sc_[i].p->solve->v);
+    v_self = push(a.data(), a.size() * sizeof(ScanVec));
+    v_pair = push(b.data(), b.size() * sizeof(ScanVec));
+  }
+  if (!lm.empty()) {
+    if ((rc = add_lateral(lst, LAT_R2C_MASK, lm, [](BScan& s) { return lfill(s.y, s.c.wsA, s.mask, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
+    if ((rc = add_row(lst, true, lm))) return rc;
+    if ((rc = add_lateral(lst, LAT_C2C_INV, lm, [](BScan& s) { return lfill(s.c.wsB, s.c.zA, nullptr, s.p->nz, 1.0); }, false))) return rc;
+    if (!lm_db4.empty()) {
+      // full analysis (no threshold) of Phi^H s y into v
+      std::vector<const void*> in;
+      std::vector<void*> coefs;
+      for (BScan* s : lm_db4) {
+        in.push_back(s->c.zA);
+        coefs.push_back(s->c.v);
       }
-      for (int lev = 0; lev < 3; ++lev) {
-        // analysis without threshold; the last level's low-low block lands in v
-        std::vector<void*> coefs;
-        for (size_t q = 0; q < lam_db4.size(); ++q) coefs.push_back(outs[q]);
-        rc = add_dwt_coef(lm, lev, lam_db4, ins.data(), coefs.data());
-        if (rc) return rc;
-      }
-      std::vector<ScanVec> vm;
-      for (int i : lam_idx) {
-        SolveState* S = sc_[i].p->solve;
-        vm.push_back({sc_[i].o.penalty == MBIR_PENALTY_DB4 ? S->v : S->zA, nullptr, S->nimg, S->part_tmp, S->scal});
-      }
-      lm_vec = push_scanvec(vm);
+      for (int lev = 0; lev < 3; ++lev)
+        if ((rc = add_dwt(lst, 0, lev, lm_db4, in, {}, coefs, {}, false))) return rc;
     }
-    if ((rc = upload())) return rc;
-    if (!pow_idx.empty()) {
-      const int np = (int)pow_idx.size();
-      if ((rc = vec_kernel(0, pw_vec, np))) return rc;
-      if ((rc = vec_kernel(1, pw_vec, np))) return rc;
-      if ((rc = vec_kernel(2, pw_vec, np))) return rc;
-      if ((rc = vec_kernel(3, pw_vec, np))) return rc;
-      int iters = 0;
-      for (int i : pow_idx) iters = std::max(iters, sc_[i].o.power_iters > 0 ? sc_[i].o.power_iters : 30);
-      for (int it = 0; it < iters; ++it) {
-        for (const Stage& g : pw)
-          if ((rc = run(g, 0.0))) return rc;
-        if ((rc = vec_kernel(1, lm_vec2, np))) return rc;
-        if ((rc = vec_kernel(2, lm_vec2, np))) return rc;
-        if ((rc = vec_kernel(3, lm_vec2, np))) return rc;
-      }
-    }
-    if (!lam_idx.empty()) {
-      for (const Stage& g : lm)
+    std::vector<ScanVec> a;
+    for (BScan* s : lm)
+      a.push_back({s->o.penalty == MBIR_PENALTY_DB4 ? s->c.v : s->c.zA, nullptr, s->c.nimg, s->c.part_tmp, s->c.scal});
+    v_lam = push(a.data(), a.size() * sizeof(ScanVec));
+  }
+  if ((rc = upload())) return rc;
+  if (!pw.empty()) {
+    const int np = (int)pw.size();
+    for (int w : {0, 1, 2, 3})
+      if ((rc = vec_kernel(w, v_self, np))) return rc;
+    int iters = 0;
+    for (BScan* s : pw) iters = std::max(iters, s->o.power_iters > 0 ? s->o.power_iters : 30);
+    for (int it = 0; it < iters; ++it) {
+      for (const Stage& g : pst)
         if ((rc = run(g, 0.0))) return rc;
-      if ((rc = vec_kernel(4, lm_vec, (int)lam_idx.size()))) return rc;
-      if ((rc = vec_kernel(5, lm_vec, (int)lam_idx.size()))) return rc;
+      for (int w : {1, 2, 3})
+        if ((rc = vec_kernel(w, v_pair, np))) return rc;
     }
-    // read the scalars back (one sync for the whole batch)
-    std::vector<double> hs(n * 8, 0.0);
-    for (int i = 0; i < n; ++i)
-      MBIR_CUDA_TRY(cudaMemcpyAsync(&hs[8 * i], sc_[i].p->solve->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st_));
-    MBIR_CUDA_TRY(cudaStreamSynchronize(st_));
-    for (int i = 0; i < n; ++i) {
-      BScan& s = sc_[i];
-      s.L = 0.0;
-      s.delta = s.o.step;
-      if (!(s.delta > 0)) {
-        s.L = hs[8 * i + 0];
-        if (!(s.L > 0) || !isfinite(s.L)) return MBIR_ERR_INVALID;
-        s.delta = 1.0 / (1.01 * s.L);
-      }
-      s.lam = s.o.lambda * (s.o.lambda_is_relative ? hs[8 * i + 4] : 1.0);
-      s.tau = s.lam * s.delta;
+  }
+  if (!lm.empty()) {
+    for (const Stage& g : lst)
+      if ((rc = run(g, 0.0))) return rc;
+    for (int w : {4, 5})
+      if ((rc = vec_kernel(w, v_lam, (int)lm.size()))) return rc;
+  }
+  std::vector<double> hs(8 * scans.size(), 0.0);
+  for (size_t i = 0; i < scans.size(); ++i)
+    MBIR_CUDA_TRY(cudaMemcpyAsync(&hs[8 * i], scans[i]->c.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st_));
+  MBIR_CUDA_TRY(cudaStreamSynchronize(st_));
+  for (size_t i = 0; i < scans.size(); ++i) {
+    BScan& s = *scans[i];
+    s.L = 0.0;
+    s.delta = s.o.step;
+    if (!(s.delta > 0)) {
+      s.L = hs[8 * i + 0];
+      if (!(s.L > 0) || !isfinite(s.L)) return MBIR_ERR_INVALID;
+      s.delta = 1.0 / (1.01 * s.L);
     }
-    // ---------------- the FISTA iterations: stages for both parities of (z1, z2)
-    hlen_ = 0;
-    std::vector<Stage> it[2];
-    for (int par = 0; par < 2; ++par) {
-      auto z1 = [&](BScan& s) { return par == 0 ? s.p->solve->zA : s.p->solve->zB; };
-      auto z2 = [&](BScan& s) { return par == 0 ? s.p->solve->zB : s.p->solve->zA; };
-      rc = add_lateral(it[par], LAT_C2C_FWD, all, [&](BScan& s) {
-        return fill(s.p, z1(s), s.p->wsA, nullptr, s.p->nz, 1.0); }, false);
-      if (rc) return rc;
-      if ((rc = add_row(it[par], false, all, 0))) return rc;
-      rc = add_lateral(it[par], LAT_SOLVE_FWD, all, [&](BScan& s) {
-        LatFill f = fill(s.p, s.p->wsB, nullptr, s.mask, s.p->m, 1.0 / s.p->nx);
-        f.y = s.y;
-        f.pz = s.p->solve->pz;
-        f.r = s.p->solve->r;
-        f.partial = s.p->solve->part_data;
-        return f; }, true);
-      if (rc) return rc;
-      rc = add_lateral(it[par], LAT_R2C_MASK, all, [&](BScan& s) {
-        return fill(s.p, s.p->solve->r, s.p->wsA, nullptr, s.p->m, 1.0 / s.p->nx); }, false);
-      if (rc) return rc;
-      if ((rc = add_row(it[par], true, all, 0))) return rc;
-      rc = add_lateral(it[par], LAT_SOLVE_ADJ_L1, l1_idx, [&](BScan& s) {
-        LatFill f = fill(s.p, s.p->wsB, nullptr, nullptr, s.p->nz, 1.0);
-        f.z1 = z1(s);
-        f.z2 = z2(s);
-        f.delta = s.delta;
-        f.tau = s.tau;
-        f.partial = s.p->solve->part_reg;
-        return f; }, true);
-      if (rc) return rc;
-      rc = add_lateral(it[par], LAT_SOLVE_ADJ_V, db4_idx, [&](BScan& s) {
-        LatFill f = fill(s.p, s.p->wsB, nullptr, nullptr, s.p->nz, 1.0);
-        f.z1 = z1(s);
-        f.z2 = z2(s);
-        f.vout = s.p->solve->v;
-        f.delta = s.delta;
-        f.tau = s.tau;
-        return f; }, true);
-      if (rc) return rc;
-      if (!db4_idx.empty()) {
-        std::vector<const void*> ins;
-        std::vector<void*> outs;
-        std::vector<double*> parts[3];
-        for (int i : db4_idx) {
-          BScan& s = sc_[i];
-          ins.push_back(s.p->solve->v);
-          outs.push_back(z2(s));
-          double* pr = s.p->solve->part_reg;
-          int P = s.p->nx, N = s.p->nz;
-          for (int lev = 0; lev < 3; ++lev) {
-            parts[lev].push_back(pr);
-            pr += dwt_level_ctas(P, N, 0);
-            P /= 2;
-            N /= 2;
-          }
-        }
-        for (int lev = 0; lev < 3; ++lev)
-          if ((rc = add_dwt(it[par], 0, lev, db4_idx, ins.data(), nullptr, parts[lev].data(), true))) return rc;
-        for (int lev = 2; lev >= 0; --lev)
-          if ((rc = add_dwt(it[par], 1, lev, db4_idx, nullptr, outs.data(), nullptr, false))) return rc;
-      }
-    }
-    if ((rc = upload())) return rc;
-    int kmax = 0;
-    for (auto& s : sc_) kmax = std::max(kmax, s.o.max_iter);
-    for (auto& s : sc_)
-      if (s.o.max_iter != kmax) return MBIR_ERR_INVALID;   // one iteration count per batch
-    for (auto& s : sc_) {
-      SolveState* S = s.p->solve;
-      MBIR_CUDA_TRY(cudaMemsetAsync(S->pz, 0, rsz_ * S->nmeas, st_));
-      if (s.o.warm_start) {
-        MBIR_CUDA_TRY(cudaMemcpyAsync(S->zA, s.x, esz_ * S->nimg, cudaMemcpyDeviceToDevice, st_));
-        MBIR_CUDA_TRY(cudaMemcpyAsync(S->zB, s.x, esz_ * S->nimg, cudaMemcpyDeviceToDevice, st_));
-      } else {
-        MBIR_CUDA_TRY(cudaMemsetAsync(S->zA, 0, esz_ * S->nimg, st_));
-        MBIR_CUDA_TRY(cudaMemsetAsync(S->zB, 0, esz_ * S->nimg, st_));
-      }
-    }
-    std::vector<double> mu(kmax + 1, 0.0);
-    {
-      double t = 1.0;
-      for (int k = 0; k <= kmax; ++k) {
-        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-        mu[k] = (t - 1.0) / tn;
-        t = tn;
-      }
-    }
-    auto iterate = [&]() -> int {
-      for (int k = 1; k <= kmax; ++k) {
-        const double m = k >= 2 ? mu[k - 2] : 0.0;
-        for (const Stage& g : it[(k - 1) & 1]) {
-          const int r = run(g, m);
-          if (r) return r;
-        }
-      }
-      return MBIR_OK;
-    };
-    if (st_ != nullptr && st_ != cudaStreamLegacy && st_ != cudaStreamPerThread) {
-      // capture the loop once and replay it as one graph launch
-      cudaGraph_t graph = nullptr;
-      cudaGraphExec_t exec = nullptr;
-      MBIR_CUDA_TRY(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
-      rc = iterate();
-      cudaError_t e = cudaStreamEndCapture(st_, &graph);
-      if (rc) {
-        if (graph) cudaGraphDestroy(graph);
-        return rc;
-      }
-      if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      if (e != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return set_cuda_error(e, "cudaGraphInstantiate");
-      }
-      e = cudaGraphLaunch(exec, st_);
-      cudaGraphExecDestroy(exec);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return set_cuda_error(e, "cudaGraphLaunch");
+    s.lam = s.o.lambda * (s.o.lambda_is_relative ? hs[8 * i + 4] : 1.0);
+    s.tau = s.lam * s.delta;
+    s.k = 0;
+    s.f1 = s.f2 = 0.0;
+    MBIR_CUDA_TRY(cudaMemsetAsync(s.c.pz, 0, rsz_ * s.c.nmeas, st_));
+    MBIR_CUDA_TRY(cudaMemsetAsync(s.c.part_reg, 0, sizeof(double) * s.c.n_reg, st_));
+    if (s.o.warm_start) {
+      MBIR_CUDA_TRY(cudaMemcpyAsync(s.c.zA, s.x, esz_ * s.c.nimg, cudaMemcpyDeviceToDevice, st_));
+      MBIR_CUDA_TRY(cudaMemcpyAsync(s.c.zB, s.x, esz_ * s.c.nimg, cudaMemcpyDeviceToDevice, st_));
     } else {
-      if ((rc = iterate())) return rc;
+      MBIR_CUDA_TRY(cudaMemsetAsync(s.c.zA, 0, esz_ * s.c.nimg, st_));
+      MBIR_CUDA_TRY(cudaMemsetAsync(s.c.zB, 0, esz_ * s.c.nimg, st_));
     }
-    // z^kmax sits in zA when kmax is even, zB when odd
-    for (auto& s : sc_) {
-      void* zlast = (kmax & 1) ? s.p->solve->zB : s.p->solve->zA;
-      MBIR_CUDA_TRY(cudaMemcpyAsync(s.x, zlast, esz_ * s.p->solve->nimg, cudaMemcpyDeviceToDevice, st_));
+  }
+  return MBIR_OK;
+}
+
+static double momentum(int k) {
+  // mu_{k-1} = (t^{k-1} - 1)/t^k used in iteration k (mu_0 = 0), t^1 = 1
+  if (k < 2) return 0.0;
+  double t = 1.0, tn = 1.0;
+  for (int i = 1; i < k; ++i) {
+    tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    if (i < k - 1) t = tn;
+  }
+  return (t - 1.0) / tn;
+}
+
+// Stages of one FISTA iteration.  parity_override >= 0 fixes which buffer holds
+// z^{k-1} for every scan (the graph-captured loop); otherwise each scan's own k
+// decides, and with per_scan_mu the momentum of its own k goes into its block.
+int Engine::build_iteration(std::vector<Stage>& out, const std::vector<BScan*>& scans, int parity_override,
+                            bool per_scan_mu, bool want_obj) {
+  std::vector<BScan*> l1, db4;
+  for (BScan* s : scans) (s->o.penalty == MBIR_PENALTY_L1 ? l1 : db4).push_back(s);
+  auto par = [&](const BScan& s) { return parity_override >= 0 ? parity_override : (s.k & 1); };
+  auto z1 = [&](const BScan& s) { return par(s) == 0 ? s.c.zA : s.c.zB; };
+  auto z2 = [&](const BScan& s) { return par(s) == 0 ? s.c.zB : s.c.zA; };
+  auto mu_of = [&](const BScan& s) { return per_scan_mu ? momentum(s.k + 1) : 0.0; };
+  int rc;
+  if ((rc = add_lateral(out, LAT_C2C_FWD, scans, [&](BScan& s) { return lfill(z1(s), s.c.wsA, nullptr, s.p->nz, 1.0); }, false))) return rc;
+  if ((rc = add_row(out, false, scans))) return rc;
+  if ((rc = add_lateral(out, LAT_SOLVE_FWD, scans, [&](BScan& s) {
+         LatFill f = lfill(s.c.wsB, nullptr, s.mask, s.p->m, 1.0 / s.p->nx);
+         f.y = s.y;
+         f.pz = s.c.pz;
+         f.r = s.c.r;
+         f.partial = s.c.part_data;
+         f.mu = mu_of(s);
+         return f; }, !per_scan_mu)))
+    return rc;
+  if (want_obj) {
+    if (dobj_cap_ < (int)scans.size()) {
+      cudaFree(dobj_);
+      dobj_ = nullptr;
+      const int cap = std::max((int)scans.size(), 2 * dobj_cap_);
+      MBIR_CUDA_TRY(cudaMalloc(&dobj_, sizeof(double) * cap));
+      dobj_cap_ = cap;
+    }
+    std::vector<ObjArgs> oa;
+    for (size_t i = 0; i < scans.size(); ++i) {
+      BScan& s = *scans[i];
+      s.slot = (int)i;
+      const int nreg = s.o.penalty == MBIR_PENALTY_L1 ? lateral_grid(s.p, s.p->nz)
+                                                      : wavelet_partial_count(s.p->nx, s.p->nz);
+      oa.push_back({s.c.part_data, s.c.n_data, s.c.part_reg, nreg, s.lam,
+                    s.k < s.c.trace_cap ? s.c.objtrace + s.k : nullptr, dobj_ + i});
+    }
+    Stage g{4, 0, 0, 0, (int)scans.size(), 0, 0, 0};
+    g.arg_off = push(oa.data(), oa.size() * sizeof(ObjArgs));
+    out.push_back(g);
+  }
+  if ((rc = add_lateral(out, LAT_R2C_MASK, scans, [&](BScan& s) { return lfill(s.c.r, s.c.wsA, nullptr, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
+  if ((rc = add_row(out, true, scans))) return rc;
+  if ((rc = add_lateral(out, LAT_SOLVE_ADJ_L1, l1, [&](BScan& s) {
+         LatFill f = lfill(s.c.wsB, nullptr, nullptr, s.p->nz, 1.0);
+         f.z1 = z1(s);
+         f.z2 = z2(s);
+         f.delta = s.delta;
+         f.tau = s.tau;
+         f.mu = mu_of(s);
+         f.partial = s.c.part_reg;
+         return f; }, !per_scan_mu)))
+    return rc;
+  if ((rc = add_lateral(out, LAT_SOLVE_ADJ_V, db4, [&](BScan& s) {
+         LatFill f = lfill(s.c.wsB, nullptr, nullptr, s.p->nz, 1.0);
+         f.z1 = z1(s);
+         f.z2 = z2(s);
+         f.vout = s.c.v;
+         f.delta = s.delta;
+         f.tau = s.tau;
+         f.mu = mu_of(s);
+         return f; }, !per_scan_mu)))
+    return rc;
+  if (!db4.empty()) {
+    std::vector<const void*> in;
+    std::vector<void*> outs, coefs;
+    std::vector<double*> parts[3];
+    for (BScan* s : db4) {
+      in.push_back(s->c.v);
+      outs.push_back(z2(*s));
+      coefs.push_back(s->c.wv_coef);
+      double* pr = s->c.part_reg;
+      int P = s->p->nx, N = s->p->nz;
+      for (int lev = 0; lev < 3; ++lev) {
+        parts[lev].push_back(pr);
+        pr += dwt_level_ctas(P, N, 0);
+        P /= 2;
+        N /= 2;
+      }
+    }
+    for (int lev = 0; lev < 3; ++lev)
+      if ((rc = add_dwt(out, 0, lev, db4, in, {}, coefs, parts[lev], true))) return rc;
+    for (int lev = 2; lev >= 0; --lev)
+      if ((rc = add_dwt(out, 1, lev, db4, {}, outs, coefs, {}, false))) return rc;
+  }
+  return MBIR_OK;
+}
+
+int Engine::step(const std::vector<BScan*>& scans, bool want_obj) {
+  if (scans.empty()) return MBIR_OK;
+  int rc = check(scans);
+  if (rc) return rc;
+  if ((rc = begin_build())) return rc;
+  std::vector<Stage> st;
+  if ((rc = build_iteration(st, scans, -1, true, want_obj))) return rc;
+  if ((rc = upload())) return rc;
+  for (const Stage& g : st)
+    if ((rc = run(g, 0.0))) return rc;
+  for (BScan* s : scans) s->k += 1;
+  return MBIR_OK;
+}
+
+int Engine::read_objectives(const std::vector<BScan*>& scans) {
+  if (scans.empty()) return MBIR_OK;
+  hobj_.resize(scans.size());
+  MBIR_CUDA_TRY(cudaMemcpyAsync(hobj_.data(), dobj_, sizeof(double) * scans.size(), cudaMemcpyDeviceToHost, st_));
+  MBIR_CUDA_TRY(cudaStreamSynchronize(st_));
+  for (BScan* s : scans) {
+    s->f2 = s->f1;
+    s->f1 = hobj_[s->slot];
+  }
+  return MBIR_OK;
+}
+
+int Engine::solve_fixed(const std::vector<BScan*>& scans) {
+  int rc = check(scans);
+  if (rc) return rc;
+  const int kmax = scans[0]->o.max_iter;
+  for (BScan* s : scans)
+    if (s->o.max_iter != kmax) return MBIR_ERR_INVALID;
+  if ((rc = begin_build())) return rc;
+  std::vector<Stage> it[2];
+  for (int par = 0; par < 2; ++par)
+    if ((rc = build_iteration(it[par], scans, par, false, false))) return rc;
+  if ((rc = upload())) return rc;
+  std::vector<double> mu(kmax + 2, 0.0);
+  {
+    double t = 1.0;
+    for (int k = 0; k <= kmax; ++k) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      mu[k] = (t - 1.0) / tn;
+      t = tn;
+    }
+  }
+  auto iterate = [&]() -> int {
+    for (int k = 1; k <= kmax; ++k) {
+      const double m = k >= 2 ? mu[k - 2] : 0.0;
+      for (const Stage& g : it[(k - 1) & 1]) {
+        const int r = run(g, m);
+        if (r) return r;
+      }
     }
     return MBIR_OK;
-  }
-
-  static LatFill fill(mbir_plan p, const void* in, void* out, const uint8_t* mask, int cols, double scale) {
-    (void)p;
-    LatFill f;
-    memset(&f, 0, sizeof(f));
-    f.in = in;
-    f.out = out;
-    f.mask = mask;
-    f.cols = cols;
-    f.scale = scale;
-    return f;
-  }
-
-  // analysis level without threshold whose coefficient array is coefs[i]
-  int add_dwt_coef(std::vector<Stage>& out, int level, const std::vector<int>& idx, const void* const* in,
-                   void* const* coefs) {
-    if (idx.empty()) return MBIR_OK;
-    const size_t ab = dwt_args_bytes(prec_);
-    std::vector<unsigned char> blocks(ab * idx.size());
-    std::vector<int> off(idx.size() + 1, 0);
-    for (size_t i = 0; i < idx.size(); ++i) {
-      BScan& s = sc_[idx[i]];
-      fill_dwt_args(s.p, level, 0, in[i], nullptr, coefs[i], 0.0, 0, nullptr, blocks.data() + i * ab);
-      off[i + 1] = off[i] + dwt_level_ctas(s.p->nx >> level, s.p->nz >> level, 0);
+  };
+  if (st_ != nullptr && st_ != cudaStreamLegacy && st_ != cudaStreamPerThread) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    MBIR_CUDA_TRY(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+    rc = iterate();
+    cudaError_t e = cudaStreamEndCapture(st_, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
     }
-    Stage g{2, 0, 0, 0, (int)idx.size(), off.back(), dwt_smem_bytes(prec_, 0), 0};
-    g.arg_off = push(blocks.data(), blocks.size());
-    g.off_off = push(off.data(), off.size() * sizeof(int));
-    out.push_back(g);
-    return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return set_cuda_error(e, "cudaGraphInstantiate");
+    }
+    e = cudaGraphLaunch(exec, st_);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaGraphLaunch");
+  } else if ((rc = iterate())) {
+    return rc;
   }
+  for (BScan* s : scans) s->k = kmax;
+  return MBIR_OK;
+}
 
- private:
-  std::vector<BScan>& sc_;
-  cudaStream_t st_;
-  int prec_ = 0, J_ = 6;
-  bool gather_ = true;
-  size_t esz_ = 8, rsz_ = 4;
-  unsigned char* hbuf_ = nullptr;
-  size_t hlen_ = 0, hcap_ = 0;
-  bool grow_failed_ = false;
-  void* dbuf_ = nullptr;
-  size_t dcap_ = 0;
-};
+int Engine::finish(BScan* s) {
+  // z^k lives in zA when k is even, zB when odd
+  void* zlast = (s->k & 1) ? s->c.zB : s->c.zA;
+  MBIR_CUDA_TRY(cudaMemcpyAsync(s->x, zlast, esz_ * s->c.nimg, cudaMemcpyDeviceToDevice, st_));
+  return MBIR_OK;
+}
 
 }  // namespace mbir
 
@@ -638,26 +785,37 @@ int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const ui
                      const mbir_solve_opts* opts, void* const* x, mbir_solve_info* info, void* stream) {
   if (!plans || n < 1 || !y || !opts || !x) return MBIR_ERR_INVALID;
   std::vector<BScan> scans(n);
+  std::vector<BScan*> ptrs(n);
   for (int i = 0; i < n; ++i) {
     const mbir_solve_opts& o = opts[i];
     if (!plans[i] || !y[i] || !x[i]) return MBIR_ERR_INVALID;
     if (o.max_iter < 1 || o.penalty < MBIR_PENALTY_L1 || o.penalty > MBIR_PENALTY_DB4) return MBIR_ERR_INVALID;
     if (!(o.lambda >= 0) || !isfinite(o.lambda) || !isfinite(o.step) || o.rel_tol != 0.0) return MBIR_ERR_INVALID;
     for (int j = 0; j < i; ++j)
-      if (plans[j] == plans[i]) return MBIR_ERR_INVALID;   // each plan once: its workspace is per scan
-    scans[i] = BScan{plans[i], y[i], mask ? mask[i] : nullptr, x[i], o, 0, 0, 0, 0};
+      if (plans[j] == plans[i]) return MBIR_ERR_INVALID;   // each plan once: its buffers are per scan
+    BScan& s = scans[i];
+    s.p = plans[i];
+    s.y = y[i];
+    s.mask = mask ? mask[i] : nullptr;
+    s.x = x[i];
+    s.o = o;
+    int rc = plan_ctx(s.p, o.penalty, o.max_iter, &s.c);
+    if (rc) return rc;
+    ptrs[i] = &s;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  Engine eng(scans, st);
-  int rc = eng.prepare();
+  Engine eng(st);
+  int rc = eng.setup(ptrs);
   if (rc) return rc;
-  rc = eng.solve();
+  rc = eng.solve_fixed(ptrs);
   if (rc) return rc;
+  for (BScan* s : ptrs)
+    if ((rc = eng.finish(s))) return rc;
   if (info) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamSynchronize");
     for (int i = 0; i < n; ++i) {
-      info[i].iters = scans[i].o.max_iter;
+      info[i].iters = scans[i].k;
       info[i].status = MBIR_OK;
       info[i].objective = NAN;
       info[i].lipschitz = scans[i].L;

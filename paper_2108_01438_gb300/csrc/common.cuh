@@ -217,7 +217,7 @@ struct LatFill {
   const void* z1;
   void* z2;
   void* vout;
-  double delta, tau;
+  double mu, delta, tau;
   double* partial;
 };
 
@@ -237,7 +237,7 @@ size_t dwt_args_bytes(int precision);
 int dwt_level_ctas(int P, int N, int inverse);
 size_t dwt_smem_bytes(int precision, int inverse);
 void fill_dwt_args(mbir_plan p, int level, int inverse, const void* in, void* out, void* coef, double tau,
-                   int thresh, double* partial, void* dst);
+                   int thresh, double* partial, void* b1, void* b2, void* dst);
 int batch_dwt(int inverse, int precision, const BatchLaunch& L, cudaStream_t st);
 
 // operator.cu

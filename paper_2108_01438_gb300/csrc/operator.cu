@@ -890,7 +890,7 @@ static void fill_lat_t(mbir_plan p, const LatFill& f, void* dst) {
   a.z1 = f.z1;
   a.z2 = f.z2;
   a.vout = f.vout;
-  a.mu = R(0);
+  a.mu = R(f.mu);
   a.delta = R(f.delta);
   a.tau = R(f.tau);
   a.partial = f.partial;

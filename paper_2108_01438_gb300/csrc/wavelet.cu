@@ -519,9 +519,9 @@ size_t dwt_smem_bytes(int precision, int inverse) {
 // 0 and the plan's low-low scratch above, synthesis writes `out` at level 0.
 template <class R>
 static void fill_dwt_t(mbir_plan p, int level, int inverse, const void* in, void* out, void* coef, double tau,
-                       int thresh, double* partial, void* dst) {
+                       int thresh, double* partial, void* b1, void* b2, void* dst) {
   const int nx = p->nx, nz = p->nz;
-  void* lls[3] = {p->wv_b1, p->wv_b2, coef};
+  void* lls[3] = {b1, b2, coef};
   const int lstr[3] = {nz / 2, nz / 4, nz};
   WArgs<R> a;
   memset(&a, 0, sizeof(a));
@@ -552,9 +552,9 @@ static void fill_dwt_t(mbir_plan p, int level, int inverse, const void* in, void
 }
 
 void fill_dwt_args(mbir_plan p, int level, int inverse, const void* in, void* out, void* coef, double tau,
-                   int thresh, double* partial, void* dst) {
-  if (p->precision == MBIR_FP64) fill_dwt_t<double>(p, level, inverse, in, out, coef, tau, thresh, partial, dst);
-  else fill_dwt_t<float>(p, level, inverse, in, out, coef, tau, thresh, partial, dst);
+                   int thresh, double* partial, void* b1, void* b2, void* dst) {
+  if (p->precision == MBIR_FP64) fill_dwt_t<double>(p, level, inverse, in, out, coef, tau, thresh, partial, b1, b2, dst);
+  else fill_dwt_t<float>(p, level, inverse, in, out, coef, tau, thresh, partial, b1, b2, dst);
 }
 
 template <class R>

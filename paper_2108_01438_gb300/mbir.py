@@ -78,6 +78,19 @@ _SIGNATURES = {
                              C.POINTER(SolveInfo), C.c_void_p]),
     "mbir_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(SolveOpts), C.POINTER(C.c_void_p), C.POINTER(SolveInfo), C.c_void_p]),
+    "mbir_server_create": (C.c_int, [C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mbir_server_destroy": (None, [C.c_void_p]),
+    "mbir_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveOpts),
+                                     C.c_void_p, C.POINTER(C.c_int64)]),
+    "mbir_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mbir_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(SolveInfo),
+                                   C.POINTER(C.c_double)]),
+    "mbir_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                    C.POINTER(C.c_int64)]),
+    "mbir_server_request_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "mbir_admission_simulate": (C.c_int, [C.c_size_t, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int64)]),
     "mbir_lipschitz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
     "mbir_prox": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "mbir_wavelet": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -332,3 +345,86 @@ def solve_batch(plans, ys, masks=None, *, penalties="l1", lams=0.01, relative=Tr
     infos = [dict(iters=I[i].iters, status=I[i].status, lipschitz=I[i].lipschitz, step=I[i].step,
                   lambda_used=I[i].lambda_used) for i in range(n)]
     return outs, infos
+
+
+def admission_simulate(budget: int, bytes_: list[int], arrive: list[int], service: list[int]):
+    """Host-only replay of the server's admission rule; returns (admit_tick, done_tick, peak)."""
+    n = len(bytes_)
+    B = (C.c_int64 * n)(*bytes_)
+    A = (C.c_int32 * n)(*arrive)
+    S = (C.c_int32 * n)(*service)
+    adm = (C.c_int32 * n)()
+    done = (C.c_int32 * n)()
+    peak = C.c_int64()
+    _check(lib().mbir_admission_simulate(int(budget), n, B, A, S, adm, done, C.byref(peak)),
+           "mbir_admission_simulate")
+    return list(adm), list(done), peak.value
+
+
+class Server:
+    """Continuous-batching reconstruction server (mbir_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, stream=None):
+        self._stream = stream
+        h = C.c_void_p()
+        _check(lib().mbir_server_create(int(hbm_budget_bytes), _stream_handle(stream), C.byref(h)),
+               "mbir_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, plan: Plan, y, mask=None, out=None, *, penalty="l1", lam=0.01, relative=True,
+               iters=100, min_iter=0, rel_tol=0.0, power_iters=30, step=0.0) -> int:
+        import torch
+        plan._meas(y, "y")
+        plan._mask(mask)
+        if out is None:
+            out = torch.zeros((plan.nx, plan.nz), dtype=plan.complex_dtype, device=y.device)
+        plan._image(out, "out")
+        o = SolveOpts(PENALTIES[penalty], float(lam), int(bool(relative)), int(iters), int(min_iter),
+                      float(rel_tol), int(power_iters), float(step), 0)
+        t = C.c_int64()
+        _check(lib().mbir_server_submit(self._h, plan.handle, _ptr(y), _ptr(mask), C.byref(o), _ptr(out),
+                                        C.byref(t)), "mbir_server_submit")
+        self._keep[t.value] = (plan, y, mask, out)
+        return t.value
+
+    def step(self):
+        a, p, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().mbir_server_step(self._h, C.byref(a), C.byref(p), C.byref(c)), "mbir_server_step")
+        return a.value, p.value, c.value
+
+    def poll(self, ticket: int):
+        """None while running, else (out tensor, info dict, latency seconds)."""
+        d = C.c_int32()
+        info = SolveInfo()
+        lat = C.c_double()
+        _check(lib().mbir_server_poll(self._h, int(ticket), C.byref(d), C.byref(info), C.byref(lat)),
+               "mbir_server_poll")
+        if not d.value:
+            return None
+        plan, y, mask, out = self._keep.pop(ticket)
+        return out, dict(iters=info.iters, status=info.status, objective=info.objective,
+                         lipschitz=info.lipschitz, step=info.step, lambda_used=info.lambda_used), lat.value
+
+    def stats(self):
+        u, pk, c = C.c_size_t(), C.c_size_t(), C.c_int64()
+        _check(lib().mbir_server_stats(self._h, C.byref(u), C.byref(pk), C.byref(c)), "mbir_server_stats")
+        return dict(bytes_in_use=u.value, peak_bytes=pk.value, completed=c.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mbir_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def request_bytes(plan: Plan, penalty: str = "l1", iters: int = 100) -> int:
+    b = C.c_size_t()
+    _check(lib().mbir_server_request_bytes(plan.handle, PENALTIES[penalty], int(iters), C.byref(b)),
+           "mbir_server_request_bytes")
+    return b.value
