@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--serve-requests", type=int, default=200)
     return ap.parse_args()
 
 
@@ -292,6 +294,87 @@ def batch_comparison(dev, stream, count: int = 64, repeats: int = 2) -> dict:
             "sequential_bscans_per_sec": res["sequential"], "speedup": res["batched"] / res["sequential"]}
 
 
+# ------------------------------------------------------------ serving
+
+def serve_comparison(dev, stream, n_req: int = 200, rate_hz: float = 200.0,
+                     budget_bytes: int = 150 * 10 ** 9) -> dict:
+    """A seeded Poisson stream of single B-scan solves (widths from 12 of the 7-smooth
+    multiples of 8 in [128, 2048], 1024 or 2048 spectral pixels, l1 / db4 half and
+    half, relative-objective tolerance 1e-4 within 30-150 iterations) served with
+    continuous batching under a 150 GB budget.  Latency runs from each request's
+    scheduled arrival to its completion.  The same requests are then solved one
+    after another with mbir_solve."""
+    import numpy as np
+    import torch
+
+    from paper_2108_01438_gb300 import mbir, workloads
+
+    rng = np.random.default_rng(workloads.BASE_SEED + 5)
+    widths = sorted(rng.choice(workloads.smooth_widths(128, 2048), 12, replace=False).tolist())
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_req))
+    plans, reqs = {}, []
+    for i in range(n_req):
+        nx, nz = int(rng.choice(widths)), int(rng.choice([1024, 2048]))
+        if (nx, nz) not in plans:
+            plans[(nx, nz)] = mbir.Plan(workloads.geometry(nx, nz, nz))
+        p = plans[(nx, nz)]
+        x = torch.from_numpy(workloads.point_scatterers(nx, nz, 40, 10_000 + i).astype(np.complex64)).to(dev)
+        m = torch.from_numpy(workloads.mask_bernoulli(nx, nz, 0.5, 20_000 + i)).to(dev)
+        clean = p.forward(x, m)
+        sig = torch.sqrt(torch.mean(clean[m == 1].double() ** 2)).item()
+        noise = torch.from_numpy(workloads.unit_noise(nx, nz, 30_000 + i).astype(np.float32)).to(dev)
+        y = (clean + float(sig * 10 ** (-30.0 / 20)) * noise * m).contiguous()
+        reqs.append((p, y, m, "l1" if i % 2 == 0 else "db4"))
+    torch.cuda.synchronize()
+    kw = dict(lam=LAMBDA_FRAC, relative=True, iters=150, min_iter=30, rel_tol=1e-4, power_iters=POWER_ITERS)
+
+    srv = mbir.Server(budget_bytes, stream=stream)
+    outs = [torch.empty((p.nx, p.nz), dtype=torch.complex64, device=dev) for p, _, _, _ in reqs]
+    lat, iters, t_submit = {}, {}, {}
+    tickets = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        while len(lat) < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                p, y, m, pen = reqs[nxt]
+                tickets[nxt] = srv.submit(p, y, m, outs[nxt], penalty=pen, **kw)
+                t_submit[nxt] = now
+                nxt += 1
+            if not tickets:
+                time.sleep(max(0.0, arrivals[nxt] - now))
+                continue
+            srv.step()
+            for i, t in list(tickets.items()):
+                r = srv.poll(t)
+                if r is not None:
+                    lat[i] = (t_submit[i] - arrivals[i]) + r[2]
+                    iters[i] = r[1]["iters"]
+                    del tickets[i]
+    t_end = time.perf_counter() - t0
+    peak = srv.stats()["peak_bytes"]
+    srv.close()
+    served = n_req / (t_end - arrivals[0])
+
+    t1 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for (p, y, m, pen), o in zip(reqs, outs):
+            p.solve(y, m, penalty=pen, out=o, iters=150, min_iter=30, rel_tol=1e-4, lam=LAMBDA_FRAC,
+                    relative=True, power_iters=POWER_ITERS, stream=stream)
+    stream.synchronize()
+    sequential = n_req / (time.perf_counter() - t1)
+    for p in plans.values():
+        p.close()
+    L = np.array([lat[i] for i in range(n_req)])
+    return {"workload": f"{n_req} Poisson requests at {rate_hz:.0f}/s, widths 128-2048, depths 1024/2048, "
+                        "l1/db4, rel_tol 1e-4 in 30-150 iterations, 150 GB budget",
+            "latency_s": {"p50": float(np.percentile(L, 50)), "p99": float(np.percentile(L, 99))},
+            "served_bscans_per_sec": served, "sequential_bscans_per_sec": sequential,
+            "speedup": served / sequential, "mean_iters": float(np.mean(list(iters.values()))),
+            "peak_bytes": int(peak)}
+
+
 # ------------------------------------------------------------ our arm
 
 def run_ours(args, rank: int, ws: int, local: int) -> None:
@@ -416,6 +499,9 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
     batch = None
     if not args.no_batch:
         batch = batch_comparison(dev, torch.cuda.Stream(device=dev))
+    serve = None
+    if not args.no_serve:
+        serve = serve_comparison(dev, torch.cuda.Stream(device=dev), n_req=args.serve_requests)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -441,6 +527,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                            "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
             "kernels_ms_per_launch": {k: v[1] / v[0] for k, v in prof.items()},
             "batch": batch,
+            "serve": serve,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),
