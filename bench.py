@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32 / FP64 comparison")
     return ap.parse_args()
 
 
@@ -294,6 +295,52 @@ def batch_comparison(dev, stream, count: int = 64, repeats: int = 2) -> dict:
             "sequential_bscans_per_sec": res["sequential"], "speedup": res["batched"] / res["sequential"]}
 
 
+# ------------------------------------------------------------ precision
+
+def precision_comparison(dev, stream, repeats: int = 20) -> dict:
+    """The 64 x 256 point-scatterer workload (l1, relative lambda, power iteration)
+    solved with FP32, FP32 with compensated KB accumulation and FP64 plans: the
+    relative L2 distance of the FP32 reconstructions to the FP64 one after 10 / 50 /
+    100 iterations, and solves per second of each precision (throughput ratio
+    FP32 / FP64)."""
+    import numpy as np
+    import torch
+
+    from paper_2108_01438_gb300 import mbir, workloads
+
+    wl = workloads.tiny_workload()
+    out = {"workload": "64x256 point scatterers, l1, relative lambda 0.01, power iteration"}
+    recon, rate = {}, {}
+    for name, mode in (("fp32", mbir.FP32), ("fp32c", mbir.FP32_COMPENSATED), ("fp64", mbir.FP64)):
+        plan = mbir.Plan(wl["geom"], precision=mode, stream=stream)
+        cdt = torch.complex128 if mode == mbir.FP64 else torch.complex64
+        x = torch.from_numpy(wl["x_true"]).to(cdt).to(dev)
+        with torch.cuda.stream(stream):
+            y = plan.forward(x, stream=stream)
+            noise = torch.from_numpy(wl["noise"]).to(y.dtype).to(dev)
+            y = (y + 0.01 * noise).contiguous()
+            recon[name] = {}
+            _, info = plan.solve(y, penalty="l1", lam=LAMBDA_FRAC, iters=1, stream=stream)
+            for k in (10, 50, 100):
+                z, _ = plan.solve(y, penalty="l1", lam=info["lambda_used"], relative=False, iters=k,
+                                  step=info["step"], stream=stream)
+                recon[name][k] = z.to(torch.complex128)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(repeats):
+                plan.solve(y, penalty="l1", lam=LAMBDA_FRAC, iters=100, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        rate[name] = repeats / (e0.elapsed_time(e1) / 1e3)
+        plan.close()
+    for name in ("fp32", "fp32c"):
+        out[f"{name}_vs_fp64_rel_l2"] = {str(k): float(torch.linalg.norm(recon[name][k] - recon["fp64"][k]) /
+                                                       torch.linalg.norm(recon["fp64"][k])) for k in (10, 50, 100)}
+    out["solves_per_sec"] = rate
+    out["fp32_over_fp64_throughput"] = rate["fp32"] / rate["fp64"]
+    return out
+
+
 # ------------------------------------------------------------ serving
 
 def serve_comparison(dev, stream, n_req: int = 200, rate_hz: float = 200.0,
@@ -499,6 +546,9 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
     batch = None
     if not args.no_batch:
         batch = batch_comparison(dev, torch.cuda.Stream(device=dev))
+    precision = None
+    if not args.no_precision:
+        precision = precision_comparison(dev, torch.cuda.Stream(device=dev))
     serve = None
     if not args.no_serve:
         serve = serve_comparison(dev, torch.cuda.Stream(device=dev), n_req=args.serve_requests)
@@ -528,6 +578,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
             "kernels_ms_per_launch": {k: v[1] / v[0] for k, v in prof.items()},
             "batch": batch,
             "serve": serve,
+            "precision": precision,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),

@@ -284,9 +284,30 @@ __device__ __forceinline__ int row_pos(int i, const Radix& rad, const int* perm)
   return rad.pow2 ? digit_reverse_pow2(i, rad) : perm[i];
 }
 
+// Accumulator of sum_i w_i b_i: plain, or error-compensated (two-product of
+// each term by FMA, two-sum of the running total; Ogita, Rump & Oishi's Dot2)
+// for the FP32-compensated precision mode.
+template <class R, bool COMP>
+struct DotAcc {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R w, R b) {
+    if constexpr (!COMP) {
+      s += w * b;
+    } else {
+      const R p = w * b;
+      const R ep = fma(w, b, -p);
+      const R t = s + p;
+      const R bp = t - s;
+      c += ((s - (t - bp)) + (p - bp)) + ep;
+      s = t;
+    }
+  }
+  __device__ __forceinline__ R value() const { return COMP ? s + c : s; }
+};
+
 // --------------------------------------------------------- row kernels (NUFFT)
 
-template <class R, int J>
+template <class R, int J, bool COMP>
 __device__ __forceinline__ void row_forward_body(const RowArgs<R>& a, const Radix& rad, int blk, const RowArgs<R>& a0) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
@@ -338,33 +359,33 @@ __device__ __forceinline__ void row_forward_body(const RowArgs<R>& a, const Radi
       if (mm >= M) continue;
       R w[J];
       kb_weights<R, J>(R(e[u].frac), a0, w);
-      V acc = cmk<V>(R(0), R(0));
       const int pc = e[u].cell & 0xFFFF;
+      DotAcc<R, COMP> ax, ay;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         int idx = pc + j;
         if (idx >= K) idx -= K;
         const V b = buf[swz(idx, sw)];
-        acc.x += w[j] * b.x;
-        acc.y += w[j] * b.y;
+        ax.add(w[j], b.x);
+        ay.add(w[j], b.y);
       }
-      S[mm] = cmul(acc, cmk<V>(R(e[u].fre), R(e[u].fim)));
+      S[mm] = cmul(cmk<V>(ax.value(), ay.value()), cmk<V>(R(e[u].fre), R(e[u].fim)));
     }
   }
 }
 
-template <class R, int J, bool BAT>
+template <class R, int J, bool BAT, bool COMP = false>
 __global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
 row_forward_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<RowArgs<R>> B) {
   if constexpr (!BAT) {
-    row_forward_body<R, J>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_forward_body<R, J, COMP>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<R>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_forward_body<R, J>(A, rad, blk, a0);
+    row_forward_body<R, J, COMP>(A, rad, blk, a0);
   }
 }
 
@@ -450,7 +471,7 @@ row_adjoint_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<RowArgs
 // staged in increasing-u order.  first[c] = min{s : u_s >= c} is built by a
 // conflict-free scatter (each cell written once); cell c then sums its run in a
 // fixed order, so the result is deterministic.
-template <class R, int J>
+template <class R, int J, bool COMP>
 __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, const Radix& rad, int blk, const RowArgs<R>& a0) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
@@ -523,7 +544,7 @@ __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, con
   for (int i = tid; i < K; i += nthr) {
     int c = i - base;
     if (c < 0) c += K;
-    V acc = cmk<V>(R(0), R(0));
+    DotAcc<R, COMP> ax, ay;
     if (c < span) {
       const int slo = c - J + 1 <= 0 ? 0 : int(sfirst[c - J + 1]);
       const int shi = int(sfirst[c + 1]) - 1;
@@ -545,11 +566,11 @@ __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, con
           w = rr < 0.0 ? 0.0 : cyl_bessel_i0(a0.alpha * sqrt(rr)) * a0.inv_i0a;
         }
         const V v = sv[sidx];
-        acc.x += w * v.x;
-        acc.y += w * v.y;
+        ax.add(w, v.x);
+        ay.add(w, v.y);
       }
     }
-    buf[swz(i, sw)] = acc;
+    buf[swz(i, sw)] = cmk<V>(ax.value(), ay.value());
   }
   __syncthreads();
   fft_dif<true>(buf, 1, rad, tw, sw);
@@ -562,18 +583,18 @@ __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, con
   }
 }
 
-template <class R, int J, bool BAT>
+template <class R, int J, bool BAT, bool COMP = false>
 __global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
 row_adjoint_gather_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<RowArgs<R>> B) {
   if constexpr (!BAT) {
-    row_adjoint_gather_body<R, J>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_adjoint_gather_body<R, J, COMP>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<R>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_adjoint_gather_body<R, J>(A, rad, blk, a0);
+    row_adjoint_gather_body<R, J, COMP>(A, rad, blk, a0);
   }
 }
 
@@ -669,39 +690,45 @@ size_t row_gather_smem(mbir_plan p) {
          sizeof(float) * p->J * (kKbDeg + 1) + sizeof(uint16_t) * (M + (M & 1) + p->K + 2);
 }
 
+bool plan_uses_gather(mbir_plan p);
+
+// kind: 0 forward, 1 adjoint gather, 2 adjoint with atomics
+template <class R, int J, bool BAT, bool COMP>
+static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid, size_t smem,
+                         cudaStream_t st) {
+  if (kind == 0) row_forward_kernel<R, J, BAT, COMP><<<grid, kRowThreads, smem, st>>>(a, B);
+  else if (kind == 1) row_adjoint_gather_kernel<R, J, BAT, COMP><<<grid, kRowThreads, smem, st>>>(a, B);
+  else row_adjoint_kernel<R, J, BAT><<<grid, kRowThreads, smem, st>>>(a, B);
+}
+
+template <class R, bool BAT>
+static void row_launch(int kind, int J, bool comp, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid,
+                       size_t smem, cudaStream_t st) {
+  if (comp && sizeof(R) == 4) {
+    switch (J) {
+      case 4: row_launch_j<R, 4, BAT, true>(kind, a, B, grid, smem, st); break;
+      case 6: row_launch_j<R, 6, BAT, true>(kind, a, B, grid, smem, st); break;
+      default: row_launch_j<R, 8, BAT, true>(kind, a, B, grid, smem, st); break;
+    }
+  } else {
+    switch (J) {
+      case 4: row_launch_j<R, 4, BAT, false>(kind, a, B, grid, smem, st); break;
+      case 6: row_launch_j<R, 6, BAT, false>(kind, a, B, grid, smem, st); break;
+      default: row_launch_j<R, 8, BAT, false>(kind, a, B, grid, smem, st); break;
+    }
+  }
+}
+
 template <class R>
 int launch_row(mbir_plan p, bool adjoint, const void* in, void* out, cudaStream_t st) {
   RowArgs<R> a = row_args<R>(p, in, out);
-  const size_t gsmem = row_gather_smem<R>(p);
-  if (adjoint && !kAdjAtomic && p->gather_ok && gsmem <= (size_t)kMaxDynSmem) {
-    {
-      ProfScope ps_(p, PC_ROW_ADJ, st);
-      switch (p->J) {
-        case 4: row_adjoint_gather_kernel<R, 4, false><<<p->nx, kRowThreads, gsmem, st>>>(a, no_batch<RowArgs<R>>()); break;
-        case 6: row_adjoint_gather_kernel<R, 6, false><<<p->nx, kRowThreads, gsmem, st>>>(a, no_batch<RowArgs<R>>()); break;
-        default: row_adjoint_gather_kernel<R, 8, false><<<p->nx, kRowThreads, gsmem, st>>>(a, no_batch<RowArgs<R>>()); break;
-      }
-    }
-    MBIR_LAUNCH_CHECK();
-    return MBIR_OK;
-  }
-  const size_t smem = row_smem<R>(p);
+  const bool gather = adjoint && plan_uses_gather(p);
+  const int kind = adjoint ? (gather ? 1 : 2) : 0;
+  const size_t smem = gather ? row_gather_smem<R>(p) : row_smem<R>(p);
   {
     ProfScope ps_(p, adjoint ? PC_ROW_ADJ : PC_ROW_FWD, st);
-    switch (p->J) {
-      case 4:
-        if (adjoint) row_adjoint_kernel<R, 4, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
-        else row_forward_kernel<R, 4, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
-        break;
-      case 6:
-        if (adjoint) row_adjoint_kernel<R, 6, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
-        else row_forward_kernel<R, 6, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
-        break;
-      default:
-        if (adjoint) row_adjoint_kernel<R, 8, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
-        else row_forward_kernel<R, 8, false><<<p->nx, kRowThreads, smem, st>>>(a, no_batch<RowArgs<R>>());
-        break;
-    }
+    row_launch<R, false>(kind, p->J, p->precision == MBIR_FP32_COMPENSATED, a, no_batch<RowArgs<R>>(), p->nx,
+                         smem, st);
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -824,6 +851,18 @@ static int configure_t() {
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6, true>), gat);
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, false>), gat);
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, true>), gat);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 4, false, true>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 6, false, true>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 8, false, true>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 4, true, true>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 6, true, true>), row);
+  MBIR_SMEM_ATTR((row_forward_kernel<R, 8, true, true>), row);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 4, false, true>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6, false, true>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, false, true>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 4, true, true>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6, true, true>), gat);
+  MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, true, true>), gat);
 #undef MBIR_SMEM_ATTR
   return MBIR_OK;
 }
@@ -947,8 +986,8 @@ int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st
   return MBIR_OK;
 }
 
-template <class R, int J>
-static void row_batch_t(int kind, const BatchLaunch& L, cudaStream_t st) {
+template <class R>
+static void row_batch_t(int kind, int J, bool comp, const BatchLaunch& L, cudaStream_t st) {
   BatchRef<RowArgs<R>> B;
   B.args = reinterpret_cast<const RowArgs<R>*>(L.dargs);
   B.off = L.doff;
@@ -957,20 +996,13 @@ static void row_batch_t(int kind, const BatchLaunch& L, cudaStream_t st) {
   B.mu = 0.0;
   RowArgs<R> a0;
   memcpy(&a0, L.host0, sizeof(a0));
-  if (kind == 0) row_forward_kernel<R, J, true><<<L.total, kRowThreads, L.smem, st>>>(a0, B);
-  else if (kind == 1) row_adjoint_gather_kernel<R, J, true><<<L.total, kRowThreads, L.smem, st>>>(a0, B);
-  else row_adjoint_kernel<R, J, true><<<L.total, kRowThreads, L.smem, st>>>(a0, B);
+  row_launch<R, true>(kind, J, comp, a0, B, L.total, L.smem, st);
 }
 
-// kind: 0 forward, 1 adjoint gather, 2 adjoint with atomics
 int batch_row(int kind, int precision, int J, const BatchLaunch& L, cudaStream_t st) {
   if (L.total <= 0) return MBIR_OK;
-  const bool f64 = precision == MBIR_FP64;
-  switch (J) {
-    case 4: f64 ? row_batch_t<double, 4>(kind, L, st) : row_batch_t<float, 4>(kind, L, st); break;
-    case 6: f64 ? row_batch_t<double, 6>(kind, L, st) : row_batch_t<float, 6>(kind, L, st); break;
-    default: f64 ? row_batch_t<double, 8>(kind, L, st) : row_batch_t<float, 8>(kind, L, st); break;
-  }
+  if (precision == MBIR_FP64) row_batch_t<double>(kind, J, false, L, st);
+  else row_batch_t<float>(kind, J, precision == MBIR_FP32_COMPENSATED, L, st);
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
 }
