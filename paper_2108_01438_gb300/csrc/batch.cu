@@ -27,8 +27,9 @@ struct ScanVec {
   void* v;
   void* w;
   size_t n;
-  double* part;   // 2 * kBBlocks doubles
+  double* part;   // partial sums (pairs for the power iteration)
   double* scal;   // scalars
+  int np;         // partial pairs b_power_finalize reads (0: kBBlocks)
 };
 
 __device__ __forceinline__ double bsum(double v) {
@@ -107,6 +108,7 @@ __global__ void b_dot_norm(const ScanVec* sv) {
 // scal[0] = <v, w>, scal[1] = 1/||w||
 __global__ void b_power_finalize(const ScanVec* sv, int nb) {
   const ScanVec s = sv[blockIdx.y];
+  if (s.np > 0) nb = s.np;
   double d = 0.0, q = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     d += s.part[2 * i];
@@ -227,7 +229,8 @@ size_t ctx_bytes(mbir_plan p, int penalty, int trace_cap) {
   const size_t img = (size_t)p->nx * p->nz, meas = (size_t)p->nx * p->m;
   size_t b = 2 * es * p->ws_elems + 3 * es * img + 2 * rs * meas;
   if (penalty == MBIR_PENALTY_DB4) b += es * (img / 4 + img / 16 + img);
-  b += sizeof(double) * ((size_t)lateral_grid(p, p->m) + reg_partials(p) + 2 * 1024 + 16 + trace_cap);
+  b += sizeof(double) * ((size_t)lateral_grid(p, p->m) + reg_partials(p) + 2 * (size_t)part_tmp_count(p) + 16 +
+                         trace_cap);
   return b;
 }
 
@@ -267,7 +270,7 @@ int ctx_alloc(mbir_plan p, int penalty, int trace_cap, Ctx* out) {
   }
   A((void**)&c.part_data, sizeof(double) * c.n_data);
   A((void**)&c.part_reg, sizeof(double) * c.n_reg);
-  A((void**)&c.part_tmp, sizeof(double) * 2 * 1024);
+  A((void**)&c.part_tmp, sizeof(double) * 2 * part_tmp_count(p));
   A((void**)&c.scal, sizeof(double) * 16);
   A((void**)&c.objtrace, sizeof(double) * std::max(trace_cap, 1));
   if (e != cudaSuccess) {
@@ -499,16 +502,26 @@ int Engine::setup(const std::vector<BScan*>& scans) {
   std::vector<Stage> pst, lst;
   size_t v_self = 0, v_pair = 0, v_lam = 0;
   if (!pw.empty()) {
-    if ((rc = add_lateral(pst, LAT_C2C_FWD, pw, [](BScan& s) { return lfill(s.c.v, s.c.wsA, nullptr, s.p->nz, 1.0); }, false))) return rc;
+    // power iteration: w = start, then v = w/||w||, w = Phi^H s Phi v per step
+    if ((rc = add_lateral(pst, LAT_POWER_FWD, pw, [](BScan& s) {
+           LatFill f = lfill(s.c.zA, s.c.wsA, nullptr, s.p->nz, 1.0);
+           f.vout = s.c.v;
+           f.scal = s.c.scal;
+           return f; }, false)))
+      return rc;
     if ((rc = add_row(pst, false, pw))) return rc;
-    if ((rc = add_lateral(pst, LAT_C2R_INV_MASK, pw, [](BScan& s) { return lfill(s.c.wsB, s.c.r, s.mask, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
-    if ((rc = add_lateral(pst, LAT_R2C_MASK, pw, [](BScan& s) { return lfill(s.c.r, s.c.wsA, s.mask, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
+    if ((rc = add_lateral(pst, LAT_POWER_MID, pw, [](BScan& s) { return lfill(s.c.wsB, s.c.wsA, s.mask, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
     if ((rc = add_row(pst, true, pw))) return rc;
-    if ((rc = add_lateral(pst, LAT_C2C_INV, pw, [](BScan& s) { return lfill(s.c.wsB, s.c.zA, nullptr, s.p->nz, 1.0); }, false))) return rc;
+    if ((rc = add_lateral(pst, LAT_POWER_ADJ, pw, [](BScan& s) {
+           LatFill f = lfill(s.c.wsB, s.c.zA, nullptr, s.p->nz, 1.0);
+           f.z1 = s.c.v;
+           f.partial = s.c.part_tmp;
+           return f; }, false)))
+      return rc;
     std::vector<ScanVec> a, b;
     for (BScan* s : pw) {
-      a.push_back({s->c.v, s->c.v, s->c.nimg, s->c.part_tmp, s->c.scal});
-      b.push_back({s->c.v, s->c.zA, s->c.nimg, s->c.part_tmp, s->c.scal});
+      a.push_back({s->c.zA, s->c.zA, s->c.nimg, s->c.part_tmp, s->c.scal, 0});
+      b.push_back({s->c.v, s->c.zA, s->c.nimg, s->c.part_tmp, s->c.scal, lateral_grid(s->p, s->p->nz)});
     }
     v_self = push(a.data(), a.size() * sizeof(ScanVec));
     v_pair = push(b.data(), b.size() * sizeof(ScanVec));
@@ -530,21 +543,20 @@ int Engine::setup(const std::vector<BScan*>& scans) {
     }
     std::vector<ScanVec> a;
     for (BScan* s : lm)
-      a.push_back({s->o.penalty == MBIR_PENALTY_DB4 ? s->c.v : s->c.zA, nullptr, s->c.nimg, s->c.part_tmp, s->c.scal});
+      a.push_back({s->o.penalty == MBIR_PENALTY_DB4 ? s->c.v : s->c.zA, nullptr, s->c.nimg, s->c.part_tmp, s->c.scal, 0});
     v_lam = push(a.data(), a.size() * sizeof(ScanVec));
   }
   if ((rc = upload())) return rc;
   if (!pw.empty()) {
     const int np = (int)pw.size();
-    for (int w : {0, 1, 2, 3})
+    for (int w : {0, 1, 2})
       if ((rc = vec_kernel(w, v_self, np))) return rc;
     int iters = 0;
     for (BScan* s : pw) iters = std::max(iters, s->o.power_iters > 0 ? s->o.power_iters : 30);
     for (int it = 0; it < iters; ++it) {
       for (const Stage& g : pst)
         if ((rc = run(g, 0.0))) return rc;
-      for (int w : {1, 2, 3})
-        if ((rc = vec_kernel(w, v_pair, np))) return rc;
+      if ((rc = vec_kernel(2, v_pair, np))) return rc;
     }
   }
   if (!lm.empty()) {
@@ -608,11 +620,10 @@ int Engine::build_iteration(std::vector<Stage>& out, const std::vector<BScan*>& 
   int rc;
   if ((rc = add_lateral(out, LAT_C2C_FWD, scans, [&](BScan& s) { return lfill(z1(s), s.c.wsA, nullptr, s.p->nz, 1.0); }, false))) return rc;
   if ((rc = add_row(out, false, scans))) return rc;
-  if ((rc = add_lateral(out, LAT_SOLVE_FWD, scans, [&](BScan& s) {
-         LatFill f = lfill(s.c.wsB, nullptr, s.mask, s.p->m, 1.0 / s.p->nx);
+  if ((rc = add_lateral(out, LAT_SOLVE_MID, scans, [&](BScan& s) {
+         LatFill f = lfill(s.c.wsB, s.c.wsA, s.mask, s.p->m, 1.0 / s.p->nx);
          f.y = s.y;
          f.pz = s.c.pz;
-         f.r = s.c.r;
          f.partial = s.c.part_data;
          f.mu = mu_of(s);
          return f; }, !per_scan_mu)))
@@ -638,7 +649,6 @@ int Engine::build_iteration(std::vector<Stage>& out, const std::vector<BScan*>& 
     g.arg_off = push(oa.data(), oa.size() * sizeof(ObjArgs));
     out.push_back(g);
   }
-  if ((rc = add_lateral(out, LAT_R2C_MASK, scans, [&](BScan& s) { return lfill(s.c.r, s.c.wsA, nullptr, s.p->m, 1.0 / s.p->nx); }, false))) return rc;
   if ((rc = add_row(out, true, scans))) return rc;
   if ((rc = add_lateral(out, LAT_SOLVE_ADJ_L1, l1, [&](BScan& s) {
          LatFill f = lfill(s.c.wsB, nullptr, nullptr, s.p->nz, 1.0);

@@ -104,6 +104,7 @@ enum ProfClass {
   PC_DWT_INV,         // wavelet synthesis level
   PC_SOFT,            // elementwise soft-threshold
   PC_REDUCE,          // reductions, scalars, power-iteration helpers
+  PC_LAT_MID,         // inverse lateral FFT + measurement epilogue + lateral FFT (Phi^H Phi middle)
   PC_COUNT
 };
 
@@ -219,6 +220,7 @@ struct LatFill {
   void* vout;
   double mu, delta, tau;
   double* partial;
+  const double* scal;
 };
 
 // operator.cu (batch helpers)
@@ -244,11 +246,16 @@ int batch_dwt(int inverse, int precision, const BatchLaunch& L, cudaStream_t st)
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st);
 int adjoint_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st);
 int configure_operator_kernels(mbir_plan p);
-int forward_solve_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
-                       double mu, double* partial, cudaStream_t st);
-// vout == nullptr: l1 prox fused (z^k written over z2); else v written to vout
-int adjoint_solve_impl(mbir_plan p, const void* r, const void* z1, void* z2, void* vout, double mu,
-                       double delta, double tau, double* partial, cudaStream_t st);
+// FISTA forward pass on z1 with the fused middle: pz = Phi z1, data-term partials,
+// R = first stage of Phi^H on r = (1 + mu) pz - mu pz_prev - s y left in wsA
+int forward_solve_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, double mu,
+                       double* partial, cudaStream_t st);
+// rest of Phi^H from wsA; vout == nullptr: l1 prox fused (z^k written over z2); else v written to vout
+int adjoint_solve_impl(mbir_plan p, const void* z1, void* z2, void* vout, double mu, double delta, double tau,
+                       double* partial, cudaStream_t st);
+// power-iteration step: v = w scal[1], w = Phi^H s Phi v, partials of <v, w>, ||w||^2
+int power_step_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, const double* scal, double* part,
+                    cudaStream_t st);
 int lateral_grid(mbir_plan p, int cols);
 
 // wavelet.cu
@@ -259,5 +266,6 @@ int configure_wavelet_kernels(mbir_plan p);
 
 // solve.cu
 void destroy_solve_state(mbir_plan p);
+int part_tmp_count(mbir_plan p);
 
 }  // namespace mbir

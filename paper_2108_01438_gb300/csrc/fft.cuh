@@ -154,6 +154,51 @@ __device__ __forceinline__ void dft_small(V (&v)[R], const Tw2<V>& tw, int N) {
   }
 }
 
+// v[q] *= w_N^{q e1} (conjugated for inverse transforms), q = 1 .. R-1.  For the
+// power-of-two radices only w^{e1} (and w^{4 e1} for R = 16) come from the
+// tables; the other powers are products of those, at most three multiplications
+// deep, which costs one complex multiplication per twiddle instead of a two-table
+// lookup and a multiplication.
+template <int R, bool INV, class V>
+__device__ __forceinline__ void apply_twiddles(V (&v)[R], const Tw2<V>& tw, int e1) {
+  auto get = [&](int e) {
+    const V w = tw(e);
+    return INV ? cconj(w) : w;
+  };
+  if constexpr (R == 2) {
+    v[1] = cmul(v[1], get(e1));
+  } else if constexpr (R == 4 || R == 8 || R == 16) {
+    const V w1 = get(e1);
+    const V w2 = cmul(w1, w1);
+    const V w3 = cmul(w2, w1);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    if constexpr (R >= 8) {
+      const V w4 = R == 16 ? get(4 * e1) : cmul(w2, w2);
+      v[4] = cmul(v[4], w4);
+      v[5] = cmul(v[5], cmul(w4, w1));
+      v[6] = cmul(v[6], cmul(w4, w2));
+      v[7] = cmul(v[7], cmul(w4, w3));
+      if constexpr (R == 16) {
+        const V w8 = cmul(w4, w4);
+        v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], cmul(w8, w1));
+        v[10] = cmul(v[10], cmul(w8, w2));
+        v[11] = cmul(v[11], cmul(w8, w3));
+        const V w12 = cmul(w8, w4);
+        v[12] = cmul(v[12], w12);
+        v[13] = cmul(v[13], cmul(w12, w1));
+        v[14] = cmul(v[14], cmul(w12, w2));
+        v[15] = cmul(v[15], cmul(w12, w3));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = cmul(v[q], get(q * e1));
+  }
+}
+
 // x = a / d and a - x d, with a shift when d is a power of two (uniform branch).
 __device__ __forceinline__ void divmod_u(int a, int d, int d_shift, int& q, int& r) {
   if (d_shift >= 0) {
@@ -184,23 +229,9 @@ __device__ __forceinline__ void ct_pass(V* s, int N, int batch, int bshift, int 
     V v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[swz(base + r * M, sw) * batch + b];
-    if (DIT && j != 0) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        V w = tw(r * j * tstep);
-        if (INV) w = cconj(w);
-        v[r] = cmul(v[r], w);
-      }
-    }
+    if (DIT && j != 0) apply_twiddles<R, INV>(v, tw, j * tstep);
     dft_small<R, INV>(v, tw, N);
-    if (!DIT && j != 0) {
-#pragma unroll
-      for (int q = 1; q < R; ++q) {
-        V w = tw(q * j * tstep);
-        if (INV) w = cconj(w);
-        v[q] = cmul(v[q], w);
-      }
-    }
+    if (!DIT && j != 0) apply_twiddles<R, INV>(v, tw, j * tstep);
 #pragma unroll
     for (int r = 0; r < R; ++r) s[swz(base + r * M, sw) * batch + b] = v[r];
   }

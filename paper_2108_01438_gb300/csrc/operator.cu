@@ -75,83 +75,232 @@ struct LatEp {
   const void* z1;
   void* z2;
   void* vout;
+  const double* scal;
   R scale, mu, delta, tau;
 };
 
+// --------------------------------------------------------- column pairs
+//
+// A lateral tile is moved as column pairs (c, c + 1): with an even row length
+// and suitably aligned bases one pair is one vector access.
+
+template <class T> struct PairOf { using V = void; };
+template <> struct PairOf<float> { using V = float2; };
+template <> struct PairOf<double> { using V = double2; };
+template <> struct PairOf<float2> { using V = float4; };
+template <> struct PairOf<uint8_t> { using V = uchar2; };
+
+// a = p[o], b = p[o + 1] where in range (unchanged otherwise)
+template <class T>
+__device__ __forceinline__ void ld2(const T* p, size_t o, bool v2, bool ok0, bool ok1, T& a, T& b) {
+  using PV = typename PairOf<T>::V;
+  if constexpr (!std::is_same<PV, void>::value) {
+    if (v2) {
+      const PV t = *reinterpret_cast<const PV*>(p + o);
+      memcpy(&a, &t, sizeof(T));
+      memcpy(&b, reinterpret_cast<const unsigned char*>(&t) + sizeof(T), sizeof(T));
+      return;
+    }
+  }
+  if (ok0) a = p[o];
+  if (ok1) b = p[o + 1];
+}
+
+template <class T>
+__device__ __forceinline__ void st2(T* p, size_t o, bool v2, bool ok0, bool ok1, T a, T b) {
+  using PV = typename PairOf<T>::V;
+  if constexpr (!std::is_same<PV, void>::value) {
+    if (v2) {
+      PV t;
+      memcpy(&t, &a, sizeof(T));
+      memcpy(reinterpret_cast<unsigned char*>(&t) + sizeof(T), &b, sizeof(T));
+      *reinterpret_cast<PV*>(p + o) = t;
+      return;
+    }
+  }
+  if (ok0) p[o] = a;
+  if (ok1) p[o + 1] = b;
+}
+
+// shared-memory pair at an even index (16-byte aligned for FP32)
+template <class V>
+__device__ __forceinline__ void lds2(const V* s, int i, V& a, V& b) {
+  if constexpr (sizeof(V) == 8) {
+    const float4 t = *reinterpret_cast<const float4*>(s + i);
+    a = cmk<V>(t.x, t.y);
+    b = cmk<V>(t.z, t.w);
+  } else {
+    a = s[i];
+    b = s[i + 1];
+  }
+}
+
+template <class V>
+__device__ __forceinline__ void sts2(V* s, int i, V a, V b) {
+  if constexpr (sizeof(V) == 8) {
+    *reinterpret_cast<float4*>(s + i) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    s[i] = a;
+    s[i + 1] = b;
+  }
+}
+
+__device__ __forceinline__ bool al(const void* p, unsigned bytes) {
+  return p == nullptr || (reinterpret_cast<uintptr_t>(p) & (bytes - 1)) == 0;
+}
+
+// Every base a mode touches allows pair accesses.
+template <class R, int MODE, class A>
+__device__ __forceinline__ bool lat_pairs_aligned(const A& a) {
+  const unsigned c2 = 2 * sizeof(cplx_t<R>) <= 16 ? 2 * sizeof(cplx_t<R>) : 16, r2 = 2 * sizeof(R);
+  const bool real_in = MODE == LAT_R2C_MASK;
+  bool ok = al(a.in, real_in ? r2 : c2) && al(a.mask, 2);
+  if constexpr (MODE == LAT_C2R_INV_MASK) ok = ok && al(a.out, r2);
+  else ok = ok && al(a.out, c2);
+  if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_MID) ok = ok && al(a.y, r2) && al(a.pz, r2) && al(a.r, r2);
+  if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V || MODE == LAT_POWER_ADJ || MODE == LAT_POWER_FWD)
+    ok = ok && al(a.z1, c2) && al(a.z2, c2) && al(a.vout, c2);
+  return ok;
+}
+
 // --------------------------------------------------------------- lateral FFT
 
-// Load element (p, c) of the lateral input as complex.
+// Load the pair (p, c), (p, c + 1) of the lateral input as complex.
 template <class R, int MODE, class A>
-__device__ __forceinline__ cplx_t<R> lat_load(const A& a, size_t off) {
+__device__ __forceinline__ void lat_load2(const A& a, size_t off, bool v2, bool ok0, bool ok1, cplx_t<R>& va,
+                                          cplx_t<R>& vb) {
   using V = cplx_t<R>;
   if constexpr (MODE == LAT_R2C_MASK) {
-    const R r = reinterpret_cast<const R*>(a.in)[off];
-    return cmk<V>((a.mask == nullptr || a.mask[off]) ? r : R(0), R(0));
+    R x0 = R(0), x1 = R(0);
+    ld2(reinterpret_cast<const R*>(a.in), off, v2, ok0, ok1, x0, x1);
+    if (a.mask != nullptr) {
+      uint8_t m0 = 0, m1 = 0;
+      ld2(a.mask, off, v2, ok0, ok1, m0, m1);
+      if (!m0) x0 = R(0);
+      if (!m1) x1 = R(0);
+    }
+    va = cmk<V>(x0, R(0));
+    vb = cmk<V>(x1, R(0));
   } else {
-    return reinterpret_cast<const V*>(a.in)[off];
+    ld2(reinterpret_cast<const V*>(a.in), off, v2, ok0, ok1, va, vb);
   }
 }
 
 // Operands an epilogue reads besides the transform output, fetched ahead of use
-// so that several elements' loads are in flight at once.
+// so that several rows' loads are in flight at once.
 template <class R>
 struct EpOps {
   R y, prev;
   cplx_t<R> z1, z2;
-  bool meas;
+  uint8_t meas;
 };
 
 template <class R, int MODE, class A>
-__device__ __forceinline__ EpOps<R> lat_prefetch(const A& a, size_t off) {
+__device__ __forceinline__ void lat_prefetch2(const A& a, size_t off, bool v2, bool ok0, bool ok1, EpOps<R>& o0,
+                                              EpOps<R>& o1) {
   using V = cplx_t<R>;
-  EpOps<R> o;
-  if constexpr (MODE == LAT_C2R_INV_MASK) {
-    o.meas = (a.mask == nullptr || a.mask[off]);
-  } else if constexpr (MODE == LAT_SOLVE_FWD) {
-    o.meas = (a.mask == nullptr || a.mask[off]);
-    o.y = a.y[off];
-    o.prev = a.pz[off];
-  } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
-    o.z1 = reinterpret_cast<const V*>(a.z1)[off];
-    o.z2 = reinterpret_cast<const V*>(a.z2)[off];
+  if constexpr (MODE == LAT_C2R_INV_MASK || MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_MID ||
+                MODE == LAT_POWER_MID) {
+    o0.meas = o1.meas = 1;
+    if (a.mask != nullptr) ld2(a.mask, off, v2, ok0, ok1, o0.meas, o1.meas);
   }
-  return o;
+  if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_MID) {
+    o0.y = o1.y = o0.prev = o1.prev = R(0);
+    ld2(a.y, off, v2, ok0, ok1, o0.y, o1.y);
+    ld2(static_cast<const R*>(a.pz), off, v2, ok0, ok1, o0.prev, o1.prev);
+  } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
+    ld2(reinterpret_cast<const V*>(a.z1), off, v2, ok0, ok1, o0.z1, o1.z1);
+    ld2(reinterpret_cast<const V*>(a.z2), off, v2, ok0, ok1, o0.z2, o1.z2);
+  } else if constexpr (MODE == LAT_POWER_ADJ) {
+    o0.z1 = o1.z1 = cmk<V>(R(0), R(0));
+    ld2(reinterpret_cast<const V*>(a.z1), off, v2, ok0, ok1, o0.z1, o1.z1);
+  }
 }
 
+// Measurement-side FISTA epilogue of one element (Eq. alg): pz = s Re{S}/nx,
+// r = (1 + mu) pz - mu pz_prev - s y; accumulates (pz - s y)^2.
+template <class R, class A>
+__device__ __forceinline__ R solve_meas(const A& a, R sre, const EpOps<R>& o, R& pz, double& part) {
+  pz = o.meas ? sre * a.scale : R(0);
+  const R yv = o.meas ? o.y : R(0);
+  const R d = pz - yv;
+  part += double(d) * double(d);
+  return (R(1) + a.mu) * pz - a.mu * o.prev - yv;
+}
+
+// Image-side epilogue of one element: x^k - delta g, then the l1 prox (ADJ_L1) or
+// the pre-prox image v (ADJ_V).
 template <class R, int MODE, class A>
-__device__ __forceinline__ void lat_store(const A& a, size_t off, cplx_t<R> v, const EpOps<R>& o,
-                                          double& part) {
+__device__ __forceinline__ cplx_t<R> solve_img(const A& a, cplx_t<R> g, const EpOps<R>& o, double& part) {
+  using V = cplx_t<R>;
+  V xv;
+  xv.x = o.z1.x + a.mu * (o.z1.x - o.z2.x) - a.delta * g.x;
+  xv.y = o.z1.y + a.mu * (o.z1.y - o.z2.y) - a.delta * g.y;
+  if constexpr (MODE == LAT_SOLVE_ADJ_L1) {
+    const R mag = sqrt(xv.x * xv.x + xv.y * xv.y);
+    const R sh = mag > a.tau ? R(1) - a.tau / mag : R(0);
+    xv.x *= sh;
+    xv.y *= sh;
+    part += mag > a.tau ? double(mag - a.tau) : 0.0;
+  }
+  return xv;
+}
+
+// Store the pair of transform outputs (va, vb) at (p, c), (p, c + 1).
+template <class R, int MODE, class A>
+__device__ __forceinline__ void lat_store2(const A& a, size_t off, bool v2, bool ok0, bool ok1, cplx_t<R> va,
+                                           cplx_t<R> vb, const EpOps<R>& o0, const EpOps<R>& o1, double& part,
+                                           double& part2) {
   using V = cplx_t<R>;
   if constexpr (MODE == LAT_C2R_INV_MASK) {
-    reinterpret_cast<R*>(a.out)[off] = o.meas ? v.x * a.scale : R(0);
+    st2(reinterpret_cast<R*>(a.out), off, v2, ok0, ok1, o0.meas ? va.x * a.scale : R(0),
+        o1.meas ? vb.x * a.scale : R(0));
   } else if constexpr (MODE == LAT_SOLVE_FWD) {
-    const R pz = o.meas ? v.x * a.scale : R(0);
-    const R yv = o.meas ? o.y : R(0);
-    const R d = pz - yv;
-    part += double(d) * double(d);
-    a.pz[off] = pz;
-    a.r[off] = (R(1) + a.mu) * pz - a.mu * o.prev - yv;
+    R pa, pb;
+    double pa_part = 0.0, pb_part = 0.0;
+    const R ra = solve_meas<R>(a, va.x, o0, pa, pa_part);
+    const R rb = solve_meas<R>(a, vb.x, o1, pb, pb_part);
+    if (ok0) part += pa_part;
+    if (ok1) part += pb_part;
+    st2(a.pz, off, v2, ok0, ok1, pa, pb);
+    st2(a.r, off, v2, ok0, ok1, ra, rb);
   } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
-    V xv;
-    xv.x = o.z1.x + a.mu * (o.z1.x - o.z2.x) - a.delta * v.x;
-    xv.y = o.z1.y + a.mu * (o.z1.y - o.z2.y) - a.delta * v.y;
-    if constexpr (MODE == LAT_SOLVE_ADJ_L1) {
-      const R mag = sqrt(xv.x * xv.x + xv.y * xv.y);
-      const R sh = mag > a.tau ? R(1) - a.tau / mag : R(0);
-      xv.x *= sh;
-      xv.y *= sh;
-      part += mag > a.tau ? double(mag - a.tau) : 0.0;
-      reinterpret_cast<V*>(a.z2)[off] = xv;
-    } else {
-      reinterpret_cast<V*>(a.vout)[off] = xv;
+    double qa = 0.0, qb = 0.0;
+    const V xa = solve_img<R, MODE>(a, va, o0, qa);
+    const V xb = solve_img<R, MODE>(a, vb, o1, qb);
+    if (ok0) part += qa;
+    if (ok1) part += qb;
+    st2(reinterpret_cast<V*>(MODE == LAT_SOLVE_ADJ_L1 ? a.z2 : a.vout), off, v2, ok0, ok1, xa, xb);
+  } else if constexpr (MODE == LAT_POWER_ADJ) {
+    // w = Phi^H Phi v, with <v, w> and ||w||^2 partial sums
+    if (ok0) {
+      part += double(o0.z1.x) * double(va.x) + double(o0.z1.y) * double(va.y);
+      part2 += double(va.x) * double(va.x) + double(va.y) * double(va.y);
     }
+    if (ok1) {
+      part += double(o1.z1.x) * double(vb.x) + double(o1.z1.y) * double(vb.y);
+      part2 += double(vb.x) * double(vb.x) + double(vb.y) * double(vb.y);
+    }
+    st2(reinterpret_cast<V*>(a.out), off, v2, ok0, ok1, va, vb);
   } else {
-    reinterpret_cast<V*>(a.out)[off] = cscale(v, a.scale);
+    st2(reinterpret_cast<V*>(a.out), off, v2, ok0, ok1, cscale(va, a.scale), cscale(vb, a.scale));
   }
+}
+
+template <int MODE>
+constexpr bool lat_is_mid() {
+  return MODE == LAT_SOLVE_MID || MODE == LAT_POWER_MID;
 }
 
 // One lateral tile: `a` supplies the operands (the launch's argument block, or a
 // register copy of a batched scan's block), `rad` the nx-point radix plan.
+// Thread t owns the column pair b = 2 (t mod TC/2) of rows p0 = t / (TC/2),
+// p0 + pstep, ...; the staging loops keep U rows of loads in flight per thread.
+//
+// Single-transform modes: stage in natural order, one decimation-in-frequency
+// FFT, epilogue on the digit-reversed result.  Mid modes (the measurement side of
+// Phi^H Phi): inverse FFT (dif), the measurement epilogue in place on the
+// digit-reversed tile, forward FFT (dit, digit-reversed in, natural out).
 template <class R, int MODE, class A>
 __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int nx, int TC, int C, int blk,
                                              const void* twg, const int* perm, double* partial) {
@@ -159,70 +308,121 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s = reinterpret_cast<V*>(smem_raw);
   V* tws = s + nx * TC;
-  const int c0 = blk * TC;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(twg), rad);
-  // stage the tile: column pairs (b, b+1), four pairs in flight per thread
-  const int half = TC >> 1;
-  const int npairs = nx * half;
+  const int half = TC >> 1, hs = __ffs(half) - 1;
+  const int b = 2 * (tid & (half - 1));
+  const int p0 = tid >> hs, pstep = (int)blockDim.x >> hs;
+  const int c = blk * TC + b;
+  const bool ok0 = c < C, ok1 = c + 1 < C;
+  const bool v2 = ok1 && (C & 1) == 0 && lat_pairs_aligned<R, MODE>(a);
   constexpr int U = 4;
-  for (int e0 = tid; e0 < npairs; e0 += U * nthr) {
+  const V zero = cmk<V>(R(0), R(0));
+  R fscale = R(1);
+  if constexpr (MODE == LAT_POWER_FWD) fscale = R(a.scal[1]);
+  for (int p = p0; p < nx; p += U * pstep) {
     V va[U], vb[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * nthr;
-      va[u] = vb[u] = cmk<V>(R(0), R(0));
-      if (e < npairs) {
-        const int p = e / half, b = 2 * (e - p * half);
-        const int c = c0 + b;
-        const size_t off = (size_t)p * C + c;
-        if (c < C) va[u] = lat_load<R, MODE>(a, off);
-        if (c + 1 < C) vb[u] = lat_load<R, MODE>(a, off + 1);
-      }
+      va[u] = vb[u] = zero;
+      const int pp = p + u * pstep;
+      if (pp < nx) lat_load2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, va[u], vb[u]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * nthr;
-      if (e < npairs) {
-        const int p = e / half, b = 2 * (e - p * half);
-        s[p * TC + b] = va[u];
-        s[p * TC + b + 1] = vb[u];
+      const int pp = p + u * pstep;
+      if (pp < nx) {
+        if constexpr (MODE == LAT_POWER_FWD) {
+          va[u] = cscale(va[u], fscale);
+          vb[u] = cscale(vb[u], fscale);
+          st2(reinterpret_cast<V*>(a.vout), (size_t)pp * C + c, v2, ok0, ok1, va[u], vb[u]);
+        }
+        if constexpr (lat_is_mid<MODE>()) {
+          // inverse transform as conj(FFT(conj S)); the epilogue reads only its real part
+          va[u].y = -va[u].y;
+          vb[u].y = -vb[u].y;
+        }
+        sts2(s, pp * TC + b, va[u], vb[u]);
       }
     }
   }
   __syncthreads();
-  constexpr bool INV = (MODE != LAT_C2C_FWD && MODE != LAT_R2C_MASK);
-  fft_dif<INV>(s, TC, rad, tw, false);
-  double part = 0.0;
-  for (int e0 = tid; e0 < npairs; e0 += U * nthr) {
-    EpOps<R> oa[U], ob[U];
+  constexpr bool kMid = lat_is_mid<MODE>();
+  constexpr bool INV = !(MODE == LAT_C2C_FWD || MODE == LAT_R2C_MASK || MODE == LAT_POWER_FWD);
+  double part = 0.0, part2 = 0.0;
+  if constexpr (kMid) {
+    // inverse as a forward dif of conj S, the epilogue in place on the
+    // digit-reversed tile, then the forward dit
+    fft_dif<false>(s, TC, rad, tw, false);
+    constexpr int UM = 2;
+    for (int p = p0; p < nx; p += UM * pstep) {
+      EpOps<R> oa[UM], ob[UM];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * nthr;
-      if (e < npairs) {
-        const int p = e / half, b = 2 * (e - p * half);
-        const int c = c0 + b;
-        const size_t off = (size_t)p * C + c;
-        if (c < C) oa[u] = lat_prefetch<R, MODE>(a, off);
-        if (c + 1 < C) ob[u] = lat_prefetch<R, MODE>(a, off + 1);
+      for (int u = 0; u < UM; ++u) {
+        const int pp = p + u * pstep;
+        if (pp < nx) lat_prefetch2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, oa[u], ob[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < UM; ++u) {
+        const int pp = p + u * pstep;
+        if (pp >= nx) continue;
+        const size_t off = (size_t)pp * C + c;
+        const int slot = perm[pp] * TC + b;
+        V xa, xb;
+        lds2(s, slot, xa, xb);
+        R ra, rb;
+        if constexpr (MODE == LAT_SOLVE_MID) {
+          R pa, pb;
+          double qa = 0.0, qb = 0.0;
+          ra = solve_meas<R>(a, xa.x, oa[u], pa, qa);
+          rb = solve_meas<R>(a, xb.x, ob[u], pb, qb);
+          if (ok0) part += qa;
+          if (ok1) part += qb;
+          st2(a.pz, off, v2, ok0, ok1, pa, pb);
+        } else {
+          ra = oa[u].meas ? xa.x * a.scale : R(0);
+          rb = ob[u].meas ? xb.x * a.scale : R(0);
+        }
+        sts2(s, slot, cmk<V>(ok0 ? ra : R(0), R(0)), cmk<V>(ok1 ? rb : R(0), R(0)));
       }
     }
+    __syncthreads();
+    fft_dit<false>(s, TC, rad, tw, false);
+    for (int p = p0; p < nx; p += pstep) {
+      V xa, xb;
+      lds2(s, p * TC + b, xa, xb);
+      st2(reinterpret_cast<V*>(a.out), (size_t)p * C + c, v2, ok0, ok1, cscale(xa, a.scale), cscale(xb, a.scale));
+    }
+  } else {
+    fft_dif<INV>(s, TC, rad, tw, false);
+    for (int p = p0; p < nx; p += U * pstep) {
+      EpOps<R> oa[U], ob[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * nthr;
-      if (e < npairs) {
-        const int p = e / half, b = 2 * (e - p * half);
-        const int c = c0 + b;
-        const size_t off = (size_t)p * C + c;
-        const int src = perm[p] * TC + b;
-        if (c < C) lat_store<R, MODE>(a, off, s[src], oa[u], part);
-        if (c + 1 < C) lat_store<R, MODE>(a, off + 1, s[src + 1], ob[u], part);
+      for (int u = 0; u < U; ++u) {
+        const int pp = p + u * pstep;
+        if (pp < nx) lat_prefetch2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, oa[u], ob[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int pp = p + u * pstep;
+        if (pp >= nx) continue;
+        V xa, xb;
+        lds2(s, perm[pp] * TC + b, xa, xb);
+        lat_store2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, xa, xb, oa[u], ob[u], part, part2);
       }
     }
   }
-  if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_ADJ_L1) {
+  if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_MID || MODE == LAT_SOLVE_ADJ_L1) {
     const double t = block_sum(part);
     if (tid == 0) partial[blk] = t;
+  } else if constexpr (MODE == LAT_POWER_ADJ) {
+    const double t = block_sum(part);
+    __syncthreads();
+    const double t2 = block_sum(part2);
+    if (tid == 0) {
+      partial[2 * blk] = t;
+      partial[2 * blk + 1] = t2;
+    }
   }
 }
 
@@ -246,6 +446,7 @@ lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>>
     e.z1 = A.z1;
     e.z2 = A.z2;
     e.vout = A.vout;
+    e.scal = A.scal;
     e.scale = A.scale;
     e.mu = B.set_mu ? R(B.mu) : A.mu;
     e.delta = A.delta;
@@ -603,10 +804,11 @@ row_adjoint_gather_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<
 int lateral_grid(mbir_plan p, int cols) { return (cols + p->tile_c - 1) / p->tile_c; }
 
 constexpr int lat_class(int mode) {
-  return mode == LAT_C2C_FWD ? PC_LAT_FWD
+  return (mode == LAT_C2C_FWD || mode == LAT_POWER_FWD) ? PC_LAT_FWD
          : mode == LAT_R2C_MASK ? PC_LAT_R2C
          : (mode == LAT_C2R_INV_MASK || mode == LAT_SOLVE_FWD) ? PC_LAT_INV
-                                                               : PC_LAT_ADJ;
+         : (mode == LAT_SOLVE_MID || mode == LAT_POWER_MID) ? PC_LAT_MID
+                                                            : PC_LAT_ADJ;
 }
 
 template <class R>
@@ -630,6 +832,7 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
   a.vout = nullptr;
   a.mu = a.delta = a.tau = R(0);
   a.partial = nullptr;
+  a.scal = nullptr;
   return a;
 }
 
@@ -752,29 +955,28 @@ int adjoint_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStre
   return launch_lateral<R, LAT_C2C_INV>(p, p->wsB, x, nullptr, p->nz, R(1), st);
 }
 
+// FISTA forward pass on z^{k-1} through the fused middle: pz = Phi z^{k-1}, the
+// data-term partials, and R = the first stage of Phi^H on the residual, left in wsA.
 template <class R>
-int forward_solve_t(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
-                    double mu, double* partial, cudaStream_t st) {
+int forward_solve_t(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, double mu,
+                    double* partial, cudaStream_t st) {
   int rc = launch_lateral<R, LAT_C2C_FWD>(p, z1, p->wsA, nullptr, p->nz, R(1), st);
   if (rc) return rc;
   rc = launch_row<R>(p, false, p->wsA, p->wsB, st);
   if (rc) return rc;
-  LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, mask, p->m, R(1) / R(p->nx));
+  LatArgs<R> a = lat_args<R>(p, p->wsB, p->wsA, mask, p->m, R(1) / R(p->nx));
   a.y = reinterpret_cast<const R*>(y);
   a.pz = reinterpret_cast<R*>(pz);
-  a.r = reinterpret_cast<R*>(r);
   a.mu = R(mu);
   a.partial = partial;
-  return launch_lateral_args<R, LAT_SOLVE_FWD>(p, a, p->m, st);
+  return launch_lateral_args<R, LAT_SOLVE_MID>(p, a, p->m, st);
 }
 
+// The rest of the FISTA adjoint pass: row adjoint of wsA, then the image epilogue.
 template <class R>
-int adjoint_solve_t(mbir_plan p, const void* r, const void* z1, void* z2, void* vout, double mu,
-                    double delta, double tau, double* partial, cudaStream_t st) {
-  // r is already zero where the mask is zero
-  int rc = launch_lateral<R, LAT_R2C_MASK>(p, r, p->wsA, nullptr, p->m, R(1) / R(p->nx), st);
-  if (rc) return rc;
-  rc = launch_row<R>(p, true, p->wsA, p->wsB, st);
+int adjoint_solve_t(mbir_plan p, const void* z1, void* z2, void* vout, double mu, double delta, double tau,
+                    double* partial, cudaStream_t st) {
+  int rc = launch_row<R>(p, true, p->wsA, p->wsB, st);
   if (rc) return rc;
   LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, nullptr, p->nz, R(1));
   a.z1 = z1;
@@ -788,6 +990,25 @@ int adjoint_solve_t(mbir_plan p, const void* r, const void* z1, void* z2, void* 
   return launch_lateral_args<R, LAT_SOLVE_ADJ_L1>(p, a, p->nz, st);
 }
 
+// One power-iteration step: v = w scal[1] (written), w = Phi^H s Phi v, partial
+// sums of <v, w> and ||w||^2 (two per lateral CTA of the image) into part.
+template <class R>
+int power_step_t(mbir_plan p, const uint8_t* mask, void* w, void* v, const double* scal, double* part,
+                 cudaStream_t st) {
+  LatArgs<R> a = lat_args<R>(p, w, p->wsA, nullptr, p->nz, R(1));
+  a.vout = v;
+  a.scal = scal;
+  int rc = launch_lateral_args<R, LAT_POWER_FWD>(p, a, p->nz, st);
+  if (rc) return rc;
+  if ((rc = launch_row<R>(p, false, p->wsA, p->wsB, st))) return rc;
+  if ((rc = launch_lateral<R, LAT_POWER_MID>(p, p->wsB, p->wsA, mask, p->m, R(1) / R(p->nx), st))) return rc;
+  if ((rc = launch_row<R>(p, true, p->wsA, p->wsB, st))) return rc;
+  LatArgs<R> b = lat_args<R>(p, p->wsB, w, nullptr, p->nz, R(1));
+  b.z1 = v;
+  b.partial = part;
+  return launch_lateral_args<R, LAT_POWER_ADJ>(p, b, p->nz, st);
+}
+
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
   return p->precision == MBIR_FP64 ? forward_t<double>(p, x, mask, y, st)
                                    : forward_t<float>(p, x, mask, y, st);
@@ -798,17 +1019,22 @@ int adjoint_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaS
                                    : adjoint_t<float>(p, y, mask, x, st);
 }
 
-int forward_solve_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
-                       double mu, double* partial, cudaStream_t st) {
-  return p->precision == MBIR_FP64 ? forward_solve_t<double>(p, z1, mask, y, pz, r, mu, partial, st)
-                                   : forward_solve_t<float>(p, z1, mask, y, pz, r, mu, partial, st);
+int forward_solve_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, double mu,
+                       double* partial, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? forward_solve_t<double>(p, z1, mask, y, pz, mu, partial, st)
+                                   : forward_solve_t<float>(p, z1, mask, y, pz, mu, partial, st);
 }
 
-int adjoint_solve_impl(mbir_plan p, const void* r, const void* z1, void* z2, void* vout, double mu,
-                       double delta, double tau, double* partial, cudaStream_t st) {
-  return p->precision == MBIR_FP64
-             ? adjoint_solve_t<double>(p, r, z1, z2, vout, mu, delta, tau, partial, st)
-             : adjoint_solve_t<float>(p, r, z1, z2, vout, mu, delta, tau, partial, st);
+int adjoint_solve_impl(mbir_plan p, const void* z1, void* z2, void* vout, double mu, double delta, double tau,
+                       double* partial, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? adjoint_solve_t<double>(p, z1, z2, vout, mu, delta, tau, partial, st)
+                                   : adjoint_solve_t<float>(p, z1, z2, vout, mu, delta, tau, partial, st);
+}
+
+int power_step_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, const double* scal, double* part,
+                    cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? power_step_t<double>(p, mask, w, v, scal, part, st)
+                                   : power_step_t<float>(p, mask, w, v, scal, part, st);
 }
 
 template <class R>
@@ -833,6 +1059,14 @@ static int configure_t() {
   MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_L1, true>), lat);
   MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V, false>), lat);
   MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_MID, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_MID, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_MID, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_MID, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_FWD, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_FWD, true>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_ADJ, false>), lat);
+  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_ADJ, true>), lat);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 4, false>), row);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 4, true>), row);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 6, false>), row);
@@ -933,6 +1167,7 @@ static void fill_lat_t(mbir_plan p, const LatFill& f, void* dst) {
   a.delta = R(f.delta);
   a.tau = R(f.tau);
   a.partial = f.partial;
+  a.scal = f.scal;
   memcpy(dst, &a, sizeof(a));
 }
 
@@ -979,6 +1214,10 @@ int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st
     MBIR_LAT_CASE(LAT_SOLVE_FWD)
     MBIR_LAT_CASE(LAT_SOLVE_ADJ_L1)
     MBIR_LAT_CASE(LAT_SOLVE_ADJ_V)
+    MBIR_LAT_CASE(LAT_SOLVE_MID)
+    MBIR_LAT_CASE(LAT_POWER_MID)
+    MBIR_LAT_CASE(LAT_POWER_FWD)
+    MBIR_LAT_CASE(LAT_POWER_ADJ)
     default: return MBIR_ERR_INVALID;
   }
 #undef MBIR_LAT_CASE

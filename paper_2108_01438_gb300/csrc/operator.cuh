@@ -1,6 +1,8 @@
 // Launch-argument blocks and tuning constants of the operator kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace mbir {
@@ -44,7 +46,14 @@ enum LatMode {
   // FISTA epilogues (Eq. alg), fused into the last stage of Phi / Phi^H:
   LAT_SOLVE_FWD = 4,      // pz = Phi z^{k-1}; r = (1+mu) pz - mu pz_prev - s y; data term
   LAT_SOLVE_ADJ_L1 = 5,   // g = Phi^H r; z^k = soft(z1 + mu (z1 - z2) - delta g, tau); |z^k| sum
-  LAT_SOLVE_ADJ_V = 6     // g = Phi^H r; v = z1 + mu (z1 - z2) - delta g (wavelet prox follows)
+  LAT_SOLVE_ADJ_V = 6,    // g = Phi^H r; v = z1 + mu (z1 - z2) - delta g (wavelet prox follows)
+  // measurement side of Phi^H Phi in one pass over the column tiles: the inverse
+  // lateral FFT ending Phi, an epilogue in p-space, the lateral FFT starting Phi^H
+  LAT_SOLVE_MID = 7,      // SOLVE_FWD's epilogue, then R = (1/nx) lateral FFT of r (r stays on chip)
+  LAT_POWER_MID = 8,      // s Re{(1/nx) inverse lateral FFT of S}, then (1/nx) lateral FFT
+  // power iteration (step-size bound) around Phi^H Phi
+  LAT_POWER_FWD = 9,      // v = w / ||w|| (1/||w|| = scal[1]) written out, X = lateral FFT of v
+  LAT_POWER_ADJ = 10      // w = inverse lateral FFT of W; partial sums of <v, w> and ||w||^2
 };
 
 template <class R>
@@ -65,7 +74,8 @@ struct LatArgs {
   void* z2;            // in: z^{k-2}; out: z^k (ADJ_L1) -- may be read before written
   void* vout;          // v out (ADJ_V)
   R mu, delta, tau;
-  double* partial;     // one FP64 partial sum per CTA
+  double* partial;     // one FP64 partial sum per CTA (two for LAT_POWER_ADJ)
+  const double* scal;  // LAT_POWER_FWD: scal[1] = 1/||w||
 };
 
 template <class R>

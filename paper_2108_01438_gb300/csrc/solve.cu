@@ -6,8 +6,10 @@
 //   forward pass on z^{k-1}, epilogue: pz = Phi z^{k-1} (kept for the next
 //     iteration), r = Phi x^k - s y = (1 + mu) pz - mu Phi z^{k-2} - s y
 //     (Phi is real-linear and x^k = z^{k-1} + mu (z^{k-1} - z^{k-2})), and the FP64
-//     partial sums of 1/2 ||pz - s y||^2, the data term of F(z^{k-1});
-//   adjoint pass on r, epilogue: z^k = prox_{tau}(x^k - delta Phi^H r) with
+//     partial sums of 1/2 ||pz - s y||^2, the data term of F(z^{k-1}); r never
+//     leaves the chip: the same pass over the column tiles applies the first
+//     (lateral) stage of Phi^H to it;
+//   rest of the adjoint pass, epilogue: z^k = prox_{tau}(x^k - delta Phi^H r) with
 //     tau = lambda delta (l1 fused; the wavelet prox follows as its own kernels),
 //     and the partial sums of ||Psi z^k||_1.
 // F(z^{k-1}) = data + lambda * reg is reduced on the device in a fixed order, so
@@ -178,6 +180,13 @@ __global__ void resid_kernel(const R* pz, const R* y, const uint8_t* mask, size_
 
 // ------------------------------------------------------------------ state
 
+// doubles in part_tmp / 2: grid-stride reductions and the power iteration's two
+// partials per lateral CTA
+int part_tmp_count(mbir_plan p) {
+  const int g = lateral_grid(p, p->nz);
+  return g > kRedBlocks ? g : kRedBlocks;
+}
+
 static size_t elem_size(mbir_plan p) { return p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2); }
 static size_t real_size(mbir_plan p) { return p->precision == MBIR_FP64 ? sizeof(double) : sizeof(float); }
 
@@ -227,7 +236,7 @@ int ensure_state(mbir_plan p, int trace_cap) {
   MBIR_CUDA_TRY(cudaMalloc(&s->r, real_size(p) * s->nmeas));
   MBIR_CUDA_TRY(cudaMalloc(&s->part_data, sizeof(double) * s->n_data));
   MBIR_CUDA_TRY(cudaMalloc(&s->part_reg, sizeof(double) * s->n_reg));
-  MBIR_CUDA_TRY(cudaMalloc(&s->part_tmp, sizeof(double) * 2 * kRedBlocks));
+  MBIR_CUDA_TRY(cudaMalloc(&s->part_tmp, sizeof(double) * 2 * part_tmp_count(p)));
   MBIR_CUDA_TRY(cudaMalloc(&s->scal, sizeof(double) * 16));
   MBIR_CUDA_TRY(cudaMalloc(&s->objtrace, sizeof(double) * trace_cap));
   return MBIR_OK;
@@ -240,6 +249,10 @@ static int grid_for(size_t n) {
 
 // ------------------------------------------------------------------ pieces
 
+// Power iteration for L = ||Phi^H diag(s) Phi|| (the step-size bound, Sec. 2.3): a
+// counter-based pseudo-random start w, then per step v = w/||w||, w = Phi^H s Phi v
+// and the Rayleigh quotient <v, w>.  The normalisation is folded into the first
+// lateral pass and the two reductions into the last one.
 template <class R>
 static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out, cudaStream_t st) {
   using V = cplx_t<R>;
@@ -248,19 +261,15 @@ static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out,
   const int gb = grid_for(n);
   V* v = (V*)s->v;
   V* w = (V*)s->zA;
-  { ProfScope ps_(p, PC_REDUCE, st); fill_hash_kernel<R><<<gb, kRedThreads, 0, st>>>(v, n); }
-  { ProfScope ps_(p, PC_REDUCE, st); dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->part_tmp); }
+  { ProfScope ps_(p, PC_REDUCE, st); fill_hash_kernel<R><<<gb, kRedThreads, 0, st>>>(w, n); }
+  { ProfScope ps_(p, PC_REDUCE, st); dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(w, w, n, s->part_tmp); }
   { ProfScope ps_(p, PC_REDUCE, st); power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal); }
-  { ProfScope ps_(p, PC_REDUCE, st); scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, v, n, s->scal); }
   MBIR_LAUNCH_CHECK();
+  const int np = lateral_grid(p, p->nz);
   for (int it = 0; it < iters; ++it) {
-    int rc = forward_impl(p, v, mask, s->r, st);
+    int rc = power_step_impl(p, mask, w, v, s->scal, s->part_tmp, st);
     if (rc) return rc;
-    rc = adjoint_impl(p, s->r, mask, w, st);
-    if (rc) return rc;
-    { ProfScope ps_(p, PC_REDUCE, st); dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->part_tmp); }
-    { ProfScope ps_(p, PC_REDUCE, st); power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal); }
-    { ProfScope ps_(p, PC_REDUCE, st); scale_kernel<R><<<gb, kRedThreads, 0, st>>>(v, w, n, s->scal); }
+    { ProfScope ps_(p, PC_REDUCE, st); power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, np, s->scal); }
     MBIR_LAUNCH_CHECK();
   }
   MBIR_CUDA_TRY(cudaMemcpyAsync(out, s->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -361,7 +370,7 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
   if (check) status = MBIR_ERR_NOT_CONVERGED;
   for (k = 1; k <= o->max_iter; ++k) {
     const double m = k >= 2 ? mu[k - 2] : 0.0;
-    int rc = forward_solve_impl(p, z1, mask, y, s->pz, s->r, m, s->part_data, st);
+    int rc = forward_solve_impl(p, z1, mask, y, s->pz, m, s->part_data, st);
     if (rc) return rc;
     if (want_trace) {
       ProfScope ps_(p, PC_REDUCE, st);
@@ -370,10 +379,10 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
     }
     MBIR_LAUNCH_CHECK();
     if (o->penalty == MBIR_PENALTY_L1) {
-      rc = adjoint_solve_impl(p, s->r, z1, z2, nullptr, m, delta, tau, s->part_reg, st);
+      rc = adjoint_solve_impl(p, z1, z2, nullptr, m, delta, tau, s->part_reg, st);
       if (rc) return rc;
     } else {
-      rc = adjoint_solve_impl(p, s->r, z1, z2, s->v, m, delta, tau, nullptr, st);
+      rc = adjoint_solve_impl(p, z1, z2, s->v, m, delta, tau, nullptr, st);
       if (rc) return rc;
       rc = prox_partial_impl(p, o->penalty, s->v, tau, z2, s->part_reg, st);
       if (rc) return rc;
