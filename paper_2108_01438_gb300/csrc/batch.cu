@@ -78,6 +78,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 // v = uniform [-1, 1) pseudo-random start of the power iteration (SplitMix64 of the index)
 template <class R>
 __global__ void b_fill_hash(const ScanVec* sv) {
+  pdl_wait_release();
   const ScanVec s = sv[blockIdx.y];
   cplx_t<R>* v = reinterpret_cast<cplx_t<R>*>(s.v);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < s.n; i += (size_t)gridDim.x * blockDim.x) {
@@ -89,6 +90,7 @@ __global__ void b_fill_hash(const ScanVec* sv) {
 // part[2 b] = sum Re(conj(v) w), part[2 b + 1] = sum |w|^2
 template <class R>
 __global__ void b_dot_norm(const ScanVec* sv) {
+  pdl_wait_release();
   const ScanVec s = sv[blockIdx.y];
   const cplx_t<R>* v = reinterpret_cast<const cplx_t<R>*>(s.v);
   const cplx_t<R>* w = reinterpret_cast<const cplx_t<R>*>(s.w);
@@ -107,6 +109,7 @@ __global__ void b_dot_norm(const ScanVec* sv) {
 
 // scal[0] = <v, w>, scal[1] = 1/||w||
 __global__ void b_power_finalize(const ScanVec* sv, int nb) {
+  pdl_wait_release();
   const ScanVec s = sv[blockIdx.y];
   if (s.np > 0) nb = s.np;
   double d = 0.0, q = 0.0;
@@ -124,6 +127,7 @@ __global__ void b_power_finalize(const ScanVec* sv, int nb) {
 // v = w * scal[1]
 template <class R>
 __global__ void b_scale(const ScanVec* sv) {
+  pdl_wait_release();
   const ScanVec s = sv[blockIdx.y];
   cplx_t<R>* v = reinterpret_cast<cplx_t<R>*>(s.v);
   const cplx_t<R>* w = reinterpret_cast<const cplx_t<R>*>(s.w);
@@ -135,6 +139,7 @@ __global__ void b_scale(const ScanVec* sv) {
 // scal[4] = max |v|
 template <class R>
 __global__ void b_maxabs(const ScanVec* sv) {
+  pdl_wait_release();
   const ScanVec s = sv[blockIdx.y];
   const cplx_t<R>* v = reinterpret_cast<const cplx_t<R>*>(s.v);
   double m = 0.0;
@@ -147,6 +152,7 @@ __global__ void b_maxabs(const ScanVec* sv) {
 }
 
 __global__ void b_max_finalize(const ScanVec* sv, int nb) {
+  pdl_wait_release();
   const ScanVec s = sv[blockIdx.y];
   double m = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, s.part[i]);
@@ -168,6 +174,7 @@ struct ObjArgs {
 };
 
 __global__ void b_objective(const ObjArgs* oa) {
+  pdl_wait_release();
   const ObjArgs o = oa[blockIdx.x];
   double s = 0.0, t = 0.0;
   for (int i = threadIdx.x; i < o.n_data; i += blockDim.x) s += o.part_data[i];
@@ -449,7 +456,7 @@ int Engine::add_dwt(std::vector<Stage>& out, int inverse, int level, const std::
 int Engine::run(const Stage& g, double mu) {
   if (g.kind == 4) {
     const ObjArgs* d = reinterpret_cast<const ObjArgs*>(static_cast<unsigned char*>(dbuf_) + g.arg_off);
-    b_objective<<<g.n, kBThreads, 0, st_>>>(d);
+    launch(b_objective, dim3(g.n), dim3(kBThreads), 0, st_, d);
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }
@@ -475,12 +482,16 @@ int Engine::vec_kernel(int which, size_t off, int n) {
   const ScanVec* d = reinterpret_cast<const ScanVec*>(static_cast<unsigned char*>(dbuf_) + off);
   const bool f64 = prec_ == MBIR_FP64;
   switch (which) {
-    case 0: f64 ? b_fill_hash<double><<<grid, kBThreads, 0, st_>>>(d) : b_fill_hash<float><<<grid, kBThreads, 0, st_>>>(d); break;
-    case 1: f64 ? b_dot_norm<double><<<grid, kBThreads, 0, st_>>>(d) : b_dot_norm<float><<<grid, kBThreads, 0, st_>>>(d); break;
-    case 2: b_power_finalize<<<dim3(1, n), kBThreads, 0, st_>>>(d, kBBlocks); break;
-    case 3: f64 ? b_scale<double><<<grid, kBThreads, 0, st_>>>(d) : b_scale<float><<<grid, kBThreads, 0, st_>>>(d); break;
-    case 4: f64 ? b_maxabs<double><<<grid, kBThreads, 0, st_>>>(d) : b_maxabs<float><<<grid, kBThreads, 0, st_>>>(d); break;
-    default: b_max_finalize<<<dim3(1, n), kBThreads, 0, st_>>>(d, kBBlocks); break;
+    case 0: f64 ? launch(b_fill_hash<double>, grid, dim3(kBThreads), 0, st_, d)
+                : launch(b_fill_hash<float>, grid, dim3(kBThreads), 0, st_, d); break;
+    case 1: f64 ? launch(b_dot_norm<double>, grid, dim3(kBThreads), 0, st_, d)
+                : launch(b_dot_norm<float>, grid, dim3(kBThreads), 0, st_, d); break;
+    case 2: launch(b_power_finalize, dim3(1, n), dim3(kBThreads), 0, st_, d, kBBlocks); break;
+    case 3: f64 ? launch(b_scale<double>, grid, dim3(kBThreads), 0, st_, d)
+                : launch(b_scale<float>, grid, dim3(kBThreads), 0, st_, d); break;
+    case 4: f64 ? launch(b_maxabs<double>, grid, dim3(kBThreads), 0, st_, d)
+                : launch(b_maxabs<float>, grid, dim3(kBThreads), 0, st_, d); break;
+    default: launch(b_max_finalize, dim3(1, n), dim3(kBThreads), 0, st_, d, kBBlocks); break;
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;

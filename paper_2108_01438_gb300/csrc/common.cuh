@@ -165,6 +165,43 @@ void set_error_text(const std::string& s);
     if (e_ != cudaSuccess) return ::mbir::set_cuda_error(e_, #call); \
   } while (0)
 
+// Programmatic dependent launch: every kernel of the path is launched with
+// programmatic stream serialisation, so its CTAs can be scheduled while the
+// previous kernel drains and run their prologue (plan constants, twiddles into
+// shared memory); each calls pdl_wait_release() before it touches any data that
+// an earlier kernel writes, which waits for the previous grid to complete and
+// flush, then lets the next kernel be scheduled.  Without the attribute the
+// instructions are no-ops.
+#ifndef MBIR_PDL
+#define MBIR_PDL 1
+#endif
+constexpr bool kPdl = MBIR_PDL != 0;
+
+__device__ __forceinline__ void pdl_wait_release() {
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   const Args&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = kPdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kernel, args...) == cudaErrorNotSupported && kPdl) {
+    // a stream that does not take the attribute: plain stream order
+    (void)cudaGetLastError();
+    cfg.numAttrs = 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
+}
+
 #define MBIR_LAUNCH_CHECK()                                                     \
   do {                                                                          \
     cudaError_t e_ = cudaGetLastError();                                        \

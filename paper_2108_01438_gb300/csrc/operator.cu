@@ -318,6 +318,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   const bool v2 = ok1 && (C & 1) == 0 && lat_pairs_aligned<R, MODE>(a);
   constexpr int U = 4;
   const V zero = cmk<V>(R(0), R(0));
+  pdl_wait_release();
   R fscale = R(1);
   if constexpr (MODE == LAT_POWER_FWD) fscale = R(a.scal[1]);
   for (int p = p0; p < nx; p += U * pstep) {
@@ -524,6 +525,7 @@ __device__ __forceinline__ void row_forward_body(const RowArgs<R>& a, const Radi
   const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), rad);
   const V* X = reinterpret_cast<const V*>(a.in) + (size_t)l * nz;
   const R* cdep = reinterpret_cast<const R*>(a.cdep);
+  pdl_wait_release();
   // centred zero-padded row, element i = (n - n0) mod K holding c_n X[l][n],
   // placed digit-reversed for the decimation-in-time transform
   constexpr int U = 4;
@@ -605,6 +607,7 @@ __device__ __forceinline__ void row_adjoint_body(const RowArgs<R>& a, const Radi
   const int* perm = a.perm;
   const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(a.tw), rad);
   for (int i = tid; i < K; i += nthr) buf[i] = cmk<V>(R(0), R(0));
+  pdl_wait_release();
   __syncthreads();
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
   const V* Rh = reinterpret_cast<const V*>(a.in) + (size_t)l * M;
@@ -699,6 +702,7 @@ __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, con
   const int base = meta.x, span = meta.y, dir = meta.z;
   const Tab* tab = reinterpret_cast<const Tab*>(a.tab) + (size_t)lp * M;
   const V* Rh = reinterpret_cast<const V*>(a.in) + (size_t)l * M;
+  pdl_wait_release();
   // stage the row in increasing-u order
   constexpr int UM = 4;
   for (int m0 = tid; m0 < M; m0 += UM * nthr) {
@@ -845,7 +849,8 @@ template <class R, int MODE>
 int launch_lateral_args(mbir_plan p, const LatArgs<R>& a, int cols, cudaStream_t st) {
   {
     ProfScope ps_(p, lat_class(MODE), st);
-    lateral_kernel<R, MODE, false><<<lateral_grid(p, cols), kLatThreads, lat_smem<R>(p), st>>>(a, no_batch<LatArgs<R>>());
+    launch(lateral_kernel<R, MODE, false>, dim3(lateral_grid(p, cols)), dim3(kLatThreads), lat_smem<R>(p), st, a,
+           no_batch<LatArgs<R>>());
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -899,9 +904,9 @@ bool plan_uses_gather(mbir_plan p);
 template <class R, int J, bool BAT, bool COMP>
 static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid, size_t smem,
                          cudaStream_t st) {
-  if (kind == 0) row_forward_kernel<R, J, BAT, COMP><<<grid, kRowThreads, smem, st>>>(a, B);
-  else if (kind == 1) row_adjoint_gather_kernel<R, J, BAT, COMP><<<grid, kRowThreads, smem, st>>>(a, B);
-  else row_adjoint_kernel<R, J, BAT><<<grid, kRowThreads, smem, st>>>(a, B);
+  if (kind == 0) launch(row_forward_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
+  else if (kind == 1) launch(row_adjoint_gather_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
+  else launch(row_adjoint_kernel<R, J, BAT>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
 }
 
 template <class R, bool BAT>
@@ -1196,7 +1201,7 @@ static void lat_batch_t(const BatchLaunch& L, cudaStream_t st) {
   B.mu = L.mu;
   LatArgs<R> a0;
   memcpy(&a0, L.host0, sizeof(a0));
-  lateral_kernel<R, MODE, true><<<L.total, kLatThreads, L.smem, st>>>(a0, B);
+  launch(lateral_kernel<R, MODE, true>, dim3(L.total), dim3(kLatThreads), L.smem, st, a0, B);
 }
 
 int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st) {

@@ -74,6 +74,7 @@ __device__ __forceinline__ double block_max_s(double v) {
 // out = wa * sum(a[0..na)) + wb * sum(b[0..nb)), one block, fixed order.
 __global__ void combine_kernel(const double* a, int na, double wa, const double* b, int nb, double wb,
                                double* out) {
+  pdl_wait_release();
   double s = 0.0, t = 0.0;
   for (int i = threadIdx.x; i < na; i += blockDim.x) s += a[i];
   for (int i = threadIdx.x; i < nb; i += blockDim.x) t += b[i];
@@ -93,6 +94,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // counter-based hash (SplitMix64) of the element index.
 template <class R>
 __global__ void fill_hash_kernel(cplx_t<R>* v, size_t n) {
+  pdl_wait_release();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const uint64_t a = splitmix64(2 * i), b = splitmix64(2 * i + 1);
     v[i] = cmk<cplx_t<R>>(R((a >> 11) * 0x1.0p-53 * 2.0 - 1.0), R((b >> 11) * 0x1.0p-53 * 2.0 - 1.0));
@@ -102,6 +104,7 @@ __global__ void fill_hash_kernel(cplx_t<R>* v, size_t n) {
 // part[2 blk] = sum Re(conj(v) w), part[2 blk + 1] = sum |w|^2
 template <class R>
 __global__ void dot_norm_kernel(const cplx_t<R>* v, const cplx_t<R>* w, size_t n, double* part) {
+  pdl_wait_release();
   double d = 0.0, q = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx_t<R> a = v[i], b = w[i];
@@ -117,6 +120,7 @@ __global__ void dot_norm_kernel(const cplx_t<R>* v, const cplx_t<R>* w, size_t n
 
 // scal[0] = <v, w>, scal[1] = 1/||w||, scal[2] = ||w||^2
 __global__ void power_finalize_kernel(const double* part, int nb, double* scal) {
+  pdl_wait_release();
   double d = 0.0, q = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     d += part[2 * i];
@@ -132,6 +136,7 @@ __global__ void power_finalize_kernel(const double* part, int nb, double* scal) 
 
 template <class R>
 __global__ void scale_kernel(cplx_t<R>* v, const cplx_t<R>* w, size_t n, const double* scal) {
+  pdl_wait_release();
   const R s = R(scal[1]);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     v[i] = cscale(w[i], s);
@@ -139,6 +144,7 @@ __global__ void scale_kernel(cplx_t<R>* v, const cplx_t<R>* w, size_t n, const d
 
 template <class R>
 __global__ void maxabs_kernel(const cplx_t<R>* v, size_t n, double* part) {
+  pdl_wait_release();
   double m = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx_t<R> a = v[i];
@@ -149,6 +155,7 @@ __global__ void maxabs_kernel(const cplx_t<R>* v, size_t n, double* part) {
 }
 
 __global__ void max_finalize_kernel(const double* part, int nb, double* out) {
+  pdl_wait_release();
   double m = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, part[i]);
   const double M = block_max_s(m);
@@ -157,6 +164,7 @@ __global__ void max_finalize_kernel(const double* part, int nb, double* out) {
 
 template <class R>
 __global__ void abs_sum_kernel(const cplx_t<R>* v, size_t n, double* part) {
+  pdl_wait_release();
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx_t<R> a = v[i];
@@ -168,6 +176,7 @@ __global__ void abs_sum_kernel(const cplx_t<R>* v, size_t n, double* part) {
 
 template <class R>
 __global__ void resid_kernel(const R* pz, const R* y, const uint8_t* mask, size_t n, double* part) {
+  pdl_wait_release();
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (mask && !mask[i]) continue;
@@ -261,15 +270,15 @@ static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out,
   const int gb = grid_for(n);
   V* v = (V*)s->v;
   V* w = (V*)s->zA;
-  { ProfScope ps_(p, PC_REDUCE, st); fill_hash_kernel<R><<<gb, kRedThreads, 0, st>>>(w, n); }
-  { ProfScope ps_(p, PC_REDUCE, st); dot_norm_kernel<R><<<gb, kRedThreads, 0, st>>>(w, w, n, s->part_tmp); }
-  { ProfScope ps_(p, PC_REDUCE, st); power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal); }
+  { ProfScope ps_(p, PC_REDUCE, st); launch(fill_hash_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, w, n); }
+  { ProfScope ps_(p, PC_REDUCE, st); launch(dot_norm_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, w, w, n, s->part_tmp); }
+  { ProfScope ps_(p, PC_REDUCE, st); launch(power_finalize_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, gb, s->scal); }
   MBIR_LAUNCH_CHECK();
   const int np = lateral_grid(p, p->nz);
   for (int it = 0; it < iters; ++it) {
     int rc = power_step_impl(p, mask, w, v, s->scal, s->part_tmp, st);
     if (rc) return rc;
-    { ProfScope ps_(p, PC_REDUCE, st); power_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, np, s->scal); }
+    { ProfScope ps_(p, PC_REDUCE, st); launch(power_finalize_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, np, s->scal); }
     MBIR_LAUNCH_CHECK();
   }
   MBIR_CUDA_TRY(cudaMemcpyAsync(out, s->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -293,8 +302,8 @@ static int lambda_scale_t(mbir_plan p, const void* y, const uint8_t* mask, int p
     src = (const V*)s->v;
   }
   const int gb = grid_for(n);
-  { ProfScope ps_(p, PC_REDUCE, st); maxabs_kernel<R><<<gb, kRedThreads, 0, st>>>(src, n, s->part_tmp); }
-  { ProfScope ps_(p, PC_REDUCE, st); max_finalize_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, s->scal + 4); }
+  { ProfScope ps_(p, PC_REDUCE, st); launch(maxabs_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, src, n, s->part_tmp); }
+  { ProfScope ps_(p, PC_REDUCE, st); launch(max_finalize_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, gb, s->scal + 4); }
   MBIR_LAUNCH_CHECK();
   MBIR_CUDA_TRY(cudaMemcpyAsync(out, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
   MBIR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -307,7 +316,7 @@ static int reg_partials_t(mbir_plan p, int penalty, const void* z, cudaStream_t 
   SolveState* s = p->solve;
   if (penalty == MBIR_PENALTY_L1) {
     const int gb = lateral_grid(p, p->nz);
-    { ProfScope ps_(p, PC_REDUCE, st); abs_sum_kernel<R><<<gb, kRedThreads, 0, st>>>((const cplx_t<R>*)z, s->nimg, s->part_reg); }
+    { ProfScope ps_(p, PC_REDUCE, st); launch(abs_sum_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, (const cplx_t<R>*)z, s->nimg, s->part_reg); }
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }
@@ -374,8 +383,8 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
     if (rc) return rc;
     if (want_trace) {
       ProfScope ps_(p, PC_REDUCE, st);
-      combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_data, s->n_data, 0.5, s->part_reg, nreg, lam,
-                                                s->objtrace + (k - 1));
+      launch(combine_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_data, s->n_data, 0.5, s->part_reg, nreg,
+             lam, s->objtrace + (k - 1));
     }
     MBIR_LAUNCH_CHECK();
     if (o->penalty == MBIR_PENALTY_L1) {
@@ -407,8 +416,8 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
     int rc = forward_impl(p, z1, mask, s->r, st);
     if (rc) return rc;
     const int gb = grid_for(s->nmeas);
-    { ProfScope ps_(p, PC_REDUCE, st); resid_kernel<R><<<gb, kRedThreads, 0, st>>>((const R*)s->r, (const R*)y, mask, s->nmeas, s->part_tmp); }
-    { ProfScope ps_(p, PC_REDUCE, st); combine_kernel<<<1, kRedThreads, 0, st>>>(s->part_tmp, gb, 0.5, s->part_reg, nreg, lam, s->scal + 6); }
+    { ProfScope ps_(p, PC_REDUCE, st); launch(resid_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, (const R*)s->r, (const R*)y, mask, s->nmeas, s->part_tmp); }
+    { ProfScope ps_(p, PC_REDUCE, st); launch(combine_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, gb, 0.5, s->part_reg, nreg, lam, s->scal + 6); }
     MBIR_LAUNCH_CHECK();
     double fin = 0.0;
     MBIR_CUDA_TRY(cudaMemcpyAsync(&fin, s->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -101,6 +101,7 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const int P = a.P, N = a.N;
   const int a0 = by * kFwdTA, b0 = bx * kFwdTB;
   const V* in = reinterpret_cast<const V*>(a.in);
+  pdl_wait_release();
   // stage the input tile with every load of a thread in flight at once
   constexpr int kFwdPer = (kFwdRows * kFwdCols + kWavThreads - 1) / kWavThreads;
   {
@@ -194,6 +195,7 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const int r0 = by * kInvTR, c0 = bx * kInvTC;
   const V* ll = reinterpret_cast<const V*>(a.in);
   const V* coef = reinterpret_cast<const V*>(a.coef);
+  pdl_wait_release();
   constexpr int kInvPer = (kInvRows * kInvCols + kWavThreads - 1) / kWavThreads;
   {
     V v0[kInvPer], v1[kInvPer], v2[kInvPer], v3[kInvPer];
@@ -257,6 +259,7 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
 
 template <class R>
 __global__ void soft_kernel(const cplx_t<R>* v, cplx_t<R>* z, size_t n, R tau, double* partial) {
+  pdl_wait_release();
   double acc = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     z[i] = soft_c<R>(v[i], tau, acc);
@@ -315,7 +318,7 @@ static int analysis_t(mbir_plan p, const void* in, void* coef, bool thresh, R ta
     a.partial = thresh ? part : nullptr;
     const int gx = (N / 2 + kFwdTB - 1) / kFwdTB, gy = (P / 2 + kFwdTA - 1) / kFwdTA;
     a.gx = gx;
-    { ProfScope ps_(p, PC_DWT_FWD, st); dwt_fwd_kernel<R><<<gx * gy, kWavThreads, fwd_smem(sizeof(cplx_t<R>)), st>>>(a, no_batch<WArgs<R>>()); }
+    { ProfScope ps_(p, PC_DWT_FWD, st); launch(dwt_fwd_kernel<R>, dim3(gx * gy), dim3(kWavThreads), fwd_smem(sizeof(cplx_t<R>)), st, a, no_batch<WArgs<R>>()); }
     MBIR_LAUNCH_CHECK();
     if (part) part += gx * gy;
     src = lls[lev];
@@ -349,7 +352,7 @@ static int synthesis_t(mbir_plan p, const void* coef, void* out, cudaStream_t st
     a.partial = nullptr;
     const int gx = (a.N + kInvTC - 1) / kInvTC, gy = (a.P + kInvTR - 1) / kInvTR;
     a.gx = gx;
-    { ProfScope ps_(p, PC_DWT_INV, st); dwt_inv_kernel<R><<<gx * gy, kWavThreads, inv_smem(sizeof(cplx_t<R>)), st>>>(a, no_batch<WArgs<R>>()); }
+    { ProfScope ps_(p, PC_DWT_INV, st); launch(dwt_inv_kernel<R>, dim3(gx * gy), dim3(kWavThreads), inv_smem(sizeof(cplx_t<R>)), st, a, no_batch<WArgs<R>>()); }
     MBIR_LAUNCH_CHECK();
   }
   return MBIR_OK;
@@ -387,9 +390,9 @@ int prox_partial_impl(mbir_plan p, int penalty, const void* v, double tau, void*
   if (penalty == MBIR_PENALTY_L1) {
     const size_t n = (size_t)p->nx * p->nz;
     if (f64)
-      { ProfScope ps_(p, PC_SOFT, st); soft_kernel<double><<<kSoftGrid, 256, 0, st>>>((const double2*)v, (double2*)z, n, tau, partial); }
+      { ProfScope ps_(p, PC_SOFT, st); launch(soft_kernel<double>, dim3(kSoftGrid), dim3(256), 0, st, (const double2*)v, (double2*)z, n, tau, partial); }
     else
-      { ProfScope ps_(p, PC_SOFT, st); soft_kernel<float><<<kSoftGrid, 256, 0, st>>>((const float2*)v, (float2*)z, n, (float)tau, partial); }
+      { ProfScope ps_(p, PC_SOFT, st); launch(soft_kernel<float>, dim3(kSoftGrid), dim3(256), 0, st, (const float2*)v, (float2*)z, n, (float)tau, partial); }
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }
@@ -567,8 +570,8 @@ static void dwt_batch_t(int inverse, const BatchLaunch& L, cudaStream_t st) {
   B.mu = 0.0;
   WArgs<R> a0;
   memcpy(&a0, L.host0, sizeof(a0));
-  if (inverse) dwt_inv_kernel<R><<<L.total, kWavThreads, L.smem, st>>>(a0, B);
-  else dwt_fwd_kernel<R><<<L.total, kWavThreads, L.smem, st>>>(a0, B);
+  if (inverse) launch(dwt_inv_kernel<R>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
+  else launch(dwt_fwd_kernel<R>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
 }
 
 int batch_dwt(int inverse, int precision, const BatchLaunch& L, cudaStream_t st) {
