@@ -204,6 +204,7 @@ def algorithmic_bytes(cls: str, nx: int, nz: int, m: int) -> float | None:
         "lateral_forward": 16.0 * img,                       # read x, write X
         "row_forward": 8.0 * img + table + 8.0 * meas,       # read X, table, write S
         "lateral_inverse_real": 25.0 * meas,                 # read S, mask, y, pz; write pz, r
+        "lateral_mid": 29.0 * meas,                          # read S, mask, y, pz; write pz, R
         "lateral_residual": 12.0 * meas,                     # read r, write R
         "row_adjoint": 8.0 * meas + table + 8.0 * img,       # read R, table, write W
         "lateral_adjoint": 32.0 * img,                       # read W, z1, z2; write v or z

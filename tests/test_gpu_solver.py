@@ -193,3 +193,46 @@ def test_full_size_db4_last_step_matches_oracle(mbir):
     z100 = fista.prox_wavelet(x - delta * grad, lam * delta, H)
     assert _rel(zs[100], z100) <= 1e-4
     plan.close()
+
+
+_L_CACHE = {}
+
+
+@pytest.mark.parametrize("penalty,use_mask", [("l1", True), ("db4", True), ("l1", False)])
+def test_fista_ragged_geometry_matches_oracle(mbir, penalty, use_mask):
+    """An odd spectral length (m = 75: unpaired columns, a ragged last column tile)
+    and a depth whose oversampled transform needs radix 5 (K = 80): the fused
+    measurement pass of every iteration and the power iteration against the oracle,
+    with a Bernoulli mask and without one."""
+    nx, nz, m = 48, 40, 75
+    d = W.geometry(nx, nz, m, focus_frac=0.4, disp_edge_rad=15.0)
+    g = isam.make_geom(d)
+    mask = W.mask_bernoulli(nx, m, 0.6, 91) if use_mask else np.ones((nx, m), dtype=np.uint8)
+    x_true = W.point_scatterers(nx, nz, 10, 92)
+    clean = isam.phi_nufft(x_true, mask, g)
+    y = clean + 0.02 * np.sqrt(np.mean(clean[mask == 1] ** 2)) * W.unit_noise(nx, m, 93) * mask
+    y = y.astype(np.float32).astype(np.float64)
+    phi = lambda v: isam.phi_nufft(v, mask, g)
+    phi_adj = lambda r: isam.phi_adj_nufft(r, mask, g)
+    # both power iterations run to convergence (their start vectors differ)
+    key = ("ragged", use_mask)
+    if key not in _L_CACHE:
+        _L_CACHE[key] = fista.power_iteration(phi, phi_adj, (nx, nz), iters=1000)
+    L_ref = _L_CACHE[key]
+    plan = mbir.Plan(d)
+    mt = torch.from_numpy(mask).cuda() if use_mask else None
+    L = plan.lipschitz(mt, iters=1000)
+    assert abs(L - L_ref) <= 1e-5 * L_ref
+    delta = 1.0 / (1.01 * L_ref)
+    if penalty == "l1":
+        lam = 0.02 * np.max(np.abs(phi_adj(y * mask)))
+        prox = fista.prox_l1
+    else:
+        lam = 0.02 * np.max(np.abs(wavelet.dwt2(phi_adj(y * mask), H, 3)))
+        prox = lambda v, t: fista.prox_wavelet(v, t, H)
+    trace = []
+    fista.fista(phi, phi_adj, y, mask, prox, lam, delta, 30, (nx, nz), trace=trace)
+    z, info = plan.solve(_f32(y), mt, penalty=penalty, lam=lam, relative=False, iters=30, step=delta)
+    assert info["iters"] == 30 and info["status"] == 0
+    assert _rel(z.cpu().numpy(), trace[-1]) <= RECON_TOL
+    plan.close()
