@@ -444,9 +444,9 @@ int Engine::add_dwt(std::vector<Stage>& out, int inverse, int level, const std::
     fill_dwt_args(s.p, level, inverse, in.empty() ? nullptr : in[i], outp.empty() ? nullptr : outp[i], coefs[i],
                   thresh ? s.tau : 0.0, th, partial.empty() ? nullptr : partial[i], s.c.wv_b1, s.c.wv_b2,
                   blocks.data() + i * ab);
-    off[i + 1] = off[i] + dwt_level_ctas(s.p->nx >> level, s.p->nz >> level, inverse);
+    off[i + 1] = off[i] + dwt_level_ctas(s.p->nx >> level, s.p->nz >> level, inverse, level);
   }
-  Stage g{inverse ? 3 : 2, 0, 0, 0, (int)idx.size(), off.back(), dwt_smem_bytes(prec_, inverse), 0};
+  Stage g{inverse ? 3 : 2, level, 0, 0, (int)idx.size(), off.back(), dwt_smem_bytes(prec_, inverse, level), 0};
   g.arg_off = push(blocks.data(), blocks.size());
   g.off_off = push(off.data(), off.size() * sizeof(int));
   out.push_back(g);
@@ -472,8 +472,8 @@ int Engine::run(const Stage& g, double mu) {
   switch (g.kind) {
     case 0: return batch_lateral(g.mode, prec_, L, st_);
     case 1: return batch_row(g.mode, prec_, J_, L, st_);
-    case 2: return batch_dwt(0, prec_, L, st_);
-    default: return batch_dwt(1, prec_, L, st_);
+    case 2: return batch_dwt(0, g.mode, prec_, L, st_);
+    default: return batch_dwt(1, g.mode, prec_, L, st_);
   }
 }
 
@@ -693,7 +693,7 @@ int Engine::build_iteration(std::vector<Stage>& out, const std::vector<BScan*>& 
       int P = s->p->nx, N = s->p->nz;
       for (int lev = 0; lev < 3; ++lev) {
         parts[lev].push_back(pr);
-        pr += dwt_level_ctas(P, N, 0);
+        pr += dwt_level_ctas(P, N, 0, lev);
         P /= 2;
         N /= 2;
       }

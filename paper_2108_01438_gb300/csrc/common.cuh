@@ -273,11 +273,12 @@ int batch_row(int kind, int precision, int J, const BatchLaunch& L, cudaStream_t
 
 // wavelet.cu (batch helpers)
 size_t dwt_args_bytes(int precision);
-int dwt_level_ctas(int P, int N, int inverse);
-size_t dwt_smem_bytes(int precision, int inverse);
+// P x N: the level's block (analysis input / synthesis output); level 0 = finest
+int dwt_level_ctas(int P, int N, int inverse, int level);
+size_t dwt_smem_bytes(int precision, int inverse, int level);
 void fill_dwt_args(mbir_plan p, int level, int inverse, const void* in, void* out, void* coef, double tau,
                    int thresh, double* partial, void* b1, void* b2, void* dst);
-int batch_dwt(int inverse, int precision, const BatchLaunch& L, cudaStream_t st);
+int batch_dwt(int inverse, int level, int precision, const BatchLaunch& L, cudaStream_t st);
 
 // operator.cu
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st);

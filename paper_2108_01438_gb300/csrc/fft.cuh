@@ -4,8 +4,12 @@
 //
 // Data: `batch` interleaved sequences of length N in shared memory, element i of
 // sequence b at s[sw(i) * batch + b], where sw is either the identity or, for
-// batch = 1 and N divisible by 16, the XOR swizzle i ^ ((i >> 4) & 15) that keeps
-// the unit-stride last passes free of bank conflicts.  With radices R_1..R_P:
+// batch = 1 and N divisible by 16, the XOR swizzle i ^ (((i >> 4) ^ (i >> 8)) & 15)
+// (a permutation within each aligned group of 16).  It keeps the unit-stride
+// last passes free of bank conflicts, and also the digit-reversed accesses
+// (staging for dit, read-out after dif): for N = 4096 = 16^3, 16 consecutive
+// indices land at positions 256 a + 16 b + c with a running and b, c fixed, and
+// the (i >> 8) term spreads those over all 16 bank pairs.  With radices R_1..R_P:
 //   decimation in frequency (dif): natural-order input; pass p works on blocks of
 //     length L = N / (R_1 ... R_{p-1}): for j < M = L/R the R points
 //     j + r M of a block go through an R-point DFT, output q is multiplied by
@@ -68,7 +72,7 @@ struct Tw2 {
   __device__ __forceinline__ V operator()(int e) const { return cmul(hi[e >> shift], lo[e & mask]); }
 };
 
-__device__ __forceinline__ int swz(int i, bool on) { return on ? (i ^ ((i >> 4) & 15)) : i; }
+__device__ __forceinline__ int swz(int i, bool on) { return on ? (i ^ (((i >> 4) ^ (i >> 8)) & 15)) : i; }
 
 template <int R, bool INV, class V>
 __device__ __forceinline__ void dft_small(V (&v)[R], const Tw2<V>& tw, int N) {

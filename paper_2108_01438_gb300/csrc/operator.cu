@@ -789,7 +789,7 @@ __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, con
 }
 
 template <class R, int J, bool BAT, bool COMP = false>
-__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? kRowMinBlocks : 1)
+__global__ void __launch_bounds__(kGatherThreads, sizeof(R) == 4 ? kGatherMinBlocks : 1)
 row_adjoint_gather_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<RowArgs<R>> B) {
   if constexpr (!BAT) {
     row_adjoint_gather_body<R, J, COMP>(a0, a0.rad, (int)blockIdx.x, a0);
@@ -905,7 +905,8 @@ template <class R, int J, bool BAT, bool COMP>
 static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid, size_t smem,
                          cudaStream_t st) {
   if (kind == 0) launch(row_forward_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
-  else if (kind == 1) launch(row_adjoint_gather_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
+  else if (kind == 1)
+    launch(row_adjoint_gather_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kGatherThreads), smem, st, a, B);
   else launch(row_adjoint_kernel<R, J, BAT>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
 }
 

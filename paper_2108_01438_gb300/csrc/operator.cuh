@@ -20,6 +20,12 @@ namespace mbir {
 #ifndef MBIR_ROW_MINB
 #define MBIR_ROW_MINB 4
 #endif
+#ifndef MBIR_GATHER_THREADS
+#define MBIR_GATHER_THREADS 512
+#endif
+#ifndef MBIR_GATHER_MINB
+#define MBIR_GATHER_MINB 2
+#endif
 #ifndef MBIR_GATHER_PRECOMP
 #define MBIR_GATHER_PRECOMP 1
 #endif
@@ -34,6 +40,10 @@ constexpr int kLatElems = MBIR_LAT_ELEMS;       // nx * columns staged per later
 constexpr int kRowThreads = MBIR_ROW_THREADS;   // row (NUFFT) block size
 constexpr int kRowMinBlocks = MBIR_ROW_MINB;    // resident CTAs per SM the register budget targets
 constexpr int kLatMinBlocks = MBIR_LAT_MINB;
+// the adjoint gather keeps per-pixel weights in shared memory (about 110 KB per row
+// at K = 4096), so two CTAs fit an SM; wider CTAs keep more warps resident
+constexpr int kGatherThreads = MBIR_GATHER_THREADS;
+constexpr int kGatherMinBlocks = MBIR_GATHER_MINB;
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
 constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics

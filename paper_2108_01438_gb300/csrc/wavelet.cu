@@ -20,11 +20,24 @@
 
 namespace mbir {
 
-constexpr int kFwdTA = 16, kFwdTB = 32;   // analysis: output coefficient tile (a x b)
-constexpr int kInvTR = 32, kInvTC = 64;   // synthesis: output pixel tile (rows x cols)
 constexpr int kWavThreads = 256;
-constexpr int kFwdRows = 2 * kFwdTA + 6, kFwdCols = 2 * kFwdTB + 6;
-constexpr int kInvRows = kInvTR / 2 + 3, kInvCols = kInvTC / 2 + 3;
+
+// Tiles.  Analysis computes a TA x TB block of every band's coefficients from a
+// (2 TA + 6) x (2 TB + 6) input block; synthesis a TR x TC block of output pixels
+// from (TR/2 + 3) x (TC/2 + 3) coefficients per band.  The coarse levels (level >=
+// 1, a quarter and a sixteenth of the image) use quarter-size tiles so that their
+// grids still cover the SMs.
+template <bool SMALL>
+struct FwdTile {
+  static constexpr int TA = SMALL ? 8 : 16, TB = SMALL ? 16 : 32;
+  static constexpr int Rows = 2 * TA + 6, Cols = 2 * TB + 6;
+};
+template <bool SMALL>
+struct InvTile {
+  static constexpr int TR = SMALL ? 16 : 32, TC = SMALL ? 32 : 64;
+  static constexpr int Rows = TR / 2 + 3, Cols = TC / 2 + 3;
+};
+constexpr bool dwt_small(int level) { return level > 0; }
 
 template <class R>
 struct WArgs {
@@ -81,17 +94,19 @@ __device__ __forceinline__ double block_sum_w(double v) {
   return t;
 }
 
-template <class R>
+template <class R, bool SMALL>
 __global__ void __launch_bounds__(kWavThreads)
 dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B) {
   using V = cplx_t<R>;
+  constexpr int kTA = FwdTile<SMALL>::TA, kTB = FwdTile<SMALL>::TB;
+  constexpr int kRows = FwdTile<SMALL>::Rows, kCols = FwdTile<SMALL>::Cols;
   int blk;
   const WArgs<R> a = resolve_wargs(arg0, B, blk);
   const int bx = blk % a.gx, by = blk / a.gx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tin = reinterpret_cast<V*>(smem_raw);              // [kFwdRows][kFwdCols]
-  V* tL = tin + kFwdRows * kFwdCols;                    // [kFwdRows][kFwdTB]
-  V* tH = tL + kFwdRows * kFwdTB;
+  V* tin = reinterpret_cast<V*>(smem_raw);              // [kRows][kCols]
+  V* tL = tin + kRows * kCols;                    // [kRows][kTB]
+  V* tH = tL + kRows * kTB;
   __shared__ R h[8], g[8];
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (tid < 8) {
@@ -99,18 +114,18 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
     g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
   }
   const int P = a.P, N = a.N;
-  const int a0 = by * kFwdTA, b0 = bx * kFwdTB;
+  const int a0 = by * kTA, b0 = bx * kTB;
   const V* in = reinterpret_cast<const V*>(a.in);
   pdl_wait_release();
   // stage the input tile with every load of a thread in flight at once
-  constexpr int kFwdPer = (kFwdRows * kFwdCols + kWavThreads - 1) / kWavThreads;
+  constexpr int kFwdPer = (kRows * kCols + kWavThreads - 1) / kWavThreads;
   {
     V vv[kFwdPer];
 #pragma unroll
     for (int q = 0; q < kFwdPer; ++q) {
       const int e = tid + q * nthr;
-      if (e < kFwdRows * kFwdCols) {
-        const int i = e / kFwdCols, j = e - i * kFwdCols;
+      if (e < kRows * kCols) {
+        const int i = e / kCols, j = e - i * kCols;
         const int row = (2 * a0 + i) % P, col = (2 * b0 + j) % N;
         vv[q] = in[(size_t)row * a.istride + col];
       }
@@ -118,13 +133,13 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
 #pragma unroll
     for (int q = 0; q < kFwdPer; ++q) {
       const int e = tid + q * nthr;
-      if (e < kFwdRows * kFwdCols) tin[e] = vv[q];
+      if (e < kRows * kCols) tin[e] = vv[q];
     }
   }
   __syncthreads();
-  for (int e = tid; e < kFwdRows * kFwdTB; e += nthr) {
-    const int i = e / kFwdTB, b = e - i * kFwdTB;
-    const V* src = tin + i * kFwdCols + 2 * b;
+  for (int e = tid; e < kRows * kTB; e += nthr) {
+    const int i = e / kTB, b = e - i * kTB;
+    const V* src = tin + i * kCols + 2 * b;
     V lo = cmk<V>(R(0), R(0)), hi = lo;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -140,15 +155,15 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   V* coef = reinterpret_cast<V*>(a.coef);
   V* llo = reinterpret_cast<V*>(a.out);
   double acc = 0.0;
-  for (int e = tid; e < kFwdTA * kFwdTB; e += nthr) {
-    const int ai = e / kFwdTB, b = e - ai * kFwdTB;
+  for (int e = tid; e < kTA * kTB; e += nthr) {
+    const int ai = e / kTB, b = e - ai * kTB;
     const int A = a0 + ai, B = b0 + b;
     if (A >= Ph || B >= Nh) continue;
     V ll = cmk<V>(R(0), R(0)), hl = ll, lh = ll, hh = ll;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      const V xl = tL[(2 * ai + t) * kFwdTB + b];
-      const V xh = tH[(2 * ai + t) * kFwdTB + b];
+      const V xl = tL[(2 * ai + t) * kTB + b];
+      const V xh = tH[(2 * ai + t) * kTB + b];
       ll.x += h[t] * xl.x; ll.y += h[t] * xl.y;
       hl.x += g[t] * xl.x; hl.y += g[t] * xl.y;
       lh.x += h[t] * xh.x; lh.y += h[t] * xh.y;
@@ -171,20 +186,22 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   }
 }
 
-template <class R>
+template <class R, bool SMALL>
 __global__ void __launch_bounds__(kWavThreads)
 dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B) {
   using V = cplx_t<R>;
+  constexpr int kTR = InvTile<SMALL>::TR, kTC = InvTile<SMALL>::TC;
+  constexpr int kRows = InvTile<SMALL>::Rows, kCols = InvTile<SMALL>::Cols;
   int blk;
   const WArgs<R> a = resolve_wargs(arg0, B, blk);
   const int bx = blk % a.gx, by = blk / a.gx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* cLL = reinterpret_cast<V*>(smem_raw);              // [kInvRows][kInvCols] each
-  V* cLH = cLL + kInvRows * kInvCols;
-  V* cHL = cLH + kInvRows * kInvCols;
-  V* cHH = cHL + kInvRows * kInvCols;
-  V* tlo = cHH + kInvRows * kInvCols;                   // [kInvTR][kInvCols]
-  V* thi = tlo + kInvTR * kInvCols;
+  V* cLL = reinterpret_cast<V*>(smem_raw);              // [kRows][kCols] each
+  V* cLH = cLL + kRows * kCols;
+  V* cHL = cLH + kRows * kCols;
+  V* cHH = cHL + kRows * kCols;
+  V* tlo = cHH + kRows * kCols;                   // [kTR][kCols]
+  V* thi = tlo + kTR * kCols;
   __shared__ R h[8], g[8];
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (tid < 8) {
@@ -192,18 +209,18 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
     g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
   }
   const int P = a.P, N = a.N, Ph = P / 2, Nh = N / 2;
-  const int r0 = by * kInvTR, c0 = bx * kInvTC;
+  const int r0 = by * kTR, c0 = bx * kTC;
   const V* ll = reinterpret_cast<const V*>(a.in);
   const V* coef = reinterpret_cast<const V*>(a.coef);
   pdl_wait_release();
-  constexpr int kInvPer = (kInvRows * kInvCols + kWavThreads - 1) / kWavThreads;
+  constexpr int kInvPer = (kRows * kCols + kWavThreads - 1) / kWavThreads;
   {
     V v0[kInvPer], v1[kInvPer], v2[kInvPer], v3[kInvPer];
 #pragma unroll
     for (int q = 0; q < kInvPer; ++q) {
       const int e = tid + q * nthr;
-      if (e < kInvRows * kInvCols) {
-        const int ia = e / kInvCols, ib = e - ia * kInvCols;
+      if (e < kRows * kCols) {
+        const int ia = e / kCols, ib = e - ia * kCols;
         const int A = ((r0 / 2 - 3 + ia) % Ph + Ph) % Ph;
         const int B = ((c0 / 2 - 3 + ib) % Nh + Nh) % Nh;
         v0[q] = ll[(size_t)A * a.istride + B];
@@ -215,7 +232,7 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
 #pragma unroll
     for (int q = 0; q < kInvPer; ++q) {
       const int e = tid + q * nthr;
-      if (e < kInvRows * kInvCols) {
+      if (e < kRows * kCols) {
         cLL[e] = v0[q];
         cLH[e] = v1[q];
         cHL[e] = v2[q];
@@ -224,15 +241,15 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
     }
   }
   __syncthreads();
-  for (int e = tid; e < kInvTR * kInvCols; e += nthr) {
-    const int r = e / kInvCols, ib = e - r * kInvCols;
+  for (int e = tid; e < kTR * kCols; e += nthr) {
+    const int r = e / kCols, ib = e - r * kCols;
     V lo = cmk<V>(R(0), R(0)), hi = lo;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int t = (r & 1) + 2 * q;
       const int ia = (r - t) / 2 + 3;
-      const V vll = cLL[ia * kInvCols + ib], vhl = cHL[ia * kInvCols + ib];
-      const V vlh = cLH[ia * kInvCols + ib], vhh = cHH[ia * kInvCols + ib];
+      const V vll = cLL[ia * kCols + ib], vhl = cHL[ia * kCols + ib];
+      const V vlh = cLH[ia * kCols + ib], vhh = cHH[ia * kCols + ib];
       lo.x += h[t] * vll.x + g[t] * vhl.x; lo.y += h[t] * vll.y + g[t] * vhl.y;
       hi.x += h[t] * vlh.x + g[t] * vhh.x; hi.y += h[t] * vlh.y + g[t] * vhh.y;
     }
@@ -241,15 +258,15 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   }
   __syncthreads();
   V* out = reinterpret_cast<V*>(a.out);
-  for (int e = tid; e < kInvTR * kInvTC; e += nthr) {
-    const int r = e / kInvTC, c = e - r * kInvTC;
+  for (int e = tid; e < kTR * kTC; e += nthr) {
+    const int r = e / kTC, c = e - r * kTC;
     if (r0 + r >= P || c0 + c >= N) continue;
     V x = cmk<V>(R(0), R(0));
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int t = (c & 1) + 2 * q;
       const int ib = (c - t) / 2 + 3;
-      const V lo = tlo[r * kInvCols + ib], hi = thi[r * kInvCols + ib];
+      const V lo = tlo[r * kCols + ib], hi = thi[r * kCols + ib];
       x.x += h[t] * lo.x + g[t] * hi.x;
       x.y += h[t] * lo.y + g[t] * hi.y;
     }
@@ -269,13 +286,42 @@ __global__ void soft_kernel(const cplx_t<R>* v, cplx_t<R>* z, size_t n, R tau, d
   }
 }
 
-static size_t fwd_smem(size_t vs) { return vs * (kFwdRows * kFwdCols + 2 * kFwdRows * kFwdTB); }
-static size_t inv_smem(size_t vs) { return vs * (4 * kInvRows * kInvCols + 2 * kInvTR * kInvCols); }
+template <bool SMALL>
+static size_t fwd_smem_t(size_t vs) {
+  using T = FwdTile<SMALL>;
+  return vs * (T::Rows * T::Cols + 2 * T::Rows * T::TB);
+}
+template <bool SMALL>
+static size_t inv_smem_t(size_t vs) {
+  using T = InvTile<SMALL>;
+  return vs * (4 * T::Rows * T::Cols + 2 * T::TR * T::Cols);
+}
+static size_t fwd_smem(size_t vs, int level) { return dwt_small(level) ? fwd_smem_t<true>(vs) : fwd_smem_t<false>(vs); }
+static size_t inv_smem(size_t vs, int level) { return dwt_small(level) ? inv_smem_t<true>(vs) : inv_smem_t<false>(vs); }
+
+// CTAs along the columns and in total of analysis (inverse = 0) or synthesis of a
+// level whose block (analysis input / synthesis output) is P x N.
+static int dwt_gx(int N, int inverse, int level) {
+  if (inverse) {
+    const int tc = dwt_small(level) ? InvTile<true>::TC : InvTile<false>::TC;
+    return (N + tc - 1) / tc;
+  }
+  const int tb = dwt_small(level) ? FwdTile<true>::TB : FwdTile<false>::TB;
+  return (N / 2 + tb - 1) / tb;
+}
+static int dwt_gy(int P, int inverse, int level) {
+  if (inverse) {
+    const int tr = dwt_small(level) ? InvTile<true>::TR : InvTile<false>::TR;
+    return (P + tr - 1) / tr;
+  }
+  const int ta = dwt_small(level) ? FwdTile<true>::TA : FwdTile<false>::TA;
+  return (P / 2 + ta - 1) / ta;
+}
 
 int wavelet_partial_count(int nx, int nz) {
   int total = 0, P = nx, N = nz;
   for (int lev = 0; lev < 3; ++lev) {
-    total += ((N / 2 + kFwdTB - 1) / kFwdTB) * ((P / 2 + kFwdTA - 1) / kFwdTA);
+    total += dwt_gx(N, 0, lev) * dwt_gy(P, 0, lev);
     P /= 2;
     N /= 2;
   }
@@ -316,9 +362,13 @@ static int analysis_t(mbir_plan p, const void* in, void* coef, bool thresh, R ta
     a.tau = tau;
     a.thresh = thresh ? (lev == 2 ? 2 : 1) : 0;
     a.partial = thresh ? part : nullptr;
-    const int gx = (N / 2 + kFwdTB - 1) / kFwdTB, gy = (P / 2 + kFwdTA - 1) / kFwdTA;
+    const int gx = dwt_gx(N, 0, lev), gy = dwt_gy(P, 0, lev);
     a.gx = gx;
-    { ProfScope ps_(p, PC_DWT_FWD, st); launch(dwt_fwd_kernel<R>, dim3(gx * gy), dim3(kWavThreads), fwd_smem(sizeof(cplx_t<R>)), st, a, no_batch<WArgs<R>>()); }
+    {
+      ProfScope ps_(p, PC_DWT_FWD, st);
+      launch(dwt_small(lev) ? dwt_fwd_kernel<R, true> : dwt_fwd_kernel<R, false>, dim3(gx * gy), dim3(kWavThreads),
+             fwd_smem(sizeof(cplx_t<R>), lev), st, a, no_batch<WArgs<R>>());
+    }
     MBIR_LAUNCH_CHECK();
     if (part) part += gx * gy;
     src = lls[lev];
@@ -350,9 +400,13 @@ static int synthesis_t(mbir_plan p, const void* coef, void* out, cudaStream_t st
     a.tau = R(0);
     a.thresh = 0;
     a.partial = nullptr;
-    const int gx = (a.N + kInvTC - 1) / kInvTC, gy = (a.P + kInvTR - 1) / kInvTR;
+    const int gx = dwt_gx(a.N, 1, lev), gy = dwt_gy(a.P, 1, lev);
     a.gx = gx;
-    { ProfScope ps_(p, PC_DWT_INV, st); launch(dwt_inv_kernel<R>, dim3(gx * gy), dim3(kWavThreads), inv_smem(sizeof(cplx_t<R>)), st, a, no_batch<WArgs<R>>()); }
+    {
+      ProfScope ps_(p, PC_DWT_INV, st);
+      launch(dwt_small(lev) ? dwt_inv_kernel<R, true> : dwt_inv_kernel<R, false>, dim3(gx * gy), dim3(kWavThreads),
+             inv_smem(sizeof(cplx_t<R>), lev), st, a, no_batch<WArgs<R>>());
+    }
     MBIR_LAUNCH_CHECK();
   }
   return MBIR_OK;
@@ -362,10 +416,14 @@ bool wavelet_supported(int nx, int nz) { return nx % 8 == 0 && nz % 8 == 0 && nx
 
 template <class R>
 static int configure_wavelet_t() {
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)fwd_smem(sizeof(cplx_t<R>))));
-  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)inv_smem(sizeof(cplx_t<R>))));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_fwd_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fwd_smem_t<false>(sizeof(cplx_t<R>))));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_fwd_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fwd_smem_t<true>(sizeof(cplx_t<R>))));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_inv_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)inv_smem_t<false>(sizeof(cplx_t<R>))));
+  MBIR_CUDA_TRY(cudaFuncSetAttribute(dwt_inv_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)inv_smem_t<true>(sizeof(cplx_t<R>))));
   return MBIR_OK;
 }
 
@@ -507,14 +565,13 @@ size_t dwt_args_bytes(int precision) {
   return precision == MBIR_FP64 ? sizeof(WArgs<double>) : sizeof(WArgs<float>);
 }
 
-int dwt_level_ctas(int P, int N, int inverse) {
-  if (inverse) return ((N + kInvTC - 1) / kInvTC) * ((P + kInvTR - 1) / kInvTR);
-  return ((N / 2 + kFwdTB - 1) / kFwdTB) * ((P / 2 + kFwdTA - 1) / kFwdTA);
+int dwt_level_ctas(int P, int N, int inverse, int level) {
+  return dwt_gx(N, inverse, level) * dwt_gy(P, inverse, level);
 }
 
-size_t dwt_smem_bytes(int precision, int inverse) {
+size_t dwt_smem_bytes(int precision, int inverse, int level) {
   const size_t vs = precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
-  return inverse ? inv_smem(vs) : fwd_smem(vs);
+  return inverse ? inv_smem(vs, level) : fwd_smem(vs, level);
 }
 
 // Argument block of analysis (inverse = 0) or synthesis level `level` (0 = finest)
@@ -541,7 +598,7 @@ static void fill_dwt_t(mbir_plan p, int level, int inverse, const void* in, void
     a.out = lls[level];
     a.ostride = lstr[level];
     a.thresh = thresh;
-    a.gx = (a.N / 2 + kFwdTB - 1) / kFwdTB;
+    a.gx = dwt_gx(a.N, 0, level);
   } else {
     a.in = lls[level];
     a.istride = lstr[level];
@@ -549,7 +606,7 @@ static void fill_dwt_t(mbir_plan p, int level, int inverse, const void* in, void
     a.ostride = level == 0 ? nz : lstr[level - 1];
     a.thresh = 0;
     a.partial = nullptr;
-    a.gx = (a.N + kInvTC - 1) / kInvTC;
+    a.gx = dwt_gx(a.N, 1, level);
   }
   memcpy(dst, &a, sizeof(a));
 }
@@ -561,7 +618,7 @@ void fill_dwt_args(mbir_plan p, int level, int inverse, const void* in, void* ou
 }
 
 template <class R>
-static void dwt_batch_t(int inverse, const BatchLaunch& L, cudaStream_t st) {
+static void dwt_batch_t(int inverse, int level, const BatchLaunch& L, cudaStream_t st) {
   BatchRef<WArgs<R>> B;
   B.args = reinterpret_cast<const WArgs<R>*>(L.dargs);
   B.off = L.doff;
@@ -570,14 +627,15 @@ static void dwt_batch_t(int inverse, const BatchLaunch& L, cudaStream_t st) {
   B.mu = 0.0;
   WArgs<R> a0;
   memcpy(&a0, L.host0, sizeof(a0));
-  if (inverse) launch(dwt_inv_kernel<R>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
-  else launch(dwt_fwd_kernel<R>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
+  const bool sm = dwt_small(level);
+  if (inverse) launch(sm ? dwt_inv_kernel<R, true> : dwt_inv_kernel<R, false>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
+  else launch(sm ? dwt_fwd_kernel<R, true> : dwt_fwd_kernel<R, false>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
 }
 
-int batch_dwt(int inverse, int precision, const BatchLaunch& L, cudaStream_t st) {
+int batch_dwt(int inverse, int level, int precision, const BatchLaunch& L, cudaStream_t st) {
   if (L.total <= 0) return MBIR_OK;
-  if (precision == MBIR_FP64) dwt_batch_t<double>(inverse, L, st);
-  else dwt_batch_t<float>(inverse, L, st);
+  if (precision == MBIR_FP64) dwt_batch_t<double>(inverse, level, L, st);
+  else dwt_batch_t<float>(inverse, level, L, st);
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
 }
