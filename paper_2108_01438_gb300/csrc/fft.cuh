@@ -42,28 +42,6 @@ __host__ __device__ inline int digit_reverse(int k, const Radix& rad) {
   return pos;
 }
 
-// Same, by shifts, when every radix is a power of two (rad.pow2).
-__device__ __forceinline__ int digit_reverse_pow2(int k, const Radix& rad) {
-  int pos = 0, rem_bits = rad.log2n;
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    if (p < rad.npass) {
-      const int b = rad.lg[p];
-      rem_bits -= b;
-      pos |= (k & ((1 << b) - 1)) << rem_bits;
-      k >>= b;
-    }
-  }
-#pragma unroll 1
-  for (int p = 4; p < rad.npass; ++p) {
-    const int b = rad.lg[p];
-    rem_bits -= b;
-    pos |= (k & ((1 << b) - 1)) << rem_bits;
-    k >>= b;
-  }
-  return pos;
-}
-
 template <class V>
 struct Tw2 {
   const V* lo;   // w_N^i, i < 2^shift

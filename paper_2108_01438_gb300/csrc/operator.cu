@@ -460,17 +460,24 @@ lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>>
 // ------------------------------------------------------------- KB weights
 
 // Weights of the J taps at fractional grid position frac (tap j at offset
-// J/2 - 1 - j + frac from the point).
+// J/2 - 1 - j + frac from the point).  The kernel is even, so tap J-1-j at x is
+// tap j at -x: one polynomial per mirrored pair, split into its even and odd
+// halves in x^2, gives both weights (w = E(x^2) +- x O(x^2)).
 template <class R, int J>
 __device__ __forceinline__ void kb_weights(R frac, const RowArgs<R>& a, R (&w)[J]) {
   if constexpr (sizeof(R) == 4) {
-    const float x = frac - 0.5f;
+    static_assert(kKbDeg % 2 == 1 && J % 2 == 0, "paired taps need an odd degree and an even width");
+    const float x = frac - 0.5f, x2 = x * x;
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      float acc = a.kbpoly[j][kKbDeg];
+    for (int j = 0; j < J / 2; ++j) {
+      float e = a.kbpoly[j][kKbDeg - 1], o = a.kbpoly[j][kKbDeg];
 #pragma unroll
-      for (int d = kKbDeg - 1; d >= 0; --d) acc = fmaf(acc, x, a.kbpoly[j][d]);
-      w[j] = acc;
+      for (int d = kKbDeg - 3; d >= 0; d -= 2) {
+        e = fmaf(e, x2, a.kbpoly[j][d]);
+        o = fmaf(o, x2, a.kbpoly[j][d + 1]);
+      }
+      w[j] = fmaf(x, o, e);
+      w[J - 1 - j] = fmaf(-x, o, e);
     }
   } else {
 #pragma unroll
@@ -482,9 +489,8 @@ __device__ __forceinline__ void kb_weights(R frac, const RowArgs<R>& a, R (&w)[J
   }
 }
 
-__device__ __forceinline__ int row_pos(int i, const Radix& rad, const int* perm) {
-  return rad.pow2 ? digit_reverse_pow2(i, rad) : perm[i];
-}
+// Position of index i after a dif transform (the plan's digit-reversal table).
+__device__ __forceinline__ int row_pos(int i, const int* perm) { return perm[i]; }
 
 // Accumulator of sum_i w_i b_i: plain, or error-compensated (two-product of
 // each term by FMA, two-sum of the running total; Ogita, Rump & Oishi's Dot2)
@@ -541,7 +547,7 @@ __device__ __forceinline__ void row_forward_body(const RowArgs<R>& a, const Radi
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * nthr;
-      if (i < K) buf[swz(row_pos(i, rad, perm), sw)] = v[u];
+      if (i < K) buf[swz(row_pos(i, perm), sw)] = v[u];
     }
   }
   __syncthreads();
@@ -649,7 +655,7 @@ __device__ __forceinline__ void row_adjoint_body(const RowArgs<R>& a, const Radi
   for (int n = tid; n < nz; n += nthr) {
     int i = n - n0;
     if (i < 0) i += K;
-    Wo[n] = cscale(buf[swz(row_pos(i, rad, perm), sw)], cdep[n]);
+    Wo[n] = cscale(buf[swz(row_pos(i, perm), sw)], cdep[n]);
   }
 }
 
@@ -784,7 +790,7 @@ __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, con
   for (int n = tid; n < nz; n += nthr) {
     int i = n - n0;
     if (i < 0) i += K;
-    Wo[n] = cscale(buf[swz(row_pos(i, rad, perm), sw)], cdep[n]);
+    Wo[n] = cscale(buf[swz(row_pos(i, perm), sw)], cdep[n]);
   }
 }
 

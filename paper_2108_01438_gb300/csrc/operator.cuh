@@ -95,7 +95,7 @@ struct RowArgs {
   const void* tab;
   const void* cdep;
   const void* tw;
-  const int* perm;   // digit reversal of the K-point transform (non power-of-two K)
+  const int* perm;   // digit reversal of the K-point transform
   const int4* rowmeta;   // per row {base, span, direction, 0} of the unwrapped tap cells
   Radix rad;
   int nx, nz, m, K, n0;
