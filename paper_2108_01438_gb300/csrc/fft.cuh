@@ -262,6 +262,267 @@ __device__ void fft_dit(V* s, int batch, const Radix& rad, const Tw2<V>& tw, boo
   }
 }
 
+// ------------------------------------------------------------------ paired
+//
+// Two complex sequences a, b that share every twiddle (two adjacent columns of a
+// lateral tile) in split form: one float4 {re_a, re_b, im_a, im_b} per index.
+// Every butterfly then runs on float2 lanes with the paired FP32 instructions of
+// sm_100 and later (FADD2 / FMUL2 / FFMA2), so one instruction does the work
+// of two scalar ones.  Twiddles are held broadcast ({c, c}, {s, s}) so that they
+// multiply both lanes.  Same algorithms, orders and twiddle tables as above.
+
+struct PC {
+  float2 re, im;   // lanes: sequence a, sequence b
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ PC padd(PC a, PC b) { return {add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ PC psub(PC a, PC b) { return {sub2(a.re, b.re), sub2(a.im, b.im)}; }
+// times -j (forward) or +j (inverse)
+template <bool INV>
+__device__ __forceinline__ PC pmul_mj(PC a) {
+  return INV ? PC{neg2(a.im), a.re} : PC{a.im, neg2(a.re)};
+}
+// a times the broadcast twiddle w (also the product of two broadcast twiddles)
+__device__ __forceinline__ PC pmulw(PC a, PC w) {
+  return {fma2(a.re, w.re, mul2(neg2(a.im), w.im)), fma2(a.re, w.im, mul2(a.im, w.re))};
+}
+__device__ __forceinline__ PC pconj(PC w) { return {w.re, neg2(w.im)}; }
+
+__device__ __forceinline__ PC ld_pc(const float4* s, int i) {
+  const float4 t = s[i];
+  return {make_float2(t.x, t.y), make_float2(t.z, t.w)};
+}
+__device__ __forceinline__ void st_pc(float4* s, int i, PC v) { s[i] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+
+struct TwP {
+  const float4* lo;   // broadcast w_N^i, i < 2^shift
+  const float4* hi;   // broadcast w_N^{i 2^shift}
+  int shift, mask;
+  __device__ __forceinline__ PC operator()(int e) const {
+    const float4 h = hi[e >> shift], l = lo[e & mask];
+    return pmulw(PC{make_float2(h.x, h.y), make_float2(h.z, h.w)}, PC{make_float2(l.x, l.y), make_float2(l.z, l.w)});
+  }
+};
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_small_p(PC (&v)[R], const TwP& tw, int N) {
+  if constexpr (R == 2) {
+    const PC a = v[0], b = v[1];
+    v[0] = padd(a, b);
+    v[1] = psub(a, b);
+  } else if constexpr (R == 4) {
+    const PC t0 = padd(v[0], v[2]), t1 = psub(v[0], v[2]);
+    const PC t2 = padd(v[1], v[3]), t3 = pmul_mj<INV>(psub(v[1], v[3]));
+    v[0] = padd(t0, t2);
+    v[2] = psub(t0, t2);
+    v[1] = padd(t1, t3);
+    v[3] = psub(t1, t3);
+  } else if constexpr (R == 8) {
+    const PC e0 = padd(v[0], v[4]), e1 = psub(v[0], v[4]);
+    const PC e2 = padd(v[2], v[6]), e3 = pmul_mj<INV>(psub(v[2], v[6]));
+    const PC E0 = padd(e0, e2), E2 = psub(e0, e2), E1 = padd(e1, e3), E3 = psub(e1, e3);
+    const PC o0 = padd(v[1], v[5]), o1 = psub(v[1], v[5]);
+    const PC o2 = padd(v[3], v[7]), o3 = pmul_mj<INV>(psub(v[3], v[7]));
+    const PC O0 = padd(o0, o2), O2 = psub(o0, o2), O1 = padd(o1, o3), O3 = psub(o1, o3);
+    const float2 h = make_float2(0.70710678118654752440f, 0.70710678118654752440f);
+    // w_8^1, w_8^2 = -+j, w_8^3 as in the scalar transform
+    const PC O1w = INV ? PC{mul2(h, sub2(O1.re, O1.im)), mul2(h, add2(O1.re, O1.im))}
+                       : PC{mul2(h, add2(O1.re, O1.im)), mul2(h, sub2(O1.im, O1.re))};
+    const PC O2w = pmul_mj<INV>(O2);
+    const PC O3w = INV ? PC{neg2(mul2(h, add2(O3.re, O3.im))), mul2(h, sub2(O3.re, O3.im))}
+                       : PC{mul2(h, sub2(O3.im, O3.re)), neg2(mul2(h, add2(O3.re, O3.im)))};
+    v[0] = padd(E0, O0);
+    v[4] = psub(E0, O0);
+    v[1] = padd(E1, O1w);
+    v[5] = psub(E1, O1w);
+    v[2] = padd(E2, O2w);
+    v[6] = psub(E2, O2w);
+    v[3] = padd(E3, O3w);
+    v[7] = psub(E3, O3w);
+  }
+}
+
+// v[q] *= w_N^{q e1} (conjugated for inverse transforms), as apply_twiddles.
+template <int R, bool INV>
+__device__ __forceinline__ void apply_twiddles_p(PC (&v)[R], const TwP& tw, int e1) {
+  auto get = [&](int e) {
+    const PC w = tw(e);
+    return INV ? pconj(w) : w;
+  };
+  if constexpr (R == 2) {
+    v[1] = pmulw(v[1], get(e1));
+  } else if constexpr (R == 4 || R == 8) {
+    const PC w1 = get(e1);
+    const PC w2 = pmulw(w1, w1);
+    v[1] = pmulw(v[1], w1);
+    v[2] = pmulw(v[2], w2);
+    v[3] = pmulw(v[3], pmulw(w2, w1));
+    if constexpr (R == 8) {
+      const PC w4 = pmulw(w2, w2);
+      v[4] = pmulw(v[4], w4);
+      v[5] = pmulw(v[5], pmulw(w4, w1));
+      v[6] = pmulw(v[6], pmulw(w4, w2));
+      v[7] = pmulw(v[7], pmulw(pmulw(w4, w2), w1));
+    }
+  } else {
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = pmulw(v[q], get(q * e1));
+  }
+}
+
+// One pass of an odd radix R (3, 5, 7) on split pairs.  With s_r = v_r + v_{R-r},
+// d_r = v_r - v_{R-r} (r = 1 .. (R-1)/2) and w^{rq} = c + i sigma,
+//   X_0 = v_0 + sum s_r,  X_q = A + i B,  X_{R-q} = A - i B,
+//   A = v_0 + sum c s_r,  B = sum sigma d_r,
+// so the sums and differences replace the inputs in place and each output pair
+// is twiddled (dif) and stored as soon as it is formed: no second array of R
+// values is held in registers.
+template <int R, bool INV, bool DIT>
+__device__ __forceinline__ void ct_pass_p_odd(float4* s, int N, int batch, int bshift, int L, const TwP& tw,
+                                              int tid, int nthr) {
+  static_assert(R % 2 == 1, "odd radix");
+  constexpr int H = (R - 1) / 2;
+  const int M = L / R;
+  const int mshift = log2_if_pow2(M);
+  const int nb = batch * (N / R);
+  const int tstep = N / L;
+  const int stride = N / R;
+  auto get = [&](int e) {
+    const PC w = tw(e);
+    return INV ? pconj(w) : w;
+  };
+  for (int idx = tid; idx < nb; idx += nthr) {
+    int t, b, blk, j;
+    divmod_u(idx, batch, bshift, t, b);
+    divmod_u(t, M, mshift, blk, j);
+    const int i0 = (blk * L + j) * batch + b, di = M * batch;
+    const int e1 = j * tstep;
+    PC v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = ld_pc(s, i0 + r * di);
+    if (DIT && j != 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = pmulw(v[r], get(r * e1));
+    }
+    PC x0 = v[0];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      const PC a = v[r], c = v[R - r];
+      v[r] = padd(a, c);
+      v[R - r] = psub(a, c);
+      x0 = padd(x0, v[r]);
+    }
+    st_pc(s, i0, x0);
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      PC A = v[0], B = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+      for (int r = 1; r <= H; ++r) {
+        const PC w = get(((r * q) % R) * stride);
+        A.re = fma2(v[r].re, w.re, A.re);
+        A.im = fma2(v[r].im, w.re, A.im);
+        B.re = fma2(v[R - r].re, w.im, B.re);
+        B.im = fma2(v[R - r].im, w.im, B.im);
+      }
+      PC xq = {sub2(A.re, B.im), add2(A.im, B.re)};        // A + i B
+      PC xr = {add2(A.re, B.im), sub2(A.im, B.re)};        // A - i B
+      if (!DIT && j != 0) {
+        xq = pmulw(xq, get(q * e1));
+        xr = pmulw(xr, get((R - q) * e1));
+      }
+      st_pc(s, i0 + q * di, xq);
+      st_pc(s, i0 + (R - q) * di, xr);
+    }
+  }
+  __syncthreads();
+}
+
+template <int R, bool INV, bool DIT>
+__device__ __forceinline__ void ct_pass_p(float4* s, int N, int batch, int bshift, int L, const TwP& tw, int tid,
+                                          int nthr) {
+  const int M = L / R;
+  const int mshift = log2_if_pow2(M);
+  const int nb = batch * (N / R);
+  const int tstep = N / L;
+  for (int idx = tid; idx < nb; idx += nthr) {
+    int t, b, blk, j;
+    divmod_u(idx, batch, bshift, t, b);
+    divmod_u(t, M, mshift, blk, j);
+    const int i0 = (blk * L + j) * batch + b, di = M * batch;
+    PC v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = ld_pc(s, i0 + r * di);
+    if (DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
+    dft_small_p<R, INV>(v, tw, N);
+    if (!DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
+#pragma unroll
+    for (int r = 0; r < R; ++r) st_pc(s, i0 + r * di, v[r]);
+  }
+  __syncthreads();
+}
+
+// Radices up to 8 (a radix-16 butterfly of split pairs would hold 64 registers).
+template <bool INV, bool DIT>
+__device__ __forceinline__ void ct_dispatch_p(int R, float4* s, int N, int batch, int bshift, int L, const TwP& tw,
+                                              int tid, int nthr) {
+  switch (R) {
+    case 8: ct_pass_p<8, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 4: ct_pass_p<4, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 2: ct_pass_p<2, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 3: ct_pass_p_odd<3, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 5: ct_pass_p_odd<5, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 7: ct_pass_p_odd<7, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    default: break;
+  }
+}
+
+// `batch` interleaved pair-sequences, element i of pair-sequence b at s[i * batch + b].
+template <bool INV>
+__device__ void fft_p_dif(float4* s, int batch, const Radix& rad, const TwP& tw) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int bshift = log2_if_pow2(batch);
+  int L = rad.n;
+  for (int p = 0; p < rad.npass; ++p) {
+    const int R = rad.r[p];
+    ct_dispatch_p<INV, false>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
+    L /= R;
+  }
+}
+
+template <bool INV>
+__device__ void fft_p_dit(float4* s, int batch, const Radix& rad, const TwP& tw) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int bshift = log2_if_pow2(batch);
+  int L = 1;
+  for (int p = rad.npass - 1; p >= 0; --p) {
+    const int R = rad.r[p];
+    L *= R;
+    ct_dispatch_p<INV, true>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
+  }
+}
+
+// Twiddle tables of a transform (global [lo | hi], float2) into shared memory in
+// broadcast form.  No barrier inside.
+__device__ __forceinline__ TwP load_twiddles_p(float4* smem, const float2* __restrict__ g, const Radix& rad) {
+  const int n = rad.tw_lo + rad.tw_hi;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 w = g[i];
+    smem[i] = make_float4(w.x, w.x, w.y, w.y);
+  }
+  TwP t;
+  t.lo = smem;
+  t.hi = smem + rad.tw_lo;
+  t.shift = rad.tw_shift;
+  t.mask = rad.tw_lo - 1;
+  return t;
+}
+
 // Copy the two twiddle tables of a transform (tw2 = [lo | hi] in global memory)
 // into shared memory and return the accessor.  No barrier inside.
 template <class V>

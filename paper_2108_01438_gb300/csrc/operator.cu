@@ -122,13 +122,15 @@ __device__ __forceinline__ void st2(T* p, size_t o, bool v2, bool ok0, bool ok1,
   if (ok1) p[o + 1] = b;
 }
 
-// shared-memory pair at an even index (16-byte aligned for FP32)
+// The column pair (c, c + 1) of a tile row in shared memory, at an even index i.
+// FP32 tiles hold the pair in split form {re_c, re_c+1, im_c, im_c+1} (the
+// layout of the paired transform); FP64 tiles hold two complex numbers.
 template <class V>
 __device__ __forceinline__ void lds2(const V* s, int i, V& a, V& b) {
   if constexpr (sizeof(V) == 8) {
     const float4 t = *reinterpret_cast<const float4*>(s + i);
-    a = cmk<V>(t.x, t.y);
-    b = cmk<V>(t.z, t.w);
+    a = cmk<V>(t.x, t.z);
+    b = cmk<V>(t.y, t.w);
   } else {
     a = s[i];
     b = s[i + 1];
@@ -138,10 +140,39 @@ __device__ __forceinline__ void lds2(const V* s, int i, V& a, V& b) {
 template <class V>
 __device__ __forceinline__ void sts2(V* s, int i, V a, V b) {
   if constexpr (sizeof(V) == 8) {
-    *reinterpret_cast<float4*>(s + i) = make_float4(a.x, a.y, b.x, b.y);
+    *reinterpret_cast<float4*>(s + i) = make_float4(a.x, b.x, a.y, b.y);
   } else {
     s[i] = a;
     s[i + 1] = b;
+  }
+}
+
+// The lateral transforms of a tile: FP32 tiles as TC/2 interleaved split pairs
+// through the paired transform, FP64 tiles as TC interleaved sequences.
+template <class R>
+struct LatFFT {
+  Tw2<cplx_t<R>> tw;
+  TwP twp;
+};
+
+template <class R>
+__device__ __forceinline__ LatFFT<R> lat_twiddles(cplx_t<R>* tws, const void* twg, const Radix& rad) {
+  LatFFT<R> f;
+  if constexpr (sizeof(R) == 4)
+    f.twp = load_twiddles_p(reinterpret_cast<float4*>(tws), reinterpret_cast<const float2*>(twg), rad);
+  else
+    f.tw = load_twiddles(tws, reinterpret_cast<const cplx_t<R>*>(twg), rad);
+  return f;
+}
+
+template <class R, bool INV, bool DIT>
+__device__ __forceinline__ void lat_fft(cplx_t<R>* s, int TC, const Radix& rad, const LatFFT<R>& f) {
+  if constexpr (sizeof(R) == 4) {
+    if constexpr (DIT) fft_p_dit<INV>(reinterpret_cast<float4*>(s), TC >> 1, rad, f.twp);
+    else fft_p_dif<INV>(reinterpret_cast<float4*>(s), TC >> 1, rad, f.twp);
+  } else {
+    if constexpr (DIT) fft_dit<INV>(s, TC, rad, f.tw, false);
+    else fft_dif<INV>(s, TC, rad, f.tw, false);
   }
 }
 
@@ -309,7 +340,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   V* s = reinterpret_cast<V*>(smem_raw);
   V* tws = s + nx * TC;
   const int tid = threadIdx.x;
-  const Tw2<V> tw = load_twiddles(tws, reinterpret_cast<const V*>(twg), rad);
+  const LatFFT<R> tw = lat_twiddles<R>(tws, twg, rad);
   const int half = TC >> 1, hs = __ffs(half) - 1;
   const int b = 2 * (tid & (half - 1));
   const int p0 = tid >> hs, pstep = (int)blockDim.x >> hs;
@@ -354,7 +385,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   if constexpr (kMid) {
     // inverse as a forward dif of conj S, the epilogue in place on the
     // digit-reversed tile, then the forward dit
-    fft_dif<false>(s, TC, rad, tw, false);
+    lat_fft<R, false, false>(s, TC, rad, tw);
     constexpr int UM = 2;
     for (int p = p0; p < nx; p += UM * pstep) {
       EpOps<R> oa[UM], ob[UM];
@@ -388,14 +419,14 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
       }
     }
     __syncthreads();
-    fft_dit<false>(s, TC, rad, tw, false);
+    lat_fft<R, false, true>(s, TC, rad, tw);
     for (int p = p0; p < nx; p += pstep) {
       V xa, xb;
       lds2(s, p * TC + b, xa, xb);
       st2(reinterpret_cast<V*>(a.out), (size_t)p * C + c, v2, ok0, ok1, cscale(xa, a.scale), cscale(xb, a.scale));
     }
   } else {
-    fft_dif<INV>(s, TC, rad, tw, false);
+    lat_fft<R, INV, false>(s, TC, rad, tw);
     for (int p = p0; p < nx; p += U * pstep) {
       EpOps<R> oa[U], ob[U];
 #pragma unroll
@@ -846,9 +877,10 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
   return a;
 }
 
+// tile plus the twiddle tables (16 bytes an entry: FP64 complex or FP32 broadcast)
 template <class R>
 size_t lat_smem(mbir_plan p) {
-  return sizeof(cplx_t<R>) * ((size_t)p->nx * p->tile_c + p->rad_x.tw_lo + p->rad_x.tw_hi);
+  return sizeof(cplx_t<R>) * (size_t)p->nx * p->tile_c + 16 * (size_t)(p->rad_x.tw_lo + p->rad_x.tw_hi);
 }
 
 template <class R, int MODE>

@@ -74,12 +74,15 @@ static double kb_hat(double nu, int J, double alpha) {
   return J * v / bessel_i0(alpha);
 }
 
-static bool factor_radix(int n, Radix* r) {
+// max_radix 16 or 8 (the paired FP32 lateral transform keeps a butterfly's
+// split pairs in registers, which radix 16 would overflow)
+static bool factor_radix(int n, Radix* r, int max_radix = 16) {
   memset(r, 0, sizeof(*r));
   r->n = n;
   int rem = n;
   const int order[] = {16, 8, 4, 2, 3, 5, 7};
   for (int f : order) {
+    if (f > max_radix) continue;
     while (rem % f == 0) {
       if (r->npass >= kMaxPasses) return false;
       r->r[r->npass++] = f;
@@ -568,7 +571,7 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
     p->dz = M_PI / (2.0 * g->nz * dkmax);
   }
   p->alpha = g->kb_alpha > 0 ? g->kb_alpha : 2.34 * g->kb_width;
-  factor_radix(p->nx, &p->rad_x);
+  factor_radix(p->nx, &p->rad_x, 8);
   factor_radix(p->K, &p->rad_k);
   // lateral tile: keep nx * tile_c <= kLatElems elements, at most 16 columns
   int tc = kLatElems / p->nx;
