@@ -308,6 +308,12 @@ typedef struct {
 } mbir_profile_entry;
 
 int mbir_profile_begin(mbir_plan plan, int32_t capacity);
+/* Between begin and end: record only launches of one kernel class (a name as
+ * returned by mbir_profile_end), or of every class again with NULL.  Recording a
+ * single class leaves the other launches undisturbed by event records, so a run
+ * can be timed while one kernel's launch durations are taken.
+ * MBIR_ERR_INVALID: no recording is active or the name is unknown. */
+int mbir_profile_only(mbir_plan plan, const char* kernel_class);
 int mbir_profile_end(mbir_plan plan, mbir_profile_entry* out, int32_t max_entries, int32_t* n_entries);
 
 /* Static description of a status code. */

@@ -112,6 +112,7 @@ struct Profiler {
   int cap = 0, n = 0;
   cudaEvent_t* ev = nullptr;   // 2 * cap
   int* cls = nullptr;          // cap
+  unsigned mask = ~0u;         // kernel classes that record (bit per ProfClass)
 };
 
 const char* prof_class_name(int c);
@@ -211,7 +212,7 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
 // Event profiler: prof_begin returns a slot (or -1 when not recording).
 inline int prof_begin(mbir_plan p, int cls, cudaStream_t st) {
   Profiler* pr = p->prof;
-  if (!pr || pr->n >= pr->cap) return -1;
+  if (!pr || pr->n >= pr->cap || !((pr->mask >> cls) & 1u)) return -1;
   const int i = pr->n++;
   pr->cls[i] = cls;
   cudaEventRecord(pr->ev[2 * i], st);

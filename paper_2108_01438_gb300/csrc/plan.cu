@@ -470,6 +470,21 @@ int mbir_profile_begin(mbir_plan p, int32_t capacity) {
   return MBIR_OK;
 }
 
+int mbir_profile_only(mbir_plan p, const char* kernel_class) {
+  if (!p || !p->prof) return MBIR_ERR_INVALID;
+  if (!kernel_class) {
+    p->prof->mask = ~0u;
+    return MBIR_OK;
+  }
+  for (int c = 0; c < PC_COUNT; ++c) {
+    if (strcmp(prof_class_name(c), kernel_class) == 0) {
+      p->prof->mask = 1u << c;
+      return MBIR_OK;
+    }
+  }
+  return MBIR_ERR_INVALID;
+}
+
 int mbir_profile_end(mbir_plan p, mbir_profile_entry* out, int32_t max_entries, int32_t* n_entries) {
   if (!p || !p->prof) return MBIR_ERR_INVALID;
   Profiler* pr = p->prof;

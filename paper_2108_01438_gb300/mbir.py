@@ -96,6 +96,7 @@ _SIGNATURES = {
     "mbir_wavelet": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_wavelet_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_profile_begin": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mbir_profile_only": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mbir_profile_end": (C.c_int, [C.c_void_p, C.POINTER(ProfileEntry), C.c_int32, C.POINTER(C.c_int32)]),
     "mbir_status_string": (C.c_char_p, [C.c_int]),
     "mbir_last_error": (C.c_char_p, []),
@@ -255,6 +256,11 @@ class Plan:
     def profile_begin(self, capacity: int = 1 << 16) -> None:
         """Record a CUDA event pair around every later kernel launch on this plan."""
         _check(lib().mbir_profile_begin(self._h, int(capacity)), "mbir_profile_begin")
+
+    def profile_only(self, kernel_class: str | None) -> None:
+        """While recording, record only launches of one kernel class (None: all)."""
+        _check(lib().mbir_profile_only(self._h, None if kernel_class is None else kernel_class.encode()),
+               "mbir_profile_only")
 
     def profile_end(self) -> dict:
         """Stop recording; returns {kernel class: (launches, total_ms)}."""
