@@ -415,14 +415,19 @@ int Engine::add_row(std::vector<Stage>& out, bool adjoint, const std::vector<BSc
   std::vector<unsigned char> blocks(ab * idx.size());
   std::vector<int> off(idx.size() + 1, 0);
   size_t smem = 0;
-  bool gather = true;
-  for (BScan* s : idx) gather = gather && plan_uses_gather(s->p);
-  const int kind = adjoint ? (gather ? 1 : 2) : 0;
+  // one kernel for the stage: the most general of the scans' own choices (the
+  // paired gather fits fewer geometries than the single-row one, atomics fit all)
+  auto level = [](int k) { return k == ROW_GATHER_PAIR ? 0 : k == ROW_GATHER ? 1 : 2; };
+  int kind = row_kind(idx[0]->p, adjoint);
+  for (BScan* s : idx) {
+    const int k = row_kind(s->p, adjoint);
+    if (adjoint && level(k) > level(kind)) kind = k;
+  }
   for (size_t i = 0; i < idx.size(); ++i) {
     BScan& s = *idx[i];
     fill_row_args(s.p, s.c.wsA, s.c.wsB, blocks.data() + i * ab);
-    off[i + 1] = off[i] + s.p->nx;
-    smem = std::max(smem, row_smem_bytes(s.p, kind == 1));
+    off[i + 1] = off[i] + row_ctas(s.p, kind);
+    smem = std::max(smem, row_kind_smem(s.p, kind));
   }
   Stage g{1, kind, 0, 0, (int)idx.size(), off.back(), smem, 0};
   g.arg_off = push(blocks.data(), blocks.size());

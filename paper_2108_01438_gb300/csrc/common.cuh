@@ -266,7 +266,11 @@ size_t lat_args_bytes(int precision);
 size_t row_args_bytes(int precision);
 size_t lat_smem_bytes(mbir_plan p);
 size_t row_smem_bytes(mbir_plan p, int adjoint_gather);
-bool plan_uses_gather(mbir_plan p);
+// Row (NUFFT) kernel of a plan: FP32 plans pair rows l and nx - l in one CTA
+enum RowKind { ROW_FWD = 0, ROW_GATHER = 1, ROW_ATOMIC = 2, ROW_FWD_PAIR = 3, ROW_GATHER_PAIR = 4 };
+int row_kind(mbir_plan p, bool adjoint);
+int row_ctas(mbir_plan p, int kind);           // CTAs of one scan
+size_t row_kind_smem(mbir_plan p, int kind);
 void fill_lat_args(mbir_plan p, const LatFill& f, void* dst);
 void fill_row_args(mbir_plan p, const void* in, void* out, void* dst);
 int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st);

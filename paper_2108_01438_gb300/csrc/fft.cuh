@@ -300,6 +300,15 @@ __device__ __forceinline__ PC ld_pc(const float4* s, int i) {
 }
 __device__ __forceinline__ void st_pc(float4* s, int i, PC v) { s[i] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
 
+// Swizzle of single split-pair sequences (a row pair in shared memory, 16-byte
+// elements): i ^ (((i >> 3) ^ (i >> 9)) & 7), a permutation within each aligned
+// group of 8.  For K = 4096 with radix 8 every pass and the digit-reversed staging
+// and read-out touch 8 distinct 16-byte bank groups per quarter warp (bank model
+// of the access patterns).  The buffer is padded to a multiple of 8 elements.
+__device__ __forceinline__ int swz8(int i) { return i ^ (((i >> 3) ^ (i >> 9)) & 7); }
+template <bool SW>
+__device__ __forceinline__ int psw(int i) { return SW ? swz8(i) : i; }
+
 struct TwP {
   const float4* lo;   // broadcast w_N^i, i < 2^shift
   const float4* hi;   // broadcast w_N^{i 2^shift}
@@ -383,7 +392,7 @@ __device__ __forceinline__ void apply_twiddles_p(PC (&v)[R], const TwP& tw, int 
 // so the sums and differences replace the inputs in place and each output pair
 // is twiddled (dif) and stored as soon as it is formed: no second array of R
 // values is held in registers.
-template <int R, bool INV, bool DIT>
+template <int R, bool INV, bool DIT, bool SW>
 __device__ __forceinline__ void ct_pass_p_odd(float4* s, int N, int batch, int bshift, int L, const TwP& tw,
                                               int tid, int nthr) {
   static_assert(R % 2 == 1, "odd radix");
@@ -405,7 +414,7 @@ __device__ __forceinline__ void ct_pass_p_odd(float4* s, int N, int batch, int b
     const int e1 = j * tstep;
     PC v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = ld_pc(s, i0 + r * di);
+    for (int r = 0; r < R; ++r) v[r] = ld_pc(s, psw<SW>(i0 + r * di));
     if (DIT && j != 0) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = pmulw(v[r], get(r * e1));
@@ -418,7 +427,7 @@ __device__ __forceinline__ void ct_pass_p_odd(float4* s, int N, int batch, int b
       v[R - r] = psub(a, c);
       x0 = padd(x0, v[r]);
     }
-    st_pc(s, i0, x0);
+    st_pc(s, psw<SW>(i0), x0);
 #pragma unroll
     for (int q = 1; q <= H; ++q) {
       PC A = v[0], B = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -436,14 +445,14 @@ __device__ __forceinline__ void ct_pass_p_odd(float4* s, int N, int batch, int b
         xq = pmulw(xq, get(q * e1));
         xr = pmulw(xr, get((R - q) * e1));
       }
-      st_pc(s, i0 + q * di, xq);
-      st_pc(s, i0 + (R - q) * di, xr);
+      st_pc(s, psw<SW>(i0 + q * di), xq);
+      st_pc(s, psw<SW>(i0 + (R - q) * di), xr);
     }
   }
   __syncthreads();
 }
 
-template <int R, bool INV, bool DIT>
+template <int R, bool INV, bool DIT, bool SW>
 __device__ __forceinline__ void ct_pass_p(float4* s, int N, int batch, int bshift, int L, const TwP& tw, int tid,
                                           int nthr) {
   const int M = L / R;
@@ -457,45 +466,46 @@ __device__ __forceinline__ void ct_pass_p(float4* s, int N, int batch, int bshif
     const int i0 = (blk * L + j) * batch + b, di = M * batch;
     PC v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = ld_pc(s, i0 + r * di);
+    for (int r = 0; r < R; ++r) v[r] = ld_pc(s, psw<SW>(i0 + r * di));
     if (DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
     dft_small_p<R, INV>(v, tw, N);
     if (!DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
 #pragma unroll
-    for (int r = 0; r < R; ++r) st_pc(s, i0 + r * di, v[r]);
+    for (int r = 0; r < R; ++r) st_pc(s, psw<SW>(i0 + r * di), v[r]);
   }
   __syncthreads();
 }
 
 // Radices up to 8 (a radix-16 butterfly of split pairs would hold 64 registers).
-template <bool INV, bool DIT>
+template <bool INV, bool DIT, bool SW>
 __device__ __forceinline__ void ct_dispatch_p(int R, float4* s, int N, int batch, int bshift, int L, const TwP& tw,
                                               int tid, int nthr) {
   switch (R) {
-    case 8: ct_pass_p<8, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 4: ct_pass_p<4, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 2: ct_pass_p<2, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 3: ct_pass_p_odd<3, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 5: ct_pass_p_odd<5, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
-    case 7: ct_pass_p_odd<7, INV, DIT>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 8: ct_pass_p<8, INV, DIT, SW>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 4: ct_pass_p<4, INV, DIT, SW>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 2: ct_pass_p<2, INV, DIT, SW>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 3: ct_pass_p_odd<3, INV, DIT, SW>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 5: ct_pass_p_odd<5, INV, DIT, SW>(s, N, batch, bshift, L, tw, tid, nthr); break;
+    case 7: ct_pass_p_odd<7, INV, DIT, SW>(s, N, batch, bshift, L, tw, tid, nthr); break;
     default: break;
   }
 }
 
-// `batch` interleaved pair-sequences, element i of pair-sequence b at s[i * batch + b].
-template <bool INV>
+// `batch` interleaved pair-sequences, element i of pair-sequence b at
+// s[psw<SW>(i * batch + b)] (SW only with batch = 1).
+template <bool INV, bool SW = false>
 __device__ void fft_p_dif(float4* s, int batch, const Radix& rad, const TwP& tw) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int bshift = log2_if_pow2(batch);
   int L = rad.n;
   for (int p = 0; p < rad.npass; ++p) {
     const int R = rad.r[p];
-    ct_dispatch_p<INV, false>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
+    ct_dispatch_p<INV, false, SW>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
     L /= R;
   }
 }
 
-template <bool INV>
+template <bool INV, bool SW = false>
 __device__ void fft_p_dit(float4* s, int batch, const Radix& rad, const TwP& tw) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int bshift = log2_if_pow2(batch);
@@ -503,7 +513,7 @@ __device__ void fft_p_dit(float4* s, int batch, const Radix& rad, const TwP& tw)
   for (int p = rad.npass - 1; p >= 0; --p) {
     const int R = rad.r[p];
     L *= R;
-    ct_dispatch_p<INV, true>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
+    ct_dispatch_p<INV, true, SW>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
   }
 }
 

@@ -840,6 +840,222 @@ row_adjoint_gather_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<
   }
 }
 
+// --------------------------------------------- paired row kernels (FP32)
+//
+// Rows l and nx - l of the lateral spectrum share |l~| and with it the resampling
+// table, the KB weights and the filter (the model sees the lateral frequency
+// only through q^2).  One CTA runs both rows: the table, the weights and the
+// gather's index arithmetic serve two rows, and the K-point transform runs on
+// split pairs {re_l, re_l', im_l, im_l'} with paired FP32 instructions.  CTA lp
+// (0 <= lp <= nx/2) takes rows lp and nx - lp; rows 0 and nx/2 are their own
+// mirror and run alone (lane b repeats lane a and is not stored).
+
+__device__ __forceinline__ int pair_row_b(int lp, int nx) {
+  const int lb = nx - lp;
+  return (lp == 0 || lb == lp) ? -1 : lb;
+}
+
+template <int J>
+__device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, const Radix& rad, int lp,
+                                                      const RowArgs<float>& a0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  const int K8 = (K + 7) & ~7;
+  float4* buf = reinterpret_cast<float4*>(smem_raw);   // [K8], swizzled
+  const int la = lp, lb = pair_row_b(lp, a.nx), lbr = lb < 0 ? la : lb;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const TwP tw = load_twiddles_p(buf + K8, reinterpret_cast<const float2*>(a.tw), rad);
+  const float2* Xa = reinterpret_cast<const float2*>(a.in) + (size_t)la * nz;
+  const float2* Xb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * nz;
+  const float* cdep = reinterpret_cast<const float*>(a.cdep);
+  const int* perm = a.perm;
+  pdl_wait_release();
+  // centred zero-padded rows, element i = (n - n0) mod K holding c_n X[l][n],
+  // placed digit-reversed for the decimation-in-time transform
+  constexpr int U = 4;
+  for (int i0 = tid; i0 < K; i0 += U * nthr) {
+    float4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      int n = i + n0;
+      if (n >= K) n -= K;
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < K && n < nz) {
+        const float c = cdep[n];
+        const float2 xa = Xa[n], xb = Xb[n];
+        v[u] = make_float4(xa.x * c, xb.x * c, xa.y * c, xb.y * c);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      if (i < K) buf[swz8(perm[i])] = v[u];
+    }
+  }
+  __syncthreads();
+  fft_p_dit<false, true>(buf, 1, rad, tw);
+  const TabF* tab = reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M;
+  float2* Sa = reinterpret_cast<float2*>(a.out) + (size_t)la * M;
+  float2* Sb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * M;
+  constexpr int UM = 2;
+  for (int m0 = tid; m0 < M; m0 += UM * nthr) {
+    TabF e[UM];
+#pragma unroll
+    for (int u = 0; u < UM; ++u) {
+      const int mm = m0 + u * nthr;
+      if (mm < M) e[u] = tab[mm];
+    }
+#pragma unroll
+    for (int u = 0; u < UM; ++u) {
+      const int mm = m0 + u * nthr;
+      if (mm >= M) continue;
+      float w[J];
+      kb_weights<float, J>(e[u].frac, a0, w);
+      const int pc = e[u].cell & 0xFFFF;
+      float2 ar = make_float2(0.f, 0.f), ai = ar;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        int idx = pc + j;
+        if (idx >= K) idx -= K;
+        const float4 t = buf[swz8(idx)];
+        const float2 ww = make_float2(w[j], w[j]);
+        ar = fma2(make_float2(t.x, t.y), ww, ar);
+        ai = fma2(make_float2(t.z, t.w), ww, ai);
+      }
+      const float2 f = make_float2(e[u].fre, e[u].fim);
+      Sa[mm] = cmul(make_float2(ar.x, ai.x), f);
+      if (lb >= 0) Sb[mm] = cmul(make_float2(ar.y, ai.y), f);
+    }
+  }
+}
+
+template <int J, bool BAT>
+__global__ void __launch_bounds__(kRowPairThreads, kRowPairMinBlocks)
+row_forward_pair_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
+  if constexpr (!BAT) {
+    row_forward_pair_body<J>(a0, a0.rad, (int)blockIdx.x, a0);
+  } else {
+    int blk;
+    const RowArgs<float>& A = *resolve_args(&a0, B, blk);
+    __shared__ Radix rad;
+    copy_radix(&rad, &A.rad);
+    __syncthreads();
+    row_forward_pair_body<J>(A, rad, blk, a0);
+  }
+}
+
+// The adjoint gather of row_adjoint_gather_body for a row pair: the pixels' KB
+// weights, unwrapped cells and run boundaries are built once, each cell sums its
+// run for both rows in the two lanes of split pairs.
+template <int J>
+__device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, const Radix& rad, int lp,
+                                                     const RowArgs<float>& a0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  const int K8 = (K + 7) & ~7;
+  float4* buf = reinterpret_cast<float4*>(smem_raw);         // [K8], swizzled
+  float4* tws = buf + K8;
+  float4* sv = tws + rad.tw_lo + rad.tw_hi;                  // [M] conj(f) R of both rows, split
+  float* sw = reinterpret_cast<float*>(sv + M);              // [M][J] weights
+  uint16_t* su = reinterpret_cast<uint16_t*>(sw + M * J);    // [M]
+  uint16_t* sfirst = su + M + (M & 1);                       // [span + 1]
+  const int la = lp, lb = pair_row_b(lp, a.nx), lbr = lb < 0 ? la : lb;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const TwP tw = load_twiddles_p(tws, reinterpret_cast<const float2*>(a.tw), rad);
+  const int4 meta = a.rowmeta[lp];
+  const int base = meta.x, span = meta.y, dir = meta.z;
+  const TabF* tab = reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M;
+  const float2* Ra = reinterpret_cast<const float2*>(a.in) + (size_t)la * M;
+  const float2* Rb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * M;
+  pdl_wait_release();
+  // stage both rows in increasing-u order
+  constexpr int UM = 2;
+  for (int m0 = tid; m0 < M; m0 += UM * nthr) {
+    TabF e[UM];
+    float2 ra[UM], rb[UM];
+#pragma unroll
+    for (int q = 0; q < UM; ++q) {
+      const int mm = m0 + q * nthr;
+      if (mm < M) {
+        e[q] = tab[mm];
+        ra[q] = Ra[mm];
+        rb[q] = Rb[mm];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < UM; ++q) {
+      const int mm = m0 + q * nthr;
+      if (mm >= M) continue;
+      const int sidx = dir > 0 ? mm : M - 1 - mm;
+      const float2 f = make_float2(e[q].fre, e[q].fim);
+      const float2 va = cmulc(ra[q], f), vb = cmulc(rb[q], f);
+      sv[sidx] = make_float4(va.x, vb.x, va.y, vb.y);
+      float w[J];
+      kb_weights<float, J>(e[q].frac, a0, w);
+#pragma unroll
+      for (int j = 0; j < J; ++j) sw[sidx * J + j] = w[j];
+      su[sidx] = (uint16_t)((unsigned)e[q].cell >> 16);
+    }
+  }
+  __syncthreads();
+  // first[c] = min{s : u_s >= c} for c in [0, span], as in the single-row kernel
+  for (int sidx = tid; sidx < M; sidx += nthr) {
+    const int lo = sidx == 0 ? 0 : int(su[sidx - 1]) + 1;
+    const int hi = su[sidx];
+    for (int c = lo; c <= hi; ++c) sfirst[c] = (uint16_t)sidx;
+    if (sidx == M - 1)
+      for (int c = hi + 1; c <= span; ++c) sfirst[c] = (uint16_t)M;
+  }
+  __syncthreads();
+  for (int i = tid; i < K; i += nthr) {
+    int c = i - base;
+    if (c < 0) c += K;
+    float2 ar = make_float2(0.f, 0.f), ai = ar;
+    if (c < span) {
+      const int slo = c - J + 1 <= 0 ? 0 : int(sfirst[c - J + 1]);
+      const int shi = int(sfirst[c + 1]) - 1;
+      for (int sidx = slo; sidx <= shi; ++sidx) {
+        const float w = sw[sidx * J + (c - int(su[sidx]))];
+        const float4 t = sv[sidx];
+        const float2 ww = make_float2(w, w);
+        ar = fma2(make_float2(t.x, t.y), ww, ar);
+        ai = fma2(make_float2(t.z, t.w), ww, ai);
+      }
+    }
+    buf[swz8(i)] = make_float4(ar.x, ar.y, ai.x, ai.y);
+  }
+  __syncthreads();
+  fft_p_dif<true, true>(buf, 1, rad, tw);
+  const float* cdep = reinterpret_cast<const float*>(a.cdep);
+  const int* perm = a.perm;
+  float2* Wa = reinterpret_cast<float2*>(a.out) + (size_t)la * nz;
+  float2* Wb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * nz;
+  for (int n = tid; n < nz; n += nthr) {
+    int i = n - n0;
+    if (i < 0) i += K;
+    const float4 t = buf[swz8(perm[i])];
+    const float cn = cdep[n];
+    Wa[n] = make_float2(t.x * cn, t.z * cn);
+    if (lb >= 0) Wb[n] = make_float2(t.y * cn, t.w * cn);
+  }
+}
+
+template <int J, bool BAT>
+__global__ void __launch_bounds__(kGatherPairThreads, 1)
+row_gather_pair_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
+  if constexpr (!BAT) {
+    row_gather_pair_body<J>(a0, a0.rad, (int)blockIdx.x, a0);
+  } else {
+    int blk;
+    const RowArgs<float>& A = *resolve_args(&a0, B, blk);
+    __shared__ Radix rad;
+    copy_radix(&rad, &A.rad);
+    __syncthreads();
+    row_gather_pair_body<J>(A, rad, blk, a0);
+  }
+}
+
 // ------------------------------------------------------------------ launch
 
 int lateral_grid(mbir_plan p, int cols) { return (cols + p->tile_c - 1) / p->tile_c; }
@@ -936,14 +1152,54 @@ size_t row_gather_smem(mbir_plan p) {
          sizeof(float) * p->J * (kKbDeg + 1) + sizeof(uint16_t) * (M + (M & 1) + p->K + 2);
 }
 
-bool plan_uses_gather(mbir_plan p);
+// paired FP32 row kernels: the row pair (16 bytes a cell, padded to a multiple of
+// 8 cells) and the broadcast twiddles; the gather adds its pixel staging
+size_t row_pair_smem(mbir_plan p) {
+  const size_t K8 = (size_t)((p->K + 7) & ~7);
+  return 16 * (K8 + p->rad_k.tw_lo + p->rad_k.tw_hi);
+}
+size_t row_gather_pair_smem(mbir_plan p) {
+  const size_t M = p->m;
+  return row_pair_smem(p) + 16 * M + sizeof(float) * M * p->J + sizeof(uint16_t) * (M + (M & 1) + p->K + 2);
+}
 
-// kind: 0 forward, 1 adjoint gather, 2 adjoint with atomics
+size_t row_smem_bytes(mbir_plan p, int adjoint_gather);
+
+int row_kind(mbir_plan p, bool adjoint) {
+  const bool pair = p->precision == MBIR_FP32;
+  if (!adjoint) return pair ? ROW_FWD_PAIR : ROW_FWD;
+  if (kAdjAtomic || !p->gather_ok) return ROW_ATOMIC;
+  if (pair && row_gather_pair_smem(p) <= (size_t)kMaxDynSmem) return ROW_GATHER_PAIR;
+  if (row_smem_bytes(p, 1) <= (size_t)kMaxDynSmem) return ROW_GATHER;
+  return ROW_ATOMIC;
+}
+
+int row_ctas(mbir_plan p, int kind) { return kind >= ROW_FWD_PAIR ? p->nlh : p->nx; }
+
+size_t row_kind_smem(mbir_plan p, int kind) {
+  switch (kind) {
+    case ROW_FWD_PAIR: return row_pair_smem(p);
+    case ROW_GATHER_PAIR: return row_gather_pair_smem(p);
+    case ROW_GATHER: return row_smem_bytes(p, 1);
+    default: return row_smem_bytes(p, 0);
+  }
+}
+
 template <class R, int J, bool BAT, bool COMP>
 static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid, size_t smem,
                          cudaStream_t st) {
-  if (kind == 0) launch(row_forward_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
-  else if (kind == 1)
+  if constexpr (sizeof(R) == 4 && !COMP) {
+    if (kind == ROW_FWD_PAIR) {
+      launch(row_forward_pair_kernel<J, BAT>, dim3(grid), dim3(kRowPairThreads), smem, st, a, B);
+      return;
+    }
+    if (kind == ROW_GATHER_PAIR) {
+      launch(row_gather_pair_kernel<J, BAT>, dim3(grid), dim3(kGatherPairThreads), smem, st, a, B);
+      return;
+    }
+  }
+  if (kind == ROW_FWD) launch(row_forward_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
+  else if (kind == ROW_GATHER)
     launch(row_adjoint_gather_kernel<R, J, BAT, COMP>, dim3(grid), dim3(kGatherThreads), smem, st, a, B);
   else launch(row_adjoint_kernel<R, J, BAT>, dim3(grid), dim3(kRowThreads), smem, st, a, B);
 }
@@ -969,13 +1225,11 @@ static void row_launch(int kind, int J, bool comp, const RowArgs<R>& a, const Ba
 template <class R>
 int launch_row(mbir_plan p, bool adjoint, const void* in, void* out, cudaStream_t st) {
   RowArgs<R> a = row_args<R>(p, in, out);
-  const bool gather = adjoint && plan_uses_gather(p);
-  const int kind = adjoint ? (gather ? 1 : 2) : 0;
-  const size_t smem = gather ? row_gather_smem<R>(p) : row_smem<R>(p);
+  const int kind = row_kind(p, adjoint);
   {
     ProfScope ps_(p, adjoint ? PC_ROW_ADJ : PC_ROW_FWD, st);
-    row_launch<R, false>(kind, p->J, p->precision == MBIR_FP32_COMPENSATED, a, no_batch<RowArgs<R>>(), p->nx,
-                         smem, st);
+    row_launch<R, false>(kind, p->J, p->precision == MBIR_FP32_COMPENSATED, a, no_batch<RowArgs<R>>(),
+                         row_ctas(p, kind), row_kind_smem(p, kind), st);
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -1141,6 +1395,20 @@ static int configure_t() {
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 4, true, true>), gat);
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6, true, true>), gat);
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, true, true>), gat);
+  if constexpr (sizeof(R) == 4) {
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, true>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, true>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, true>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true>), gat);
+  }
 #undef MBIR_SMEM_ATTR
   return MBIR_OK;
 }
@@ -1193,9 +1461,6 @@ size_t lat_smem_bytes(mbir_plan p) {
 size_t row_smem_bytes(mbir_plan p, int adjoint_gather) {
   if (p->precision == MBIR_FP64) return adjoint_gather ? row_gather_smem<double>(p) : row_smem<double>(p);
   return adjoint_gather ? row_gather_smem<float>(p) : row_smem<float>(p);
-}
-bool plan_uses_gather(mbir_plan p) {
-  return !kAdjAtomic && p->gather_ok && row_smem_bytes(p, 1) <= (size_t)kMaxDynSmem;
 }
 
 template <class R>

@@ -44,6 +44,12 @@ constexpr int kLatMinBlocks = MBIR_LAT_MINB;
 // at K = 4096), so two CTAs fit an SM; wider CTAs keep more warps resident
 constexpr int kGatherThreads = MBIR_GATHER_THREADS;
 constexpr int kGatherMinBlocks = MBIR_GATHER_MINB;
+// paired FP32 row kernels (two rows per CTA): the forward keeps a 16-byte-per-cell
+// row pair (66 KB at K = 4096), three CTAs an SM; the gather's staging and row
+// pair take about 160 KB, one 1024-thread CTA an SM
+constexpr int kRowPairThreads = 256;
+constexpr int kRowPairMinBlocks = 3;
+constexpr int kGatherPairThreads = 1024;
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
 constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics

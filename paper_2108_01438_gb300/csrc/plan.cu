@@ -74,8 +74,8 @@ static double kb_hat(double nu, int J, double alpha) {
   return J * v / bessel_i0(alpha);
 }
 
-// max_radix 16 or 8 (the paired FP32 lateral transform keeps a butterfly's
-// split pairs in registers, which radix 16 would overflow)
+// max_radix 16 or 8 (the paired FP32 transforms keep a butterfly's split pairs
+// in registers, which radix 16 would overflow)
 static bool factor_radix(int n, Radix* r, int max_radix = 16) {
   memset(r, 0, sizeof(*r));
   r->n = n;
@@ -587,7 +587,7 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   }
   p->alpha = g->kb_alpha > 0 ? g->kb_alpha : 2.34 * g->kb_width;
   factor_radix(p->nx, &p->rad_x, 8);
-  factor_radix(p->K, &p->rad_k);
+  factor_radix(p->K, &p->rad_k, 8);
   // lateral tile: keep nx * tile_c <= kLatElems elements, at most 16 columns
   int tc = kLatElems / p->nx;
   if (tc > 16) tc = 16;
