@@ -45,10 +45,17 @@ constexpr int kLatMinBlocks = MBIR_LAT_MINB;
 constexpr int kGatherThreads = MBIR_GATHER_THREADS;
 constexpr int kGatherMinBlocks = MBIR_GATHER_MINB;
 // paired FP32 row kernels (two rows per CTA): the forward keeps a 16-byte-per-cell
-// row pair (66 KB at K = 4096), three CTAs an SM; the gather's staging and row
-// pair take about 160 KB, one 1024-thread CTA an SM
-constexpr int kRowPairThreads = 256;
-constexpr int kRowPairMinBlocks = 3;
+// row pair (66 KB at K = 4096) in 512-thread CTAs, two an SM (a sweep of 256 x 3,
+// 256 x 2 and 512 x 2 favoured the last); the gather's staging and row pair take
+// about 160 KB, one 1024-thread CTA an SM
+#ifndef MBIR_ROWPAIR_THREADS
+#define MBIR_ROWPAIR_THREADS 512
+#endif
+#ifndef MBIR_ROWPAIR_MINB
+#define MBIR_ROWPAIR_MINB 2
+#endif
+constexpr int kRowPairThreads = MBIR_ROWPAIR_THREADS;
+constexpr int kRowPairMinBlocks = MBIR_ROWPAIR_MINB;
 constexpr int kGatherPairThreads = 1024;
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
