@@ -94,6 +94,32 @@ __device__ __forceinline__ double block_sum_w(double v) {
   return t;
 }
 
+// acc += w x for a complex x and a real tap given broadcast ({w, w}): one paired
+// FP32 instruction (FFMA2) in single precision.
+template <class V>
+__device__ __forceinline__ void tap(V& acc, V wb, V x) {
+  if constexpr (sizeof(V) == 8) {
+    acc = __ffma2_rn(x, wb, acc);
+  } else {
+    acc.x += wb.x * x.x;
+    acc.y += wb.y * x.y;
+  }
+}
+
+// The 8 low-pass taps h and the high-pass taps g_t = (-1)^t h_{7-t}, broadcast.
+template <class R>
+__device__ __forceinline__ void load_taps(const R* hsrc, cplx_t<R>* hb, cplx_t<R>* gb) {
+  const int t = threadIdx.x;
+  if (t < 8) {
+    const R hv = hsrc[t], gv = ((t & 1) ? R(-1) : R(1)) * hsrc[7 - t];
+    hb[t] = cmk<cplx_t<R>>(hv, hv);
+    gb[t] = cmk<cplx_t<R>>(gv, gv);
+  }
+}
+
+// Every thread computes two neighbouring outputs of a filter stage: they share
+// 6 of their 8 inputs (analysis) or all 4 coefficient positions (synthesis),
+// which are loaded from shared memory once.
 template <class R, bool SMALL>
 __global__ void __launch_bounds__(kWavThreads)
 dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B) {
@@ -104,20 +130,18 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const WArgs<R> a = resolve_wargs(arg0, B, blk);
   const int bx = blk % a.gx, by = blk / a.gx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tin = reinterpret_cast<V*>(smem_raw);              // [kRows][kCols]
+  V* tin = reinterpret_cast<V*>(smem_raw);        // [kRows][kCols]
   V* tL = tin + kRows * kCols;                    // [kRows][kTB]
   V* tH = tL + kRows * kTB;
-  __shared__ R h[8], g[8];
+  __shared__ V hb[8], gb[8];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  if (tid < 8) {
-    h[tid] = a.h[tid];
-    g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
-  }
+  load_taps<R>(a.h, hb, gb);
   const int P = a.P, N = a.N;
   const int a0 = by * kTA, b0 = bx * kTB;
   const V* in = reinterpret_cast<const V*>(a.in);
   pdl_wait_release();
-  // stage the input tile with every load of a thread in flight at once
+  // stage the input tile with every load of a thread in flight at once; the
+  // periodic wrap is a conditional subtraction (2 a0 + i < 2 P)
   constexpr int kFwdPer = (kRows * kCols + kWavThreads - 1) / kWavThreads;
   {
     V vv[kFwdPer];
@@ -126,7 +150,9 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
       const int e = tid + q * nthr;
       if (e < kRows * kCols) {
         const int i = e / kCols, j = e - i * kCols;
-        const int row = (2 * a0 + i) % P, col = (2 * b0 + j) % N;
+        int row = 2 * a0 + i, col = 2 * b0 + j;
+        if (row >= P) row -= P;
+        if (col >= N) col -= N;
         vv[q] = in[(size_t)row * a.istride + col];
       }
     }
@@ -137,48 +163,69 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
     }
   }
   __syncthreads();
-  for (int e = tid; e < kRows * kTB; e += nthr) {
-    const int i = e / kTB, b = e - i * kTB;
-    const V* src = tin + i * kCols + 2 * b;
-    V lo = cmk<V>(R(0), R(0)), hi = lo;
+  // along depth: outputs b, b + 1 of row i from inputs 2b .. 2b + 9
+  for (int e = tid; e < kRows * (kTB / 2); e += nthr) {
+    const int i = e / (kTB / 2), bp = e - i * (kTB / 2);
+    const V* src = tin + i * kCols + 4 * bp;
+    const V z = cmk<V>(R(0), R(0));
+    V lo0 = z, hi0 = z, lo1 = z, hi1 = z;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < 10; ++t) {
       const V x = src[t];
-      lo.x += h[t] * x.x; lo.y += h[t] * x.y;
-      hi.x += g[t] * x.x; hi.y += g[t] * x.y;
+      if (t < 8) {
+        tap(lo0, hb[t], x);
+        tap(hi0, gb[t], x);
+      }
+      if (t >= 2) {
+        tap(lo1, hb[t - 2], x);
+        tap(hi1, gb[t - 2], x);
+      }
     }
-    tL[e] = lo;
-    tH[e] = hi;
+    tL[i * kTB + 2 * bp] = lo0;
+    tL[i * kTB + 2 * bp + 1] = lo1;
+    tH[i * kTB + 2 * bp] = hi0;
+    tH[i * kTB + 2 * bp + 1] = hi1;
   }
   __syncthreads();
   const int Ph = P / 2, Nh = N / 2;
   V* coef = reinterpret_cast<V*>(a.coef);
   V* llo = reinterpret_cast<V*>(a.out);
   double acc = 0.0;
-  for (int e = tid; e < kTA * kTB; e += nthr) {
-    const int ai = e / kTB, b = e - ai * kTB;
-    const int A = a0 + ai, B = b0 + b;
-    if (A >= Ph || B >= Nh) continue;
-    V ll = cmk<V>(R(0), R(0)), hl = ll, lh = ll, hh = ll;
+  // along the A-scans: outputs ai, ai + 1 of column b from rows 2 ai .. 2 ai + 9
+  for (int e = tid; e < (kTA / 2) * kTB; e += nthr) {
+    const int ap = e / kTB, b = e - ap * kTB;
+    const V z = cmk<V>(R(0), R(0));
+    V ll[2] = {z, z}, hl[2] = {z, z}, lh[2] = {z, z}, hh[2] = {z, z};
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const V xl = tL[(2 * ai + t) * kTB + b];
-      const V xh = tH[(2 * ai + t) * kTB + b];
-      ll.x += h[t] * xl.x; ll.y += h[t] * xl.y;
-      hl.x += g[t] * xl.x; hl.y += g[t] * xl.y;
-      lh.x += h[t] * xh.x; lh.y += h[t] * xh.y;
-      hh.x += g[t] * xh.x; hh.y += g[t] * xh.y;
+    for (int t = 0; t < 10; ++t) {
+      const V xl = tL[(4 * ap + t) * kTB + b];
+      const V xh = tH[(4 * ap + t) * kTB + b];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int tt = t - 2 * k;
+        if (tt < 0 || tt >= 8) continue;
+        tap(ll[k], hb[tt], xl);
+        tap(hl[k], gb[tt], xl);
+        tap(lh[k], hb[tt], xh);
+        tap(hh[k], gb[tt], xh);
+      }
     }
-    if (a.thresh >= 1) {
-      lh = soft_c<R>(lh, a.tau, acc);
-      hl = soft_c<R>(hl, a.tau, acc);
-      hh = soft_c<R>(hh, a.tau, acc);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int A = a0 + 2 * ap + k, Bc = b0 + b;
+      if (A >= Ph || Bc >= Nh) continue;
+      V vll = ll[k], vhl = hl[k], vlh = lh[k], vhh = hh[k];
+      if (a.thresh >= 1) {
+        vlh = soft_c<R>(vlh, a.tau, acc);
+        vhl = soft_c<R>(vhl, a.tau, acc);
+        vhh = soft_c<R>(vhh, a.tau, acc);
+      }
+      if (a.thresh == 2) vll = soft_c<R>(vll, a.tau, acc);
+      llo[(size_t)A * a.ostride + Bc] = vll;
+      coef[(size_t)A * a.cstride + Nh + Bc] = vlh;
+      coef[(size_t)(Ph + A) * a.cstride + Bc] = vhl;
+      coef[(size_t)(Ph + A) * a.cstride + Nh + Bc] = vhh;
     }
-    if (a.thresh == 2) ll = soft_c<R>(ll, a.tau, acc);
-    llo[(size_t)A * a.ostride + B] = ll;
-    coef[(size_t)A * a.cstride + Nh + B] = lh;
-    coef[(size_t)(Ph + A) * a.cstride + B] = hl;
-    coef[(size_t)(Ph + A) * a.cstride + Nh + B] = hh;
   }
   if (a.partial) {
     const double t = block_sum_w(acc);
@@ -196,18 +243,15 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const WArgs<R> a = resolve_wargs(arg0, B, blk);
   const int bx = blk % a.gx, by = blk / a.gx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* cLL = reinterpret_cast<V*>(smem_raw);              // [kRows][kCols] each
+  V* cLL = reinterpret_cast<V*>(smem_raw);        // [kRows][kCols] each
   V* cLH = cLL + kRows * kCols;
   V* cHL = cLH + kRows * kCols;
   V* cHH = cHL + kRows * kCols;
   V* tlo = cHH + kRows * kCols;                   // [kTR][kCols]
   V* thi = tlo + kTR * kCols;
-  __shared__ R h[8], g[8];
+  __shared__ V hb[8], gb[8];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  if (tid < 8) {
-    h[tid] = a.h[tid];
-    g[tid] = ((tid & 1) ? R(-1) : R(1)) * a.h[7 - tid];
-  }
+  load_taps<R>(a.h, hb, gb);
   const int P = a.P, N = a.N, Ph = P / 2, Nh = N / 2;
   const int r0 = by * kTR, c0 = bx * kTC;
   const V* ll = reinterpret_cast<const V*>(a.in);
@@ -221,12 +265,16 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
       const int e = tid + q * nthr;
       if (e < kRows * kCols) {
         const int ia = e / kCols, ib = e - ia * kCols;
-        const int A = ((r0 / 2 - 3 + ia) % Ph + Ph) % Ph;
-        const int B = ((c0 / 2 - 3 + ib) % Nh + Nh) % Nh;
-        v0[q] = ll[(size_t)A * a.istride + B];
-        v1[q] = coef[(size_t)A * a.cstride + Nh + B];
-        v2[q] = coef[(size_t)(Ph + A) * a.cstride + B];
-        v3[q] = coef[(size_t)(Ph + A) * a.cstride + Nh + B];
+        // r0/2 - 3 + ia lies in [-3, Ph + kRows): one conditional wrap each way
+        int A = r0 / 2 - 3 + ia, Bc = c0 / 2 - 3 + ib;
+        if (A < 0) A += Ph;
+        if (A >= Ph) A -= Ph;
+        if (Bc < 0) Bc += Nh;
+        if (Bc >= Nh) Bc -= Nh;
+        v0[q] = ll[(size_t)A * a.istride + Bc];
+        v1[q] = coef[(size_t)A * a.cstride + Nh + Bc];
+        v2[q] = coef[(size_t)(Ph + A) * a.cstride + Bc];
+        v3[q] = coef[(size_t)(Ph + A) * a.cstride + Nh + Bc];
       }
     }
 #pragma unroll
@@ -241,36 +289,51 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
     }
   }
   __syncthreads();
-  for (int e = tid; e < kTR * kCols; e += nthr) {
-    const int r = e / kCols, ib = e - r * kCols;
-    V lo = cmk<V>(R(0), R(0)), hi = lo;
+  // along the A-scans: output rows r = 2 rp (taps 0, 2, 4, 6) and r + 1 (taps
+  // 1, 3, 5, 7) read the same coefficient rows rp + 3 - q, q = 0 .. 3
+  for (int e = tid; e < (kTR / 2) * kCols; e += nthr) {
+    const int rp = e / kCols, ib = e - rp * kCols;
+    const V z = cmk<V>(R(0), R(0));
+    V lo0 = z, hi0 = z, lo1 = z, hi1 = z;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int t = (r & 1) + 2 * q;
-      const int ia = (r - t) / 2 + 3;
+      const int ia = rp + 3 - q;
       const V vll = cLL[ia * kCols + ib], vhl = cHL[ia * kCols + ib];
       const V vlh = cLH[ia * kCols + ib], vhh = cHH[ia * kCols + ib];
-      lo.x += h[t] * vll.x + g[t] * vhl.x; lo.y += h[t] * vll.y + g[t] * vhl.y;
-      hi.x += h[t] * vlh.x + g[t] * vhh.x; hi.y += h[t] * vlh.y + g[t] * vhh.y;
+      tap(lo0, hb[2 * q], vll);
+      tap(lo0, gb[2 * q], vhl);
+      tap(hi0, hb[2 * q], vlh);
+      tap(hi0, gb[2 * q], vhh);
+      tap(lo1, hb[2 * q + 1], vll);
+      tap(lo1, gb[2 * q + 1], vhl);
+      tap(hi1, hb[2 * q + 1], vlh);
+      tap(hi1, gb[2 * q + 1], vhh);
     }
-    tlo[e] = lo;
-    thi[e] = hi;
+    tlo[(2 * rp) * kCols + ib] = lo0;
+    thi[(2 * rp) * kCols + ib] = hi0;
+    tlo[(2 * rp + 1) * kCols + ib] = lo1;
+    thi[(2 * rp + 1) * kCols + ib] = hi1;
   }
   __syncthreads();
   V* out = reinterpret_cast<V*>(a.out);
-  for (int e = tid; e < kTR * kTC; e += nthr) {
-    const int r = e / kTC, c = e - r * kTC;
-    if (r0 + r >= P || c0 + c >= N) continue;
-    V x = cmk<V>(R(0), R(0));
+  // along depth: output columns c = 2 cp and c + 1 share the coefficient columns
+  for (int e = tid; e < kTR * (kTC / 2); e += nthr) {
+    const int r = e / (kTC / 2), cp = e - r * (kTC / 2);
+    if (r0 + r >= P) continue;
+    const V z = cmk<V>(R(0), R(0));
+    V x0 = z, x1 = z;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int t = (c & 1) + 2 * q;
-      const int ib = (c - t) / 2 + 3;
+      const int ib = cp + 3 - q;
       const V lo = tlo[r * kCols + ib], hi = thi[r * kCols + ib];
-      x.x += h[t] * lo.x + g[t] * hi.x;
-      x.y += h[t] * lo.y + g[t] * hi.y;
+      tap(x0, hb[2 * q], lo);
+      tap(x0, gb[2 * q], hi);
+      tap(x1, hb[2 * q + 1], lo);
+      tap(x1, gb[2 * q + 1], hi);
     }
-    out[(size_t)(r0 + r) * a.ostride + c0 + c] = x;
+    const int c = c0 + 2 * cp;
+    if (c < N) out[(size_t)(r0 + r) * a.ostride + c] = x0;
+    if (c + 1 < N) out[(size_t)(r0 + r) * a.ostride + c + 1] = x1;
   }
 }
 
