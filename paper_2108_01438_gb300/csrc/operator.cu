@@ -347,7 +347,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   const int c = blk * TC + b;
   const bool ok0 = c < C, ok1 = c + 1 < C;
   const bool v2 = ok1 && (C & 1) == 0 && lat_pairs_aligned<R, MODE>(a);
-  constexpr int U = 4;
+  constexpr int U = kLatUnroll;
   const V zero = cmk<V>(R(0), R(0));
   pdl_wait_release();
   R fscale = R(1);
@@ -427,15 +427,16 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
     }
   } else {
     lat_fft<R, INV, false>(s, TC, rad, tw);
-    for (int p = p0; p < nx; p += U * pstep) {
-      EpOps<R> oa[U], ob[U];
+    constexpr int UE = 4;
+    for (int p = p0; p < nx; p += UE * pstep) {
+      EpOps<R> oa[UE], ob[UE];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
+      for (int u = 0; u < UE; ++u) {
         const int pp = p + u * pstep;
         if (pp < nx) lat_prefetch2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, oa[u], ob[u]);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
+      for (int u = 0; u < UE; ++u) {
         const int pp = p + u * pstep;
         if (pp >= nx) continue;
         V xa, xb;

@@ -47,7 +47,9 @@ constexpr int kGatherMinBlocks = MBIR_GATHER_MINB;
 // paired FP32 row kernels (two rows per CTA): the forward keeps a 16-byte-per-cell
 // row pair (66 KB at K = 4096) in 512-thread CTAs, two an SM (a sweep of 256 x 3,
 // 256 x 2 and 512 x 2 favoured the last); the gather's staging and row pair take
-// about 160 KB, one 1024-thread CTA an SM
+// about 160 KB, one CTA an SM, of 512 threads: a radix-8 pass of a 4096-point row
+// has 512 butterflies, and with 1024 threads half of them waited at every pass
+// barrier (51.99 vs 53.53 us at 1024 x 2048)
 #ifndef MBIR_ROWPAIR_THREADS
 #define MBIR_ROWPAIR_THREADS 512
 #endif
@@ -56,7 +58,14 @@ constexpr int kGatherMinBlocks = MBIR_GATHER_MINB;
 #endif
 constexpr int kRowPairThreads = MBIR_ROWPAIR_THREADS;
 constexpr int kRowPairMinBlocks = MBIR_ROWPAIR_MINB;
-constexpr int kGatherPairThreads = 1024;
+#ifndef MBIR_GATHERPAIR_THREADS
+#define MBIR_GATHERPAIR_THREADS 512
+#endif
+#ifndef MBIR_LAT_UNROLL
+#define MBIR_LAT_UNROLL 4
+#endif
+constexpr int kGatherPairThreads = MBIR_GATHERPAIR_THREADS;
+constexpr int kLatUnroll = MBIR_LAT_UNROLL;   // rows of loads in flight per thread when staging a lateral tile
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
 constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics
