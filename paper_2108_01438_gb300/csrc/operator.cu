@@ -251,18 +251,18 @@ __device__ __forceinline__ void lat_prefetch2(const A& a, size_t off, bool v2, b
 // Measurement-side FISTA epilogue of one element (Eq. alg): pz = s Re{S}/nx,
 // r = (1 + mu) pz - mu pz_prev - s y; accumulates (pz - s y)^2.
 template <class R, class A>
-__device__ __forceinline__ R solve_meas(const A& a, R sre, const EpOps<R>& o, R& pz, double& part) {
+__device__ __forceinline__ R solve_meas(const A& a, R sre, const EpOps<R>& o, R& pz, R& part) {
   pz = o.meas ? sre * a.scale : R(0);
   const R yv = o.meas ? o.y : R(0);
   const R d = pz - yv;
-  part += double(d) * double(d);
+  part += d * d;
   return (R(1) + a.mu) * pz - a.mu * o.prev - yv;
 }
 
 // Image-side epilogue of one element: x^k - delta g, then the l1 prox (ADJ_L1) or
 // the pre-prox image v (ADJ_V).
 template <class R, int MODE, class A>
-__device__ __forceinline__ cplx_t<R> solve_img(const A& a, cplx_t<R> g, const EpOps<R>& o, double& part) {
+__device__ __forceinline__ cplx_t<R> solve_img(const A& a, cplx_t<R> g, const EpOps<R>& o, R& part) {
   using V = cplx_t<R>;
   V xv;
   xv.x = o.z1.x + a.mu * (o.z1.x - o.z2.x) - a.delta * g.x;
@@ -272,7 +272,7 @@ __device__ __forceinline__ cplx_t<R> solve_img(const A& a, cplx_t<R> g, const Ep
     const R sh = mag > a.tau ? R(1) - a.tau / mag : R(0);
     xv.x *= sh;
     xv.y *= sh;
-    part += mag > a.tau ? double(mag - a.tau) : 0.0;
+    part += mag > a.tau ? mag - a.tau : R(0);
   }
   return xv;
 }
@@ -280,15 +280,15 @@ __device__ __forceinline__ cplx_t<R> solve_img(const A& a, cplx_t<R> g, const Ep
 // Store the pair of transform outputs (va, vb) at (p, c), (p, c + 1).
 template <class R, int MODE, class A>
 __device__ __forceinline__ void lat_store2(const A& a, size_t off, bool v2, bool ok0, bool ok1, cplx_t<R> va,
-                                           cplx_t<R> vb, const EpOps<R>& o0, const EpOps<R>& o1, double& part,
-                                           double& part2) {
+                                           cplx_t<R> vb, const EpOps<R>& o0, const EpOps<R>& o1, R& part,
+                                           R& part2) {
   using V = cplx_t<R>;
   if constexpr (MODE == LAT_C2R_INV_MASK) {
     st2(reinterpret_cast<R*>(a.out), off, v2, ok0, ok1, o0.meas ? va.x * a.scale : R(0),
         o1.meas ? vb.x * a.scale : R(0));
   } else if constexpr (MODE == LAT_SOLVE_FWD) {
     R pa, pb;
-    double pa_part = 0.0, pb_part = 0.0;
+    R pa_part = R(0), pb_part = R(0);
     const R ra = solve_meas<R>(a, va.x, o0, pa, pa_part);
     const R rb = solve_meas<R>(a, vb.x, o1, pb, pb_part);
     if (ok0) part += pa_part;
@@ -296,7 +296,7 @@ __device__ __forceinline__ void lat_store2(const A& a, size_t off, bool v2, bool
     st2(a.pz, off, v2, ok0, ok1, pa, pb);
     st2(a.r, off, v2, ok0, ok1, ra, rb);
   } else if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V) {
-    double qa = 0.0, qb = 0.0;
+    R qa = R(0), qb = R(0);
     const V xa = solve_img<R, MODE>(a, va, o0, qa);
     const V xb = solve_img<R, MODE>(a, vb, o1, qb);
     if (ok0) part += qa;
@@ -305,12 +305,12 @@ __device__ __forceinline__ void lat_store2(const A& a, size_t off, bool v2, bool
   } else if constexpr (MODE == LAT_POWER_ADJ) {
     // w = Phi^H Phi v, with <v, w> and ||w||^2 partial sums
     if (ok0) {
-      part += double(o0.z1.x) * double(va.x) + double(o0.z1.y) * double(va.y);
-      part2 += double(va.x) * double(va.x) + double(va.y) * double(va.y);
+      part += o0.z1.x * va.x + o0.z1.y * va.y;
+      part2 += va.x * va.x + va.y * va.y;
     }
     if (ok1) {
-      part += double(o1.z1.x) * double(vb.x) + double(o1.z1.y) * double(vb.y);
-      part2 += double(vb.x) * double(vb.x) + double(vb.y) * double(vb.y);
+      part += o1.z1.x * vb.x + o1.z1.y * vb.y;
+      part2 += vb.x * vb.x + vb.y * vb.y;
     }
     st2(reinterpret_cast<V*>(a.out), off, v2, ok0, ok1, va, vb);
   } else {
@@ -381,7 +381,10 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   __syncthreads();
   constexpr bool kMid = lat_is_mid<MODE>();
   constexpr bool INV = !(MODE == LAT_C2C_FWD || MODE == LAT_R2C_MASK || MODE == LAT_POWER_FWD);
-  double part = 0.0, part2 = 0.0;
+  // per-thread partial sums in the working precision (a thread adds a few dozen
+  // terms; FP64 arithmetic is a small fraction of FP32 throughput on this GPU),
+  // the block and grid reductions in FP64
+  R part = R(0), part2 = R(0);
   if constexpr (kMid) {
     // inverse as a forward dif of conj S, the epilogue in place on the
     // digit-reversed tile, then the forward dit
@@ -405,7 +408,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
         R ra, rb;
         if constexpr (MODE == LAT_SOLVE_MID) {
           R pa, pb;
-          double qa = 0.0, qb = 0.0;
+          R qa = R(0), qb = R(0);
           ra = solve_meas<R>(a, xa.x, oa[u], pa, qa);
           rb = solve_meas<R>(a, xb.x, ob[u], pb, qb);
           if (ok0) part += qa;
@@ -446,12 +449,12 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
     }
   }
   if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_MID || MODE == LAT_SOLVE_ADJ_L1) {
-    const double t = block_sum(part);
+    const double t = block_sum(double(part));
     if (tid == 0) partial[blk] = t;
   } else if constexpr (MODE == LAT_POWER_ADJ) {
-    const double t = block_sum(part);
+    const double t = block_sum(double(part));
     __syncthreads();
-    const double t2 = block_sum(part2);
+    const double t2 = block_sum(double(part2));
     if (tid == 0) {
       partial[2 * blk] = t;
       partial[2 * blk + 1] = t2;

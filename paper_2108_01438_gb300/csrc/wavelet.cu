@@ -70,10 +70,10 @@ __device__ __forceinline__ Args resolve_wargs(const Args& a0, const BatchRef<Arg
 }
 
 template <class R>
-__device__ __forceinline__ cplx_t<R> soft_c(cplx_t<R> c, R tau, double& acc) {
+__device__ __forceinline__ cplx_t<R> soft_c(cplx_t<R> c, R tau, R& acc) {
   const R mag = sqrt(c.x * c.x + c.y * c.y);
   const R s = mag > tau ? R(1) - tau / mag : R(0);
-  if (mag > tau) acc += double(mag - tau);
+  if (mag > tau) acc += mag - tau;
   return cmk<cplx_t<R>>(c.x * s, c.y * s);
 }
 
@@ -190,7 +190,7 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const int Ph = P / 2, Nh = N / 2;
   V* coef = reinterpret_cast<V*>(a.coef);
   V* llo = reinterpret_cast<V*>(a.out);
-  double acc = 0.0;
+  R acc = R(0);   // a thread's few terms in the working precision; FP64 across the block
   // along the A-scans: outputs ai, ai + 1 of column b from rows 2 ai .. 2 ai + 9
   for (int e = tid; e < (kTA / 2) * kTB; e += nthr) {
     const int ap = e / kTB, b = e - ap * kTB;
@@ -228,7 +228,7 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
     }
   }
   if (a.partial) {
-    const double t = block_sum_w(acc);
+    const double t = block_sum_w(double(acc));
     if (tid == 0) a.partial[blk] = t;
   }
 }
@@ -340,11 +340,11 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
 template <class R>
 __global__ void soft_kernel(const cplx_t<R>* v, cplx_t<R>* z, size_t n, R tau, double* partial) {
   pdl_wait_release();
-  double acc = 0.0;
+  R acc = R(0);   // a thread's few terms in the working precision; FP64 across the block
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     z[i] = soft_c<R>(v[i], tau, acc);
   if (partial) {
-    const double t = block_sum_w(acc);
+    const double t = block_sum_w(double(acc));
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
   }
 }
