@@ -20,21 +20,23 @@
 
 namespace mbir {
 
-constexpr int kWavThreads = 256;
+// threads per CTA: 256 for the finest level, 128 for the coarse levels' tiles
+template <bool SMALL>
+constexpr int wav_threads() { return SMALL ? 128 : 256; }
 
 // Tiles.  Analysis computes a TA x TB block of every band's coefficients from a
 // (2 TA + 6) x (2 TB + 6) input block; synthesis a TR x TC block of output pixels
 // from (TR/2 + 3) x (TC/2 + 3) coefficients per band.  The coarse levels (level >=
-// 1, a quarter and a sixteenth of the image) use quarter-size tiles so that their
-// grids still cover the SMs.
+// 1, a quarter and a sixteenth of the image) use half-width tiles in half-size
+// CTAs so that their grids still cover the SMs and every thread has work.
 template <bool SMALL>
 struct FwdTile {
-  static constexpr int TA = SMALL ? 8 : 16, TB = SMALL ? 16 : 32;
+  static constexpr int TA = 16, TB = SMALL ? 16 : 32;
   static constexpr int Rows = 2 * TA + 6, Cols = 2 * TB + 6;
 };
 template <bool SMALL>
 struct InvTile {
-  static constexpr int TR = SMALL ? 16 : 32, TC = SMALL ? 32 : 64;
+  static constexpr int TR = 32, TC = SMALL ? 32 : 64;
   static constexpr int Rows = TR / 2 + 3, Cols = TC / 2 + 3;
 };
 constexpr bool dwt_small(int level) { return level > 0; }
@@ -121,7 +123,7 @@ __device__ __forceinline__ void load_taps(const R* hsrc, cplx_t<R>* hb, cplx_t<R
 // 6 of their 8 inputs (analysis) or all 4 coefficient positions (synthesis),
 // which are loaded from shared memory once.
 template <class R, bool SMALL>
-__global__ void __launch_bounds__(kWavThreads)
+__global__ void __launch_bounds__(wav_threads<SMALL>())
 dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B) {
   using V = cplx_t<R>;
   constexpr int kTA = FwdTile<SMALL>::TA, kTB = FwdTile<SMALL>::TB;
@@ -142,7 +144,7 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   pdl_wait_release();
   // stage the input tile with every load of a thread in flight at once; the
   // periodic wrap is a conditional subtraction (2 a0 + i < 2 P)
-  constexpr int kFwdPer = (kRows * kCols + kWavThreads - 1) / kWavThreads;
+  constexpr int kFwdPer = (kRows * kCols + wav_threads<SMALL>() - 1) / wav_threads<SMALL>();
   {
     V vv[kFwdPer];
 #pragma unroll
@@ -234,7 +236,7 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
 }
 
 template <class R, bool SMALL>
-__global__ void __launch_bounds__(kWavThreads)
+__global__ void __launch_bounds__(wav_threads<SMALL>())
 dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B) {
   using V = cplx_t<R>;
   constexpr int kTR = InvTile<SMALL>::TR, kTC = InvTile<SMALL>::TC;
@@ -257,7 +259,7 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const V* ll = reinterpret_cast<const V*>(a.in);
   const V* coef = reinterpret_cast<const V*>(a.coef);
   pdl_wait_release();
-  constexpr int kInvPer = (kRows * kCols + kWavThreads - 1) / kWavThreads;
+  constexpr int kInvPer = (kRows * kCols + wav_threads<SMALL>() - 1) / wav_threads<SMALL>();
   {
     V v0[kInvPer], v1[kInvPer], v2[kInvPer], v3[kInvPer];
 #pragma unroll
@@ -429,7 +431,8 @@ static int analysis_t(mbir_plan p, const void* in, void* coef, bool thresh, R ta
     a.gx = gx;
     {
       ProfScope ps_(p, PC_DWT_FWD, st);
-      launch(dwt_small(lev) ? dwt_fwd_kernel<R, true> : dwt_fwd_kernel<R, false>, dim3(gx * gy), dim3(kWavThreads),
+      launch(dwt_small(lev) ? dwt_fwd_kernel<R, true> : dwt_fwd_kernel<R, false>, dim3(gx * gy),
+             dim3(dwt_small(lev) ? wav_threads<true>() : wav_threads<false>()),
              fwd_smem(sizeof(cplx_t<R>), lev), st, a, no_batch<WArgs<R>>());
     }
     MBIR_LAUNCH_CHECK();
@@ -467,7 +470,8 @@ static int synthesis_t(mbir_plan p, const void* coef, void* out, cudaStream_t st
     a.gx = gx;
     {
       ProfScope ps_(p, PC_DWT_INV, st);
-      launch(dwt_small(lev) ? dwt_inv_kernel<R, true> : dwt_inv_kernel<R, false>, dim3(gx * gy), dim3(kWavThreads),
+      launch(dwt_small(lev) ? dwt_inv_kernel<R, true> : dwt_inv_kernel<R, false>, dim3(gx * gy),
+             dim3(dwt_small(lev) ? wav_threads<true>() : wav_threads<false>()),
              inv_smem(sizeof(cplx_t<R>), lev), st, a, no_batch<WArgs<R>>());
     }
     MBIR_LAUNCH_CHECK();
@@ -691,8 +695,9 @@ static void dwt_batch_t(int inverse, int level, const BatchLaunch& L, cudaStream
   WArgs<R> a0;
   memcpy(&a0, L.host0, sizeof(a0));
   const bool sm = dwt_small(level);
-  if (inverse) launch(sm ? dwt_inv_kernel<R, true> : dwt_inv_kernel<R, false>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
-  else launch(sm ? dwt_fwd_kernel<R, true> : dwt_fwd_kernel<R, false>, dim3(L.total), dim3(kWavThreads), L.smem, st, a0, B);
+  const dim3 thr(sm ? wav_threads<true>() : wav_threads<false>());
+  if (inverse) launch(sm ? dwt_inv_kernel<R, true> : dwt_inv_kernel<R, false>, dim3(L.total), thr, L.smem, st, a0, B);
+  else launch(sm ? dwt_fwd_kernel<R, true> : dwt_fwd_kernel<R, false>, dim3(L.total), thr, L.smem, st, a0, B);
 }
 
 int batch_dwt(int inverse, int level, int precision, const BatchLaunch& L, cudaStream_t st) {
