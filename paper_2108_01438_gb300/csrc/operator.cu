@@ -341,6 +341,11 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   V* tws = s + nx * TC;
   const int tid = threadIdx.x;
   const LatFFT<R> tw = lat_twiddles<R>(tws, twg, rad);
+  // digit-reversal table in shared memory: the read-out and the middle epilogue
+  // index the tile with it once per row, and a global load there would stall
+  // the dependent shared-memory read (first read after the transform's barriers)
+  int* sperm = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(tws) + 16 * (rad.tw_lo + rad.tw_hi));
+  for (int i = tid; i < nx; i += blockDim.x) sperm[i] = perm[i];
   const int half = TC >> 1, hs = __ffs(half) - 1;
   const int b = 2 * (tid & (half - 1));
   const int p0 = tid >> hs, pstep = (int)blockDim.x >> hs;
@@ -402,7 +407,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
         const int pp = p + u * pstep;
         if (pp >= nx) continue;
         const size_t off = (size_t)pp * C + c;
-        const int slot = perm[pp] * TC + b;
+        const int slot = sperm[pp] * TC + b;
         V xa, xb;
         lds2(s, slot, xa, xb);
         R ra, rb;
@@ -443,7 +448,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
         const int pp = p + u * pstep;
         if (pp >= nx) continue;
         V xa, xb;
-        lds2(s, perm[pp] * TC + b, xa, xb);
+        lds2(s, sperm[pp] * TC + b, xa, xb);
         lat_store2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, xa, xb, oa[u], ob[u], part, part2);
       }
     }
@@ -1097,10 +1102,12 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
   return a;
 }
 
-// tile plus the twiddle tables (16 bytes an entry: FP64 complex or FP32 broadcast)
+// tile, the twiddle tables (16 bytes an entry: FP64 complex or FP32 broadcast) and
+// the digit-reversal table
 template <class R>
 size_t lat_smem(mbir_plan p) {
-  return sizeof(cplx_t<R>) * (size_t)p->nx * p->tile_c + 16 * (size_t)(p->rad_x.tw_lo + p->rad_x.tw_hi);
+  return sizeof(cplx_t<R>) * (size_t)p->nx * p->tile_c + 16 * (size_t)(p->rad_x.tw_lo + p->rad_x.tw_hi) +
+         sizeof(int) * (size_t)p->nx;
 }
 
 template <class R, int MODE>
@@ -1341,7 +1348,7 @@ int power_step_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, const do
 
 template <class R>
 static int configure_t() {
-  const int lat = (int)(sizeof(cplx_t<R>) * (kLatElems + 512));
+  const int lat = (int)(sizeof(cplx_t<R>) * kLatElems + 16 * 512 + sizeof(int) * 4096);
   const int row = (int)(sizeof(cplx_t<R>) * (kMaxFFT + 512));
   const int gat = kMaxDynSmem;
 #define MBIR_SMEM_ATTR(fn, bytes)                                                                  \
