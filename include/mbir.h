@@ -295,6 +295,40 @@ int mbir_wavelet(mbir_plan plan, int32_t inverse, const void* in, void* out, voi
 int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in, void* out, void* stream);
 
 /*
+ * Launch-shape autotuner for a plan's shape class (batched and single-scan solves
+ * alike; the paper, which ran Matlab on a CPU, has no counterpart).  Candidates:
+ * the lateral tile width (columns per CTA, powers of two up to 16 within the
+ * kernels' shared-memory tile), the order of the lateral radices, and the row
+ * adjoint kernel (paired gather, single-row gather, shared-memory atomics, as far
+ * as the plan can run each).  The lateral ones are timed first with the automatic
+ * adjoint kernel, then the adjoint kernels with the best lateral choice.  Each
+ * candidate is warmed once, then timed over `reps` forward + adjoint pairs on
+ * synthetic data with CUDA events on `stream`.  The fastest is kept on the plan and
+ * recorded for the shape class (nx, nz, m, KB width, precision), and plans of that
+ * class created later in the process start from it.  The choices only reorder
+ * floating-point operations.
+ *
+ * Tune a plan before its first solve or server submission: a new tile width
+ * resizes the solver's per-CTA partial-sum buffers, and the plan's own solver state
+ * is dropped for that (request contexts made earlier would not be).  Allocates and
+ * frees two scratch buffers; synchronises the stream.  *best receives the kept
+ * tuning and its time, *n_tried the number of timed candidates (either may be NULL).
+ */
+typedef struct {
+  int32_t tile_c;          /* lateral tile width, columns per CTA */
+  int32_t lateral_order;   /* 0: largest radix first, 1: smallest radix first */
+  int32_t adjoint_kernel;  /* 4: paired gather, 1: single-row gather, 2: atomics, -1: automatic */
+  double pair_ms;          /* measured forward + adjoint time (autotune), else 0 */
+} mbir_tuning;
+
+int mbir_plan_autotune(mbir_plan plan, int32_t reps, mbir_tuning* best, int32_t* n_tried, void* stream);
+/* The plan's current launch choices (pair_ms = 0). */
+int mbir_plan_get_tuning(mbir_plan plan, mbir_tuning* out);
+/* Apply a tuning (e.g. one found for another plan of the same shape).  MBIR_ERR_INVALID
+ * when a choice does not fit the plan; the same caveat as for mbir_plan_autotune. */
+int mbir_plan_set_tuning(mbir_plan plan, const mbir_tuning* t);
+
+/*
  * Kernel timing (tracing).  mbir_profile_begin makes every later launch on the plan
  * record a CUDA event pair on its stream (up to `capacity` launches; further
  * launches run unrecorded).  mbir_profile_end waits for the recorded events, fills

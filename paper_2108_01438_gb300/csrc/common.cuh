@@ -126,6 +126,8 @@ struct mbir_plan_s {
   double dx, dz, alpha;
   mbir::Radix rad_x, rad_k;
   int tile_c;                 // lateral FFT columns per CTA
+  int lat_order;              // lateral radix order: 0 largest radix first, 1 smallest first
+  int adj_kind;               // row adjoint kernel override (RowKind), -1: automatic
   // device tables (one precision, per plan)
   void* tw_x;                 // nx-point twiddle tables [lo | hi]
   void* tw_k;                 // K-point twiddle tables [lo | hi]
@@ -269,6 +271,7 @@ size_t row_smem_bytes(mbir_plan p, int adjoint_gather);
 // Row (NUFFT) kernel of a plan: FP32 plans pair rows l and nx - l in one CTA
 enum RowKind { ROW_FWD = 0, ROW_GATHER = 1, ROW_ATOMIC = 2, ROW_FWD_PAIR = 3, ROW_GATHER_PAIR = 4 };
 int row_kind(mbir_plan p, bool adjoint);
+bool row_kind_fits(mbir_plan p, int kind);     // adjoint kinds a plan can run
 int row_ctas(mbir_plan p, int kind);           // CTAs of one scan
 size_t row_kind_smem(mbir_plan p, int kind);
 void fill_lat_args(mbir_plan p, const LatFill& f, void* dst);
@@ -306,6 +309,11 @@ int wavelet_impl(mbir_plan p, int inverse, const void* in, void* out, cudaStream
 int prox_impl(mbir_plan p, int penalty, const void* v, double tau, void* z, cudaStream_t st);
 bool wavelet_supported(int nx, int nz);
 int configure_wavelet_kernels(mbir_plan p);
+
+// tune.cu: a recorded tuning for the plan's shape class, applied at creation
+int apply_class_tuning(mbir_plan p);
+// plan.cu: radix plan of an n-point transform, radices at most max_radix
+bool plan_factor_radix(int n, Radix* r, int max_radix);
 
 // solve.cu
 void destroy_solve_state(mbir_plan p);

@@ -1176,9 +1176,20 @@ size_t row_gather_pair_smem(mbir_plan p) {
 
 size_t row_smem_bytes(mbir_plan p, int adjoint_gather);
 
+bool row_kind_fits(mbir_plan p, int kind) {
+  switch (kind) {
+    case ROW_GATHER_PAIR:
+      return p->precision == MBIR_FP32 && p->gather_ok && row_gather_pair_smem(p) <= (size_t)kMaxDynSmem;
+    case ROW_GATHER: return p->gather_ok && row_smem_bytes(p, 1) <= (size_t)kMaxDynSmem;
+    case ROW_ATOMIC: return true;
+    default: return false;
+  }
+}
+
 int row_kind(mbir_plan p, bool adjoint) {
   const bool pair = p->precision == MBIR_FP32;
   if (!adjoint) return pair ? ROW_FWD_PAIR : ROW_FWD;
+  if (p->adj_kind >= 0 && row_kind_fits(p, p->adj_kind)) return p->adj_kind;
   if (kAdjAtomic || !p->gather_ok) return ROW_ATOMIC;
   if (pair && row_gather_pair_smem(p) <= (size_t)kMaxDynSmem) return ROW_GATHER_PAIR;
   if (row_smem_bytes(p, 1) <= (size_t)kMaxDynSmem) return ROW_GATHER;

@@ -116,6 +116,8 @@ static bool factor_radix(int n, Radix* r, int max_radix = 16) {
   return true;
 }
 
+bool plan_factor_radix(int n, Radix* r, int max_radix) { return factor_radix(n, r, max_radix); }
+
 // [lo | hi] twiddle tables of an n-point transform, w = e^{-2 pi j / n}, in FP64.
 template <class V>
 static void make_twiddles(const Radix& rad, std::vector<V>& out) {
@@ -626,6 +628,9 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   rc = configure_operator_kernels(p);
   if (rc != MBIR_OK) return fail(rc);
   rc = configure_wavelet_kernels(p);
+  if (rc != MBIR_OK) return fail(rc);
+  p->adj_kind = -1;
+  rc = apply_class_tuning(p);
   if (rc != MBIR_OK) return fail(rc);
   *out = p;
   return MBIR_OK;

@@ -1,0 +1,177 @@
+// Launch-shape autotuner (the batched path's per-shape-class tuning): times the
+// candidate launch configurations of a plan's operator -- lateral tile width,
+// lateral radix order, row adjoint kernel -- on forward + adjoint pairs of
+// synthetic data, keeps the fastest on the plan and records it for the plan's
+// shape class, so that plans of that class created later start from it.  Every
+// candidate computes the same operator; only the order of floating-point
+// operations differs.
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "operator.cuh"
+
+namespace mbir {
+
+namespace {
+
+using ClassKey = std::tuple<int, int, int, int, int>;   // nx, nz, m, KB width, precision
+std::mutex g_tune_mutex;
+std::map<ClassKey, mbir_tuning> g_tune_cache;
+
+ClassKey class_key(mbir_plan p) { return ClassKey(p->nx, p->nz, p->m, p->J, p->precision); }
+
+bool tile_ok(mbir_plan p, int tc) {
+  return tc >= 2 && tc <= 16 && (tc & (tc - 1)) == 0 && (size_t)p->nx * tc <= (size_t)kLatElems;
+}
+
+// Apply a launch choice.  A new tile width drops the plan's solver state (its
+// per-CTA partial-sum buffers are sized by the lateral grid); a new radix order
+// rebuilds the lateral radix plan and uploads its digit-reversal table.
+int apply_tuning(mbir_plan p, int tile_c, int order, int adj) {
+  if (!tile_ok(p, tile_c) || (order != 0 && order != 1)) return MBIR_ERR_INVALID;
+  if (adj != -1 && (adj == ROW_FWD || adj == ROW_FWD_PAIR || !row_kind_fits(p, adj))) return MBIR_ERR_INVALID;
+  if (tile_c != p->tile_c) {
+    destroy_solve_state(p);
+    p->tile_c = tile_c;
+  }
+  if (order != p->lat_order) {
+    Radix r;
+    if (!plan_factor_radix(p->nx, &r, 8)) return MBIR_ERR_INVALID;
+    if (order == 1) {
+      std::reverse(r.r, r.r + r.npass);
+      std::reverse(r.lg, r.lg + r.npass);
+    }
+    std::vector<int> px(p->nx);
+    for (int i = 0; i < p->nx; ++i) px[i] = digit_reverse(i, r);
+    MBIR_CUDA_TRY(cudaMemcpy(p->perm_x, px.data(), sizeof(int) * p->nx, cudaMemcpyHostToDevice));
+    p->rad_x = r;
+    p->lat_order = order;
+  }
+  p->adj_kind = adj;
+  return MBIR_OK;
+}
+
+}  // namespace
+
+int apply_class_tuning(mbir_plan p) {
+  mbir_tuning t;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(class_key(p));
+    if (it == g_tune_cache.end()) return MBIR_OK;
+    t = it->second;
+  }
+  const int rc = apply_tuning(p, t.tile_c, t.lateral_order, t.adjoint_kernel);
+  return rc == MBIR_ERR_INVALID ? MBIR_OK : rc;   // a choice this plan cannot run: keep the defaults
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
+extern "C" {
+
+int mbir_plan_get_tuning(mbir_plan p, mbir_tuning* out) {
+  if (!p || !out) return MBIR_ERR_INVALID;
+  out->tile_c = p->tile_c;
+  out->lateral_order = p->lat_order;
+  out->adjoint_kernel = p->adj_kind;
+  out->pair_ms = 0.0;
+  return MBIR_OK;
+}
+
+int mbir_plan_set_tuning(mbir_plan p, const mbir_tuning* t) {
+  if (!p || !t) return MBIR_ERR_INVALID;
+  return apply_tuning(p, t->tile_c, t->lateral_order, t->adjoint_kernel);
+}
+
+int mbir_plan_autotune(mbir_plan p, int32_t reps, mbir_tuning* best, int32_t* n_tried, void* stream) {
+  if (!p || reps < 1 || reps > 1000) return MBIR_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t esz = p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t rsz = p->precision == MBIR_FP64 ? sizeof(double) : sizeof(float);
+  const size_t nimg = (size_t)p->nx * p->nz, nmeas = (size_t)p->nx * p->m;
+  const mbir_tuning orig = {p->tile_c, p->lat_order, p->adj_kind, 0.0};
+  void *x = nullptr, *xa = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = MBIR_OK, tried = 0;
+  mbir_tuning top = orig;
+  top.pair_ms = -1.0;
+  auto cleanup = [&]() {
+    cudaFree(x);
+    cudaFree(xa);
+    cudaFree(y);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  // one candidate: a warm pair, then `reps` timed pairs (the adjoint writes its own
+  // buffer, so the input stays the same)
+  auto time_cfg = [&](int tc, int ord, int adj) -> int {
+    int r = apply_tuning(p, tc, ord, adj);
+    if (r) return r;
+    for (int k = 0; k <= reps; ++k) {
+      if (k == 1) MBIR_CUDA_TRY(cudaEventRecord(e0, st));
+      if ((r = forward_impl(p, x, nullptr, y, st))) return r;
+      if ((r = adjoint_impl(p, y, nullptr, xa, st))) return r;
+    }
+    MBIR_CUDA_TRY(cudaEventRecord(e1, st));
+    MBIR_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MBIR_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    const double per = ms / reps;
+    ++tried;
+    if (top.pair_ms < 0 || per < top.pair_ms) top = {tc, ord, adj, per};
+    return MBIR_OK;
+  };
+  do {
+    cudaError_t e = cudaMalloc(&x, esz * nimg);
+    if (e == cudaSuccess) e = cudaMalloc(&xa, esz * nimg);
+    if (e == cudaSuccess) e = cudaMalloc(&y, rsz * nmeas);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0x3c, esz * nimg, st);   // small nonzero values
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rc = set_cuda_error(e, "autotune scratch");
+      break;
+    }
+    // 1. lateral tile width and radix order, automatic adjoint kernel
+    Radix r;
+    plan_factor_radix(p->nx, &r, 8);
+    const int orders = r.npass > 1 ? 2 : 1;
+    for (int tc = 2; tc <= 16 && rc == MBIR_OK; tc *= 2) {
+      if (!tile_ok(p, tc)) continue;
+      for (int ord = 0; ord < orders && rc == MBIR_OK; ++ord) rc = time_cfg(tc, ord, -1);
+    }
+    if (rc) break;
+    // 2. row adjoint kernel at the best lateral choice
+    const int tc = top.tile_c, ord = top.lateral_order;
+    for (int adj : {(int)ROW_GATHER_PAIR, (int)ROW_GATHER, (int)ROW_ATOMIC}) {
+      if (!row_kind_fits(p, adj)) continue;
+      if ((rc = time_cfg(tc, ord, adj))) break;
+    }
+  } while (false);
+  cleanup();
+  if (rc) {
+    apply_tuning(p, orig.tile_c, orig.lateral_order, orig.adjoint_kernel);
+    return rc;
+  }
+  rc = apply_tuning(p, top.tile_c, top.lateral_order, top.adjoint_kernel);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[class_key(p)] = top;
+  }
+  if (best) *best = top;
+  if (n_tried) *n_tried = tried;
+  return MBIR_OK;
+}
+
+}  // extern "C"

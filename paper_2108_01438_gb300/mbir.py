@@ -64,6 +64,11 @@ class ProfileEntry(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("tile_c", C.c_int32), ("lateral_order", C.c_int32), ("adjoint_kernel", C.c_int32),
+                ("pair_ms", C.c_double)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -97,6 +102,9 @@ _SIGNATURES = {
     "mbir_wavelet_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_profile_begin": (C.c_int, [C.c_void_p, C.c_int32]),
     "mbir_profile_only": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "mbir_plan_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+    "mbir_plan_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mbir_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mbir_profile_end": (C.c_int, [C.c_void_p, C.POINTER(ProfileEntry), C.c_int32, C.POINTER(C.c_int32)]),
     "mbir_status_string": (C.c_char_p, [C.c_int]),
     "mbir_last_error": (C.c_char_p, []),
@@ -245,6 +253,23 @@ class Plan:
         _check(lib().mbir_adjoint(self._h, _ptr(y), _ptr(mask), _ptr(out), _stream_handle(stream)),
                "mbir_adjoint")
         return out
+
+    def autotune(self, reps: int = 5, stream=None) -> dict:
+        """Time the candidate launch choices (mbir_plan_autotune); keep and return the fastest."""
+        t, n = Tuning(), C.c_int32()
+        _check(lib().mbir_plan_autotune(self._h, int(reps), C.byref(t), C.byref(n), _stream_handle(stream)),
+               "mbir_plan_autotune")
+        return dict(tile_c=t.tile_c, lateral_order=t.lateral_order, adjoint_kernel=t.adjoint_kernel,
+                    pair_ms=t.pair_ms, tried=n.value)
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().mbir_plan_get_tuning(self._h, C.byref(t)), "mbir_plan_get_tuning")
+        return dict(tile_c=t.tile_c, lateral_order=t.lateral_order, adjoint_kernel=t.adjoint_kernel)
+
+    def set_tuning(self, tile_c: int, lateral_order: int = 0, adjoint_kernel: int = -1) -> None:
+        t = Tuning(int(tile_c), int(lateral_order), int(adjoint_kernel), 0.0)
+        _check(lib().mbir_plan_set_tuning(self._h, C.byref(t)), "mbir_plan_set_tuning")
 
     def lipschitz(self, mask=None, iters: int = 30, stream=None) -> float:
         mask = self._mask(mask)
