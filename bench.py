@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32 / FP64 comparison")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch choices (no mbir_plan_autotune before timing)")
     return ap.parse_args()
 
 
@@ -242,7 +244,22 @@ def traffic_for(cls: str) -> float | None:
 
 # ------------------------------------------------------------ uneven batch
 
-def batch_comparison(dev, stream, count: int = 64, repeats: int = 2) -> dict:
+def tune_plans(plans, enabled: bool = True) -> dict:
+    """Autotune the launch choices once per shape class (mbir_plan_autotune) and
+    apply the result to the class's other plans; outside every timed region."""
+    done = {}
+    if not enabled:
+        return done
+    for p in plans:
+        key = (p.nx, p.nz, p.m)
+        if key in done:
+            p.set_tuning(done[key]["tile_c"], done[key]["lateral_order"], done[key]["adjoint_kernel"])
+        else:
+            done[key] = p.autotune(reps=3)
+    return done
+
+
+def batch_comparison(dev, stream, count: int = 64, repeats: int = 2, autotune: bool = True) -> dict:
     """The uneven-batch workload (64 B-scans, widths 256-2048, depths 1024/2048,
     l1, 100 iterations, power iteration and relative lambda per scan): one batched,
     graph-captured solve (mbir_solve_batch) against the same scans solved one at a
@@ -264,6 +281,7 @@ def batch_comparison(dev, stream, count: int = 64, repeats: int = 2) -> dict:
         ys.append((clean + float(sig * 10 ** (-wl["snr_db"] / 20)) * noise * m).contiguous())
         plans.append(p)
         ms.append(m)
+    tuned = tune_plans(plans, autotune)
     outs = [torch.empty((p.nx, p.nz), dtype=torch.complex64, device=dev) for p in plans]
     kw = dict(penalties="l1", lams=LAMBDA_FRAC, relative=True, iters=ITERS, power_iters=POWER_ITERS)
 
@@ -292,7 +310,8 @@ def batch_comparison(dev, stream, count: int = 64, repeats: int = 2) -> dict:
         p.close()
     pix = sum(w["geom"]["nx"] * w["geom"]["nz"] for w in wls)
     return {"workload": f"{count} uneven B-scans, widths 256-2048, depths 1024/2048, l1, {ITERS} iterations",
-            "image_megapixels": round(pix / 1e6, 2), "batched_bscans_per_sec": res["batched"],
+            "image_megapixels": round(pix / 1e6, 2), "shape_classes_tuned": len(tuned),
+            "batched_bscans_per_sec": res["batched"],
             "sequential_bscans_per_sec": res["sequential"], "speedup": res["batched"] / res["sequential"]}
 
 
@@ -345,7 +364,7 @@ def precision_comparison(dev, stream, repeats: int = 20) -> dict:
 # ------------------------------------------------------------ serving
 
 def serve_comparison(dev, stream, n_req: int = 200, rate_hz: float = 200.0,
-                     budget_bytes: int = 150 * 10 ** 9) -> dict:
+                     budget_bytes: int = 150 * 10 ** 9, autotune: bool = True) -> dict:
     """A seeded Poisson stream of single B-scan solves (widths from 12 of the 7-smooth
     multiples of 8 in [128, 2048], 1024 or 2048 spectral pixels, l1 / db4 half and
     half, relative-objective tolerance 1e-4 within 30-150 iterations) served with
@@ -374,6 +393,7 @@ def serve_comparison(dev, stream, n_req: int = 200, rate_hz: float = 200.0,
         y = (clean + float(sig * 10 ** (-30.0 / 20)) * noise * m).contiguous()
         reqs.append((p, y, m, "l1" if i % 2 == 0 else "db4"))
     torch.cuda.synchronize()
+    tune_plans(list(plans.values()), autotune)
     kw = dict(lam=LAMBDA_FRAC, relative=True, iters=150, min_iter=30, rel_tol=1e-4, power_iters=POWER_ITERS)
 
     srv = mbir.Server(budget_bytes, stream=stream)
@@ -448,6 +468,8 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
     d = wl["geom"]
     nx, nz, m = d["nx"], d["nz"], d["m"]
     plan = mbir.Plan(d)
+    # launch choices for this shape class, timed before anything else (not in the timed region)
+    tuning = None if args.no_autotune else plan.autotune(reps=5)
     stream = torch.cuda.current_stream()
     x_true = torch.from_numpy(wl["x_true"].astype(np.complex64)).to(dev)
     mask = torch.from_numpy(wl["mask"]).to(dev)
@@ -554,13 +576,14 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
 
     batch = None
     if not args.no_batch:
-        batch = batch_comparison(dev, torch.cuda.Stream(device=dev))
+        batch = batch_comparison(dev, torch.cuda.Stream(device=dev), autotune=not args.no_autotune)
     precision = None
     if not args.no_precision:
         precision = precision_comparison(dev, torch.cuda.Stream(device=dev))
     serve = None
     if not args.no_serve:
-        serve = serve_comparison(dev, torch.cuda.Stream(device=dev), n_req=args.serve_requests)
+        serve = serve_comparison(dev, torch.cuda.Stream(device=dev), n_req=args.serve_requests,
+                                 autotune=not args.no_autotune)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -580,7 +603,9 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": nx, "nz": nz, "m": m, "penalty": "db4",
                        "iters": ITERS, "power_iters": POWER_ITERS, "mask": "50% of A-scans",
-                       "l2": "flushed between steps (256 MiB write)"},
+                       "l2": "flushed between steps (256 MiB write)",
+                       "launch_tuning": None if tuning is None else
+                       {k: tuning[k] for k in ("tile_c", "lateral_order", "adjoint_kernel")}},
             "pairs_per_sec": ws * 1e3 / pair_ms,
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},

@@ -409,30 +409,41 @@ int Engine::add_lateral(std::vector<Stage>& out, int mode, const std::vector<BSc
   return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
 }
 
+// One launch per (row kernel, shared-memory size) among the scans: each scan runs
+// the kernel its own plan chooses (tuned or automatic), and scans with shorter
+// rows keep the occupancy of their own footprint.
 int Engine::add_row(std::vector<Stage>& out, bool adjoint, const std::vector<BScan*>& idx) {
   if (idx.empty()) return MBIR_OK;
   const size_t ab = row_args_bytes(prec_);
-  std::vector<unsigned char> blocks(ab * idx.size());
-  std::vector<int> off(idx.size() + 1, 0);
-  size_t smem = 0;
-  // one kernel for the stage: the most general of the scans' own choices (the
-  // paired gather fits fewer geometries than the single-row one, atomics fit all)
-  auto level = [](int k) { return k == ROW_GATHER_PAIR ? 0 : k == ROW_GATHER ? 1 : 2; };
-  int kind = row_kind(idx[0]->p, adjoint);
-  for (BScan* s : idx) {
+  using Key = std::pair<int, size_t>;
+  auto key_of = [&](BScan* s) {
     const int k = row_kind(s->p, adjoint);
-    if (adjoint && level(k) > level(kind)) kind = k;
+    return Key(k, row_kind_smem(s->p, k));
+  };
+  std::vector<Key> keys;
+  for (BScan* s : idx) {
+    const Key k = key_of(s);
+    if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
   }
-  for (size_t i = 0; i < idx.size(); ++i) {
-    BScan& s = *idx[i];
-    fill_row_args(s.p, s.c.wsA, s.c.wsB, blocks.data() + i * ab);
-    off[i + 1] = off[i] + row_ctas(s.p, kind);
-    smem = std::max(smem, row_kind_smem(s.p, kind));
+  for (const Key& key : keys) {
+    const int kind = key.first;
+    std::vector<BScan*> grp;
+    for (BScan* s : idx)
+      if (key_of(s) == key) grp.push_back(s);
+    std::vector<unsigned char> blocks(ab * grp.size());
+    std::vector<int> off(grp.size() + 1, 0);
+    size_t smem = 0;
+    for (size_t i = 0; i < grp.size(); ++i) {
+      BScan& s = *grp[i];
+      fill_row_args(s.p, s.c.wsA, s.c.wsB, blocks.data() + i * ab);
+      off[i + 1] = off[i] + row_ctas(s.p, kind);
+      smem = std::max(smem, row_kind_smem(s.p, kind));
+    }
+    Stage g{1, kind, 0, 0, (int)grp.size(), off.back(), smem, 0};
+    g.arg_off = push(blocks.data(), blocks.size());
+    g.off_off = push(off.data(), off.size() * sizeof(int));
+    out.push_back(g);
   }
-  Stage g{1, kind, 0, 0, (int)idx.size(), off.back(), smem, 0};
-  g.arg_off = push(blocks.data(), blocks.size());
-  g.off_off = push(off.data(), off.size() * sizeof(int));
-  out.push_back(g);
   return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
 }
 
