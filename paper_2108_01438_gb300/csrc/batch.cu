@@ -142,12 +142,12 @@ __global__ void b_maxabs(const ScanVec* sv) {
   pdl_wait_release();
   const ScanVec s = sv[blockIdx.y];
   const cplx_t<R>* v = reinterpret_cast<const cplx_t<R>*>(s.v);
-  double m = 0.0;
+  R m2 = R(0);   // largest |v|^2 of the thread, one square root at the end
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < s.n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx_t<R> a = v[i];
-    m = fmax(m, sqrt(double(a.x) * double(a.x) + double(a.y) * double(a.y)));
+    m2 = fmax(m2, a.x * a.x + a.y * a.y);
   }
-  const double M = bmax(m);
+  const double M = bmax(sqrt(double(m2)));
   if (threadIdx.x == 0) s.part[blockIdx.x] = M;
 }
 

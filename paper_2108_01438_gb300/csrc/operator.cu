@@ -1024,6 +1024,7 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
     if (c < span) {
       const int slo = c - J + 1 <= 0 ? 0 : int(sfirst[c - J + 1]);
       const int shi = int(sfirst[c + 1]) - 1;
+#pragma unroll 4
       for (int sidx = slo; sidx <= shi; ++sidx) {
         const float w = sw[sidx * J + (c - int(su[sidx]))];
         const float4 t = sv[sidx];

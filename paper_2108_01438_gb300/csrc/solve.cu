@@ -105,13 +105,15 @@ __global__ void fill_hash_kernel(cplx_t<R>* v, size_t n) {
 template <class R>
 __global__ void dot_norm_kernel(const cplx_t<R>* v, const cplx_t<R>* w, size_t n, double* part) {
   pdl_wait_release();
-  double d = 0.0, q = 0.0;
+  // a thread's few terms in the working precision, FP64 across the block (FP64
+  // arithmetic per element is slow on this GPU)
+  R d = R(0), q = R(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx_t<R> a = v[i], b = w[i];
-    d += double(a.x) * double(b.x) + double(a.y) * double(b.y);
-    q += double(b.x) * double(b.x) + double(b.y) * double(b.y);
+    d += a.x * b.x + a.y * b.y;
+    q += b.x * b.x + b.y * b.y;
   }
-  const double D = block_sum_s(d), Q = block_sum_s(q);
+  const double D = block_sum_s(double(d)), Q = block_sum_s(double(q));
   if (threadIdx.x == 0) {
     part[2 * blockIdx.x] = D;
     part[2 * blockIdx.x + 1] = Q;
@@ -145,12 +147,12 @@ __global__ void scale_kernel(cplx_t<R>* v, const cplx_t<R>* w, size_t n, const d
 template <class R>
 __global__ void maxabs_kernel(const cplx_t<R>* v, size_t n, double* part) {
   pdl_wait_release();
-  double m = 0.0;
+  R m2 = R(0);   // largest |v|^2 of the thread, one square root at the end
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx_t<R> a = v[i];
-    m = fmax(m, sqrt(double(a.x) * double(a.x) + double(a.y) * double(a.y)));
+    m2 = fmax(m2, a.x * a.x + a.y * a.y);
   }
-  const double M = block_max_s(m);
+  const double M = block_max_s(sqrt(double(m2)));
   if (threadIdx.x == 0) part[blockIdx.x] = M;
 }
 
@@ -165,25 +167,25 @@ __global__ void max_finalize_kernel(const double* part, int nb, double* out) {
 template <class R>
 __global__ void abs_sum_kernel(const cplx_t<R>* v, size_t n, double* part) {
   pdl_wait_release();
-  double s = 0.0;
+  R s = R(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx_t<R> a = v[i];
-    s += sqrt(double(a.x) * double(a.x) + double(a.y) * double(a.y));
+    s += sqrt(a.x * a.x + a.y * a.y);
   }
-  const double S = block_sum_s(s);
+  const double S = block_sum_s(double(s));
   if (threadIdx.x == 0) part[blockIdx.x] = S;
 }
 
 template <class R>
 __global__ void resid_kernel(const R* pz, const R* y, const uint8_t* mask, size_t n, double* part) {
   pdl_wait_release();
-  double s = 0.0;
+  R s = R(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (mask && !mask[i]) continue;
-    const double d = double(pz[i]) - double(y[i]);
+    const R d = pz[i] - y[i];
     s += d * d;
   }
-  const double S = block_sum_s(s);
+  const double S = block_sum_s(double(s));
   if (threadIdx.x == 0) part[blockIdx.x] = S;
 }
 

@@ -27,6 +27,8 @@ std::map<ClassKey, mbir_tuning> g_tune_cache;
 
 ClassKey class_key(mbir_plan p) { return ClassKey(p->nx, p->nz, p->m, p->J, p->precision); }
 
+constexpr double kTuneMargin = 0.98;   // a new choice must be at least 2 % faster
+
 bool tile_ok(mbir_plan p, int tc) {
   return tc >= 2 && tc <= 16 && (tc & (tc - 1)) == 0 && (size_t)p->nx * tc <= (size_t)kLatElems;
 }
@@ -127,7 +129,9 @@ int mbir_plan_autotune(mbir_plan p, int32_t reps, mbir_tuning* best, int32_t* n_
     MBIR_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
     const double per = ms / reps;
     ++tried;
-    if (top.pair_ms < 0 || per < top.pair_ms) top = {tc, ord, adj, per};
+    // a candidate must beat the kept choice by 2 %: choices within timing noise
+    // do not displace the plan's current one
+    if (top.pair_ms < 0 || per < kTuneMargin * top.pair_ms) top = {tc, ord, adj, per};
     return MBIR_OK;
   };
   do {
@@ -142,13 +146,16 @@ int mbir_plan_autotune(mbir_plan p, int32_t reps, mbir_tuning* best, int32_t* n_
       rc = set_cuda_error(e, "autotune scratch");
       break;
     }
+    // 0. the plan's current choice, the one to beat
+    if ((rc = time_cfg(orig.tile_c, orig.lateral_order, orig.adjoint_kernel))) break;
     // 1. lateral tile width and radix order, automatic adjoint kernel
     Radix r;
     plan_factor_radix(p->nx, &r, 8);
     const int orders = r.npass > 1 ? 2 : 1;
     for (int tc = 2; tc <= 16 && rc == MBIR_OK; tc *= 2) {
       if (!tile_ok(p, tc)) continue;
-      for (int ord = 0; ord < orders && rc == MBIR_OK; ++ord) rc = time_cfg(tc, ord, -1);
+      for (int ord = 0; ord < orders && rc == MBIR_OK; ++ord)
+        if (!(tc == orig.tile_c && ord == orig.lateral_order && orig.adjoint_kernel == -1)) rc = time_cfg(tc, ord, -1);
     }
     if (rc) break;
     // 2. row adjoint kernel at the best lateral choice
