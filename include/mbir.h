@@ -303,7 +303,9 @@ int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in,
  * as the plan can run each).  The lateral ones are timed first with the automatic
  * adjoint kernel, then the adjoint kernels with the best lateral choice.  Each
  * candidate is warmed once, then timed over `reps` forward + adjoint pairs on
- * synthetic data with CUDA events on `stream`.  The fastest is kept on the plan and
+ * synthetic data with CUDA events on `stream`.  The plan's current choice is timed
+ * first and a candidate replaces the kept one only when it is at least 2 % faster
+ * (choices within timing noise do not churn).  The kept one stays on the plan and is
  * recorded for the shape class (nx, nz, m, KB width, precision), and plans of that
  * class created later in the process start from it.  The choices only reorder
  * floating-point operations.
