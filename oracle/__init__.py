@@ -15,4 +15,6 @@ Modules:
               spectral factorisation, and its periodic 2-D transform.
   fista    -- penalties, proximal maps, power iteration, ISTA and FISTA
               (Sec. 2.2-2.3, Eq. alg).
+  tv       -- isotropic total variation (Sec. 2.2) and its prox by fast gradient
+              projection on the dual.
 """
