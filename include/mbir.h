@@ -59,7 +59,9 @@ typedef enum {
 
 typedef enum { MBIR_FP32 = 0, MBIR_FP32_COMPENSATED = 1, MBIR_FP64 = 2 } mbir_precision;
 
-typedef enum { MBIR_PENALTY_L1 = 0, MBIR_PENALTY_DB4 = 1 } mbir_penalty;
+/* MBIR_PENALTY_TV: the isotropic total variation of Sec. 2.2 (single-scan solves and
+ * the prox entry points; the batch and serving paths take L1 and DB4 only). */
+typedef enum { MBIR_PENALTY_L1 = 0, MBIR_PENALTY_DB4 = 1, MBIR_PENALTY_TV = 2 } mbir_penalty;
 
 /*
  * Optical geometry of one B-scan (Sec. 2.1).  Host memory; copied by
@@ -99,10 +101,12 @@ typedef struct {
 
 /*
  * Solver options (Sec. 2.3).
- *  penalty            mbir_penalty: l1 on pixels (Psi = I) or on the 3-level periodic
- *                     orthonormal Daubechies wavelet with 4 vanishing moments.
+ *  penalty            mbir_penalty: l1 on pixels (Psi = I), on the 3-level periodic
+ *                     orthonormal Daubechies wavelet with 4 vanishing moments, or the
+ *                     isotropic total variation (TV) of Sec. 2.2.
  *  lambda             penalty weight; if lambda_is_relative != 0 the weight used is
- *                     lambda * max|Psi Phi^H(s y)| (one extra adjoint at set-up).
+ *                     lambda * max|Psi Phi^H(s y)| (one extra adjoint at set-up; for TV
+ *                     the pixel maximum max|Phi^H(s y)|, as for l1).
  *  max_iter           FISTA iterations (>= 1).
  *  min_iter, rel_tol  if rel_tol > 0 the solve stops after iteration k >= min_iter
  *                     once |F(z^{k-1}) - F(z^{k-2})| <= rel_tol * F(z^{k-2}); the
@@ -110,6 +114,8 @@ typedef struct {
  *  power_iters        power iterations for L = lambda_max(Phi^H Phi) when step <= 0.
  *  step               gradient step delta; <= 0 selects 1 / (1.01 L).
  *  warm_start         != 0: start from the x passed in instead of 0.
+ *  tv_iters           TV only: dual projected-gradient (FGP) steps per prox, from the
+ *                     zero dual at every prox; <= 0 selects 20.
  */
 typedef struct {
   int32_t penalty;
@@ -121,6 +127,7 @@ typedef struct {
   int32_t power_iters;
   double step;
   int32_t warm_start;
+  int32_t tv_iters;
 } mbir_solve_opts;
 
 /*
@@ -264,6 +271,20 @@ int mbir_lipschitz(mbir_plan plan, const uint8_t* mask, int32_t iters, double* o
  * divisible by 8 with nx/8, nz/8 >= 1 and nx/4, nz/4 >= 8.
  */
 int mbir_prox(mbir_plan plan, int32_t penalty, const void* v, double tau, void* z, void* stream);
+
+/*
+ * Proximal map of tau * TV (Sec. 2.2-2.3): z = argmin 1/2 ||x - v||^2 + tau TV(x), TV the
+ * isotropic total variation sum_ij sqrt(|x(i+1,j) - x(i,j)|^2 + |x(i,j+1) - x(i,j)|^2)
+ * with the differences that would leave the image taken as zero.  Computed by
+ * `iters` steps of fast gradient projection on the dual problem (the dual field p
+ * holds one complex number per direction and pixel, |p1|^2 + |p2|^2 <= 1), from p = 0:
+ *   p_k = project(r_k + grad(v + tau div r_k) / (8 tau)),  r_{k+1} = p_k + m_k (p_k - p_{k-1}),
+ * with FISTA's momentum m_k, and z = v + tau div p_iters.  tau = 0 or iters <= 0 copy v.
+ * v, z: device [nx][nz] complex, distinct.  mbir_prox with MBIR_PENALTY_TV uses 20
+ * steps.  The plan keeps three dual fields (16 bytes a pixel each in FP32, 32 in FP64),
+ * allocated on first use.
+ */
+int mbir_prox_tv(mbir_plan plan, const void* v, double tau, int32_t iters, void* z, void* stream);
 
 /*
  * Orthonormal 3-level periodic 2-D wavelet analysis c = Psi x (inverse = 0) or

@@ -148,6 +148,8 @@ struct mbir_plan_s {
   void* wv_b1;
   void* wv_b2;
   void* wv_coef;
+  // TV prox scratch (lazily allocated): three dual fields [nx][nz] x 4 reals
+  void* tv_p[3];
   // reductions: partial sums
   double* red;                // kRedSlots doubles
   mbir::SolveState* solve;    // lazily created
@@ -314,6 +316,12 @@ int configure_wavelet_kernels(mbir_plan p);
 int apply_class_tuning(mbir_plan p);
 // plan.cu: radix plan of an n-point transform, radices at most max_radix
 bool plan_factor_radix(int n, Radix* r, int max_radix);
+
+// tv.cu: z = prox_{tau TV}(v) by `iters` FGP steps; partial (may be null) receives
+// per-CTA sums of TV(z), tv_partial_count(nx, nz) of them
+int tv_prox_impl(mbir_plan p, const void* v, double tau, int iters, void* z, double* partial, cudaStream_t st);
+int tv_partial_count(int nx, int nz);
+constexpr int kTvDefaultIters = 20;
 
 // solve.cu
 void destroy_solve_state(mbir_plan p);

@@ -554,6 +554,7 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaFree(p->wv_b1);
   cudaFree(p->wv_b2);
   cudaFree(p->wv_coef);
+  for (void* q : p->tv_p) cudaFree(q);
   cudaFree(p->wsA);
   cudaFree(p->wsB);
   cudaFree(p->red);

@@ -238,6 +238,7 @@ int ensure_state(mbir_plan p, int trace_cap) {
     const int w = wavelet_partial_count(p->nx, p->nz);
     if (w > nr) nr = w;
   }
+  if (tv_partial_count(p->nx, p->nz) > nr) nr = tv_partial_count(p->nx, p->nz);
   s->n_reg = nr;
   s->trace_cap = trace_cap;
   MBIR_CUDA_TRY(cudaMalloc(&s->zA, elem_size(p) * s->nimg));
@@ -322,10 +323,12 @@ static int reg_partials_t(mbir_plan p, int penalty, const void* z, cudaStream_t 
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }
+  if (penalty == MBIR_PENALTY_TV) return tv_prox_impl(p, z, 0.0, 0, s->v, s->part_reg, st);
   return prox_partial_impl(p, penalty, z, 0.0, s->v, s->part_reg, st);
 }
 
 static int reg_count(mbir_plan p, int penalty) {
+  if (penalty == MBIR_PENALTY_TV) return tv_partial_count(p->nx, p->nz);
   return penalty == MBIR_PENALTY_L1 ? lateral_grid(p, p->nz) : wavelet_partial_count(p->nx, p->nz);
 }
 
@@ -395,7 +398,10 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
     } else {
       rc = adjoint_solve_impl(p, z1, z2, s->v, m, delta, tau, nullptr, st);
       if (rc) return rc;
-      rc = prox_partial_impl(p, o->penalty, s->v, tau, z2, s->part_reg, st);
+      if (o->penalty == MBIR_PENALTY_TV)
+        rc = tv_prox_impl(p, s->v, tau, o->tv_iters > 0 ? o->tv_iters : kTvDefaultIters, z2, s->part_reg, st);
+      else
+        rc = prox_partial_impl(p, o->penalty, s->v, tau, z2, s->part_reg, st);
       if (rc) return rc;
     }
     void* t = z1;
@@ -458,7 +464,8 @@ int mbir_solve(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve
                mbir_solve_info* info, void* stream) {
   if (!p || !y || !o || !x) return MBIR_ERR_INVALID;
   if (o->max_iter < 1 || o->min_iter < 0) return MBIR_ERR_INVALID;
-  if (o->penalty != MBIR_PENALTY_L1 && o->penalty != MBIR_PENALTY_DB4) return MBIR_ERR_INVALID;
+  if (o->penalty != MBIR_PENALTY_L1 && o->penalty != MBIR_PENALTY_DB4 && o->penalty != MBIR_PENALTY_TV)
+    return MBIR_ERR_INVALID;
   if (!(o->lambda >= 0) || !isfinite(o->lambda) || !isfinite(o->step) || !(o->rel_tol >= 0))
     return MBIR_ERR_INVALID;
   if (o->penalty == MBIR_PENALTY_DB4 && !wavelet_supported(p->nx, p->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;

@@ -1,0 +1,267 @@
+// Isotropic total-variation penalty (Sec. 2.2) and its proximal map (the prox of
+// Eq. alg with R = TV):
+//
+//   TV(x) = sum_ij sqrt(|x(i+1,j) - x(i,j)|^2 + |x(i,j+1) - x(i,j)|^2),
+//
+// differences that would leave the image taken as zero.  The prox
+// argmin_x 1/2 ||x - v||^2 + tau TV(x) is x = v + tau div p for the dual field p
+// (one complex number per direction and pixel, |p1|^2 + |p2|^2 <= 1) minimising
+// 1/2 ||v + tau div p||^2, where div = -grad^T.  That smooth problem is solved by
+// fast gradient projection from p = 0:
+//
+//   p_k     = project(r_k + grad(v + tau div r_k) / (8 tau))
+//   r_{k+1} = p_k + m_k (p_k - p_{k-1}),   m_k = (t_k - 1)/t_{k+1}, FISTA's t,
+//
+// one kernel per step over 16 x 32 pixel tiles with a one-pixel halo: the tile
+// forms r on the halo, x = v + tau div r on the tile plus one row and column, and
+// the projected step.  Three dual fields rotate (p_k, p_{k-1}, p_{k-2}).  A last
+// kernel forms z = v + tau div p and the per-CTA sums of TV(z).  Each step reads
+// p_{k-1}, p_{k-2} and v and writes p_k: streaming stencil work.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace mbir {
+
+constexpr int kTvTI = 16, kTvTJ = 32;   // tile rows (lateral) x columns (depth)
+constexpr int kTvThreads = 256;
+
+// dual pair at one pixel: p1 (lateral) and p2 (depth), complex each
+template <class R>
+struct Dual {
+  cplx_t<R> p1, p2;
+};
+
+template <class R>
+__device__ __forceinline__ Dual<R> dzero() {
+  Dual<R> d;
+  d.p1 = cmk<cplx_t<R>>(R(0), R(0));
+  d.p2 = d.p1;
+  return d;
+}
+
+template <class R>
+__device__ __forceinline__ Dual<R> dload(const void* base, size_t i) {
+  const cplx_t<R>* q = reinterpret_cast<const cplx_t<R>*>(base) + 2 * i;
+  Dual<R> d;
+  d.p1 = q[0];
+  d.p2 = q[1];
+  return d;
+}
+
+template <class R>
+__device__ __forceinline__ void dstore(void* base, size_t i, const Dual<R>& d) {
+  cplx_t<R>* q = reinterpret_cast<cplx_t<R>*>(base) + 2 * i;
+  q[0] = d.p1;
+  q[1] = d.p2;
+}
+
+__device__ __forceinline__ double tv_block_sum(double v) {
+  __shared__ double ws[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+// Load a dual field on the tile plus a one-pixel halo into shared memory:
+// d[(ii + 1) * (TJ + 2) + jj + 1] for ii in [-1, TI], jj in [-1, TJ]; zero outside the
+// image.  With pa: r = pa + m (pa - pb) (pb read only when m != 0); without: zero.
+template <class R>
+__device__ __forceinline__ void load_dual_halo(Dual<R>* d, const void* pa, const void* pb, R m, int i0, int j0,
+                                               int P, int N) {
+  constexpr int W = kTvTJ + 2, H = kTvTI + 2;
+  for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+    const int ii = e / W - 1, jj = e - (e / W) * W - 1;
+    const int gi = i0 + ii, gj = j0 + jj;
+    Dual<R> r = dzero<R>();
+    if (pa && gi >= 0 && gi < P && gj >= 0 && gj < N) {
+      const size_t g = (size_t)gi * N + gj;
+      r = dload<R>(pa, g);
+      if (m != R(0)) {
+        const Dual<R> b = dload<R>(pb, g);
+        r.p1.x += m * (r.p1.x - b.p1.x);
+        r.p1.y += m * (r.p1.y - b.p1.y);
+        r.p2.x += m * (r.p2.x - b.p2.x);
+        r.p2.y += m * (r.p2.y - b.p2.y);
+      }
+    }
+    d[e] = r;
+  }
+}
+
+// x = v + tau div r on tile rows [0, TI] and columns [0, TJ] (one beyond the tile
+// for the forward differences); div r = r1(i) - r1(i-1) + r2(j) - r2(j-1) with the
+// terms of p1 on the last row and p2 on the last column dropped (grad never fills
+// them) and the terms outside the image zero.
+template <class R>
+__device__ __forceinline__ void form_x(cplx_t<R>* x, const Dual<R>* d, const cplx_t<R>* v, R tau, int i0, int j0,
+                                       int P, int N) {
+  using V = cplx_t<R>;
+  constexpr int W = kTvTJ + 2, XW = kTvTJ + 1;
+  for (int e = threadIdx.x; e < (kTvTI + 1) * XW; e += blockDim.x) {
+    const int ii = e / XW, jj = e - (e / XW) * XW;
+    const int gi = i0 + ii, gj = j0 + jj;
+    V xv = cmk<V>(R(0), R(0));
+    if (gi < P && gj < N) {
+      const Dual<R>& c = d[(ii + 1) * W + jj + 1];
+      const Dual<R>& up = d[ii * W + jj + 1];
+      const Dual<R>& lf = d[(ii + 1) * W + jj];
+      V dv = cmk<V>(R(0), R(0));
+      if (gi < P - 1) dv = cadd(dv, c.p1);
+      if (gi >= 1) dv = csub(dv, up.p1);
+      if (gj < N - 1) dv = cadd(dv, c.p2);
+      if (gj >= 1) dv = csub(dv, lf.p2);
+      const V vv = v[(size_t)gi * N + gj];
+      xv = cmk<V>(vv.x + tau * dv.x, vv.y + tau * dv.y);
+    }
+    x[e] = xv;
+  }
+}
+
+// One FGP step: pout = project(r + grad(v + tau div r) / (8 tau)), r from pa, pb, m
+// (pa = nullptr: r = 0, the first step).
+template <class R>
+__global__ void __launch_bounds__(kTvThreads)
+tv_step_kernel(const void* v, const void* pa, const void* pb, R m, R tau, void* pout, int P, int N, int gx) {
+  using V = cplx_t<R>;
+  __shared__ Dual<R> d[(kTvTI + 2) * (kTvTJ + 2)];
+  __shared__ V x[(kTvTI + 1) * (kTvTJ + 1)];
+  const int bx = blockIdx.x % gx, by = blockIdx.x / gx;
+  const int i0 = by * kTvTI, j0 = bx * kTvTJ;
+  pdl_wait_release();
+  load_dual_halo<R>(d, pa, pb, m, i0, j0, P, N);
+  __syncthreads();
+  form_x<R>(x, d, reinterpret_cast<const V*>(v), tau, i0, j0, P, N);
+  __syncthreads();
+  constexpr int W = kTvTJ + 2, XW = kTvTJ + 1;
+  const R step = R(1) / (R(8) * tau);
+  for (int e = threadIdx.x; e < kTvTI * kTvTJ; e += blockDim.x) {
+    const int ii = e / kTvTJ, jj = e - (e / kTvTJ) * kTvTJ;
+    const int gi = i0 + ii, gj = j0 + jj;
+    if (gi >= P || gj >= N) continue;
+    const V xc = x[ii * XW + jj];
+    const V g1 = gi < P - 1 ? csub(x[(ii + 1) * XW + jj], xc) : cmk<V>(R(0), R(0));
+    const V g2 = gj < N - 1 ? csub(x[ii * XW + jj + 1], xc) : cmk<V>(R(0), R(0));
+    Dual<R> q = d[(ii + 1) * W + jj + 1];
+    q.p1 = cmk<V>(q.p1.x + step * g1.x, q.p1.y + step * g1.y);
+    q.p2 = cmk<V>(q.p2.x + step * g2.x, q.p2.y + step * g2.y);
+    const R n2 = q.p1.x * q.p1.x + q.p1.y * q.p1.y + q.p2.x * q.p2.x + q.p2.y * q.p2.y;
+    if (n2 > R(1)) {
+      const R s = R(1) / sqrt(n2);
+      q.p1 = cscale(q.p1, s);
+      q.p2 = cscale(q.p2, s);
+    }
+    dstore<R>(pout, (size_t)gi * N + gj, q);
+  }
+}
+
+// z = v + tau div p on the tile (p = nullptr: z = v), and the per-CTA sum of TV(z)
+// (from z on the tile plus one row and column).
+template <class R>
+__global__ void __launch_bounds__(kTvThreads)
+tv_finish_kernel(const void* v, const void* p, R tau, void* z, double* partial, int P, int N, int gx) {
+  using V = cplx_t<R>;
+  __shared__ Dual<R> d[(kTvTI + 2) * (kTvTJ + 2)];
+  __shared__ V x[(kTvTI + 1) * (kTvTJ + 1)];
+  const int bx = blockIdx.x % gx, by = blockIdx.x / gx;
+  const int i0 = by * kTvTI, j0 = bx * kTvTJ;
+  pdl_wait_release();
+  load_dual_halo<R>(d, p, nullptr, R(0), i0, j0, P, N);
+  __syncthreads();
+  form_x<R>(x, d, reinterpret_cast<const V*>(v), tau, i0, j0, P, N);
+  __syncthreads();
+  constexpr int XW = kTvTJ + 1;
+  R acc = R(0);   // a thread's few terms in the working precision, FP64 across the block
+  V* zo = reinterpret_cast<V*>(z);
+  for (int e = threadIdx.x; e < kTvTI * kTvTJ; e += blockDim.x) {
+    const int ii = e / kTvTJ, jj = e - (e / kTvTJ) * kTvTJ;
+    const int gi = i0 + ii, gj = j0 + jj;
+    if (gi >= P || gj >= N) continue;
+    const V xc = x[ii * XW + jj];
+    zo[(size_t)gi * N + gj] = xc;
+    const V g1 = gi < P - 1 ? csub(x[(ii + 1) * XW + jj], xc) : cmk<V>(R(0), R(0));
+    const V g2 = gj < N - 1 ? csub(x[ii * XW + jj + 1], xc) : cmk<V>(R(0), R(0));
+    acc += sqrt(g1.x * g1.x + g1.y * g1.y + g2.x * g2.x + g2.y * g2.y);
+  }
+  if (partial) {
+    const double t = tv_block_sum(double(acc));
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+// ------------------------------------------------------------------ host
+
+static int tv_grid_x(int N) { return (N + kTvTJ - 1) / kTvTJ; }
+static int tv_grid_y(int P) { return (P + kTvTI - 1) / kTvTI; }
+
+int tv_partial_count(int nx, int nz) { return tv_grid_x(nz) * tv_grid_y(nx); }
+
+static int ensure_tv_scratch(mbir_plan p) {
+  if (p->tv_p[0]) return MBIR_OK;
+  const size_t bytes = (p->precision == MBIR_FP64 ? 4 * sizeof(double) : 4 * sizeof(float)) * (size_t)p->nx * p->nz;
+  for (void*& q : p->tv_p) MBIR_CUDA_TRY(cudaMalloc(&q, bytes));
+  return MBIR_OK;
+}
+
+template <class R>
+static int tv_prox_t(mbir_plan p, const void* v, double tau, int iters, void* z, double* partial, cudaStream_t st) {
+  const int P = p->nx, N = p->nz, gx = tv_grid_x(N), grid = gx * tv_grid_y(P);
+  if (!(tau > 0) || iters <= 0) {
+    { ProfScope ps_(p, PC_SOFT, st); launch(tv_finish_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, (const void*)nullptr, R(0), z, partial, P, N, gx); }
+    MBIR_LAUNCH_CHECK();
+    return MBIR_OK;
+  }
+  int rc = ensure_tv_scratch(p);
+  if (rc) return rc;
+  // step k (1-based) writes buffer (k-1) % 3 from r_k = p_{k-1} + m_{k-1} (p_{k-1} - p_{k-2})
+  double t = 1.0, m_prev = 0.0;
+  for (int k = 1; k <= iters; ++k) {
+    const void* pa = k >= 2 ? p->tv_p[(k - 2) % 3] : nullptr;
+    const void* pb = k >= 3 ? p->tv_p[(k - 3) % 3] : nullptr;
+    const R m = k >= 3 ? R(m_prev) : R(0);
+    {
+      ProfScope ps_(p, PC_SOFT, st);
+      launch(tv_step_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, pa, pb, m, R(tau), p->tv_p[(k - 1) % 3], P,
+             N, gx);
+    }
+    MBIR_LAUNCH_CHECK();
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    m_prev = (t - 1.0) / tn;   // m_k, used by step k + 1
+    t = tn;
+  }
+  {
+    ProfScope ps_(p, PC_SOFT, st);
+    launch(tv_finish_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, (const void*)p->tv_p[(iters - 1) % 3], R(tau),
+           z, partial, P, N, gx);
+  }
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+int tv_prox_impl(mbir_plan p, const void* v, double tau, int iters, void* z, double* partial, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? tv_prox_t<double>(p, v, tau, iters, z, partial, st)
+                                   : tv_prox_t<float>(p, v, tau, iters, z, partial, st);
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
+extern "C" {
+
+int mbir_prox_tv(mbir_plan p, const void* v, double tau, int32_t iters, void* z, void* stream) {
+  if (!p || !v || !z || v == z || !(tau >= 0) || !isfinite(tau)) return MBIR_ERR_INVALID;
+  return tv_prox_impl(p, v, tau, iters, z, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -512,6 +512,15 @@ int wavelet_impl(mbir_plan p, int inverse, const void* in, void* out, cudaStream
 int prox_partial_impl(mbir_plan p, int penalty, const void* v, double tau, void* z, double* partial,
                       cudaStream_t st) {
   const bool f64 = p->precision == MBIR_FP64;
+  if (penalty == MBIR_PENALTY_TV) {
+    // the TV stencil reads neighbouring tiles of v: an aliased v is copied first
+    if (v == z) {
+      MBIR_CUDA_TRY(cudaMemcpyAsync(p->wsA, v, (f64 ? sizeof(double2) : sizeof(float2)) * (size_t)p->nx * p->nz,
+                                    cudaMemcpyDeviceToDevice, st));
+      v = p->wsA;
+    }
+    return tv_prox_impl(p, v, tau, kTvDefaultIters, z, partial, st);
+  }
   if (penalty == MBIR_PENALTY_L1) {
     const size_t n = (size_t)p->nx * p->nz;
     if (f64)
@@ -613,7 +622,7 @@ int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in,
 
 int mbir_prox(mbir_plan p, int32_t penalty, const void* v, double tau, void* z, void* stream) {
   if (!p || !v || !z || !(tau >= 0) || !isfinite(tau)) return MBIR_ERR_INVALID;
-  if (penalty != MBIR_PENALTY_L1 && penalty != MBIR_PENALTY_DB4) return MBIR_ERR_INVALID;
+  if (penalty != MBIR_PENALTY_L1 && penalty != MBIR_PENALTY_DB4 && penalty != MBIR_PENALTY_TV) return MBIR_ERR_INVALID;
   return prox_partial_impl(p, penalty, v, tau, z, nullptr, (cudaStream_t)stream);
 }
 

@@ -18,7 +18,8 @@ LIB_PATH = os.environ.get("MBIR_LIBRARY") or os.path.join(HERE, "libmbir.so")
 
 FP32, FP32_COMPENSATED, FP64 = 0, 1, 2
 PENALTY_L1, PENALTY_DB4 = 0, 1
-PENALTIES = {"l1": PENALTY_L1, "db4": PENALTY_DB4}
+PENALTY_TV = 2
+PENALTIES = {"l1": PENALTY_L1, "db4": PENALTY_DB4, "tv": PENALTY_TV}
 
 STATUS = {0: "MBIR_OK", -1: "MBIR_ERR_INVALID", -2: "MBIR_ERR_UNSUPPORTED_SIZE",
           -3: "MBIR_ERR_OOM", -4: "MBIR_ERR_CUDA", -5: "MBIR_ERR_TIMEOUT",
@@ -49,6 +50,7 @@ class SolveOpts(C.Structure):
         ("penalty", C.c_int32), ("lam", C.c_double), ("lambda_is_relative", C.c_int32),
         ("max_iter", C.c_int32), ("min_iter", C.c_int32), ("rel_tol", C.c_double),
         ("power_iters", C.c_int32), ("step", C.c_double), ("warm_start", C.c_int32),
+        ("tv_iters", C.c_int32),
     ]
 
 
@@ -98,6 +100,7 @@ _SIGNATURES = {
                                           C.POINTER(C.c_int64)]),
     "mbir_lipschitz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
     "mbir_prox": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    "mbir_prox_tv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
     "mbir_wavelet": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_wavelet_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_profile_begin": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -305,6 +308,17 @@ class Plan:
                                _stream_handle(stream)), "mbir_prox")
         return out
 
+    def prox_tv(self, v, tau: float, iters: int = 20, out=None, stream=None):
+        """prox of tau * TV by `iters` dual projected-gradient steps (mbir_prox_tv); out != v."""
+        import torch
+        self._image(v, "v")
+        if out is None:
+            out = torch.empty_like(v)
+        self._image(out, "out")
+        _check(lib().mbir_prox_tv(self._h, _ptr(v), float(tau), int(iters), _ptr(out), _stream_handle(stream)),
+               "mbir_prox_tv")
+        return out
+
     def wavelet(self, x, inverse: bool = False, out=None, stream=None):
         import torch
         self._image(x, "x")
@@ -317,8 +331,8 @@ class Plan:
 
     def solve(self, y, mask=None, *, penalty: str = "l1", lam: float = 0.01, relative: bool = True,
               iters: int = 100, min_iter: int = 0, rel_tol: float = 0.0, power_iters: int = 30,
-              step: float = 0.0, x0=None, out=None, trace: bool = False, stream=None):
-        """FISTA (mbir_solve).  Returns (x, info dict)."""
+              step: float = 0.0, x0=None, out=None, trace: bool = False, tv_iters: int = 0, stream=None):
+        """FISTA (mbir_solve).  Returns (x, info dict).  tv_iters: dual steps per TV prox (0: 20)."""
         import torch
         self._meas(y, "y")
         mask = self._mask(mask)
@@ -329,7 +343,7 @@ class Plan:
             out.copy_(x0)
         self._image(out, "out")
         o = SolveOpts(PENALTIES[penalty], float(lam), int(bool(relative)), int(iters), int(min_iter),
-                      float(rel_tol), int(power_iters), float(step), int(x0 is not None))
+                      float(rel_tol), int(power_iters), float(step), int(x0 is not None), int(tv_iters))
         info = SolveInfo()
         tr = None
         if trace:
