@@ -35,6 +35,7 @@ METRIC = "fista_bscans_per_sec"
 UNIT = "B-scans/s"
 ITERS = 100
 POWER_ITERS = 30
+TV_ITERS = 20           # dual steps per TV prox (the library's default)
 LAMBDA_FRAC = 0.01
 L2_FLUSH_BYTES = 256 << 20
 
@@ -50,6 +51,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32 / FP64 comparison")
+    ap.add_argument("--no-tv", action="store_true", help="skip the TV-penalty solve")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch choices (no mbir_plan_autotune before timing)")
     return ap.parse_args()
@@ -537,6 +539,41 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
     torch.cuda.synchronize()
     pair_ms = e0.elapsed_time(e1) / pairs
 
+    # the isotropic TV penalty on the same B-scan (Sec. 2.2): a whole solve, and the
+    # TV prox kernels against the HBM roof (they stream the dual fields)
+    tv_res = None
+    if not args.no_tv:
+        tv_kw = dict(penalty="tv", lam=LAMBDA_FRAC, relative=True, iters=ITERS, power_iters=POWER_ITERS,
+                     out=out, tv_iters=TV_ITERS)
+        plan.solve(y, mask, **tv_kw)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(2):
+            flush.zero_()
+            plan.solve(y, mask, **tv_kw)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        tv_solve_ms = t0.elapsed_time(t1) / 2
+        plan.profile_begin(1 << 14)
+        plan.profile_only("tv_prox")
+        plan.solve(y, mask, **tv_kw)
+        torch.cuda.synchronize()
+        n_launch, tv_total_ms = plan.profile_end()["tv_prox"]
+        n_prox = n_launch / (TV_ITERS + 1)
+        # bytes a prox must move per pixel (FP32): step 1 reads v, writes p (24); step 2
+        # reads p_1 and v, writes p_2 (40); later steps read p_{k-1}, p_{k-2}, v and write
+        # p_k (56); the finishing pass reads p and v, writes z (32)
+        bpp = 24 + 40 + 56 * (TV_ITERS - 2) + 32
+        prox_ms = tv_total_ms / n_prox
+        peak_gbs = measured_peak()[0]
+        gbs = bpp * nx * nz / (prox_ms * 1e-3) / 1e9
+        tv_res = {"workload": f"bscan-1024x2048-tv-{ITERS}it-half-ascans, {TV_ITERS} dual steps per prox",
+                  "bscans_per_sec": 1e3 / tv_solve_ms, "ms_per_solve": tv_solve_ms,
+                  "prox_ms": prox_ms, "prox_launches": TV_ITERS + 1,
+                  "roofline": {"bound": "hbm", "kernel": "tv_prox", "achieved": gbs, "peak": peak_gbs,
+                               "unit": "GB/s", "frac": gbs / peak_gbs, "alg_bytes_per_prox": bpp * nx * nz}}
+
     # end to end through host buffers: pinned inputs in, reconstruction out, each step
     y_host = y.cpu().pin_memory()
     m_host = mask.cpu().pin_memory()
@@ -613,6 +650,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
             "batch": batch,
             "serve": serve,
             "precision": precision,
+            "tv": tv_res,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),

@@ -105,6 +105,7 @@ enum ProfClass {
   PC_SOFT,            // elementwise soft-threshold
   PC_REDUCE,          // reductions, scalars, power-iteration helpers
   PC_LAT_MID,         // inverse lateral FFT + measurement epilogue + lateral FFT (Phi^H Phi middle)
+  PC_TV,              // TV prox: dual projected-gradient steps and the finishing pass
   PC_COUNT
 };
 
@@ -318,9 +319,9 @@ int apply_class_tuning(mbir_plan p);
 bool plan_factor_radix(int n, Radix* r, int max_radix);
 
 // tv.cu: z = prox_{tau TV}(v) by `iters` FGP steps; partial (may be null) receives
-// per-CTA sums of TV(z), tv_partial_count(nx, nz) of them
+// per-CTA sums of TV(z), tv_partial_count(p) of them
 int tv_prox_impl(mbir_plan p, const void* v, double tau, int iters, void* z, double* partial, cudaStream_t st);
-int tv_partial_count(int nx, int nz);
+int tv_partial_count(mbir_plan p);
 constexpr int kTvDefaultIters = 20;
 
 // solve.cu

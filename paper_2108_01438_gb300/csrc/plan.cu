@@ -422,7 +422,7 @@ const char* prof_class_name(int c) {
   static const char* names[PC_COUNT] = {"lateral_forward", "row_forward", "lateral_inverse_real",
                                         "lateral_residual", "row_adjoint", "lateral_adjoint",
                                         "dwt_analysis", "dwt_synthesis", "soft_threshold", "reduce",
-                                        "lateral_mid"};
+                                        "lateral_mid", "tv_prox"};
   return (c >= 0 && c < PC_COUNT) ? names[c] : "unknown";
 }
 

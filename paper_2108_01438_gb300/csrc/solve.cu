@@ -238,7 +238,7 @@ int ensure_state(mbir_plan p, int trace_cap) {
     const int w = wavelet_partial_count(p->nx, p->nz);
     if (w > nr) nr = w;
   }
-  if (tv_partial_count(p->nx, p->nz) > nr) nr = tv_partial_count(p->nx, p->nz);
+  if (tv_partial_count(p) > nr) nr = tv_partial_count(p);
   s->n_reg = nr;
   s->trace_cap = trace_cap;
   MBIR_CUDA_TRY(cudaMalloc(&s->zA, elem_size(p) * s->nimg));
@@ -328,7 +328,7 @@ static int reg_partials_t(mbir_plan p, int penalty, const void* z, cudaStream_t 
 }
 
 static int reg_count(mbir_plan p, int penalty) {
-  if (penalty == MBIR_PENALTY_TV) return tv_partial_count(p->nx, p->nz);
+  if (penalty == MBIR_PENALTY_TV) return tv_partial_count(p);
   return penalty == MBIR_PENALTY_L1 ? lateral_grid(p, p->nz) : wavelet_partial_count(p->nx, p->nz);
 }
 

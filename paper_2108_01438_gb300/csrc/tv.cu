@@ -12,7 +12,7 @@
 //   p_k     = project(r_k + grad(v + tau div r_k) / (8 tau))
 //   r_{k+1} = p_k + m_k (p_k - p_{k-1}),   m_k = (t_k - 1)/t_{k+1}, FISTA's t,
 //
-// one kernel per step over 16 x 32 pixel tiles with a one-pixel halo: the tile
+// one kernel per step over 16 x 64 pixel tiles (16 x 32 in FP64) with a one-pixel halo: the tile
 // forms r on the halo, x = v + tau div r on the tile plus one row and column, and
 // the projected step.  Three dual fields rotate (p_k, p_{k-1}, p_{k-2}).  A last
 // kernel forms z = v + tau div p and the per-CTA sums of TV(z).  Each step reads
@@ -23,7 +23,11 @@
 
 namespace mbir {
 
-constexpr int kTvTI = 16, kTvTJ = 32;   // tile rows (lateral) x columns (depth)
+// tile rows (lateral) x columns (depth): 16 x 64 in FP32, 16 x 32 in FP64 (the
+// halo tiles of a step stay within 48 KB of static shared memory)
+constexpr int kTvTI = 16;
+template <class R>
+constexpr int tv_tj() { return sizeof(R) == 4 ? 64 : 32; }
 constexpr int kTvThreads = 256;
 
 // dual pair at one pixel: p1 (lateral) and p2 (depth), complex each
@@ -40,20 +44,31 @@ __device__ __forceinline__ Dual<R> dzero() {
   return d;
 }
 
+// a pixel's dual pair moves as one 16-byte access in FP32 (two in FP64)
 template <class R>
 __device__ __forceinline__ Dual<R> dload(const void* base, size_t i) {
-  const cplx_t<R>* q = reinterpret_cast<const cplx_t<R>*>(base) + 2 * i;
   Dual<R> d;
-  d.p1 = q[0];
-  d.p2 = q[1];
+  if constexpr (sizeof(R) == 4) {
+    const float4 t = reinterpret_cast<const float4*>(base)[i];
+    d.p1 = make_float2(t.x, t.y);
+    d.p2 = make_float2(t.z, t.w);
+  } else {
+    const cplx_t<R>* q = reinterpret_cast<const cplx_t<R>*>(base) + 2 * i;
+    d.p1 = q[0];
+    d.p2 = q[1];
+  }
   return d;
 }
 
 template <class R>
 __device__ __forceinline__ void dstore(void* base, size_t i, const Dual<R>& d) {
-  cplx_t<R>* q = reinterpret_cast<cplx_t<R>*>(base) + 2 * i;
-  q[0] = d.p1;
-  q[1] = d.p2;
+  if constexpr (sizeof(R) == 4) {
+    reinterpret_cast<float4*>(base)[i] = make_float4(d.p1.x, d.p1.y, d.p2.x, d.p2.y);
+  } else {
+    cplx_t<R>* q = reinterpret_cast<cplx_t<R>*>(base) + 2 * i;
+    q[0] = d.p1;
+    q[1] = d.p2;
+  }
 }
 
 __device__ __forceinline__ double tv_block_sum(double v) {
@@ -79,7 +94,7 @@ __device__ __forceinline__ double tv_block_sum(double v) {
 template <class R>
 __device__ __forceinline__ void load_dual_halo(Dual<R>* d, const void* pa, const void* pb, R m, int i0, int j0,
                                                int P, int N) {
-  constexpr int W = kTvTJ + 2, H = kTvTI + 2;
+  constexpr int TJ = tv_tj<R>(), W = TJ + 2, H = kTvTI + 2;
   for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
     const int ii = e / W - 1, jj = e - (e / W) * W - 1;
     const int gi = i0 + ii, gj = j0 + jj;
@@ -107,7 +122,7 @@ template <class R>
 __device__ __forceinline__ void form_x(cplx_t<R>* x, const Dual<R>* d, const cplx_t<R>* v, R tau, int i0, int j0,
                                        int P, int N) {
   using V = cplx_t<R>;
-  constexpr int W = kTvTJ + 2, XW = kTvTJ + 1;
+  constexpr int TJ = tv_tj<R>(), W = TJ + 2, XW = TJ + 1;
   for (int e = threadIdx.x; e < (kTvTI + 1) * XW; e += blockDim.x) {
     const int ii = e / XW, jj = e - (e / XW) * XW;
     const int gi = i0 + ii, gj = j0 + jj;
@@ -134,19 +149,20 @@ template <class R>
 __global__ void __launch_bounds__(kTvThreads)
 tv_step_kernel(const void* v, const void* pa, const void* pb, R m, R tau, void* pout, int P, int N, int gx) {
   using V = cplx_t<R>;
-  __shared__ Dual<R> d[(kTvTI + 2) * (kTvTJ + 2)];
-  __shared__ V x[(kTvTI + 1) * (kTvTJ + 1)];
+  constexpr int TJ = tv_tj<R>();
+  __shared__ Dual<R> d[(kTvTI + 2) * (TJ + 2)];
+  __shared__ V x[(kTvTI + 1) * (TJ + 1)];
   const int bx = blockIdx.x % gx, by = blockIdx.x / gx;
-  const int i0 = by * kTvTI, j0 = bx * kTvTJ;
+  const int i0 = by * kTvTI, j0 = bx * TJ;
   pdl_wait_release();
   load_dual_halo<R>(d, pa, pb, m, i0, j0, P, N);
   __syncthreads();
   form_x<R>(x, d, reinterpret_cast<const V*>(v), tau, i0, j0, P, N);
   __syncthreads();
-  constexpr int W = kTvTJ + 2, XW = kTvTJ + 1;
+  constexpr int W = TJ + 2, XW = TJ + 1;
   const R step = R(1) / (R(8) * tau);
-  for (int e = threadIdx.x; e < kTvTI * kTvTJ; e += blockDim.x) {
-    const int ii = e / kTvTJ, jj = e - (e / kTvTJ) * kTvTJ;
+  for (int e = threadIdx.x; e < kTvTI * TJ; e += blockDim.x) {
+    const int ii = e / TJ, jj = e - (e / TJ) * TJ;
     const int gi = i0 + ii, gj = j0 + jj;
     if (gi >= P || gj >= N) continue;
     const V xc = x[ii * XW + jj];
@@ -171,20 +187,21 @@ template <class R>
 __global__ void __launch_bounds__(kTvThreads)
 tv_finish_kernel(const void* v, const void* p, R tau, void* z, double* partial, int P, int N, int gx) {
   using V = cplx_t<R>;
-  __shared__ Dual<R> d[(kTvTI + 2) * (kTvTJ + 2)];
-  __shared__ V x[(kTvTI + 1) * (kTvTJ + 1)];
+  constexpr int TJ = tv_tj<R>();
+  __shared__ Dual<R> d[(kTvTI + 2) * (TJ + 2)];
+  __shared__ V x[(kTvTI + 1) * (TJ + 1)];
   const int bx = blockIdx.x % gx, by = blockIdx.x / gx;
-  const int i0 = by * kTvTI, j0 = bx * kTvTJ;
+  const int i0 = by * kTvTI, j0 = bx * TJ;
   pdl_wait_release();
   load_dual_halo<R>(d, p, nullptr, R(0), i0, j0, P, N);
   __syncthreads();
   form_x<R>(x, d, reinterpret_cast<const V*>(v), tau, i0, j0, P, N);
   __syncthreads();
-  constexpr int XW = kTvTJ + 1;
+  constexpr int XW = TJ + 1;
   R acc = R(0);   // a thread's few terms in the working precision, FP64 across the block
   V* zo = reinterpret_cast<V*>(z);
-  for (int e = threadIdx.x; e < kTvTI * kTvTJ; e += blockDim.x) {
-    const int ii = e / kTvTJ, jj = e - (e / kTvTJ) * kTvTJ;
+  for (int e = threadIdx.x; e < kTvTI * TJ; e += blockDim.x) {
+    const int ii = e / TJ, jj = e - (e / TJ) * TJ;
     const int gi = i0 + ii, gj = j0 + jj;
     if (gi >= P || gj >= N) continue;
     const V xc = x[ii * XW + jj];
@@ -201,10 +218,13 @@ tv_finish_kernel(const void* v, const void* p, R tau, void* z, double* partial, 
 
 // ------------------------------------------------------------------ host
 
-static int tv_grid_x(int N) { return (N + kTvTJ - 1) / kTvTJ; }
-static int tv_grid_y(int P) { return (P + kTvTI - 1) / kTvTI; }
+static int tv_grid_x(mbir_plan p) {
+  const int tj = p->precision == MBIR_FP64 ? tv_tj<double>() : tv_tj<float>();
+  return (p->nz + tj - 1) / tj;
+}
+static int tv_grid_y(mbir_plan p) { return (p->nx + kTvTI - 1) / kTvTI; }
 
-int tv_partial_count(int nx, int nz) { return tv_grid_x(nz) * tv_grid_y(nx); }
+int tv_partial_count(mbir_plan p) { return tv_grid_x(p) * tv_grid_y(p); }
 
 static int ensure_tv_scratch(mbir_plan p) {
   if (p->tv_p[0]) return MBIR_OK;
@@ -215,9 +235,9 @@ static int ensure_tv_scratch(mbir_plan p) {
 
 template <class R>
 static int tv_prox_t(mbir_plan p, const void* v, double tau, int iters, void* z, double* partial, cudaStream_t st) {
-  const int P = p->nx, N = p->nz, gx = tv_grid_x(N), grid = gx * tv_grid_y(P);
+  const int P = p->nx, N = p->nz, gx = tv_grid_x(p), grid = gx * tv_grid_y(p);
   if (!(tau > 0) || iters <= 0) {
-    { ProfScope ps_(p, PC_SOFT, st); launch(tv_finish_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, (const void*)nullptr, R(0), z, partial, P, N, gx); }
+    { ProfScope ps_(p, PC_TV, st); launch(tv_finish_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, (const void*)nullptr, R(0), z, partial, P, N, gx); }
     MBIR_LAUNCH_CHECK();
     return MBIR_OK;
   }
@@ -230,7 +250,7 @@ static int tv_prox_t(mbir_plan p, const void* v, double tau, int iters, void* z,
     const void* pb = k >= 3 ? p->tv_p[(k - 3) % 3] : nullptr;
     const R m = k >= 3 ? R(m_prev) : R(0);
     {
-      ProfScope ps_(p, PC_SOFT, st);
+      ProfScope ps_(p, PC_TV, st);
       launch(tv_step_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, pa, pb, m, R(tau), p->tv_p[(k - 1) % 3], P,
              N, gx);
     }
@@ -240,7 +260,7 @@ static int tv_prox_t(mbir_plan p, const void* v, double tau, int iters, void* z,
     t = tn;
   }
   {
-    ProfScope ps_(p, PC_SOFT, st);
+    ProfScope ps_(p, PC_TV, st);
     launch(tv_finish_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, (const void*)p->tv_p[(iters - 1) % 3], R(tau),
            z, partial, P, N, gx);
   }

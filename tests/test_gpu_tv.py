@@ -39,7 +39,7 @@ def _img(shape, seed):
 @pytest.mark.parametrize("nx,nz,tau,iters", [(64, 96, 0.3, 20), (35, 50, 0.8, 20), (16, 45, 0.1, 100),
                                              (2, 40, 0.5, 20), (48, 64, 2.0, 50)])
 def test_prox_tv_matches_oracle(mbir, nx, nz, tau, iters):
-    """Tiles of 16 x 32 with ragged edges in both directions, a two-row image, a
+    """Tiles of 16 x 64 with ragged edges in both directions, a two-row image, a
     strong and a weak tau."""
     plan = mbir.Plan(W.geometry(nx, nz, 16))
     v = _img((nx, nz), 800 + nx)
