@@ -10,7 +10,8 @@ workload generators, which hold no reconstruction arithmetic).
 Modules:
   isam     -- system operator Phi and its adjoint (Sec. 2.1, Eqs. for_model /
               back_model), both as a direct non-uniform DFT and as the
-              Kaiser-Bessel NUFFT the paper uses.
+              Kaiser-Bessel NUFFT the paper uses; the paper's Hilbert-form
+              back-projection and the literal zero-pad / DFT form of Phi.
   wavelet  -- orthonormal Daubechies wavelet (4 vanishing moments) built by
               spectral factorisation, and its periodic 2-D transform.
   fista    -- penalties, proximal maps, power iteration, ISTA and FISTA

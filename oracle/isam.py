@@ -29,9 +29,18 @@ The forward model written out (Eq. for_model, with the readings below):
     the axial transform directly at the spectrometer wavenumbers, with the image
     confined to the positive half of the unambiguous depth range.
 The adjoint used is the exact transpose of Phi in the real inner products
-<a,b> = Re sum conj(a) b, i.e. Phi^H y = B^H (s * y) with y embedded as y + 0j;
-the paper's Hilbert-transform back-projection (Eq. back_model) coincides with
-it on analytic signals.
+<a,b> = Re sum conj(a) b, i.e. Phi^H y = B^H (s * y) with y embedded as y + 0j.
+
+The paper's own back-projection (Eq. back_model) is given too:
+  Phi*(y) = B^H A(s * y),  A(r) = r - j d H(r)   (phi_adj_hilbert_*)
+with H the discrete Hilbert transform along the spectrometer axis (the DFT
+multiplier -j sgn(f), zero at DC and at the Nyquist bin).  Readings: the printed
+order "K^H D^H Q^T" is taken as K^H Q^T D^H (the only order whose sizes agree),
+and d = +1 when k increases with the pixel index (A = Re - jH, as printed) and
+d = -1 when it decreases (A = Re + jH): A keeps the side of the spectrum on which
+e^{-j 2 k z}, z > 0, lies, so that A(Re{w}) = w for such a signal w.  On those
+signals Phi* = 2 Phi^H on the image the twin cannot reach: the conjugate (twin)
+term of the transpose is dropped and the kept term is doubled.
 
 Two realisations are given:
   phi_exact / phi_adj_exact  - a direct non-uniform DFT over depth.
@@ -51,6 +60,8 @@ __all__ = [
     "Geom", "make_geom", "lateral_q", "axial_beta", "system_filter", "depth_weight",
     "kb_kernel", "kb_ft", "kb_grid_position", "phi_exact", "phi_adj_exact",
     "phi_exact_at", "phi_nufft", "phi_adj_nufft", "nufft_axial", "nufft_axial_adjoint",
+    "b_adj_exact", "b_adj_nufft", "hilbert", "conj_analytic", "k_increasing",
+    "phi_adj_hilbert_exact", "phi_adj_hilbert_nufft", "phi_qd",
 ]
 
 
@@ -184,14 +195,20 @@ def phi_exact_at(x: np.ndarray, g: Geom, ps: np.ndarray, ms: np.ndarray) -> np.n
 
 def phi_adj_exact(y: np.ndarray, mask: np.ndarray | None, g: Geom) -> np.ndarray:
     """Phi^H y, the transpose of phi_exact in the real inner products."""
+    r = np.asarray(y, dtype=np.float64)
+    if mask is not None:
+        r = r * mask
+    return b_adj_exact(r.astype(np.complex128), g)
+
+
+def b_adj_exact(c: np.ndarray, g: Geom) -> np.ndarray:
+    """B^H c for a complex measurement-domain array c[p, m], B the complex-valued
+    forward map before the real part (direct sum over depth)."""
     beta, _ = axial_beta(g)
     H = system_filter(g)
     w = depth_weight(g)
     z = np.arange(g.nz) * g.dz
-    r = np.asarray(y, dtype=np.float64)
-    if mask is not None:
-        r = r * mask
-    R = np.fft.fft(r.astype(np.complex128), axis=0) / g.nx
+    R = np.fft.fft(np.asarray(c, dtype=np.complex128), axis=0) / g.nx
     V = np.conj(H) * R
     W = np.empty((g.nx, g.nz), dtype=np.complex128)
     for l in range(g.nx):
@@ -296,14 +313,94 @@ def phi_nufft(x: np.ndarray, mask: np.ndarray | None, g: Geom) -> np.ndarray:
 
 def phi_adj_nufft(y: np.ndarray, mask: np.ndarray | None, g: Geom) -> np.ndarray:
     """Phi^H y for phi_nufft: the transpose of each of its steps, in reverse order."""
+    r = np.asarray(y, dtype=np.float64)
+    if mask is not None:
+        r = r * mask
+    return b_adj_nufft(r.astype(np.complex128), g)
+
+
+def b_adj_nufft(c: np.ndarray, g: Geom) -> np.ndarray:
+    """B^H c with the KB NUFFT, for a complex measurement-domain array c[p, m]."""
     beta, _ = axial_beta(g)
     H = system_filter(g)
     w = depth_weight(g)
     t = kb_grid_position(g)
-    r = np.asarray(y, dtype=np.float64)
-    if mask is not None:
-        r = r * mask
-    R = np.fft.fft(r.astype(np.complex128), axis=0) / g.nx
+    R = np.fft.fft(np.asarray(c, dtype=np.complex128), axis=0) / g.nx
     V = np.conj(H) * R * np.exp(-1j * beta * (g.z_f - g.n0 * g.dz))
     a = nufft_axial_adjoint(V, t, g)
     return g.nx * np.fft.ifft(a * w[None, :], axis=0)
+
+
+# ------------------------------------------- Hilbert-form back-projection
+
+def hilbert(r: np.ndarray) -> np.ndarray:
+    """Discrete Hilbert transform of real r along its last axis: the DFT
+    multiplier -j sgn(f), with f the signed frequency index and sgn = 0 at DC and,
+    for even lengths, at the Nyquist bin."""
+    r = np.asarray(r, dtype=np.float64)
+    M = r.shape[-1]
+    f = np.arange(M)
+    sgn = np.where((f > 0) & (2 * f < M), 1.0, np.where(2 * f > M, -1.0, 0.0))
+    return np.fft.ifft(-1j * sgn * np.fft.fft(r, axis=-1), axis=-1).real
+
+
+def conj_analytic(r: np.ndarray, d: int = 1) -> np.ndarray:
+    """A(r) = r - j d H(r) of Eq. back_model (d = +1 as printed, the conjugate
+    analytic signal; d = -1 its mirror for a descending wavenumber axis)."""
+    r = np.asarray(r, dtype=np.float64)
+    return r - 1j * d * hilbert(r)
+
+
+def k_increasing(g: Geom) -> bool:
+    return bool(g.k[-1] > g.k[0])
+
+
+def _hilbert_side(g: Geom) -> int:
+    return 1 if k_increasing(g) else -1
+
+
+def phi_adj_hilbert_exact(y: np.ndarray, mask: np.ndarray | None, g: Geom) -> np.ndarray:
+    """The paper's back-projection Phi*(y) = B^H A(s y) (Eq. back_model), direct sum."""
+    r = np.asarray(y, dtype=np.float64)
+    if mask is not None:
+        r = r * mask
+    return b_adj_exact(conj_analytic(r, _hilbert_side(g)), g)
+
+
+def phi_adj_hilbert_nufft(y: np.ndarray, mask: np.ndarray | None, g: Geom) -> np.ndarray:
+    """Phi*(y) = B^H A(s y) (Eq. back_model) with the KB NUFFT."""
+    r = np.asarray(y, dtype=np.float64)
+    if mask is not None:
+        r = r * mask
+    return b_adj_nufft(conj_analytic(r, _hilbert_side(g)), g)
+
+
+# ------------------------------------------------ literal Q and D of Eq. for_model
+
+def phi_qd(x: np.ndarray, mask: np.ndarray | None, g: Geom) -> np.ndarray:
+    """Phi x through the literal steps of Eq. for_model: per lateral frequency the
+    weighted depth profile is zero-padded to P = 2 nz (Q) and transformed by a
+    P-point DFT (D); the ISAM resampling (K) then reads the profile's spectrum at
+    theta = beta dz from those P samples by band-limited (Dirichlet) interpolation,
+        A(theta) = (1/P) sum_i S_i sum_{n<P} e^{j (2 pi i/P - theta) n},
+    which is exact because the profile vanishes on the padding.  The inner sum
+    is the closed-form geometric series."""
+    beta, _ = axial_beta(g)
+    H = system_filter(g)
+    w = depth_weight(g)
+    P = 2 * g.nz
+    X = np.fft.fft(np.asarray(x, dtype=np.complex128), axis=0) * w[None, :]
+    S = np.fft.fft(np.concatenate([X, np.zeros_like(X)], axis=1), axis=1)      # D Q
+    i = np.arange(P)
+    U = np.empty((g.nx, g.m), dtype=np.complex128)
+    for l in range(g.nx):
+        theta = beta[l] * g.dz
+        phi = 2.0 * np.pi * i[None, :] / P - theta[:, None]
+        den = 1.0 - np.exp(1j * phi)
+        num = 1.0 - np.exp(-1j * theta[:, None] * P)
+        on_grid = np.abs(den) < 1e-12
+        ker = np.where(on_grid, P, num / np.where(on_grid, 1.0, den))
+        U[l] = (ker @ S[l]) / P
+    U = U * np.exp(1j * beta * g.z_f)
+    y = np.fft.ifft(H * U, axis=0).real
+    return y if mask is None else y * mask
