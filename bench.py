@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32 / FP64 comparison")
     ap.add_argument("--no-tv", action="store_true", help="skip the TV-penalty solve")
+    ap.add_argument("--no-hilbert", action="store_true",
+                    help="skip the Hilbert-form back-projection (Phi*) measurements")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch choices (no mbir_plan_autotune before timing)")
     return ap.parse_args()
@@ -574,6 +576,53 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                   "roofline": {"bound": "hbm", "kernel": "tv_prox", "achieved": gbs, "peak": peak_gbs,
                                "unit": "GB/s", "frac": gbs / peak_gbs, "alg_bytes_per_prox": bpp * nx * nz}}
 
+    # the paper's back-projection Phi* = B^H A(s .) (Eq. back_model) on the same B-scan:
+    # Phi + Phi* pairs, a db4 solve with Phi* in the gradient, the Hilbert kernel
+    # against the HBM roof, and how far Phi* is from 2 Phi^H on these measurements
+    hil_res = None
+    if not args.no_hilbert:
+        xh = torch.empty_like(out)
+        plan.adjoint_hilbert(y, mask, out=xh)
+        e0.record(stream)
+        for _ in range(pairs):
+            plan.forward(out, mask, out=yb)
+            plan.adjoint_hilbert(yb, mask, out=xh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hpair_ms = e0.elapsed_time(e1) / pairs
+        plan.profile_begin(4096)
+        plan.profile_only("hilbert")
+        for _ in range(20):
+            plan.adjoint_hilbert(yb, mask, out=xh)
+        torch.cuda.synchronize()
+        n_h, h_ms = plan.profile_end()["hilbert"]
+        h_avg = h_ms / n_h
+        # y (4 B) and the mask (1 B) in, A(s y) (8 B) out, per sample
+        h_bytes = 13.0 * nx * m
+        peak_gbs = measured_peak()[0]
+        h_gbs = h_bytes / (h_avg * 1e-3) / 1e9
+        hil_kw = dict(penalty="db4", lam=LAMBDA_FRAC, relative=True, iters=ITERS, power_iters=POWER_ITERS,
+                      out=out, backprojection="hilbert")
+        plan.solve(y, mask, **hil_kw)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        t0.record(stream)
+        for _ in range(2):
+            plan.solve(y, mask, **hil_kw)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        hsolve_ms = t0.elapsed_time(t1) / 2
+        plan.adjoint_hilbert(clean, mask, out=xh)
+        plan.adjoint(clean, mask, out=xa)
+        gap = (torch.linalg.vector_norm(xh - 2 * xa) / torch.linalg.vector_norm(2 * xa)).item()
+        hil_res = {"workload": f"bscan-1024x2048-db4-{ITERS}it-half-ascans, Phi* in the gradient",
+                   "bscans_per_sec": 1e3 / hsolve_ms, "ms_per_solve": hsolve_ms,
+                   "pairs_per_sec": 1e3 / hpair_ms, "hilbert_ms": h_avg,
+                   "rel_gap_to_twice_transpose": gap,
+                   "roofline": {"bound": "hbm", "kernel": "hilbert", "achieved": h_gbs, "peak": peak_gbs,
+                                "unit": "GB/s", "frac": h_gbs / peak_gbs, "alg_bytes": h_bytes}}
+
     # end to end through host buffers: pinned inputs in, reconstruction out, each step
     y_host = y.cpu().pin_memory()
     m_host = mask.cpu().pin_memory()
@@ -651,6 +700,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
             "serve": serve,
             "precision": precision,
             "tv": tv_res,
+            "hilbert": hil_res,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),

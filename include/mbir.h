@@ -63,6 +63,11 @@ typedef enum { MBIR_FP32 = 0, MBIR_FP32_COMPENSATED = 1, MBIR_FP64 = 2 } mbir_pr
  * the prox entry points; the batch and serving paths take L1 and DB4 only). */
 typedef enum { MBIR_PENALTY_L1 = 0, MBIR_PENALTY_DB4 = 1, MBIR_PENALTY_TV = 2 } mbir_penalty;
 
+/* Back-projection used for the gradient (single-scan solves only):
+ * MBIR_BACKPROJ_TRANSPOSE  the exact transpose Phi^H of mbir_adjoint;
+ * MBIR_BACKPROJ_HILBERT    the paper's Phi* of mbir_adjoint_hilbert (Eq. back_model). */
+typedef enum { MBIR_BACKPROJ_TRANSPOSE = 0, MBIR_BACKPROJ_HILBERT = 1 } mbir_backprojection;
+
 /*
  * Optical geometry of one B-scan (Sec. 2.1).  Host memory; copied by
  * mbir_plan_create, so the caller may free it afterwards.
@@ -116,6 +121,11 @@ typedef struct {
  *  warm_start         != 0: start from the x passed in instead of 0.
  *  tv_iters           TV only: dual projected-gradient (FGP) steps per prox, from the
  *                     zero dual at every prox; <= 0 selects 20.
+ *  backprojection     mbir_backprojection of the gradient step.  With
+ *                     MBIR_BACKPROJ_HILBERT the step bound L is the power iteration's
+ *                     estimate for Phi* Phi and the relative lambda uses Phi*(s y);
+ *                     the spectrometer length m must then be a product of 2, 3, 5, 7
+ *                     and at most 8192 (else MBIR_ERR_UNSUPPORTED_SIZE).
  */
 typedef struct {
   int32_t penalty;
@@ -128,6 +138,7 @@ typedef struct {
   double step;
   int32_t warm_start;
   int32_t tv_iters;
+  int32_t backprojection;
 } mbir_solve_opts;
 
 /*
@@ -187,6 +198,22 @@ int mbir_forward(mbir_plan plan, const void* x, const uint8_t* mask, void* y, vo
 int mbir_adjoint(mbir_plan plan, const void* y, const uint8_t* mask, void* x, void* stream);
 
 /*
+ * x = Phi*(y) = K^H Q^T D^H diag(e^{-j Omega}) A(s y), the paper's back-projection
+ * (Sec. 2.1, Eq. back_model), with A(r) = r - j d H(r) the conjugate analytic
+ * signal along the spectrometer axis of each A-scan: H is the discrete Hilbert
+ * transform (DFT multiplier -j sgn(f), zero at DC and at the Nyquist bin), d = +1
+ * when the plan's wavenumbers increase with the pixel index (as printed) and
+ * d = -1 when they decrease (the side on which the model's e^{-j 2 k z} lies).
+ * The mask is applied before A.  On measurements whose A-scans are one-sided
+ * along m, Phi* = 2 Phi^H; in general the two differ (dispersion, edges).
+ * y: device [nx][m] real; x: device [nx][nz] complex, fully written.  Uses the
+ * plan's workspace; builds the m-point transform tables on the first call
+ * (synchronous then).  m must be a product of 2, 3, 5, 7 and at most 8192, else
+ * MBIR_ERR_UNSUPPORTED_SIZE.
+ */
+int mbir_adjoint_hilbert(mbir_plan plan, const void* y, const uint8_t* mask, void* x, void* stream);
+
+/*
  * FISTA (Eq. alg) from x^1 = z^0 = 0 (or the x passed in when warm_start),
  * t^1 = 1, for opts->max_iter iterations (or until rel_tol), writing z^k to x.
  * Allocates the iteration state on the first call for a given plan and keeps it.
@@ -204,8 +231,9 @@ int mbir_solve(mbir_plan plan, const void* y, const uint8_t* mask, const mbir_so
  * epilogues and the wavelet levels -- is one launch over all scans; the iteration
  * loop is captured into a CUDA graph and replayed when `stream` is a created
  * stream (not the legacy or per-thread default).  Each scan's result does not
- * depend on what it is batched with.  All opts[i].max_iter must be equal and
- * rel_tol must be 0 (fixed iteration count).  info (NULL or n entries) receives
+ * depend on what it is batched with.  All opts[i].max_iter must be equal,
+ * rel_tol must be 0 (fixed iteration count), the penalty l1 or db4 and the
+ * back-projection the transpose.  info (NULL or n entries) receives
  * iters, lipschitz, step and lambda_used; objective is not evaluated (NaN).
  * Synchronous at set-up (one read-back for the whole batch) and when info != NULL.
  */
@@ -224,7 +252,8 @@ int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const ui
  * copied to their x and their state freed.  Iterates, momentum, step size and the
  * objective history stay on the device.  A request's result does not depend on
  * the other requests it shared ticks with.  y, mask and x of a request must stay
- * valid until it is done.  Synchronous (each step waits for its work).
+ * valid until it is done.  Requests take the l1 or db4 penalty and the transpose
+ * back-projection.  Synchronous (each step waits for its work).
  */
 typedef struct mbir_server_s* mbir_server;
 

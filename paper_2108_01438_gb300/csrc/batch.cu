@@ -827,6 +827,7 @@ int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const ui
     const mbir_solve_opts& o = opts[i];
     if (!plans[i] || !y[i] || !x[i]) return MBIR_ERR_INVALID;
     if (o.max_iter < 1 || o.penalty < MBIR_PENALTY_L1 || o.penalty > MBIR_PENALTY_DB4) return MBIR_ERR_INVALID;
+    if (o.backprojection != MBIR_BACKPROJ_TRANSPOSE) return MBIR_ERR_INVALID;
     if (!(o.lambda >= 0) || !isfinite(o.lambda) || !isfinite(o.step) || o.rel_tol != 0.0) return MBIR_ERR_INVALID;
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return MBIR_ERR_INVALID;   // each plan once: its buffers are per scan

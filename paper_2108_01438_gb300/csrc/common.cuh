@@ -106,6 +106,7 @@ enum ProfClass {
   PC_REDUCE,          // reductions, scalars, power-iteration helpers
   PC_LAT_MID,         // inverse lateral FFT + measurement epilogue + lateral FFT (Phi^H Phi middle)
   PC_TV,              // TV prox: dual projected-gradient steps and the finishing pass
+  PC_HILBERT,         // conjugate analytic signal along the spectrometer axis
   PC_COUNT
 };
 
@@ -129,6 +130,7 @@ struct mbir_plan_s {
   int tile_c;                 // lateral FFT columns per CTA
   int lat_order;              // lateral radix order: 0 largest radix first, 1 smallest first
   int adj_kind;               // row adjoint kernel override (RowKind), -1: automatic
+  int k_ascending;            // wavenumbers increase with the spectrometer pixel index
   // device tables (one precision, per plan)
   void* tw_x;                 // nx-point twiddle tables [lo | hi]
   void* tw_k;                 // K-point twiddle tables [lo | hi]
@@ -151,6 +153,10 @@ struct mbir_plan_s {
   void* wv_coef;
   // TV prox scratch (lazily allocated): three dual fields [nx][nz] x 4 reals
   void* tv_p[3];
+  // m-point transform of the Hilbert-form back-projection (built on first use)
+  mbir::Radix rad_m;
+  void* tw_m;
+  int* perm_m;
   // reductions: partial sums
   double* red;                // kRedSlots doubles
   mbir::SolveState* solve;    // lazily created
@@ -317,6 +323,22 @@ int configure_wavelet_kernels(mbir_plan p);
 int apply_class_tuning(mbir_plan p);
 // plan.cu: radix plan of an n-point transform, radices at most max_radix
 bool plan_factor_radix(int n, Radix* r, int max_radix);
+
+// plan.cu: radix plan, [lo | hi] twiddles (plan precision) and digit-reversal
+// table of an n-point transform, uploaded; UNSUPPORTED_SIZE unless n is 7-smooth
+int plan_fft_tables(mbir_plan p, int n, Radix* rad, void** tw, int** perm);
+
+// hilbert.cu: c = A(s y) = s y - j d H(s y) along the spectrometer axis, c [nx][m]
+// complex (d = +1 for ascending wavenumbers); the tables are built on first use
+int hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* c, cudaStream_t st);
+int ensure_hilbert(mbir_plan p);
+// operator.cu: the paper's back-projection Phi*(y) = B^H A(s y), and its FISTA /
+// power-iteration passes (the residual is written to r, then A, then B^H)
+int adjoint_hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st);
+int forward_solve_hilbert_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
+                               double mu, double* partial, cudaStream_t st);
+int power_step_hilbert_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, void* r, const double* scal,
+                            double* part, cudaStream_t st);
 
 // tv.cu: z = prox_{tau TV}(v) by `iters` FGP steps; partial (may be null) receives
 // per-CTA sums of TV(z), tv_partial_count(p) of them

@@ -1330,6 +1330,88 @@ int power_step_t(mbir_plan p, const uint8_t* mask, void* w, void* v, const doubl
   return launch_lateral_args<R, LAT_POWER_ADJ>(p, b, p->nz, st);
 }
 
+// ------------------------------------------- Hilbert-form back-projection
+//
+// Phi*(y) = B^H A(s y) (Eq. back_model): A along the spectrometer axis into wsB,
+// then B^H of a complex array: the (1/nx) lateral FFT of wsB into wsA, the row
+// adjoint and the inverse lateral FFT.
+
+// c = A(s y) into wsB, R = (1/nx) lateral FFT of c into wsA
+template <class R>
+static int hilbert_lateral_t(mbir_plan p, const void* y, const uint8_t* mask, cudaStream_t st) {
+  int rc = hilbert_impl(p, y, mask, p->wsB, st);
+  if (rc) return rc;
+  return launch_lateral<R, LAT_C2C_FWD>(p, p->wsB, p->wsA, nullptr, p->m, R(1) / R(p->nx), st);
+}
+
+template <class R>
+int adjoint_hilbert_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
+  int rc = hilbert_lateral_t<R>(p, y, mask, st);
+  if (rc) return rc;
+  rc = launch_row<R>(p, true, p->wsA, p->wsB, st);
+  if (rc) return rc;
+  return launch_lateral<R, LAT_C2C_INV>(p, p->wsB, x, nullptr, p->nz, R(1), st);
+}
+
+// FISTA forward pass for Phi*: pz = Phi z^{k-1}, the data-term partials and the
+// residual r written out (the Hilbert transform runs along m, across the
+// lateral column tiles, so r leaves the chip), then A(r) and its lateral FFT
+// into wsA for adjoint_solve_impl.  r is zero where the mask is.
+template <class R>
+int forward_solve_hilbert_t(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
+                            double mu, double* partial, cudaStream_t st) {
+  int rc = launch_lateral<R, LAT_C2C_FWD>(p, z1, p->wsA, nullptr, p->nz, R(1), st);
+  if (rc) return rc;
+  rc = launch_row<R>(p, false, p->wsA, p->wsB, st);
+  if (rc) return rc;
+  LatArgs<R> a = lat_args<R>(p, p->wsB, nullptr, mask, p->m, R(1) / R(p->nx));
+  a.y = reinterpret_cast<const R*>(y);
+  a.pz = reinterpret_cast<R*>(pz);
+  a.r = reinterpret_cast<R*>(r);
+  a.mu = R(mu);
+  a.partial = partial;
+  rc = launch_lateral_args<R, LAT_SOLVE_FWD>(p, a, p->m, st);
+  if (rc) return rc;
+  return hilbert_lateral_t<R>(p, r, nullptr, st);
+}
+
+// Power-iteration step for Phi* Phi: v = w scal[1] (written), w = Phi*(s Phi v)
+// through the measurement buffer r, partial sums of <v, w> and ||w||^2.
+template <class R>
+int power_step_hilbert_t(mbir_plan p, const uint8_t* mask, void* w, void* v, void* r, const double* scal,
+                         double* part, cudaStream_t st) {
+  LatArgs<R> a = lat_args<R>(p, w, p->wsA, nullptr, p->nz, R(1));
+  a.vout = v;
+  a.scal = scal;
+  int rc = launch_lateral_args<R, LAT_POWER_FWD>(p, a, p->nz, st);
+  if (rc) return rc;
+  if ((rc = launch_row<R>(p, false, p->wsA, p->wsB, st))) return rc;
+  if ((rc = launch_lateral<R, LAT_C2R_INV_MASK>(p, p->wsB, r, mask, p->m, R(1) / R(p->nx), st))) return rc;
+  if ((rc = hilbert_lateral_t<R>(p, r, nullptr, st))) return rc;
+  if ((rc = launch_row<R>(p, true, p->wsA, p->wsB, st))) return rc;
+  LatArgs<R> b = lat_args<R>(p, p->wsB, w, nullptr, p->nz, R(1));
+  b.z1 = v;
+  b.partial = part;
+  return launch_lateral_args<R, LAT_POWER_ADJ>(p, b, p->nz, st);
+}
+
+int adjoint_hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? adjoint_hilbert_t<double>(p, y, mask, x, st)
+                                   : adjoint_hilbert_t<float>(p, y, mask, x, st);
+}
+
+int forward_solve_hilbert_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
+                               double mu, double* partial, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? forward_solve_hilbert_t<double>(p, z1, mask, y, pz, r, mu, partial, st)
+                                   : forward_solve_hilbert_t<float>(p, z1, mask, y, pz, r, mu, partial, st);
+}
+
+int power_step_hilbert_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, void* r, const double* scal,
+                            double* part, cudaStream_t st) {
+  return p->precision == MBIR_FP64 ? power_step_hilbert_t<double>(p, mask, w, v, r, scal, part, st)
+                                   : power_step_hilbert_t<float>(p, mask, w, v, r, scal, part, st);
+}
+
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
   return p->precision == MBIR_FP64 ? forward_t<double>(p, x, mask, y, st)
                                    : forward_t<float>(p, x, mask, y, st);
@@ -1461,6 +1543,12 @@ int mbir_adjoint(mbir_plan p, const void* y, const uint8_t* mask, void* x, void*
   const int rc = check_common(p, y, x);
   if (rc) return rc;
   return adjoint_impl(p, y, mask, x, (cudaStream_t)stream);
+}
+
+int mbir_adjoint_hilbert(mbir_plan p, const void* y, const uint8_t* mask, void* x, void* stream) {
+  const int rc = check_common(p, y, x);
+  if (rc) return rc;
+  return adjoint_hilbert_impl(p, y, mask, x, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -118,6 +118,33 @@ static bool factor_radix(int n, Radix* r, int max_radix = 16) {
 
 bool plan_factor_radix(int n, Radix* r, int max_radix) { return factor_radix(n, r, max_radix); }
 
+template <class V>
+static void make_twiddles(const Radix& rad, std::vector<V>& out);
+
+int plan_fft_tables(mbir_plan p, int n, Radix* rad, void** tw, int** perm) {
+  if (n < 1 || n > kMaxFFT || !factor_radix(n, rad, 8)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  std::vector<int> pr(n);
+  for (int i = 0; i < n; ++i) pr[i] = digit_reverse(i, *rad);
+  size_t bytes;
+  std::vector<double2> t64;
+  std::vector<float2> t32;
+  const void* src;
+  if (p->precision == MBIR_FP64) {
+    make_twiddles(*rad, t64);
+    bytes = sizeof(double2) * t64.size();
+    src = t64.data();
+  } else {
+    make_twiddles(*rad, t32);
+    bytes = sizeof(float2) * t32.size();
+    src = t32.data();
+  }
+  MBIR_CUDA_TRY(cudaMalloc(tw, bytes));
+  MBIR_CUDA_TRY(cudaMalloc(perm, sizeof(int) * n));
+  MBIR_CUDA_TRY(cudaMemcpy(*tw, src, bytes, cudaMemcpyHostToDevice));
+  MBIR_CUDA_TRY(cudaMemcpy(*perm, pr.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  return MBIR_OK;
+}
+
 // [lo | hi] twiddle tables of an n-point transform, w = e^{-2 pi j / n}, in FP64.
 template <class V>
 static void make_twiddles(const Radix& rad, std::vector<V>& out) {
@@ -422,7 +449,7 @@ const char* prof_class_name(int c) {
   static const char* names[PC_COUNT] = {"lateral_forward", "row_forward", "lateral_inverse_real",
                                         "lateral_residual", "row_adjoint", "lateral_adjoint",
                                         "dwt_analysis", "dwt_synthesis", "soft_threshold", "reduce",
-                                        "lateral_mid", "tv_prox"};
+                                        "lateral_mid", "tv_prox", "hilbert"};
   return (c >= 0 && c < PC_COUNT) ? names[c] : "unknown";
 }
 
@@ -555,6 +582,8 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaFree(p->wv_b2);
   cudaFree(p->wv_coef);
   for (void* q : p->tv_p) cudaFree(q);
+  cudaFree(p->tw_m);
+  cudaFree(p->perm_m);
   cudaFree(p->wsA);
   cudaFree(p->wsB);
   cudaFree(p->red);
@@ -589,6 +618,7 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
     p->dz = M_PI / (2.0 * g->nz * dkmax);
   }
   p->alpha = g->kb_alpha > 0 ? g->kb_alpha : 2.34 * g->kb_width;
+  p->k_ascending = g->m < 2 || g->k[g->m - 1] > g->k[0];
   factor_radix(p->nx, &p->rad_x, 8);
   factor_radix(p->K, &p->rad_k, 8);
   // lateral tile: keep nx * tile_c <= kLatElems elements, at most 16 columns

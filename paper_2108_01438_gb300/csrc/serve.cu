@@ -175,6 +175,7 @@ int mbir_server_submit(mbir_server srv, mbir_plan plan, const void* y, const uin
   if (!srv || !plan || !y || !o || !x || !ticket) return MBIR_ERR_INVALID;
   if (o->max_iter < 1 || o->min_iter < 0 || o->penalty < MBIR_PENALTY_L1 || o->penalty > MBIR_PENALTY_DB4)
     return MBIR_ERR_INVALID;
+  if (o->backprojection != MBIR_BACKPROJ_TRANSPOSE) return MBIR_ERR_INVALID;
   if (!(o->lambda >= 0) || !isfinite(o->lambda) || !isfinite(o->step) || !(o->rel_tol >= 0))
     return MBIR_ERR_INVALID;
   if (o->penalty == MBIR_PENALTY_DB4 && !wavelet_supported(plan->nx, plan->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;

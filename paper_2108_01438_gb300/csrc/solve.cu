@@ -12,6 +12,9 @@
 //   rest of the adjoint pass, epilogue: z^k = prox_{tau}(x^k - delta Phi^H r) with
 //     tau = lambda delta (l1 fused; the wavelet prox follows as its own kernels),
 //     and the partial sums of ||Psi z^k||_1.
+// With the paper's back-projection Phi* (Eq. back_model) in place of Phi^H, the
+// residual r is written out by the measurement pass and A(r) is formed along the
+// spectrometer axis before the lateral stage of B^H.
 // F(z^{k-1}) = data + lambda * reg is reduced on the device in a fixed order, so
 // the objective trace is deterministic.
 #include <math.h>
@@ -265,8 +268,10 @@ static int grid_for(size_t n) {
 // counter-based pseudo-random start w, then per step v = w/||w||, w = Phi^H s Phi v
 // and the Rayleigh quotient <v, w>.  The normalisation is folded into the first
 // lateral pass and the two reductions into the last one.
+// With the Hilbert-form back-projection the same iteration runs on Phi* s Phi.
 template <class R>
-static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out, cudaStream_t st) {
+static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out, cudaStream_t st,
+                       bool hilbert = false) {
   using V = cplx_t<R>;
   SolveState* s = p->solve;
   const size_t n = s->nimg;
@@ -279,7 +284,8 @@ static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out,
   MBIR_LAUNCH_CHECK();
   const int np = lateral_grid(p, p->nz);
   for (int it = 0; it < iters; ++it) {
-    int rc = power_step_impl(p, mask, w, v, s->scal, s->part_tmp, st);
+    int rc = hilbert ? power_step_hilbert_impl(p, mask, w, v, s->r, s->scal, s->part_tmp, st)
+                     : power_step_impl(p, mask, w, v, s->scal, s->part_tmp, st);
     if (rc) return rc;
     { ProfScope ps_(p, PC_REDUCE, st); launch(power_finalize_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, np, s->scal); }
     MBIR_LAUNCH_CHECK();
@@ -289,14 +295,14 @@ static int lipschitz_t(mbir_plan p, const uint8_t* mask, int iters, double* out,
   return MBIR_OK;
 }
 
-// max |Psi Phi^H (s y)|
+// max |Psi Phi^H (s y)| (Phi* in place of Phi^H for the Hilbert-form back-projection)
 template <class R>
 static int lambda_scale_t(mbir_plan p, const void* y, const uint8_t* mask, int penalty, double* out,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool hilbert = false) {
   using V = cplx_t<R>;
   SolveState* s = p->solve;
   const size_t n = s->nimg;
-  int rc = adjoint_impl(p, y, mask, s->zA, st);
+  int rc = hilbert ? adjoint_hilbert_impl(p, y, mask, s->zA, st) : adjoint_impl(p, y, mask, s->zA, st);
   if (rc) return rc;
   const V* src = (const V*)s->zA;
   if (penalty == MBIR_PENALTY_DB4) {
@@ -337,10 +343,11 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
                    mbir_solve_info* info, cudaStream_t st) {
   SolveState* s = p->solve;
   const size_t es = elem_size(p);
+  const bool hil = o->backprojection == MBIR_BACKPROJ_HILBERT;
   double L = 0.0, delta = o->step;
   if (!(delta > 0)) {
     const int pit = o->power_iters > 0 ? o->power_iters : 30;
-    int rc = lipschitz_t<R>(p, mask, pit, &L, st);
+    int rc = lipschitz_t<R>(p, mask, pit, &L, st, hil);
     if (rc) return rc;
     if (!(L > 0) || !isfinite(L)) return MBIR_ERR_INVALID;
     delta = 1.0 / (1.01 * L);
@@ -348,7 +355,7 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
   double lam = o->lambda;
   if (o->lambda_is_relative) {
     double m = 0.0;
-    int rc = lambda_scale_t<R>(p, y, mask, o->penalty, &m, st);
+    int rc = lambda_scale_t<R>(p, y, mask, o->penalty, &m, st, hil);
     if (rc) return rc;
     lam *= m;
   }
@@ -384,7 +391,8 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
   if (check) status = MBIR_ERR_NOT_CONVERGED;
   for (k = 1; k <= o->max_iter; ++k) {
     const double m = k >= 2 ? mu[k - 2] : 0.0;
-    int rc = forward_solve_impl(p, z1, mask, y, s->pz, m, s->part_data, st);
+    int rc = hil ? forward_solve_hilbert_impl(p, z1, mask, y, s->pz, s->r, m, s->part_data, st)
+                 : forward_solve_impl(p, z1, mask, y, s->pz, m, s->part_data, st);
     if (rc) return rc;
     if (want_trace) {
       ProfScope ps_(p, PC_REDUCE, st);
@@ -468,9 +476,15 @@ int mbir_solve(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve
     return MBIR_ERR_INVALID;
   if (!(o->lambda >= 0) || !isfinite(o->lambda) || !isfinite(o->step) || !(o->rel_tol >= 0))
     return MBIR_ERR_INVALID;
+  if (o->backprojection != MBIR_BACKPROJ_TRANSPOSE && o->backprojection != MBIR_BACKPROJ_HILBERT)
+    return MBIR_ERR_INVALID;
   if (o->penalty == MBIR_PENALTY_DB4 && !wavelet_supported(p->nx, p->nz)) return MBIR_ERR_UNSUPPORTED_SIZE;
   int rc = ensure_state(p, o->max_iter);
   if (rc) return rc;
+  if (o->backprojection == MBIR_BACKPROJ_HILBERT) {
+    rc = ensure_hilbert(p);
+    if (rc) return rc;
+  }
   if (o->penalty == MBIR_PENALTY_DB4) {
     rc = ensure_wavelet_scratch(p);
     if (rc) return rc;

@@ -20,6 +20,7 @@ FP32, FP32_COMPENSATED, FP64 = 0, 1, 2
 PENALTY_L1, PENALTY_DB4 = 0, 1
 PENALTY_TV = 2
 PENALTIES = {"l1": PENALTY_L1, "db4": PENALTY_DB4, "tv": PENALTY_TV}
+BACKPROJECTIONS = {"transpose": 0, "hilbert": 1}
 
 STATUS = {0: "MBIR_OK", -1: "MBIR_ERR_INVALID", -2: "MBIR_ERR_UNSUPPORTED_SIZE",
           -3: "MBIR_ERR_OOM", -4: "MBIR_ERR_CUDA", -5: "MBIR_ERR_TIMEOUT",
@@ -50,7 +51,7 @@ class SolveOpts(C.Structure):
         ("penalty", C.c_int32), ("lam", C.c_double), ("lambda_is_relative", C.c_int32),
         ("max_iter", C.c_int32), ("min_iter", C.c_int32), ("rel_tol", C.c_double),
         ("power_iters", C.c_int32), ("step", C.c_double), ("warm_start", C.c_int32),
-        ("tv_iters", C.c_int32),
+        ("tv_iters", C.c_int32), ("backprojection", C.c_int32),
     ]
 
 
@@ -81,6 +82,7 @@ _SIGNATURES = {
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mbir_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_adjoint_hilbert": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveOpts), C.c_void_p,
                              C.POINTER(SolveInfo), C.c_void_p]),
     "mbir_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
@@ -257,6 +259,18 @@ class Plan:
                "mbir_adjoint")
         return out
 
+    def adjoint_hilbert(self, y, mask=None, out=None, stream=None):
+        """The paper's back-projection Phi*(y) = B^H A(s y) (mbir_adjoint_hilbert)."""
+        import torch
+        self._meas(y, "y")
+        mask = self._mask(mask)
+        if out is None:
+            out = torch.empty((self.nx, self.nz), dtype=self.complex_dtype, device=y.device)
+        self._image(out, "out")
+        _check(lib().mbir_adjoint_hilbert(self._h, _ptr(y), _ptr(mask), _ptr(out), _stream_handle(stream)),
+               "mbir_adjoint_hilbert")
+        return out
+
     def autotune(self, reps: int = 5, stream=None) -> dict:
         """Time the candidate launch choices (mbir_plan_autotune); keep and return the fastest."""
         t, n = Tuning(), C.c_int32()
@@ -331,8 +345,10 @@ class Plan:
 
     def solve(self, y, mask=None, *, penalty: str = "l1", lam: float = 0.01, relative: bool = True,
               iters: int = 100, min_iter: int = 0, rel_tol: float = 0.0, power_iters: int = 30,
-              step: float = 0.0, x0=None, out=None, trace: bool = False, tv_iters: int = 0, stream=None):
-        """FISTA (mbir_solve).  Returns (x, info dict).  tv_iters: dual steps per TV prox (0: 20)."""
+              step: float = 0.0, x0=None, out=None, trace: bool = False, tv_iters: int = 0,
+              backprojection: str = "transpose", stream=None):
+        """FISTA (mbir_solve).  Returns (x, info dict).  tv_iters: dual steps per TV prox (0: 20);
+        backprojection: "transpose" (Phi^H) or "hilbert" (the paper's Phi*)."""
         import torch
         self._meas(y, "y")
         mask = self._mask(mask)
@@ -343,7 +359,8 @@ class Plan:
             out.copy_(x0)
         self._image(out, "out")
         o = SolveOpts(PENALTIES[penalty], float(lam), int(bool(relative)), int(iters), int(min_iter),
-                      float(rel_tol), int(power_iters), float(step), int(x0 is not None), int(tv_iters))
+                      float(rel_tol), int(power_iters), float(step), int(x0 is not None), int(tv_iters),
+                      BACKPROJECTIONS[backprojection])
         info = SolveInfo()
         tr = None
         if trace:
