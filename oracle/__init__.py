@@ -18,4 +18,6 @@ Modules:
               (Sec. 2.2-2.3, Eq. alg).
   tv       -- isotropic total variation (Sec. 2.2) and its prox by fast gradient
               projection on the dual.
+  evaluate -- the evaluation loop of Sec. 3: direct ISAM on interpolated
+              measurements, the NCC of Eq. ncc, the golden-section lambda search.
 """
