@@ -37,6 +37,7 @@ ITERS = 100
 POWER_ITERS = 30
 TV_ITERS = 20           # dual steps per TV prox (the library's default)
 LAMBDA_FRAC = 0.01
+EVAL_N = 8              # golden-section evaluations of the lambda search
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -54,6 +55,8 @@ def parse():
     ap.add_argument("--no-tv", action="store_true", help="skip the TV-penalty solve")
     ap.add_argument("--no-hilbert", action="store_true",
                     help="skip the Hilbert-form back-projection (Phi*) measurements")
+    ap.add_argument("--no-eval", action="store_true",
+                    help="skip the evaluation loop (interpolated ISAM, NCC, lambda search)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch choices (no mbir_plan_autotune before timing)")
     return ap.parse_args()
@@ -623,6 +626,36 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                    "roofline": {"bound": "hbm", "kernel": "hilbert", "achieved": h_gbs, "peak": peak_gbs,
                                 "unit": "GB/s", "frac": h_gbs / peak_gbs, "alg_bytes": h_bytes}}
 
+    # the evaluation loop of Sec. 3 on the same phantom with the paper's random
+    # pattern (half the spectrometer samples, Bernoulli): the interpolated-ISAM
+    # baseline, and MBIR with the lambda that a golden-section search finds best
+    eval_res = None
+    if not args.no_eval:
+        mask_r = torch.from_numpy(workloads.mask_bernoulli(nx, m, 0.5, 4242)).to(dev)
+        clean_r = plan.forward(x_true, mask_r)
+        sig_r = torch.sqrt(torch.mean(clean_r[mask_r == 1].double() ** 2)).item()
+        y_r = (clean_r + float(sig_r * 10 ** (-wl["snr_db"] / 20)) * noise * mask_r).contiguous()
+        base = plan.isam_interpolated(y_r, mask_r)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(20):
+            plan.isam_interpolated(y_r, mask_r, out=base)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        base_ms = t0.elapsed_time(t1) / 20
+        eval_res = {"workload": "bscan-1024x2048 beads, random half of the spectrometer samples, 25 dB",
+                    "isam_interpolated": {"ncc": plan.ncc(base, x_true), "ms": base_ms}}
+        for pen in ("db4", "tv"):
+            t_start = time.perf_counter()
+            _, info = plan.lambda_search(y_r, mask_r, x_true, lo=-3.0, hi=0.0, n_eval=EVAL_N, penalty=pen,
+                                         iters=ITERS, power_iters=POWER_ITERS, tv_iters=TV_ITERS)
+            wall = time.perf_counter() - t_start
+            eval_res["mbir_" + pen] = {"ncc": info["ncc"], "lambda_rel": info["lambda_rel"],
+                                       "evaluations": info["evaluations"], "search_s": wall,
+                                       "trace_lambda_rel": info["trace_lambda_rel"].tolist(),
+                                       "trace_ncc": info["trace_ncc"].tolist()}
+
     # end to end through host buffers: pinned inputs in, reconstruction out, each step
     y_host = y.cpu().pin_memory()
     m_host = mask.cpu().pin_memory()
@@ -701,6 +734,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
             "precision": precision,
             "tv": tv_res,
             "hilbert": hil_res,
+            "evaluation": eval_res,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),

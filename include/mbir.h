@@ -214,6 +214,55 @@ int mbir_adjoint(mbir_plan plan, const void* y, const uint8_t* mask, void* x, vo
 int mbir_adjoint_hilbert(mbir_plan plan, const void* y, const uint8_t* mask, void* x, void* stream);
 
 /*
+ * The paper's baseline (Sec. 3, "direct ISAM on linearly interpolated
+ * measurements"): every unmeasured sample of an A-scan is filled by linear
+ * interpolation in the spectrometer pixel index between the nearest measured
+ * samples on either side (the nearest measured value is held before the first and
+ * after the last one; an A-scan without a measured sample stays zero), then
+ * x = Phi*(y_interp) as in mbir_adjoint_hilbert with every sample counted as
+ * measured.  mask NULL: no interpolation.  Same layouts, sizes and errors as
+ * mbir_adjoint_hilbert (the interpolation needs twice its shared memory: FP64
+ * plans take m <= 4096).
+ */
+int mbir_isam_interpolated(mbir_plan plan, const void* y, const uint8_t* mask, void* x, void* stream);
+
+/*
+ * Normalised cross-correlation of magnitudes (Sec. 3, Eq. ncc):
+ *   r = sum (|x_i| - mean|x|)(|z_i| - mean|z|) / sqrt(sum (|x_i| - mean|x|)^2 sum (|z_i| - mean|z|)^2)
+ * over the plan's [nx][nz] images x and z (device, complex, plan precision).
+ * Two passes (means, then centred sums), FP64 accumulation in a fixed order.
+ * *r (host) is 0 when either image has constant magnitude.  Synchronous.
+ */
+int mbir_ncc(mbir_plan plan, const void* x, const void* z, double* r, void* stream);
+
+/*
+ * Golden-section search of the penalty weight (Sec. 3: lambda chosen to maximise
+ * the NCC with the ground truth).  t = log10 of the relative lambda (the weight is
+ * 10^t * max|Psi Phi^H(s y)|, or Phi* with MBIR_BACKPROJ_HILBERT) is searched in
+ * [log10_lo, log10_hi] with n_eval >= 2 evaluations: interior points
+ * c = b - g (b - a), d = a + g (b - a), g = (sqrt 5 - 1)/2; while evaluations
+ * remain, f(c) >= f(d) keeps [a, d], else [c, b]; one new point per step.  Each
+ * evaluation is an mbir_solve with opts (lambda and lambda_is_relative are
+ * replaced; the first evaluation derives the step when opts->step <= 0 and every
+ * later one reuses it) followed by mbir_ncc against z_true.  x (device [nx][nz])
+ * receives the reconstruction of the best evaluation (the first one on ties).
+ * Synchronous.  Allocates one image of scratch for the duration of the call.
+ */
+typedef struct {
+  double lambda_rel;         /* best 10^t */
+  double lambda;             /* absolute weight used there */
+  double ncc;                /* its NCC */
+  double step;               /* gradient step used by every evaluation */
+  int32_t evaluations;
+  double* trace_lambda_rel;  /* optional host [n_eval]: evaluated 10^t in order (NULL: not recorded) */
+  double* trace_ncc;         /* optional host [n_eval]: their NCC */
+} mbir_lambda_search_info;
+
+int mbir_lambda_search(mbir_plan plan, const void* y, const uint8_t* mask, const void* z_true,
+                       const mbir_solve_opts* opts, double log10_lo, double log10_hi, int32_t n_eval, void* x,
+                       mbir_lambda_search_info* info, void* stream);
+
+/*
  * FISTA (Eq. alg) from x^1 = z^0 = 0 (or the x passed in when warm_start),
  * t^1 = 1, for opts->max_iter iterations (or until rel_tol), writing z^k to x.
  * Allocates the iteration state on the first call for a given plan and keeps it.

@@ -157,6 +157,7 @@ struct mbir_plan_s {
   mbir::Radix rad_m;
   void* tw_m;
   int* perm_m;
+  double* ncc_scratch;        // NCC partial sums and scalars (lazily allocated)
   // reductions: partial sums
   double* red;                // kRedSlots doubles
   mbir::SolveState* solve;    // lazily created
@@ -329,16 +330,22 @@ bool plan_factor_radix(int n, Radix* r, int max_radix);
 int plan_fft_tables(mbir_plan p, int n, Radix* rad, void** tw, int** perm);
 
 // hilbert.cu: c = A(s y) = s y - j d H(s y) along the spectrometer axis, c [nx][m]
-// complex (d = +1 for ascending wavenumbers); the tables are built on first use
-int hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* c, cudaStream_t st);
+// complex (d = +1 for ascending wavenumbers); interp: the unmeasured samples are
+// first filled by linear interpolation (the baseline of Sec. 3); the tables are
+// built on first use
+int hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* c, cudaStream_t st, bool interp = false);
 int ensure_hilbert(mbir_plan p);
 // operator.cu: the paper's back-projection Phi*(y) = B^H A(s y), and its FISTA /
 // power-iteration passes (the residual is written to r, then A, then B^H)
-int adjoint_hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st);
+int adjoint_hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st,
+                         bool interp = false);
 int forward_solve_hilbert_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
                                double mu, double* partial, cudaStream_t st);
 int power_step_hilbert_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, void* r, const double* scal,
                             double* part, cudaStream_t st);
+
+// eval.cu: NCC of magnitudes of two [nx][nz] images (Eq. ncc), synchronous
+int ncc_impl(mbir_plan p, const void* x, const void* z, double* r, cudaStream_t st);
 
 // tv.cu: z = prox_{tau TV}(v) by `iters` FGP steps; partial (may be null) receives
 // per-CTA sums of TV(z), tv_partial_count(p) of them

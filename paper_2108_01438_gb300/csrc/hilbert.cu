@@ -11,6 +11,15 @@
 // dit (natural order out), so no reordering pass is needed.  HBM traffic per
 // sample: y and the mask in (5 bytes in FP32), c out (8 bytes); the measurements
 // are read a second time for the real part, from L2.
+//
+// The interpolating variant (the baseline of Sec. 3, direct ISAM on linearly
+// interpolated measurements) first fills every unmeasured sample from the nearest
+// measured ones on either side, in the pixel index.  Thread t owns a contiguous
+// chunk of the row: it finds the last and first measured sample of its chunk,
+// a block-wide max-scan (min-scan) of those gives the last measured sample
+// before (first after) the chunk, a forward walk records each sample's previous
+// measured index, and a backward walk interpolates.  Both rows of the CTA are
+// handled at once (int2 indices); the filled rows are kept for the real part.
 #include <math.h>
 
 #include "common.cuh"
@@ -21,7 +30,80 @@ namespace mbir {
 
 constexpr int kHilThreads = 256;
 
+// Linear interpolation at i between the measured samples p < i < n of one row
+// (lane 0: the .x component of s, lane 1: .y); p < 0 or n >= m: hold the other
+// end, neither: zero.
+template <class R, class V>
+__device__ __forceinline__ R interp_at(const V* s, bool on, int lane, int i, int p, int n, int m) {
+  auto val = [&](int j) { const V v = s[swz(j, on)]; return lane == 0 ? v.x : v.y; };
+  if (p < 0) return n < m ? val(n) : R(0);
+  if (n >= m) return val(p);
+  const R yp = val(p), yn = val(n);
+  return yp + (yn - yp) * (R(i - p) / R(n - p));
+}
+
+// Fill the unmeasured samples of the two staged rows in s (flags in M: bit 0 row
+// a measured, bit 1 row b) into Q, which first holds each sample's previous
+// measured indices; scan: 2 * blockDim.x int2.
 template <class R>
+__device__ void interp_rows(const cplx_t<R>* s, cplx_t<R>* Q, const uint8_t* M, int2* scan, int m, bool on) {
+  using V = cplx_t<R>;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int chunk = (m + T - 1) / T;
+  const int c0 = min(m, t * chunk), c1 = min(m, c0 + chunk);
+  int2 last = make_int2(-1, -1), first = make_int2(m, m);
+  for (int i = c0; i < c1; ++i) {
+    const int f = M[i];
+    if (f & 1) {
+      last.x = i;
+      first.x = min(first.x, i);
+    }
+    if (f & 2) {
+      last.y = i;
+      first.y = min(first.y, i);
+    }
+  }
+  int2* smax = scan;
+  int2* smin = scan + T;
+  smax[t] = last;
+  smin[t] = first;
+  __syncthreads();
+  for (int off = 1; off < T; off <<= 1) {   // inclusive scans, Hillis-Steele
+    int2 a = smax[t], b = smin[t];
+    if (t >= off) {
+      const int2 o = smax[t - off];
+      a = make_int2(max(a.x, o.x), max(a.y, o.y));
+    }
+    if (t + off < T) {
+      const int2 o = smin[t + off];
+      b = make_int2(min(b.x, o.x), min(b.y, o.y));
+    }
+    __syncthreads();
+    smax[t] = a;
+    smin[t] = b;
+    __syncthreads();
+  }
+  int2 prev = t > 0 ? smax[t - 1] : make_int2(-1, -1);
+  int2 next = t + 1 < T ? smin[t + 1] : make_int2(m, m);
+  for (int i = c0; i < c1; ++i) {
+    const int f = M[i];
+    if (f & 1) prev.x = i;
+    if (f & 2) prev.y = i;
+    *reinterpret_cast<int2*>(Q + i) = prev;
+  }
+  for (int i = c1 - 1; i >= c0; --i) {
+    const int f = M[i];
+    if (f & 1) next.x = i;
+    if (f & 2) next.y = i;
+    const int2 pv = *reinterpret_cast<const int2*>(Q + i);
+    const V cur = s[swz(i, on)];
+    const R va = (f & 1) ? cur.x : interp_at<R>(s, on, 0, i, pv.x, next.x, m);
+    const R vb = (f & 2) ? cur.y : interp_at<R>(s, on, 1, i, pv.y, next.y, m);
+    Q[i] = cmk<V>(va, vb);
+  }
+}
+
+template <class R, bool INTERP>
 __global__ void __launch_bounds__(kHilThreads)
     hilbert_kernel(const R* __restrict__ y, const uint8_t* __restrict__ mask, cplx_t<R>* __restrict__ c, int nx,
                    int m, Radix rad, const cplx_t<R>* __restrict__ twg, const int* __restrict__ perm, R side,
@@ -30,6 +112,11 @@ __global__ void __launch_bounds__(kHilThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s = reinterpret_cast<V*>(smem_raw);
   const Tw2<V> tw = load_twiddles(s + m, twg, rad);
+  // interpolating variant: Q [m] (indices, then the filled rows), scan, flags
+  V* Q = s + m + rad.tw_lo + rad.tw_hi;
+  int2* scan = reinterpret_cast<int2*>(Q + m);
+  uint8_t* M = reinterpret_cast<uint8_t*>(scan + 2 * blockDim.x);
+  const bool interp = INTERP && mask != nullptr;
   const bool on = sw != 0;
   const int pa = 2 * blockIdx.x;
   const bool hb = pa + 1 < nx;
@@ -39,12 +126,20 @@ __global__ void __launch_bounds__(kHilThreads)
     R a = y[oa + i];
     R b = hb ? y[ob + i] : R(0);
     if (mask) {
-      if (!mask[oa + i]) a = R(0);
-      if (hb && !mask[ob + i]) b = R(0);
+      const bool ma = mask[oa + i] != 0, mb = hb && mask[ob + i] != 0;
+      if (!ma) a = R(0);
+      if (!mb) b = R(0);
+      if (interp) M[i] = (uint8_t)((ma ? 1 : 0) | (mb ? 2 : 0));
     }
     s[swz(i, on)] = cmk<V>(a, b);
   }
   __syncthreads();
+  if (interp) {
+    interp_rows<R>(s, Q, M, scan, m, on);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s[swz(i, on)] = Q[i];
+    __syncthreads();
+  }
   fft_dif<false>(s, 1, rad, tw, on);
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
     const int q = swz(perm[k], on);
@@ -57,20 +152,29 @@ __global__ void __launch_bounds__(kHilThreads)
   const R f = -side / R(m);   // the inverse transform is unnormalised
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const V h = s[swz(i, on)];
-    R a = y[oa + i];
-    R b = hb ? y[ob + i] : R(0);
-    if (mask) {
-      if (!mask[oa + i]) a = R(0);
-      if (hb && !mask[ob + i]) b = R(0);
+    R a, b;
+    if (interp) {
+      a = Q[i].x;
+      b = Q[i].y;
+    } else {
+      a = y[oa + i];
+      b = hb ? y[ob + i] : R(0);
+      if (mask) {
+        if (!mask[oa + i]) a = R(0);
+        if (hb && !mask[ob + i]) b = R(0);
+      }
     }
     c[oa + i] = cmk<V>(a, f * h.x);
     if (hb) c[ob + i] = cmk<V>(b, f * h.y);
   }
 }
 
-template <class R>
-static size_t hilbert_smem(mbir_plan p) {
-  return sizeof(cplx_t<R>) * ((size_t)p->m + p->rad_m.tw_lo + p->rad_m.tw_hi);
+// bytes of dynamic shared memory: s and the twiddles, plus Q, the scan and the
+// flags for the interpolating variant
+static size_t hilbert_smem_bytes(size_t es, int m, const Radix& r, bool interp) {
+  size_t b = es * ((size_t)m + r.tw_lo + r.tw_hi);
+  if (interp) b += es * (size_t)m + 2 * sizeof(int2) * kHilThreads + (size_t)m;
+  return b;
 }
 
 int ensure_hilbert(mbir_plan p) {
@@ -78,8 +182,7 @@ int ensure_hilbert(mbir_plan p) {
   Radix r;
   if (p->m > kMaxFFT || !plan_factor_radix(p->m, &r, 8)) return MBIR_ERR_UNSUPPORTED_SIZE;
   const size_t es = p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
-  const size_t smem = es * ((size_t)p->m + r.tw_lo + r.tw_hi);
-  if (smem > (size_t)kMaxDynSmem) return MBIR_ERR_UNSUPPORTED_SIZE;
+  if (hilbert_smem_bytes(es, p->m, r, false) > (size_t)kMaxDynSmem) return MBIR_ERR_UNSUPPORTED_SIZE;
   int rc = plan_fft_tables(p, p->m, &p->rad_m, &p->tw_m, &p->perm_m);
   if (rc) {
     cudaFree(p->tw_m);
@@ -89,20 +192,29 @@ int ensure_hilbert(mbir_plan p) {
     return rc;
   }
   // the cap, not this plan's size: plans of other lengths share the kernel
-  if (p->precision == MBIR_FP64)
-    MBIR_CUDA_TRY(cudaFuncSetAttribute(hilbert_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-  else
-    MBIR_CUDA_TRY(cudaFuncSetAttribute(hilbert_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+#define MBIR_HIL_ATTR(fn) MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem))
+  if (p->precision == MBIR_FP64) {
+    MBIR_HIL_ATTR((hilbert_kernel<double, false>));
+    MBIR_HIL_ATTR((hilbert_kernel<double, true>));
+  } else {
+    MBIR_HIL_ATTR((hilbert_kernel<float, false>));
+    MBIR_HIL_ATTR((hilbert_kernel<float, true>));
+  }
+#undef MBIR_HIL_ATTR
   return MBIR_OK;
 }
 
 template <class R>
-static int hilbert_t(mbir_plan p, const void* y, const uint8_t* mask, void* c, cudaStream_t st) {
+static int hilbert_t(mbir_plan p, const void* y, const uint8_t* mask, void* c, bool interp, cudaStream_t st) {
   const int grid = (p->nx + 1) / 2;
   const R side = p->k_ascending ? R(1) : R(-1);
+  const bool iv = interp && mask != nullptr;
+  const size_t smem = hilbert_smem_bytes(sizeof(cplx_t<R>), p->m, p->rad_m, iv);
+  if (smem > (size_t)kMaxDynSmem) return MBIR_ERR_UNSUPPORTED_SIZE;
   {
     ProfScope ps_(p, PC_HILBERT, st);
-    launch(hilbert_kernel<R>, dim3(grid), dim3(kHilThreads), hilbert_smem<R>(p), st, static_cast<const R*>(y), mask,
+    auto kernel = iv ? hilbert_kernel<R, true> : hilbert_kernel<R, false>;
+    launch(kernel, dim3(grid), dim3(kHilThreads), smem, st, static_cast<const R*>(y), mask,
            static_cast<cplx_t<R>*>(c), p->nx, p->m, p->rad_m, static_cast<const cplx_t<R>*>(p->tw_m),
            (const int*)p->perm_m, side, (p->m & 15) == 0 ? 1 : 0);
   }
@@ -110,10 +222,11 @@ static int hilbert_t(mbir_plan p, const void* y, const uint8_t* mask, void* c, c
   return MBIR_OK;
 }
 
-int hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* c, cudaStream_t st) {
+int hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* c, cudaStream_t st, bool interp) {
   int rc = ensure_hilbert(p);
   if (rc) return rc;
-  return p->precision == MBIR_FP64 ? hilbert_t<double>(p, y, mask, c, st) : hilbert_t<float>(p, y, mask, c, st);
+  return p->precision == MBIR_FP64 ? hilbert_t<double>(p, y, mask, c, interp, st)
+                                   : hilbert_t<float>(p, y, mask, c, interp, st);
 }
 
 }  // namespace mbir

@@ -1336,17 +1336,18 @@ int power_step_t(mbir_plan p, const uint8_t* mask, void* w, void* v, const doubl
 // then B^H of a complex array: the (1/nx) lateral FFT of wsB into wsA, the row
 // adjoint and the inverse lateral FFT.
 
-// c = A(s y) into wsB, R = (1/nx) lateral FFT of c into wsA
+// c = A(s y) into wsB (interp: unmeasured samples filled first), R = (1/nx)
+// lateral FFT of c into wsA
 template <class R>
-static int hilbert_lateral_t(mbir_plan p, const void* y, const uint8_t* mask, cudaStream_t st) {
-  int rc = hilbert_impl(p, y, mask, p->wsB, st);
+static int hilbert_lateral_t(mbir_plan p, const void* y, const uint8_t* mask, cudaStream_t st, bool interp = false) {
+  int rc = hilbert_impl(p, y, mask, p->wsB, st, interp);
   if (rc) return rc;
   return launch_lateral<R, LAT_C2C_FWD>(p, p->wsB, p->wsA, nullptr, p->m, R(1) / R(p->nx), st);
 }
 
 template <class R>
-int adjoint_hilbert_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
-  int rc = hilbert_lateral_t<R>(p, y, mask, st);
+int adjoint_hilbert_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st, bool interp) {
+  int rc = hilbert_lateral_t<R>(p, y, mask, st, interp);
   if (rc) return rc;
   rc = launch_row<R>(p, true, p->wsA, p->wsB, st);
   if (rc) return rc;
@@ -1395,9 +1396,9 @@ int power_step_hilbert_t(mbir_plan p, const uint8_t* mask, void* w, void* v, voi
   return launch_lateral_args<R, LAT_POWER_ADJ>(p, b, p->nz, st);
 }
 
-int adjoint_hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
-  return p->precision == MBIR_FP64 ? adjoint_hilbert_t<double>(p, y, mask, x, st)
-                                   : adjoint_hilbert_t<float>(p, y, mask, x, st);
+int adjoint_hilbert_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st, bool interp) {
+  return p->precision == MBIR_FP64 ? adjoint_hilbert_t<double>(p, y, mask, x, st, interp)
+                                   : adjoint_hilbert_t<float>(p, y, mask, x, st, interp);
 }
 
 int forward_solve_hilbert_impl(mbir_plan p, const void* z1, const uint8_t* mask, const void* y, void* pz, void* r,
@@ -1549,6 +1550,12 @@ int mbir_adjoint_hilbert(mbir_plan p, const void* y, const uint8_t* mask, void* 
   const int rc = check_common(p, y, x);
   if (rc) return rc;
   return adjoint_hilbert_impl(p, y, mask, x, (cudaStream_t)stream);
+}
+
+int mbir_isam_interpolated(mbir_plan p, const void* y, const uint8_t* mask, void* x, void* stream) {
+  const int rc = check_common(p, y, x);
+  if (rc) return rc;
+  return adjoint_hilbert_impl(p, y, mask, x, (cudaStream_t)stream, true);
 }
 
 }  // extern "C"

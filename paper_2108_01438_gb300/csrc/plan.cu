@@ -584,6 +584,7 @@ void mbir_plan_destroy(mbir_plan p) {
   for (void* q : p->tv_p) cudaFree(q);
   cudaFree(p->tw_m);
   cudaFree(p->perm_m);
+  cudaFree(p->ncc_scratch);
   cudaFree(p->wsA);
   cudaFree(p->wsB);
   cudaFree(p->red);

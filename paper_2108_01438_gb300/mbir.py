@@ -55,6 +55,14 @@ class SolveOpts(C.Structure):
     ]
 
 
+class LambdaSearchInfo(C.Structure):
+    _fields_ = [
+        ("lambda_rel", C.c_double), ("lam", C.c_double), ("ncc", C.c_double), ("step", C.c_double),
+        ("evaluations", C.c_int32), ("trace_lambda_rel", C.POINTER(C.c_double)),
+        ("trace_ncc", C.POINTER(C.c_double)),
+    ]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [
         ("iters", C.c_int32), ("status", C.c_int32), ("objective", C.c_double),
@@ -83,6 +91,11 @@ _SIGNATURES = {
     "mbir_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mbir_adjoint_hilbert": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_isam_interpolated": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mbir_ncc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "mbir_lambda_search": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                     C.POINTER(LambdaSearchInfo), C.c_void_p]),
     "mbir_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveOpts), C.c_void_p,
                              C.POINTER(SolveInfo), C.c_void_p]),
     "mbir_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
@@ -270,6 +283,52 @@ class Plan:
         _check(lib().mbir_adjoint_hilbert(self._h, _ptr(y), _ptr(mask), _ptr(out), _stream_handle(stream)),
                "mbir_adjoint_hilbert")
         return out
+
+    def isam_interpolated(self, y, mask=None, out=None, stream=None):
+        """The direct-ISAM baseline on linearly interpolated measurements (mbir_isam_interpolated)."""
+        import torch
+        self._meas(y, "y")
+        mask = self._mask(mask)
+        if out is None:
+            out = torch.empty((self.nx, self.nz), dtype=self.complex_dtype, device=y.device)
+        self._image(out, "out")
+        _check(lib().mbir_isam_interpolated(self._h, _ptr(y), _ptr(mask), _ptr(out), _stream_handle(stream)),
+               "mbir_isam_interpolated")
+        return out
+
+    def ncc(self, x, z, stream=None) -> float:
+        """NCC of magnitudes (Eq. ncc) of two images of the plan (mbir_ncc)."""
+        self._image(x, "x")
+        self._image(z, "z")
+        r = C.c_double()
+        _check(lib().mbir_ncc(self._h, _ptr(x), _ptr(z), C.byref(r), _stream_handle(stream)), "mbir_ncc")
+        return r.value
+
+    def lambda_search(self, y, mask, z_true, *, lo: float = -4.0, hi: float = 0.0, n_eval: int = 10,
+                      penalty: str = "db4", iters: int = 100, power_iters: int = 30, step: float = 0.0,
+                      tv_iters: int = 0, backprojection: str = "transpose", out=None, stream=None):
+        """Golden-section search of log10(relative lambda) in [lo, hi] maximising the NCC with
+        z_true (mbir_lambda_search).  Returns (best x, info dict with the evaluation trace)."""
+        import torch
+        self._meas(y, "y")
+        mask = self._mask(mask)
+        self._image(z_true, "z_true")
+        if out is None:
+            out = torch.empty((self.nx, self.nz), dtype=self.complex_dtype, device=y.device)
+        self._image(out, "out")
+        o = SolveOpts(PENALTIES[penalty], 0.0, 1, int(iters), 0, 0.0, int(power_iters), float(step), 0,
+                      int(tv_iters), BACKPROJECTIONS[backprojection])
+        tl = (C.c_double * n_eval)()
+        tn = (C.c_double * n_eval)()
+        info = LambdaSearchInfo()
+        info.trace_lambda_rel = C.cast(tl, C.POINTER(C.c_double))
+        info.trace_ncc = C.cast(tn, C.POINTER(C.c_double))
+        _check(lib().mbir_lambda_search(self._h, _ptr(y), _ptr(mask), _ptr(z_true), C.byref(o), float(lo),
+                                        float(hi), int(n_eval), _ptr(out), C.byref(info),
+                                        _stream_handle(stream)), "mbir_lambda_search")
+        n = info.evaluations
+        return out, dict(lambda_rel=info.lambda_rel, lam=info.lam, ncc=info.ncc, step=info.step,
+                         evaluations=n, trace_lambda_rel=np.array(tl[:n]), trace_ncc=np.array(tn[:n]))
 
     def autotune(self, reps: int = 5, stream=None) -> dict:
         """Time the candidate launch choices (mbir_plan_autotune); keep and return the fastest."""
