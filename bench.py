@@ -37,7 +37,8 @@ ITERS = 100
 POWER_ITERS = 30
 TV_ITERS = 20           # dual steps per TV prox (the library's default)
 LAMBDA_FRAC = 0.01
-EVAL_N = 8              # golden-section evaluations of the lambda search
+EVAL_N = 10             # golden-section evaluations of the lambda search
+EVAL_LO, EVAL_HI = -5.0, -1.0   # its bracket of log10(relative lambda)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -648,7 +649,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                     "isam_interpolated": {"ncc": plan.ncc(base, x_true), "ms": base_ms}}
         for pen in ("db4", "tv"):
             t_start = time.perf_counter()
-            _, info = plan.lambda_search(y_r, mask_r, x_true, lo=-3.0, hi=0.0, n_eval=EVAL_N, penalty=pen,
+            _, info = plan.lambda_search(y_r, mask_r, x_true, lo=EVAL_LO, hi=EVAL_HI, n_eval=EVAL_N, penalty=pen,
                                          iters=ITERS, power_iters=POWER_ITERS, tv_iters=TV_ITERS)
             wall = time.perf_counter() - t_start
             eval_res["mbir_" + pen] = {"ncc": info["ncc"], "lambda_rel": info["lambda_rel"],

@@ -29,6 +29,11 @@
 namespace mbir {
 
 constexpr int kHilThreads = 256;
+// resident CTAs an SM for FP32 (the launch-bounds register cap): four fit the
+// 1024 x 2048 B-scan's 512 row pairs in one wave on 152 SMs
+#ifndef MBIR_HIL_MINB
+#define MBIR_HIL_MINB 4
+#endif
 
 // Linear interpolation at i between the measured samples p < i < n of one row
 // (lane 0: the .x component of s, lane 1: .y); p < 0 or n >= m: hold the other
@@ -103,35 +108,80 @@ __device__ void interp_rows(const cplx_t<R>* s, cplx_t<R>* Q, const uint8_t* M, 
   }
 }
 
+// Shared-memory layout (bytes): the row pair s [m], the twiddles, the
+// digit-reversal table [m], then for the interpolating variant Q [m], the scans
+// and the flags.
+struct HilLayout {
+  size_t tw, perm, q, scan, flags, total;
+};
+__host__ __device__ inline HilLayout hil_layout(size_t es, int m, int tw_n, int threads, bool interp) {
+  HilLayout L;
+  L.tw = es * (size_t)m;
+  L.perm = L.tw + es * (size_t)tw_n;
+  L.q = (L.perm + sizeof(int) * (size_t)m + 15) & ~size_t(15);
+  L.scan = L.q + (interp ? es * (size_t)m : 0);
+  L.flags = L.scan + (interp ? 2 * sizeof(int2) * (size_t)threads : 0);
+  L.total = L.flags + (interp ? (size_t)m : 0);
+  return L;
+}
+
+// vec (FP32 only, m % 4 == 0, 16-byte aligned rows): four samples per access.
 template <class R, bool INTERP>
-__global__ void __launch_bounds__(kHilThreads)
+__global__ void __launch_bounds__(kHilThreads, sizeof(R) == 4 ? MBIR_HIL_MINB : 2)
     hilbert_kernel(const R* __restrict__ y, const uint8_t* __restrict__ mask, cplx_t<R>* __restrict__ c, int nx,
                    int m, Radix rad, const cplx_t<R>* __restrict__ twg, const int* __restrict__ perm, R side,
-                   int sw) {
+                   int sw, int vec) {
   using V = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const HilLayout L = hil_layout(sizeof(V), m, rad.tw_lo + rad.tw_hi, blockDim.x, INTERP);
   V* s = reinterpret_cast<V*>(smem_raw);
-  const Tw2<V> tw = load_twiddles(s + m, twg, rad);
+  const Tw2<V> tw = load_twiddles(reinterpret_cast<V*>(smem_raw + L.tw), twg, rad);
+  int* sperm = reinterpret_cast<int*>(smem_raw + L.perm);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) sperm[i] = perm[i];
   // interpolating variant: Q [m] (indices, then the filled rows), scan, flags
-  V* Q = s + m + rad.tw_lo + rad.tw_hi;
-  int2* scan = reinterpret_cast<int2*>(Q + m);
-  uint8_t* M = reinterpret_cast<uint8_t*>(scan + 2 * blockDim.x);
+  V* Q = reinterpret_cast<V*>(smem_raw + L.q);
+  int2* scan = reinterpret_cast<int2*>(smem_raw + L.scan);
+  uint8_t* M = smem_raw + L.flags;
   const bool interp = INTERP && mask != nullptr;
   const bool on = sw != 0;
   const int pa = 2 * blockIdx.x;
   const bool hb = pa + 1 < nx;
   const size_t oa = (size_t)pa * m, ob = oa + m;
   pdl_wait_release();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    R a = y[oa + i];
-    R b = hb ? y[ob + i] : R(0);
-    if (mask) {
-      const bool ma = mask[oa + i] != 0, mb = hb && mask[ob + i] != 0;
-      if (!ma) a = R(0);
-      if (!mb) b = R(0);
-      if (interp) M[i] = (uint8_t)((ma ? 1 : 0) | (mb ? 2 : 0));
-    }
+  // one sample of both rows: mask, flags, staging
+  auto stage = [&](int i, R a, R b, bool ma, bool mb) {
+    if (!ma) a = R(0);
+    if (!mb) b = R(0);
+    if (interp) M[i] = (uint8_t)((ma ? 1 : 0) | (mb ? 2 : 0));
     s[swz(i, on)] = cmk<V>(a, b);
+  };
+  bool done = false;
+  if constexpr (sizeof(R) == 4) {
+    if (vec) {
+      for (int i = 4 * threadIdx.x; i < m; i += 4 * blockDim.x) {
+        const float4 a4 = *reinterpret_cast<const float4*>(y + oa + i);
+        const float4 b4 = hb ? *reinterpret_cast<const float4*>(y + ob + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        uchar4 ma = make_uchar4(1, 1, 1, 1), mb = hb ? ma : make_uchar4(0, 0, 0, 0);
+        if (mask) {
+          ma = *reinterpret_cast<const uchar4*>(mask + oa + i);
+          if (hb) mb = *reinterpret_cast<const uchar4*>(mask + ob + i);
+        }
+        stage(i, a4.x, b4.x, ma.x != 0, mb.x != 0);
+        stage(i + 1, a4.y, b4.y, ma.y != 0, mb.y != 0);
+        stage(i + 2, a4.z, b4.z, ma.z != 0, mb.z != 0);
+        stage(i + 3, a4.w, b4.w, ma.w != 0, mb.w != 0);
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const R a = y[oa + i];
+      const R b = hb ? y[ob + i] : R(0);
+      const bool ma = !mask || mask[oa + i] != 0;
+      const bool mb = hb && (!mask || mask[ob + i] != 0);
+      stage(i, a, b, ma, mb);
+    }
   }
   __syncthreads();
   if (interp) {
@@ -142,7 +192,7 @@ __global__ void __launch_bounds__(kHilThreads)
   }
   fft_dif<false>(s, 1, rad, tw, on);
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    const int q = swz(perm[k], on);
+    const int q = swz(sperm[k], on);
     const V v = s[q];
     const R g = (k == 0 || 2 * k == m) ? R(0) : (2 * k < m ? R(1) : R(-1));
     s[q] = cmk<V>(g * v.y, -g * v.x);   // -j g (v.x + j v.y)
@@ -150,9 +200,8 @@ __global__ void __launch_bounds__(kHilThreads)
   __syncthreads();
   fft_dit<true>(s, 1, rad, tw, on);
   const R f = -side / R(m);   // the inverse transform is unnormalised
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const V h = s[swz(i, on)];
-    R a, b;
+  // the real part of one sample of both rows: the filled rows, or y again (L2)
+  auto real_part = [&](int i, R& a, R& b) {
     if (interp) {
       a = Q[i].x;
       b = Q[i].y;
@@ -164,17 +213,41 @@ __global__ void __launch_bounds__(kHilThreads)
         if (hb && !mask[ob + i]) b = R(0);
       }
     }
+  };
+  if constexpr (sizeof(R) == 4) {
+    if (vec) {
+      for (int i = 4 * threadIdx.x; i < m; i += 4 * blockDim.x) {
+        float a[4], b[4], ha[4], hbv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          real_part(i + j, a[j], b[j]);
+          const V h = s[swz(i + j, on)];
+          ha[j] = f * h.x;
+          hbv[j] = f * h.y;
+        }
+        float4* ca = reinterpret_cast<float4*>(c + oa + i);
+        ca[0] = make_float4(a[0], ha[0], a[1], ha[1]);
+        ca[1] = make_float4(a[2], ha[2], a[3], ha[3]);
+        if (hb) {
+          float4* cb = reinterpret_cast<float4*>(c + ob + i);
+          cb[0] = make_float4(b[0], hbv[0], b[1], hbv[1]);
+          cb[1] = make_float4(b[2], hbv[2], b[3], hbv[3]);
+        }
+      }
+      return;
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const V h = s[swz(i, on)];
+    R a, b;
+    real_part(i, a, b);
     c[oa + i] = cmk<V>(a, f * h.x);
     if (hb) c[ob + i] = cmk<V>(b, f * h.y);
   }
 }
 
-// bytes of dynamic shared memory: s and the twiddles, plus Q, the scan and the
-// flags for the interpolating variant
 static size_t hilbert_smem_bytes(size_t es, int m, const Radix& r, bool interp) {
-  size_t b = es * ((size_t)m + r.tw_lo + r.tw_hi);
-  if (interp) b += es * (size_t)m + 2 * sizeof(int2) * kHilThreads + (size_t)m;
-  return b;
+  return hil_layout(es, m, r.tw_lo + r.tw_hi, kHilThreads, interp).total;
 }
 
 int ensure_hilbert(mbir_plan p) {
@@ -211,12 +284,14 @@ static int hilbert_t(mbir_plan p, const void* y, const uint8_t* mask, void* c, b
   const bool iv = interp && mask != nullptr;
   const size_t smem = hilbert_smem_bytes(sizeof(cplx_t<R>), p->m, p->rad_m, iv);
   if (smem > (size_t)kMaxDynSmem) return MBIR_ERR_UNSUPPORTED_SIZE;
+  const auto al = [](const void* q, uintptr_t b) { return (reinterpret_cast<uintptr_t>(q) & (b - 1)) == 0; };
+  const int vec = sizeof(R) == 4 && (p->m & 3) == 0 && al(y, 16) && al(c, 16) && (!mask || al(mask, 4)) ? 1 : 0;
   {
     ProfScope ps_(p, PC_HILBERT, st);
     auto kernel = iv ? hilbert_kernel<R, true> : hilbert_kernel<R, false>;
     launch(kernel, dim3(grid), dim3(kHilThreads), smem, st, static_cast<const R*>(y), mask,
            static_cast<cplx_t<R>*>(c), p->nx, p->m, p->rad_m, static_cast<const cplx_t<R>*>(p->tw_m),
-           (const int*)p->perm_m, side, (p->m & 15) == 0 ? 1 : 0);
+           (const int*)p->perm_m, side, (p->m & 15) == 0 ? 1 : 0, vec);
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
