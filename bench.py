@@ -566,17 +566,20 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
         plan.solve(y, mask, **tv_kw)
         torch.cuda.synchronize()
         n_launch, tv_total_ms = plan.profile_end()["tv_prox"]
-        n_prox = n_launch / (TV_ITERS + 1)
-        # bytes a prox must move per pixel (FP32): step 1 reads v, writes p (24); step 2
-        # reads p_1 and v, writes p_2 (40); later steps read p_{k-1}, p_{k-2}, v and write
-        # p_k (56); the finishing pass reads p and v, writes z (32)
-        bpp = 24 + 40 + 56 * (TV_ITERS - 2) + 32
+        per_prox = TV_ITERS // 2 + TV_ITERS % 2 + 1      # two-step passes, an odd last step, the finish
+        n_prox = n_launch / per_prox
+        # bytes a prox must move per pixel (FP32): the first two-step pass reads v and
+        # writes p_1, p_2 (40); later two-step passes read p_{k-1}, p_{k-2}, v and write
+        # p_k, p_{k+1} (72); an odd last step reads p_{k-1}, p_{k-2}, v and writes p_k
+        # (56); the finishing pass reads p and v and writes z (32)
+        pairs = TV_ITERS // 2
+        bpp = (40 + 72 * (pairs - 1) if pairs else 0) + (TV_ITERS % 2) * (56 if pairs else 24) + 32
         prox_ms = tv_total_ms / n_prox
         peak_gbs = measured_peak()[0]
         gbs = bpp * nx * nz / (prox_ms * 1e-3) / 1e9
         tv_res = {"workload": f"bscan-1024x2048-tv-{ITERS}it-half-ascans, {TV_ITERS} dual steps per prox",
                   "bscans_per_sec": 1e3 / tv_solve_ms, "ms_per_solve": tv_solve_ms,
-                  "prox_ms": prox_ms, "prox_launches": TV_ITERS + 1,
+                  "prox_ms": prox_ms, "prox_launches": per_prox,
                   "roofline": {"bound": "hbm", "kernel": "tv_prox", "achieved": gbs, "peak": peak_gbs,
                                "unit": "GB/s", "frac": gbs / peak_gbs, "alg_bytes_per_prox": bpp * nx * nz}}
 

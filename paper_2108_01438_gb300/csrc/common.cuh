@@ -151,8 +151,8 @@ struct mbir_plan_s {
   void* wv_b1;
   void* wv_b2;
   void* wv_coef;
-  // TV prox scratch (lazily allocated): three dual fields [nx][nz] x 4 reals
-  void* tv_p[3];
+  // TV prox scratch (lazily allocated): four dual fields [nx][nz] x 4 reals
+  void* tv_p[4];
   // m-point transform of the Hilbert-form back-projection (built on first use)
   mbir::Radix rad_m;
   void* tw_m;

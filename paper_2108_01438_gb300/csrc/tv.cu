@@ -12,12 +12,17 @@
 //   p_k     = project(r_k + grad(v + tau div r_k) / (8 tau))
 //   r_{k+1} = p_k + m_k (p_k - p_{k-1}),   m_k = (t_k - 1)/t_{k+1}, FISTA's t,
 //
-// one kernel per step over 16 x 64 pixel tiles (16 x 32 in FP64) with a one-pixel halo: the tile
-// forms r on the halo, x = v + tau div r on the tile plus one row and column, and
-// the projected step.  Three dual fields rotate (p_k, p_{k-1}, p_{k-2}).  A last
-// kernel forms z = v + tau div p and the per-CTA sums of TV(z).  Each step reads
-// p_{k-1}, p_{k-2} and v and writes p_k: streaming stencil work.
+// two steps per kernel over 16 x 64 pixel tiles (8 x 32 in FP64) with a two-pixel
+// halo (tv_step2_kernel): step k runs on the tile plus a one-pixel ring so that
+// step k + 1 can run on the tile.  p_k depends on r_k within one pixel, so the ring
+// is recomputed by the neighbouring tiles instead of exchanged.  A pass reads
+// p_{k-1}, p_{k-2} and v and writes p_k and p_{k+1}: 72 bytes a pixel (FP32) for
+// two steps instead of 112 for two one-step passes.  An odd step count ends with
+// one one-step pass (tv_step_kernel, one-pixel halo).  Four dual fields rotate.  A
+// last kernel forms z = v + tau div p and the per-CTA sums of TV(z).
 #include <math.h>
+
+#include <vector>
 
 #include "common.cuh"
 
@@ -181,6 +186,137 @@ tv_step_kernel(const void* v, const void* pa, const void* pb, R m, R tau, void* 
   }
 }
 
+// Two FGP steps: p_k from r_k = pa + m1 (pa - pb) (pa = nullptr: r_k = 0; pb read
+// only when m1 != 0), then r_{k+1} = p_k + m2 (p_k - pa) and p_{k+1}.  Shared
+// memory (dynamic): r_k on the tile plus two pixels (rows and columns -2 .. T+1),
+// p_{k-1} on the tile plus one (later r_{k+1}), and x on rows and columns -1 .. T+1.
+template <class R>
+constexpr int tv2_ti() { return sizeof(R) == 4 ? 16 : 8; }
+template <class R>
+constexpr int tv2_tj() { return sizeof(R) == 4 ? 64 : 32; }
+template <class R>
+constexpr size_t tv2_smem() {
+  return sizeof(Dual<R>) * ((tv2_ti<R>() + 4) * (tv2_tj<R>() + 4) + (tv2_ti<R>() + 2) * (tv2_tj<R>() + 2)) +
+         sizeof(cplx_t<R>) * (tv2_ti<R>() + 3) * (tv2_tj<R>() + 3);
+}
+
+template <class R>
+__device__ __forceinline__ Dual<R> project_step(Dual<R> q, cplx_t<R> g1, cplx_t<R> g2, R step) {
+  using V = cplx_t<R>;
+  q.p1 = cmk<V>(q.p1.x + step * g1.x, q.p1.y + step * g1.y);
+  q.p2 = cmk<V>(q.p2.x + step * g2.x, q.p2.y + step * g2.y);
+  const R n2 = q.p1.x * q.p1.x + q.p1.y * q.p1.y + q.p2.x * q.p2.x + q.p2.y * q.p2.y;
+  if (n2 > R(1)) {
+    const R s = R(1) / sqrt(n2);
+    q.p1 = cscale(q.p1, s);
+    q.p2 = cscale(q.p2, s);
+  }
+  return q;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kTvThreads)
+tv_step2_kernel(const void* v, const void* pa, const void* pb, R m1, R m2, R tau, void* pout1, void* pout2, int P,
+                int N, int gx) {
+  using V = cplx_t<R>;
+  constexpr int TI = tv2_ti<R>(), TJ = tv2_tj<R>();
+  constexpr int W2 = TJ + 4, W1 = TJ + 2, XW = TJ + 3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Dual<R>* d2 = reinterpret_cast<Dual<R>*>(smem_raw);      // r_k, rows/cols -2 .. T+1
+  Dual<R>* d1 = d2 + (TI + 4) * W2;                         // p_{k-1}, then r_{k+1}, rows/cols -1 .. T
+  V* x = reinterpret_cast<V*>(d1 + (TI + 2) * W1);          // x, rows/cols -1 .. T+1
+  const int bx = blockIdx.x % gx, by = blockIdx.x / gx;
+  const int i0 = by * TI, j0 = bx * TJ;
+  const V* vv = reinterpret_cast<const V*>(v);
+  const V zero = cmk<V>(R(0), R(0));
+  const R step = R(1) / (R(8) * tau);
+  pdl_wait_release();
+  for (int e = threadIdx.x; e < (TI + 4) * W2; e += blockDim.x) {
+    const int a = e / W2 - 2, b = e - (e / W2) * W2 - 2;
+    const int gi = i0 + a, gj = j0 + b;
+    Dual<R> pk1 = dzero<R>(), r = dzero<R>();
+    if (pa && gi >= 0 && gi < P && gj >= 0 && gj < N) {
+      const size_t g = (size_t)gi * N + gj;
+      pk1 = dload<R>(pa, g);
+      r = pk1;
+      if (m1 != R(0)) {
+        const Dual<R> q = dload<R>(pb, g);
+        r.p1.x += m1 * (pk1.p1.x - q.p1.x);
+        r.p1.y += m1 * (pk1.p1.y - q.p1.y);
+        r.p2.x += m1 * (pk1.p2.x - q.p2.x);
+        r.p2.y += m1 * (pk1.p2.y - q.p2.y);
+      }
+    }
+    d2[e] = r;
+    if (a >= -1 && a <= TI && b >= -1 && b <= TJ) d1[(a + 1) * W1 + b + 1] = pk1;
+  }
+  __syncthreads();
+  // x_k = v + tau div r_k on rows and columns -1 .. T+1
+  for (int e = threadIdx.x; e < (TI + 3) * XW; e += blockDim.x) {
+    const int a = e / XW - 1, b = e - (e / XW) * XW - 1;
+    const int gi = i0 + a, gj = j0 + b;
+    V xv = zero;
+    if (gi >= 0 && gi < P && gj >= 0 && gj < N) {
+      const Dual<R>& c = d2[(a + 2) * W2 + b + 2];
+      V dv = zero;
+      if (gi < P - 1) dv = cadd(dv, c.p1);
+      if (gi >= 1) dv = csub(dv, d2[(a + 1) * W2 + b + 2].p1);
+      if (gj < N - 1) dv = cadd(dv, c.p2);
+      if (gj >= 1) dv = csub(dv, d2[(a + 2) * W2 + b + 1].p2);
+      const V v0 = vv[(size_t)gi * N + gj];
+      xv = cmk<V>(v0.x + tau * dv.x, v0.y + tau * dv.y);
+    }
+    x[e] = xv;
+  }
+  __syncthreads();
+  // p_k on the tile plus one (stored on the tile), r_{k+1} into d1
+  for (int e = threadIdx.x; e < (TI + 2) * W1; e += blockDim.x) {
+    const int a = e / W1 - 1, b = e - (e / W1) * W1 - 1;
+    const int gi = i0 + a, gj = j0 + b;
+    Dual<R> rn = dzero<R>();
+    if (gi >= 0 && gi < P && gj >= 0 && gj < N) {
+      const V xc = x[(a + 1) * XW + b + 1];
+      const V g1 = gi < P - 1 ? csub(x[(a + 2) * XW + b + 1], xc) : zero;
+      const V g2 = gj < N - 1 ? csub(x[(a + 1) * XW + b + 2], xc) : zero;
+      const Dual<R> q = project_step<R>(d2[(a + 2) * W2 + b + 2], g1, g2, step);
+      if (a >= 0 && a < TI && b >= 0 && b < TJ) dstore<R>(pout1, (size_t)gi * N + gj, q);
+      const Dual<R> o = d1[e];
+      rn.p1 = cmk<V>(q.p1.x + m2 * (q.p1.x - o.p1.x), q.p1.y + m2 * (q.p1.y - o.p1.y));
+      rn.p2 = cmk<V>(q.p2.x + m2 * (q.p2.x - o.p2.x), q.p2.y + m2 * (q.p2.y - o.p2.y));
+    }
+    d1[e] = rn;
+  }
+  __syncthreads();
+  // x_{k+1} = v + tau div r_{k+1} on rows and columns 0 .. T
+  for (int e = threadIdx.x; e < (TI + 1) * (TJ + 1); e += blockDim.x) {
+    const int a = e / (TJ + 1), b = e - (e / (TJ + 1)) * (TJ + 1);
+    const int gi = i0 + a, gj = j0 + b;
+    V xv = zero;
+    if (gi < P && gj < N) {
+      const Dual<R>& c = d1[(a + 1) * W1 + b + 1];
+      V dv = zero;
+      if (gi < P - 1) dv = cadd(dv, c.p1);
+      if (gi >= 1) dv = csub(dv, d1[a * W1 + b + 1].p1);
+      if (gj < N - 1) dv = cadd(dv, c.p2);
+      if (gj >= 1) dv = csub(dv, d1[(a + 1) * W1 + b].p2);
+      const V v0 = vv[(size_t)gi * N + gj];
+      xv = cmk<V>(v0.x + tau * dv.x, v0.y + tau * dv.y);
+    }
+    x[(a + 1) * XW + b + 1] = xv;
+  }
+  __syncthreads();
+  // p_{k+1} on the tile
+  for (int e = threadIdx.x; e < TI * TJ; e += blockDim.x) {
+    const int a = e / TJ, b = e - (e / TJ) * TJ;
+    const int gi = i0 + a, gj = j0 + b;
+    if (gi >= P || gj >= N) continue;
+    const V xc = x[(a + 1) * XW + b + 1];
+    const V g1 = gi < P - 1 ? csub(x[(a + 2) * XW + b + 1], xc) : zero;
+    const V g2 = gj < N - 1 ? csub(x[(a + 1) * XW + b + 2], xc) : zero;
+    dstore<R>(pout2, (size_t)gi * N + gj, project_step<R>(d1[(a + 1) * W1 + b + 1], g1, g2, step));
+  }
+}
+
 // z = v + tau div p on the tile (p = nullptr: z = v), and the per-CTA sum of TV(z)
 // (from z on the tile plus one row and column).
 template <class R>
@@ -230,6 +366,12 @@ static int ensure_tv_scratch(mbir_plan p) {
   if (p->tv_p[0]) return MBIR_OK;
   const size_t bytes = (p->precision == MBIR_FP64 ? 4 * sizeof(double) : 4 * sizeof(float)) * (size_t)p->nx * p->nz;
   for (void*& q : p->tv_p) MBIR_CUDA_TRY(cudaMalloc(&q, bytes));
+  if (p->precision == MBIR_FP64)
+    MBIR_CUDA_TRY(cudaFuncSetAttribute(tv_step2_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tv2_smem<double>()));
+  else
+    MBIR_CUDA_TRY(cudaFuncSetAttribute(tv_step2_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tv2_smem<float>()));
   return MBIR_OK;
 }
 
@@ -243,25 +385,46 @@ static int tv_prox_t(mbir_plan p, const void* v, double tau, int iters, void* z,
   }
   int rc = ensure_tv_scratch(p);
   if (rc) return rc;
-  // step k (1-based) writes buffer (k-1) % 3 from r_k = p_{k-1} + m_{k-1} (p_{k-1} - p_{k-2})
-  double t = 1.0, m_prev = 0.0;
-  for (int k = 1; k <= iters; ++k) {
-    const void* pa = k >= 2 ? p->tv_p[(k - 2) % 3] : nullptr;
-    const void* pb = k >= 3 ? p->tv_p[(k - 3) % 3] : nullptr;
-    const R m = k >= 3 ? R(m_prev) : R(0);
+  // momenta m_j = (t_j - 1)/t_{j+1}, j = 1 .. iters (m_1 = 0)
+  std::vector<double> mom(iters + 1, 0.0);
+  {
+    double t = 1.0;
+    for (int j = 1; j <= iters; ++j) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      mom[j] = (t - 1.0) / tn;
+      t = tn;
+    }
+  }
+  // p_j lives in buffer (j - 1) % 4: a pass never writes a field that it or a
+  // neighbouring tile still reads
+  auto buf = [&](int j) { return p->tv_p[(j - 1) & 3]; };
+  constexpr int TI2 = tv2_ti<R>(), TJ2 = tv2_tj<R>();
+  const int gx2 = (N + TJ2 - 1) / TJ2, grid2 = gx2 * ((P + TI2 - 1) / TI2);
+  int k = 1;
+  for (; k + 1 <= iters; k += 2) {   // steps k and k + 1
+    const void* pa = k >= 2 ? buf(k - 1) : nullptr;
+    const void* pb = k >= 3 ? buf(k - 2) : nullptr;
+    const R m1 = k >= 3 ? R(mom[k - 1]) : R(0);
     {
       ProfScope ps_(p, PC_TV, st);
-      launch(tv_step_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, pa, pb, m, R(tau), p->tv_p[(k - 1) % 3], P,
-             N, gx);
+      launch(tv_step2_kernel<R>, dim3(grid2), dim3(kTvThreads), tv2_smem<R>(), st, v, pa, pb, m1, R(mom[k]),
+             R(tau), buf(k), buf(k + 1), P, N, gx2);
     }
     MBIR_LAUNCH_CHECK();
-    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    m_prev = (t - 1.0) / tn;   // m_k, used by step k + 1
-    t = tn;
+  }
+  if (k == iters) {   // an odd count ends with one one-step pass
+    const void* pa = k >= 2 ? buf(k - 1) : nullptr;
+    const void* pb = k >= 3 ? buf(k - 2) : nullptr;
+    const R m = k >= 3 ? R(mom[k - 1]) : R(0);
+    {
+      ProfScope ps_(p, PC_TV, st);
+      launch(tv_step_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, pa, pb, m, R(tau), buf(k), P, N, gx);
+    }
+    MBIR_LAUNCH_CHECK();
   }
   {
     ProfScope ps_(p, PC_TV, st);
-    launch(tv_finish_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, (const void*)p->tv_p[(iters - 1) % 3], R(tau),
+    launch(tv_finish_kernel<R>, dim3(grid), dim3(kTvThreads), 0, st, v, (const void*)buf(iters), R(tau),
            z, partial, P, N, gx);
   }
   MBIR_LAUNCH_CHECK();

@@ -37,10 +37,12 @@ def _img(shape, seed):
 
 
 @pytest.mark.parametrize("nx,nz,tau,iters", [(64, 96, 0.3, 20), (35, 50, 0.8, 20), (16, 45, 0.1, 100),
-                                             (2, 40, 0.5, 20), (48, 64, 2.0, 50)])
+                                             (2, 40, 0.5, 20), (48, 64, 2.0, 50), (35, 50, 0.8, 21),
+                                             (20, 70, 0.4, 3), (9, 35, 0.4, 1), (18, 130, 0.6, 2)])
 def test_prox_tv_matches_oracle(mbir, nx, nz, tau, iters):
     """Tiles of 16 x 64 with ragged edges in both directions, a two-row image, a
-    strong and a weak tau."""
+    strong and a weak tau; odd step counts (two-step passes, then one one-step
+    pass), a single step, a single two-step pass."""
     plan = mbir.Plan(W.geometry(nx, nz, 16))
     v = _img((nx, nz), 800 + nx)
     v32 = v.astype(np.complex64)
@@ -68,12 +70,14 @@ def test_prox_entry_point_and_aliasing(mbir):
     plan.close()
 
 
-def test_prox_tv_fp64_plan_is_tight(mbir):
-    nx, nz, tau = 32, 48, 0.6
+@pytest.mark.parametrize("nx,nz,iters", [(32, 48, 30), (20, 70, 7)])
+def test_prox_tv_fp64_plan_is_tight(mbir, nx, nz, iters):
+    """FP64 plans (8 x 32 two-step tiles, 16 x 32 one-step tiles), even and odd counts."""
+    tau = 0.6
     plan = mbir.Plan(W.geometry(nx, nz, 16), precision=2)
     v = _img((nx, nz), 820)
-    z = plan.prox_tv(torch.from_numpy(v).cuda(), tau, 30).cpu().numpy()
-    assert _rel(z, tv.prox_tv(v, tau, 30)) <= 1e-11
+    z = plan.prox_tv(torch.from_numpy(v).cuda(), tau, iters).cpu().numpy()
+    assert _rel(z, tv.prox_tv(v, tau, iters)) <= 1e-11
     plan.close()
 
 
