@@ -81,3 +81,60 @@ def test_null_arguments(lib):
     h = C.c_void_p()
     assert lib.mbir_plan_create(None, None, C.byref(h)) == -1
     lib.mbir_plan_destroy(None)
+
+
+# ctypes type of each C field type used in include/mbir.h
+_CTYPE = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double, "size_t": C.c_size_t}
+
+
+def _c_structs():
+    """{typedef name: [(field, C type text), ...]} of the header's plain structs."""
+    text = open(os.path.join(ROOT, "include", "mbir.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"((?:const )?\w+\s*\**)\s*(.*)", decl)
+            ctype, names = m.group(1).replace(" ", ""), m.group(2)
+            for n in names.split(","):
+                n = n.strip()
+                stars = len(n) - len(n.lstrip("*"))
+                fields.append((n.lstrip("*"), ctype + "*" * stars))
+        out[name] = fields
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [
+    ("mbir_geometry", "Geometry"), ("mbir_solve_opts", "SolveOpts"), ("mbir_solve_info", "SolveInfo"),
+    ("mbir_lambda_search_info", "LambdaSearchInfo"), ("mbir_tuning", "Tuning"),
+    ("mbir_profile_entry", "ProfileEntry"),
+])
+def test_binding_structs_match_the_header(cname, pyname):
+    """Field order, count and type of every ctypes struct equal the C declaration
+    (a field added on one side only would shift every later one)."""
+    cf = _c_structs()[cname]
+    pf = getattr(mbir, pyname)._fields_
+    assert len(cf) == len(pf), (cname, [f for f, _ in cf], [f for f, _ in pf])
+    for (cn, ct), (pn, pt) in zip(cf, pf):
+        if ct.endswith("*"):
+            assert pt is C.c_char_p or issubclass(pt, C._Pointer) or pt is C.c_void_p, (cname, cn, pt)
+        else:
+            assert pt is _CTYPE[ct], (cname, cn, ct, pt)
+        assert pn.replace("lam", "lambda") == cn or pn == cn, (cname, cn, pn)
+    assert C.sizeof(getattr(mbir, pyname)) >= 8 * (len(pf) // 2)
+
+
+def test_new_entry_points_validate_on_the_host(lib):
+    """NULL plans and arguments are refused before any device work."""
+    assert lib.mbir_adjoint_hilbert(None, None, None, None, None) == -1
+    assert lib.mbir_isam_interpolated(None, None, None, None, None) == -1
+    r = C.c_double()
+    assert lib.mbir_ncc(None, None, None, C.byref(r), None) == -1
+    info = mbir.LambdaSearchInfo()
+    o = mbir.SolveOpts()
+    assert lib.mbir_lambda_search(None, None, None, None, C.byref(o), -3.0, 0.0, 5, None, C.byref(info), None) == -1
+    assert lib.mbir_prox_tv(None, None, 0.5, 5, None, None) == -1
