@@ -20,4 +20,5 @@ Modules:
               projection on the dual.
   evaluate -- the evaluation loop of Sec. 3: direct ISAM on interpolated
               measurements, the NCC of Eq. ncc, the golden-section lambda search.
+  volume   -- the ISAM operator of a 3-D volume (both lateral axes), direct sum.
 """
