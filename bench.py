@@ -628,7 +628,8 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                    "pairs_per_sec": 1e3 / hpair_ms, "hilbert_ms": h_avg,
                    "rel_gap_to_twice_transpose": gap,
                    "roofline": {"bound": "hbm", "kernel": "hilbert", "achieved": h_gbs, "peak": peak_gbs,
-                                "unit": "GB/s", "frac": h_gbs / peak_gbs, "alg_bytes": h_bytes}}
+                                "unit": "GB/s", "frac": h_gbs / peak_gbs, "alg_bytes": h_bytes,
+                                "traffic": traffic_for("hilbert")}}
 
     # the evaluation loop of Sec. 3 on the same phantom with the paper's three
     # sub-sampling schemes (half of the spectrometer samples each): the
