@@ -32,11 +32,13 @@ def _dense(op, shape_in, complex_in):
 
 
 @pytest.mark.parametrize("which", ["exact", "nufft"])
-def test_adjoint_is_transpose_dense(which):
+@pytest.mark.parametrize("nx", [4, 11])
+def test_adjoint_is_transpose_dense(which, nx):
     """Phi^H must be the transpose of Phi as real matrices (Sec. 2.1, Eq. ls_grad
-    needs the true adjoint)."""
-    g = _geom(4, 8, 8)
-    mask = (np.random.default_rng(3).random((4, 8)) < 0.7).astype(np.uint8)
+    needs the true adjoint); also at a prime width (the oracle takes any width, the
+    reference for a future arbitrary-width lateral transform)."""
+    g = _geom(nx, 8, 8)
+    mask = (np.random.default_rng(3).random((nx, 8)) < 0.7).astype(np.uint8)
     fwd = isam.phi_exact if which == "exact" else isam.phi_nufft
     adj = isam.phi_adj_exact if which == "exact" else isam.phi_adj_nufft
     A = _dense(lambda x: fwd(x, mask, g), (g.nx, g.nz), True)      # (M, 2N)
