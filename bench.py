@@ -221,9 +221,22 @@ def algorithmic_bytes(cls: str, nx: int, nz: int, m: int) -> float | None:
     }.get(cls)
 
 
-def source_hash() -> str:
+# sources that define each kernel class's code (its counters stay valid while these are unchanged)
+_OPERATOR_SOURCES = ["common.cuh", "fft.cuh", "operator.cuh", "operator.cu", "plan.cu"]
+CLASS_SOURCES = {
+    "row_forward": _OPERATOR_SOURCES, "row_adjoint": _OPERATOR_SOURCES, "lateral_forward": _OPERATOR_SOURCES,
+    "lateral_mid": _OPERATOR_SOURCES, "lateral_adjoint": _OPERATOR_SOURCES, "lateral_inverse_real": _OPERATOR_SOURCES,
+    "lateral_residual": _OPERATOR_SOURCES, "hilbert": ["common.cuh", "fft.cuh", "operator.cuh", "hilbert.cu", "plan.cu"],
+}
+
+
+def source_hash(cls: str | None = None) -> str:
+    """Hash of the kernel sources of one class (every csrc file when the class is unknown)."""
+    csrc = os.path.join(ROOT, "paper_2108_01438_gb300", "csrc")
+    names = CLASS_SOURCES.get(cls) if cls else None
+    files = sorted(os.path.join(csrc, n) for n in names) if names else sorted(glob.glob(os.path.join(csrc, "*")))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2108_01438_gb300", "csrc", "*"))):
+    for f in files:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -245,7 +258,7 @@ def traffic_for(cls: str) -> float | None:
     except (OSError, ValueError):
         return None
     e = t.get(cls)
-    if not e or e.get("source_hash") != source_hash() or e.get("workload") != WORKLOAD:
+    if not e or e.get("source_hash") != source_hash(cls) or e.get("workload") != WORKLOAD:
         return None
     return float(e["dram_bytes_per_launch"])
 
