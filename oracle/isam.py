@@ -51,9 +51,12 @@ Two realisations are given:
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
+import scipy.fft as sfft
 from scipy.special import i0
 
 __all__ = [
@@ -218,6 +221,34 @@ def b_adj_exact(c: np.ndarray, g: Geom) -> np.ndarray:
 
 
 # ------------------------------------------------------ Kaiser-Bessel NUFFT
+#
+# The NUFFT path runs on every host core: its FFTs through scipy.fft with one
+# worker per core, and its per-row steps (deapodise, pad, axial FFT, interpolate
+# or spread) on blocks of rows in threads.  Rows never interact in those steps,
+# so a block's arithmetic is the same as the whole array's, element by element.
+
+WORKERS = max(1, os.cpu_count() or 1)
+
+
+def _fft(a, axis):
+    return sfft.fft(a, axis=axis, workers=WORKERS)
+
+
+def _ifft(a, axis):
+    return sfft.ifft(a, axis=axis, workers=WORKERS)
+
+
+def _by_rows(fn, *arrays):
+    """fn(*arrays) evaluated on blocks of rows (axis 0) in threads, concatenated."""
+    n = arrays[0].shape[0]
+    nb = min(WORKERS, n)
+    if nb <= 1 or arrays[0].size < (1 << 15):
+        return fn(*arrays)
+    cut = np.linspace(0, n, nb + 1).astype(int)
+    with ThreadPoolExecutor(nb) as ex:
+        parts = list(ex.map(lambda b: fn(*(a[cut[b]:cut[b + 1]] for a in arrays)), range(nb)))
+    return np.concatenate(parts, axis=0)
+
 
 def kb_kernel(u: np.ndarray, J: int, alpha: float) -> np.ndarray:
     """psi(u) = I0(alpha sqrt(1 - (2u/J)^2)) / I0(alpha) on |u| <= J/2, else 0."""
@@ -261,12 +292,16 @@ def nufft_axial(a: np.ndarray, t: np.ndarray, g: Geom) -> np.ndarray:
       1. deapodise: b_n = a_n / Psi((n - n0)/K)
       2. zero-pad to K with the index centred at n0 and take a K-point FFT
       3. interpolate with J taps i = floor(t - J/2) + 1 + j, weights psi(t - i)."""
+    return _by_rows(lambda a_, t_: _nufft_axial_rows(a_, t_, g), a, t)
+
+
+def _nufft_axial_rows(a: np.ndarray, t: np.ndarray, g: Geom) -> np.ndarray:
     K, J = g.K, g.J
     n = np.arange(g.nz)
     b = a / kb_ft((n - g.n0) / K, J, g.alpha)[None, :]
     pad = np.zeros((a.shape[0], K), dtype=np.complex128)
     pad[:, (n - g.n0) % K] = b
-    Y = np.fft.fft(pad, axis=1)
+    Y = sfft.fft(pad, axis=1)
     base = np.floor(t - J / 2.0).astype(np.int64) + 1
     rows = np.arange(a.shape[0])[:, None]
     U = np.zeros(t.shape, dtype=np.complex128)
@@ -279,6 +314,10 @@ def nufft_axial(a: np.ndarray, t: np.ndarray, g: Geom) -> np.ndarray:
 def nufft_axial_adjoint(V: np.ndarray, t: np.ndarray, g: Geom) -> np.ndarray:
     """Transpose of nufft_axial: spread each V[l,m] onto its J grid taps, take the
     unnormalised inverse K-point FFT, keep the nz centred samples, deapodise."""
+    return _by_rows(lambda v_, t_: _nufft_axial_adjoint_rows(v_, t_, g), V, t)
+
+
+def _nufft_axial_adjoint_rows(V: np.ndarray, t: np.ndarray, g: Geom) -> np.ndarray:
     K, J = g.K, g.J
     rows_n = V.shape[0]
     base = np.floor(t - J / 2.0).astype(np.int64) + 1
@@ -290,7 +329,7 @@ def nufft_axial_adjoint(V: np.ndarray, t: np.ndarray, g: Geom) -> np.ndarray:
         flat = (rows * K + i % K).ravel()
         Gk += np.bincount(flat, weights=contrib.real.ravel(), minlength=rows_n * K)
         Gk += 1j * np.bincount(flat, weights=contrib.imag.ravel(), minlength=rows_n * K)
-    Yb = K * np.fft.ifft(Gk.reshape(rows_n, K), axis=1)
+    Yb = K * sfft.ifft(Gk.reshape(rows_n, K), axis=1)
     n = np.arange(g.nz)
     b = Yb[:, (n - g.n0) % K]
     return b / kb_ft((n - g.n0) / K, J, g.alpha)[None, :]
@@ -304,10 +343,10 @@ def phi_nufft(x: np.ndarray, mask: np.ndarray | None, g: Geom) -> np.ndarray:
     H = system_filter(g)
     w = depth_weight(g)
     t = kb_grid_position(g)
-    X = np.fft.fft(np.asarray(x, dtype=np.complex128), axis=0)
+    X = _fft(np.asarray(x, dtype=np.complex128), 0)
     U = nufft_axial(X * w[None, :], t, g)
     U = U * np.exp(1j * beta * (g.z_f - g.n0 * g.dz))
-    y = np.fft.ifft(H * U, axis=0).real
+    y = _ifft(H * U, 0).real
     return y if mask is None else y * mask
 
 
@@ -325,10 +364,10 @@ def b_adj_nufft(c: np.ndarray, g: Geom) -> np.ndarray:
     H = system_filter(g)
     w = depth_weight(g)
     t = kb_grid_position(g)
-    R = np.fft.fft(np.asarray(c, dtype=np.complex128), axis=0) / g.nx
+    R = _fft(np.asarray(c, dtype=np.complex128), 0) / g.nx
     V = np.conj(H) * R * np.exp(-1j * beta * (g.z_f - g.n0 * g.dz))
     a = nufft_axial_adjoint(V, t, g)
-    return g.nx * np.fft.ifft(a * w[None, :], axis=0)
+    return g.nx * _ifft(a * w[None, :], 0)
 
 
 # ------------------------------------------- Hilbert-form back-projection
