@@ -6,6 +6,7 @@ lambda search (mbir_lambda_search), against the FP64 oracle
 import numpy as np
 import pytest
 
+from _parity import assert_parity
 from oracle import evaluate, fista, isam
 from paper_2108_01438_gb300 import workloads as W
 
@@ -55,7 +56,7 @@ def test_isam_interpolated_matches_oracle(mbir, nx, nz, m, pattern):
     plan = mbir.Plan(d)
     got = plan.isam_interpolated(torch.from_numpy(y.astype(np.float32)).cuda(),
                                  torch.from_numpy(mask).cuda()).cpu().numpy().astype(np.complex128)
-    assert _rel(got, evaluate.isam_interpolated(y32, mask, g)) <= OP_TOL
+    assert_parity(got, evaluate.isam_interpolated(y32, mask, g), OP_TOL, what=f"interpolated ISAM {pattern}")
     # no mask: the baseline is Phi* itself
     yt = torch.from_numpy(y.astype(np.float32)).cuda()
     assert torch.equal(plan.isam_interpolated(yt), plan.adjoint_hilbert(yt))
@@ -81,7 +82,7 @@ def test_isam_interpolated_fp64_and_full_size(mbir):
     plan = mbir.Plan(d)
     got = plan.isam_interpolated(torch.from_numpy(y.astype(np.float32)).cuda(),
                                  torch.from_numpy(mask).cuda()).cpu().numpy().astype(np.complex128)
-    assert _rel(got, evaluate.isam_interpolated(y32, mask, g)) <= OP_TOL
+    assert_parity(got, evaluate.isam_interpolated(y32, mask, g), OP_TOL, what="interpolated ISAM 1024x2048")
     plan.close()
 
 

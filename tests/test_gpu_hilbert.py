@@ -4,6 +4,7 @@ the C ABI, against the FP64 oracle (oracle/isam.py, oracle/fista.py)."""
 import numpy as np
 import pytest
 
+from _parity import assert_parity
 from oracle import fista, isam, wavelet
 from paper_2108_01438_gb300 import workloads as W
 
@@ -52,9 +53,9 @@ def test_adjoint_hilbert_matches_oracle(mbir, nx, nz, m):
     y32 = y.astype(np.float32).astype(np.float64)
     got = _hil(mbir, d, y, mask)
     ref = isam.phi_adj_hilbert_nufft(y32, mask, g)
-    assert _rel(got, ref) <= OP_TOL
+    assert_parity(got, ref, OP_TOL, what=f"Phi* {nx}x{nz}x{m}")
     # no mask is every sample measured
-    assert _rel(_hil(mbir, d, y, None), isam.phi_adj_hilbert_nufft(y32, None, g)) <= OP_TOL
+    assert_parity(_hil(mbir, d, y, None), isam.phi_adj_hilbert_nufft(y32, None, g), OP_TOL, what="Phi* no mask")
 
 
 def test_unsupported_spectrometer_length_is_refused(mbir):
@@ -113,7 +114,7 @@ def test_full_size_hilbert_elementwise(mbir):
     y = np.random.default_rng(5).standard_normal((g.nx, g.m))
     y32 = y.astype(np.float32).astype(np.float64)
     got = _hil(mbir, d, y, wl["mask"])
-    assert _rel(got, isam.phi_adj_hilbert_nufft(y32, wl["mask"], g)) <= OP_TOL
+    assert_parity(got, isam.phi_adj_hilbert_nufft(y32, wl["mask"], g), OP_TOL, what="Phi* 1024x2048")
 
 
 def _fista_case(use_mask):
