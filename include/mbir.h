@@ -386,10 +386,20 @@ int mbir_wavelet(mbir_plan plan, int32_t inverse, const void* in, void* out, voi
  * Scratch: a file-scope device array of 5 MiB + 256 bytes (the filter taps and
  * the level-1/2 low-low blocks) that every GPU loading the library holds until
  * exit; nothing in it needs to start at zero, since a call writes every element it
- * reads.  All calls on a device share it, so calls that overlap on the GPU (other
- * streams, other threads) race: order them.  The first call on a device sets up
- * (looks up the array's device address and uploads the taps, synchronously); make
- * that first call before any stream capture.  Allocates nothing, ever.
+ * reads.  The array is placed in device memory when the library's module loads
+ * into a context, which with CUDA's default lazy module loading is the first
+ * call of the library there (this one or any other); make that first call at
+ * start-up, before another allocator takes the device's memory.  A placement that
+ * fails returns MBIR_ERR_CUDA with the reason in mbir_last_error.
+ * All calls in a context share the array, so calls that overlap on the GPU (other
+ * streams, other threads) race: order them.  The first call in a context sets up:
+ * it looks up the array's device address for that context, sets the kernels'
+ * attributes and writes the taps into the array, then synchronises the device;
+ * make that first call before any stream capture.  Addresses are kept per CUDA
+ * context handle (a device's primary context, or a context the caller made
+ * current), up to 64 contexts.  A context made after cudaDeviceReset that happens
+ * to reuse the old context's handle would keep the old address: do not reset the
+ * device between calls.  Allocates nothing, ever.
  */
 int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in, void* out, void* stream);
 

@@ -142,6 +142,10 @@ int plan_fft_tables(mbir_plan p, int n, Radix* rad, void** tw, int** perm) {
   MBIR_CUDA_TRY(cudaMalloc(perm, sizeof(int) * n));
   MBIR_CUDA_TRY(cudaMemcpy(*tw, src, bytes, cudaMemcpyHostToDevice));
   MBIR_CUDA_TRY(cudaMemcpy(*perm, pr.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  // a copy from pageable memory may return before its DMA lands, and it is
+  // ordered only against the legacy default stream: wait for it, so that kernels
+  // on any stream of the caller see the tables
+  MBIR_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
   return MBIR_OK;
 }
 
@@ -646,6 +650,8 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
     if (e == cudaSuccess) e = cudaMalloc(&p->h_db4f, sizeof(hf));
     if (e == cudaSuccess) e = cudaMemcpy(p->h_db4, h, sizeof(h), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->h_db4f, hf, sizeof(hf), cudaMemcpyHostToDevice);
+    // pageable copies: wait until they have landed (see plan_fft_tables)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) return fail(set_cuda_error(e, "wavelet filter upload"));
   }
   {

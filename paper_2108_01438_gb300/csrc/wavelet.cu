@@ -558,28 +558,89 @@ constexpr size_t kStaticTapSlots = 32;                         // 256 bytes for 
 constexpr size_t kStaticElems = kStaticTapSlots + kStaticMaxPixels / 4 + kStaticMaxPixels / 16;
 static __device__ __align__(256) float2 g_static_scratch[kStaticElems];
 
-constexpr int kStaticMaxDevices = 64;
+// The array's device address belongs to a CUDA context: it is looked up once per
+// context (the primary context of each device, or a context the caller made
+// current) and kept in this table.
+typedef int (*CtxGetCurrentFn)(void** ctx);   // the driver's cuCtxGetCurrent
+constexpr int kStaticMaxContexts = 64;
+struct StaticSlot {
+  void* ctx;
+  float2* base;
+};
 static std::mutex g_static_mutex;
-static float2* g_static_base[kStaticMaxDevices];   // device address of g_static_scratch, per device
+static StaticSlot g_static_slots[kStaticMaxContexts];
+static int g_static_nslots = 0;
+static CtxGetCurrentFn g_ctx_get_current = nullptr;
 
-// Once per device, with that device current: the array's device address (its
-// name in host code is only a host-side stand-in) and the filter taps.
-static int static_scratch_setup(int dev, float2** base) {
-  if (dev < 0 || dev >= kStaticMaxDevices) return MBIR_ERR_UNSUPPORTED_SIZE;
+// The context current on this thread, or null when the runtime has made none yet.
+static void* current_context() {
+  if (!g_ctx_get_current) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+  }
+  void* ctx = nullptr;
+  return g_ctx_get_current(&ctx) == 0 ? ctx : nullptr;
+}
+
+// The db4 taps, passed by value to a one-CTA kernel that writes them into the
+// array: no host-to-device copy is involved.
+struct Taps8 {
+  float h[8];
+};
+
+__global__ void static_taps_kernel(Taps8 t, float* dst) {
+  if (threadIdx.x < 8) dst[threadIdx.x] = t.h[threadIdx.x];
+}
+
+// Once per context, with the caller's device current: the array's device address
+// (its name in host code is only a host-side stand-in), the kernels' shared
+// memory attributes and the taps.
+static int static_scratch_setup(float2** base) {
   std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_base[dev]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess) return set_cuda_error(e, "cudaGetSymbolAddress(static wavelet scratch)");
+  void* ctx = current_context();
+  for (int i = 0; ctx && i < g_static_nslots; ++i)
+    if (g_static_slots[i].ctx == ctx) {
+      *base = g_static_slots[i].base;
+      return MBIR_OK;
+    }
+  // the lookup loads the library's module into the context if it is not yet (lazy
+  // module loading), which is when the array is placed in device memory
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+  if (e != cudaSuccess) {
+    const int rc = set_cuda_error(e, "cudaGetSymbolAddress(static wavelet scratch)");
+    set_error_text(std::string("mbir_wavelet_static: the 5 MiB static scratch array could not be placed on the "
+                               "device (the module loads at the first call; make it at start-up, before other "
+                               "allocators take the memory): ") + cudaGetErrorString(e));
+    return rc;
+  }
+  const int rc = configure_wavelet_t<float>();
+  if (rc) return rc;
+  // the taps, written once per context and waited for: the transform kernels read
+  // them in their prologue, before they wait on the previous kernel of the stream
+  Taps8 taps;
+  {
     double h[8];
     daubechies8_taps(h);
-    float hf[8];
-    for (int i = 0; i < 8; ++i) hf[i] = (float)h[i];
-    e = cudaMemcpy(ptr, hf, sizeof(hf), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return set_cuda_error(e, "static wavelet taps upload");
-    g_static_base[dev] = static_cast<float2*>(ptr);
+    for (int i = 0; i < 8; ++i) taps.h[i] = (float)h[i];
   }
-  *base = g_static_base[dev];
+  static_taps_kernel<<<1, 32>>>(taps, static_cast<float*>(ptr));
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_cuda_error(e, "static wavelet taps");
+  if (!ctx) ctx = current_context();   // the lookup made the runtime's context current
+  if (ctx) {
+    if (g_static_nslots >= kStaticMaxContexts) {
+      set_error_text("mbir_wavelet_static: more than 64 CUDA contexts used the static scratch");
+      return MBIR_ERR_INVALID;
+    }
+    g_static_slots[g_static_nslots++] = {ctx, static_cast<float2*>(ptr)};
+  }
+  *base = static_cast<float2*>(ptr);
   return MBIR_OK;
 }
 
@@ -594,7 +655,7 @@ int wavelet_static_impl(int nx, int nz, int inverse, const void* in, void* out, 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
   float2* base = nullptr;
-  int rc = static_scratch_setup(dev, &base);
+  int rc = static_scratch_setup(&base);
   if (rc) return rc;
   // a plan-shaped view onto the static scratch: no tables, no allocation
   mbir_plan_s view;

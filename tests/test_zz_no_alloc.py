@@ -3,9 +3,14 @@ cannot call cudaMalloc, against the plan-based mbir_wavelet.
 
 Kept in its own file, collected last, so that a stop-at-first-failure run has
 already run every other test if this one fails.  It must pass alone in a fresh
-process as well as after the other tests (the first call on a device does the
-static-scratch set-up)."""
+process as well as after the other tests (the first call in a context does the
+static-scratch set-up); one test runs it in a child process that creates no
+plan at all, so the set-up there is the static call's own."""
 import ctypes as C
+import os
+import subprocess
+import sys
+import textwrap
 
 import numpy as np
 import pytest
@@ -61,3 +66,48 @@ def test_static_wavelet_rejects_oversize_and_bad_shapes(mbir):
     assert _static(mbir, 60, 256, False, x, y) == -2          # not divisible by 8
     assert _static(mbir, 64, 256, False, x, x) == -1          # in == out
     torch.cuda.synchronize()
+
+
+_CHILD = textwrap.dedent("""
+    import ctypes as C, sys
+    import numpy as np, torch
+    sys.path.insert(0, {root!r})
+    from oracle import wavelet
+    from paper_2108_01438_gb300 import mbir
+    lib = mbir.lib()                       # the library only: no plan is ever created
+    nx, nz = 64, 96
+    h = wavelet.daubechies_lowpass(4)
+    rng = np.random.default_rng(7)
+    st = torch.cuda.Stream()               # a non-blocking side stream, as torch makes them
+    worst = 0.0
+    for call in range(2):
+        x = rng.standard_normal((nx, nz)) + 1j * rng.standard_normal((nx, nz))
+        with torch.cuda.stream(st):
+            xt = torch.from_numpy(x.astype(np.complex64)).cuda()
+            c = torch.empty_like(xt)
+            r = torch.empty_like(xt)
+            a = lib.mbir_wavelet_static(nx, nz, 0, C.c_void_p(xt.data_ptr()), C.c_void_p(c.data_ptr()),
+                                        C.c_void_p(st.cuda_stream))
+            b = lib.mbir_wavelet_static(nx, nz, 1, C.c_void_p(c.data_ptr()), C.c_void_p(r.data_ptr()),
+                                        C.c_void_p(st.cuda_stream))
+        st.synchronize()
+        assert a == 0 and b == 0, (a, b, lib.mbir_last_error())
+        x32 = x.astype(np.complex64).astype(np.complex128)
+        ref = wavelet.dwt2(x32, h, 3)
+        got = c.cpu().numpy().astype(np.complex128)
+        worst = max(worst, np.linalg.norm(got - ref) / np.linalg.norm(ref),
+                    np.linalg.norm(r.cpu().numpy() - x32) / np.linalg.norm(x32))
+    print("WORST", worst)
+""")
+
+
+def test_static_wavelet_first_call_without_any_plan(mbir):
+    """A fresh process whose first library call is mbir_wavelet_static, on a
+    non-blocking stream: the set-up (address, attributes, taps) is its own, and
+    the result matches the FP64 oracle transform on two calls in a row."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _CHILD.format(root=root)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    worst = float(r.stdout.split("WORST")[1].split()[0])
+    assert worst <= TOL, worst
