@@ -12,8 +12,10 @@ mask) is the B-scan model of oracle/isam.py; a volume with ny = 1 is a B-scan.
     y(p, m) = s(p, m) Re{ ifft2_l[ H(|q_l|, k_m) sum_n w_n X(l, n) e^{-j beta_lm (z_n - z_f)} ] },
     X = fft2 over (px, py) of x.
 
-Only the direct depth sum is given here; it is the definition that a GPU path
-for volumes will be checked against.
+Two realisations, as for the B-scan: the direct depth sum (phi3_exact and its
+transpose) and the Kaiser-Bessel NUFFT of oracle/isam.py applied to every
+lateral-frequency row (lx, ly) of the 2-D lateral spectrum (phi3_nufft and its
+transpose), which the GPU path is checked against.
 """
 from __future__ import annotations
 
@@ -23,7 +25,8 @@ import numpy as np
 
 from . import isam
 
-__all__ = ["VolGeom", "make_vol_geom", "lateral_q2", "phi3_exact", "phi3_adj_exact"]
+__all__ = ["VolGeom", "make_vol_geom", "lateral_q2", "phi3_exact", "phi3_adj_exact", "phi3_nufft",
+           "phi3_adj_nufft"]
 
 
 @dataclass
@@ -94,3 +97,39 @@ def phi3_adj_exact(y: np.ndarray, mask: np.ndarray | None, v: VolGeom) -> np.nda
             E = np.exp(1j * (z[:, None] - g.z_f) * beta[lx, ly][None, :])
             W[lx, ly] = w * (E @ V[lx, ly])
     return (g.nx * v.ny) * np.fft.ifft2(W, axes=(0, 1))
+
+
+def _kb_position(v: VolGeom, beta: np.ndarray) -> np.ndarray:
+    """t = K/(2 pi) (beta dz mod 2 pi) on the K-point axial grid, per (lx, ly, m)."""
+    g = v.g
+    return np.mod((g.K / (2.0 * np.pi)) * np.mod(beta * g.dz, 2.0 * np.pi), g.K)
+
+
+def phi3_nufft(x: np.ndarray, mask: np.ndarray | None, v: VolGeom) -> np.ndarray:
+    """Phi x for a volume x[nx, ny, nz] with the axial resampling done by the KB
+    NUFFT of oracle/isam.py on each of the nx * ny lateral-frequency rows."""
+    g = v.g
+    beta, H = _beta_filter(v)
+    w = isam.depth_weight(g)
+    t = _kb_position(v, beta)
+    X = np.fft.fft2(np.asarray(x, dtype=np.complex128), axes=(0, 1)) * w[None, None, :]
+    U = isam.nufft_axial(X.reshape(g.nx * v.ny, g.nz), t.reshape(g.nx * v.ny, g.m), g).reshape(g.nx, v.ny, g.m)
+    U = U * np.exp(1j * beta * (g.z_f - g.n0 * g.dz))
+    y = np.fft.ifft2(H * U, axes=(0, 1)).real
+    return y if mask is None else y * mask
+
+
+def phi3_adj_nufft(y: np.ndarray, mask: np.ndarray | None, v: VolGeom) -> np.ndarray:
+    """The transpose of phi3_nufft: each of its steps transposed, in reverse order."""
+    g = v.g
+    beta, H = _beta_filter(v)
+    w = isam.depth_weight(g)
+    t = _kb_position(v, beta)
+    r = np.asarray(y, dtype=np.float64)
+    if mask is not None:
+        r = r * mask
+    R = np.fft.fft2(r.astype(np.complex128), axes=(0, 1)) / (g.nx * v.ny)
+    V = np.conj(H) * R * np.exp(-1j * beta * (g.z_f - g.n0 * g.dz))
+    a = isam.nufft_axial_adjoint(V.reshape(g.nx * v.ny, g.m), t.reshape(g.nx * v.ny, g.m), g)
+    a = a.reshape(g.nx, v.ny, g.nz)
+    return (g.nx * v.ny) * np.fft.ifft2(a * w[None, None, :], axes=(0, 1))

@@ -96,3 +96,63 @@ def test_in_focus_point_is_its_interferogram_at_its_a_scan():
     assert np.max(np.abs(y[2, 3] - want)) <= 1e-12 * np.max(np.abs(want))
     y[2, 3] = 0
     assert np.max(np.abs(y)) <= 1e-12 * np.max(np.abs(want))
+
+
+# ------------------------------------------------ the NUFFT realisation of the volume
+
+
+def test_nufft_volume_with_ny_one_is_the_b_scan_nufft():
+    v = _vol(12, 1, 32, 40)
+    rng = np.random.default_rng(11)
+    x = _cx(rng, (12, 1, 32))
+    mask = (rng.random((12, 1, 40)) < 0.6).astype(np.uint8)
+    y = volume.phi3_nufft(x, mask, v)
+    want = isam.phi_nufft(x[:, 0], mask[:, 0], v.g)
+    assert np.max(np.abs(y[:, 0] - want)) <= 1e-12 * np.max(np.abs(want))
+    r = rng.standard_normal((12, 1, 40))
+    a = volume.phi3_adj_nufft(r, mask, v)
+    want = isam.phi_adj_nufft(r[:, 0], mask[:, 0], v.g)
+    assert np.max(np.abs(a[:, 0] - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_nufft_volume_is_close_to_the_direct_sum():
+    """The Kaiser-Bessel NUFFT (J = 6, sigma = 2) against the exact depth sum on a
+    volume with both lateral axes excited: the same ~1e-6 gap as the B-scan."""
+    v = _vol(6, 5, 32, 40, focus_frac=0.3, disp_edge_rad=12.0)
+    rng = np.random.default_rng(12)
+    x = _cx(rng, (6, 5, 32))
+    mask = (rng.random((6, 5, 40)) < 0.7).astype(np.uint8)
+    y, ye = volume.phi3_nufft(x, mask, v), volume.phi3_exact(x, mask, v)
+    assert np.linalg.norm(y - ye) / np.linalg.norm(ye) <= 2e-5
+    r = rng.standard_normal((6, 5, 40))
+    a, ae = volume.phi3_adj_nufft(r, mask, v), volume.phi3_adj_exact(r, mask, v)
+    assert np.linalg.norm(a - ae) / np.linalg.norm(ae) <= 2e-5
+
+
+def test_nufft_volume_adjoint_is_the_dense_transpose():
+    v = _vol(4, 3, 8, 6)
+    rng = np.random.default_rng(13)
+    mask = (rng.random((4, 3, 6)) < 0.7).astype(np.uint8)
+    n_in = 4 * 3 * 8
+    A = np.zeros((4 * 3 * 6, 2 * n_in))
+    for i in range(n_in):
+        for part, c in ((0, 1.0), (1, 1j)):
+            e = np.zeros(n_in, complex)
+            e[i] = c
+            A[:, part * n_in + i] = volume.phi3_nufft(e.reshape(4, 3, 8), mask, v).ravel()
+    r = rng.standard_normal((4, 3, 6))
+    a = volume.phi3_adj_nufft(r, mask, v).ravel()
+    want = A.T @ r.ravel()
+    assert np.max(np.abs(np.concatenate([a.real, a.imag]) - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+def test_nufft_volume_axis_swap_and_shift():
+    """Isotropy of |q| and lateral shift invariance hold for the NUFFT form too."""
+    v = _vol(6, 6, 16, 20)
+    rng = np.random.default_rng(14)
+    x = _cx(rng, (6, 6, 16))
+    y = volume.phi3_nufft(x, None, v)
+    yt = volume.phi3_nufft(np.transpose(x, (1, 0, 2)), None, v)
+    assert np.max(np.abs(yt - np.transpose(y, (1, 0, 2)))) <= 1e-11 * np.max(np.abs(y))
+    ys = volume.phi3_nufft(np.roll(x, (2, -1), axis=(0, 1)), None, v)
+    assert np.max(np.abs(ys - np.roll(y, (2, -1), axis=(0, 1)))) <= 1e-11 * np.max(np.abs(y))
