@@ -168,8 +168,12 @@ typedef struct {
  * frequencies, beta = sqrt(4k^2 - q^2) grid positions, filter, deapodisation,
  * KB kernel, FFT twiddles) on the host and uploads them, and allocates the
  * workspace, on the current CUDA device.  Synchronous.
- * Supported sizes: nx in [2, 4096] and nz in [8, 4096] with every prime factor
- * <= 7; nx * nz and nx * m below 2^31; m in [1, 65536]; K = 2 nz.
+ * Supported sizes: nz in [8, 4096] with every prime factor <= 7 (K = 2 nz); nx
+ * in [2, 4096]; nx * nz and nx * m below 2^31; m in [1, 65536].  A width nx with
+ * a prime factor above 7 runs its lateral transform (Eq. 4) in the Bluestein
+ * (chirp-z) form, a convolution through transforms of the smallest length
+ * L >= 2 nx - 1 whose prime factors are <= 7; L must be at most 4096, which
+ * admits every width up to 2048 (wider ones return MBIR_ERR_UNSUPPORTED_SIZE).
  * Returns MBIR_ERR_INVALID / MBIR_ERR_UNSUPPORTED_SIZE before touching the GPU.
  * stream: used for the uploads; *out receives the plan (NULL on failure).
  */
@@ -180,6 +184,27 @@ void mbir_plan_destroy(mbir_plan plan);
 
 /* Geometry sizes of a plan; any output pointer may be NULL. */
 int mbir_plan_dims(mbir_plan plan, int32_t* nx, int32_t* nz, int32_t* m, int32_t* precision);
+
+/*
+ * A plan for a 3-D volume: the B-scan geometry plus a second lateral axis of ny
+ * pixels spaced dy_um (<= 0 selects dx_um), the volumetric acquisition of
+ * Sec. 3.1 with the operator of Sec. 2.1 over both lateral axes: the lateral
+ * Fourier transform of Eq. 4 is 2-D, and the ISAM resampling of Eq. 5 and the
+ * beam filter see |q|^2 = q_x^2 + q_y^2 with q_y = 2 pi l~_y / (ny dy).
+ * Layouts: image x [nx][ny][nz] complex, measurements y and mask [nx][ny][m],
+ * depth / spectrum contiguous.  A volume plan runs mbir_forward and mbir_adjoint
+ * (same arguments, these layouts); the other calls that take a plan return
+ * MBIR_ERR_UNSUPPORTED_SIZE for it.  Sizes: ny in [2, 4096] with the same rule as
+ * nx (Bluestein beyond 7-smooth), nx * ny * nz and nx * ny * m below 2^31; the
+ * other limits as mbir_plan_create.  The resampling table has one row per
+ * (|lx|, |ly|): (nx/2 + 1)(ny/2 + 1) m entries of 16 bytes (FP32), built on the
+ * host.  Returns MBIR_ERR_INVALID for ny < 2.  Synchronous.
+ */
+int mbir_volume_plan_create(const mbir_geometry* geometry, int32_t ny, double dy_um, void* stream,
+                            mbir_plan* out);
+
+/* The second lateral size of a plan (1 for a B-scan plan). */
+int mbir_volume_dims(mbir_plan plan, int32_t* ny);
 
 /*
  * y = Phi(x) (Eq. for_model): lateral FFT, KB-NUFFT resampling onto
@@ -408,7 +433,8 @@ int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in,
  * alike; the paper, which ran Matlab on a CPU, has no counterpart).  Candidates:
  * the lateral tile width (columns per CTA, powers of two up to 16 within the
  * kernels' shared-memory tile), the order of the lateral radices, and the row
- * adjoint kernel (paired gather, single-row gather, shared-memory atomics, as far
+ * adjoint kernel (paired gather with per-term weights, paired gather, single-row gather,
+ * shared-memory atomics, as far
  * as the plan can run each).  The lateral ones are timed first with the automatic
  * adjoint kernel, then the adjoint kernels with the best lateral choice.  Each
  * candidate is warmed once, then timed over `reps` forward + adjoint pairs on
@@ -428,7 +454,8 @@ int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in,
 typedef struct {
   int32_t tile_c;          /* lateral tile width, columns per CTA */
   int32_t lateral_order;   /* 0: largest radix first, 1: smallest radix first */
-  int32_t adjoint_kernel;  /* 4: paired gather, 1: single-row gather, 2: atomics, -1: automatic */
+  int32_t adjoint_kernel;  /* 5: paired gather with per-term weights (two CTAs an SM), 4: paired gather,
+                              1: single-row gather, 2: atomics, -1: automatic */
   double pair_ms;          /* measured forward + adjoint time (autotune), else 0 */
 } mbir_tuning;
 

@@ -821,6 +821,8 @@ extern "C" {
 int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const uint8_t* const* mask,
                      const mbir_solve_opts* opts, void* const* x, mbir_solve_info* info, void* stream) {
   if (!plans || n < 1 || !y || !opts || !x) return MBIR_ERR_INVALID;
+  for (int i = 0; i < n; ++i)
+    if (const int vrc = bscan_only(plans[i], "mbir_solve_batch")) return vrc;
   std::vector<BScan> scans(n);
   std::vector<BScan*> ptrs(n);
   for (int i = 0; i < n; ++i) {

@@ -124,22 +124,41 @@ struct BatchCache;
 
 struct mbir_plan_s {
   int nx, nz, m, K, J, n0, nlh, precision;
+  // volumes (mbir_volume_plan_create): a second lateral axis of ny pixels; ny = 1
+  // for a B-scan.  The resampling table has ntab rows, one per (|lx|, |ly|); the
+  // paired row kernels run npair CTAs, CTA c on rows rowmap[c].x and rowmap[c].y
+  // (-1: none) with table row rowmap[c].z (rowmap null for a B-scan: CTA l' runs
+  // rows l' and nx - l' with table row l')
+  int ny, ntab, npair;
+  double dy;
+  int4* rowmap;
+  mbir::Radix rad_y;          // the y-axis transform, of length nyl
+  int nyl, tile_y;
+  void* tw_y;
+  int* perm_y;
+  void* chirp_y;
+  void* bhat_y;
   int device;
   double dx, dz, alpha;
-  mbir::Radix rad_x, rad_k;
+  mbir::Radix rad_x, rad_k;   // rad_x: the lateral transform, of length nxl
+  int nxl;                    // lateral transform length: nx, or the Bluestein length when nx is not 7-smooth
+  void* chirp;                // Bluestein: [nx] e^{-j pi p^2 / nx} (plan precision complex), else null
+  void* bhat;                 // Bluestein: [nxl] DFT of the conjugate chirp / nxl, digit-reversed
   int tile_c;                 // lateral FFT columns per CTA
   int lat_order;              // lateral radix order: 0 largest radix first, 1 smallest first
   int adj_kind;               // row adjoint kernel override (RowKind), -1: automatic
   int k_ascending;            // wavenumbers increase with the spectrometer pixel index
   // device tables (one precision, per plan)
-  void* tw_x;                 // nx-point twiddle tables [lo | hi]
+  void* tw_x;                 // nxl-point twiddle tables [lo | hi]
   void* tw_k;                 // K-point twiddle tables [lo | hi]
-  int* perm_x;                // digit reversal of the nx-point transform
+  int* perm_x;                // [nx] tile row of lateral output p: digit reversal of the nx-point
+                              // transform, the identity for Bluestein (natural-order output)
   int* perm_k;                // digit reversal of the K-point transform
   void* cdep;                 // [nz] falloff / KB deapodisation
-  void* tab;                  // [nlh][m] TabF or TabD
-  int4* rowmeta;              // [nlh] {base cell of u = 0, span of u + J, direction, 0}
+  void* tab;                  // [ntab][m] TabF or TabD
+  int4* rowmeta;              // [ntab] {base cell of u = 0, span of u + J, direction, 0}
   int gather_ok;              // every row monotone with span <= K: deterministic adjoint gather
+  int max_span;               // largest row span (rowmeta .y) of the plan
   float kbpoly[mbir::kMaxJ][mbir::kKbDeg + 1];   // FP32 KB weight polynomials per tap
   double* h_db4;              // 8 wavelet taps (device, double)
   float* h_db4f;              // same, float
@@ -171,6 +190,15 @@ constexpr int kSoftGrid = 1024;
 
 int set_cuda_error(cudaError_t e, const char* where);
 void set_error_text(const std::string& s);
+
+// Volume plans (ny > 1) run the operator only: the B-scan calls refuse them.
+inline int bscan_only(mbir_plan p, const char* call) {
+  if (p && p->ny > 1) {
+    set_error_text(std::string(call) + ": a volume plan takes mbir_forward and mbir_adjoint only");
+    return MBIR_ERR_UNSUPPORTED_SIZE;
+  }
+  return MBIR_OK;
+}
 
 #define MBIR_CUDA_TRY(call)                                         \
   do {                                                              \
@@ -279,7 +307,8 @@ size_t row_args_bytes(int precision);
 size_t lat_smem_bytes(mbir_plan p);
 size_t row_smem_bytes(mbir_plan p, int adjoint_gather);
 // Row (NUFFT) kernel of a plan: FP32 plans pair rows l and nx - l in one CTA
-enum RowKind { ROW_FWD = 0, ROW_GATHER = 1, ROW_ATOMIC = 2, ROW_FWD_PAIR = 3, ROW_GATHER_PAIR = 4 };
+enum RowKind { ROW_FWD = 0, ROW_GATHER = 1, ROW_ATOMIC = 2, ROW_FWD_PAIR = 3, ROW_GATHER_PAIR = 4,
+               ROW_GATHER_PAIR_LEAN = 5 };
 int row_kind(mbir_plan p, bool adjoint);
 bool row_kind_fits(mbir_plan p, int kind);     // adjoint kinds a plan can run
 int row_ctas(mbir_plan p, int kind);           // CTAs of one scan

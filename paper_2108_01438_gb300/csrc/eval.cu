@@ -136,6 +136,7 @@ using namespace mbir;
 extern "C" {
 
 int mbir_ncc(mbir_plan p, const void* x, const void* z, double* r, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_ncc")) return vrc;
   if (!p || !x || !z || !r) return MBIR_ERR_INVALID;
   return ncc_impl(p, x, z, r, (cudaStream_t)stream);
 }
@@ -144,6 +145,7 @@ int mbir_lambda_search(mbir_plan p, const void* y, const uint8_t* mask, const vo
                        const mbir_solve_opts* opts, double log10_lo, double log10_hi, int32_t n_eval, void* x,
                        mbir_lambda_search_info* info, void* stream) {
   if (!p || !y || !z_true || !opts || !x || !info || n_eval < 2) return MBIR_ERR_INVALID;
+  if (const int vrc = bscan_only(p, "mbir_lambda_search")) return vrc;
   if (!isfinite(log10_lo) || !isfinite(log10_hi) || !(log10_lo < log10_hi)) return MBIR_ERR_INVALID;
   if (log10_lo < -30 || log10_hi > 30) return MBIR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;

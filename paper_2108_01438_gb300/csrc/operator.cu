@@ -76,6 +76,8 @@ struct LatEp {
   void* z2;
   void* vout;
   const double* scal;
+  const void* chirp;
+  const void* bhat;
   R scale, mu, delta, tau;
 };
 
@@ -174,6 +176,79 @@ __device__ __forceinline__ void lat_fft(cplx_t<R>* s, int TC, const Radix& rad, 
     if constexpr (DIT) fft_dit<INV>(s, TC, rad, f.tw, false);
     else fft_dif<INV>(s, TC, rad, f.tw, false);
   }
+}
+
+// Bluestein (chirp-z) form of the lateral transform, for widths nx that do not
+// factor into radices 2..8: with c_k = e^{-j pi k^2 / nx},
+//   X_l = sum_p x_p e^{-2 pi j l p / nx} = c_l sum_p (x_p c_p) conj(c)_{l-p},
+// a linear convolution that an nxl-point transform pair computes exactly
+// (nxl = rad.n >= 2 nx - 1, so indices l - p never wrap onto each other).  The
+// tile holds rows [0, nxl): rows p < nx are multiplied by the chirp and the rest
+// zeroed, a forward dif transform leaves the spectrum digit-reversed, where it
+// is multiplied by the plan's transformed conjugate chirp (stored digit-reversed,
+// divided by nxl), and an inverse dit transform brings the convolution back to
+// natural order, multiplied by the chirp again.  The inverse transform is
+// conj(forward(conj x)).  Output rows [0, nx) are in natural order.
+template <class R, bool INV>
+__device__ __noinline__ void lat_bluestein(cplx_t<R>* s, int TC, int nx, const Radix& rad, const LatFFT<R>& tw,
+                                           const cplx_t<R>* chirp, const cplx_t<R>* bhat) {
+  using V = cplx_t<R>;
+  const int half = TC >> 1, hs = __ffs(half) - 1;
+  const int npairs = rad.n * half;
+  const V zero = cmk<V>(R(0), R(0));
+  for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+    const int p = i >> hs, idx = p * TC + 2 * (i & (half - 1));
+    V va = zero, vb = zero;
+    if (p < nx) {
+      lds2(s, idx, va, vb);
+      if (INV) {
+        va = cconj(va);
+        vb = cconj(vb);
+      }
+      const V c = chirp[p];
+      va = cmul(va, c);
+      vb = cmul(vb, c);
+    }
+    sts2(s, idx, va, vb);
+  }
+  __syncthreads();
+  lat_fft<R, false, false>(s, TC, rad, tw);
+  for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+    const int p = i >> hs, idx = p * TC + 2 * (i & (half - 1));
+    V va, vb;
+    lds2(s, idx, va, vb);
+    const V h = bhat[p];
+    sts2(s, idx, cmul(va, h), cmul(vb, h));
+  }
+  __syncthreads();
+  lat_fft<R, true, true>(s, TC, rad, tw);
+  for (int i = threadIdx.x; i < nx * half; i += blockDim.x) {
+    const int p = i >> hs, idx = p * TC + 2 * (i & (half - 1));
+    V va, vb;
+    lds2(s, idx, va, vb);
+    const V c = chirp[p];
+    va = cmul(va, c);
+    vb = cmul(vb, c);
+    if (INV) {
+      va = cconj(va);
+      vb = cconj(vb);
+    }
+    sts2(s, idx, va, vb);
+  }
+  __syncthreads();
+}
+
+// The lateral transform of a tile: the plan's mixed-radix FFT (dif: digit-reversed
+// out; dit: digit-reversed in, natural out), or the Bluestein form when the plan
+// has a chirp (natural order in and out either way).
+template <class R, bool INV, bool DIT>
+__device__ __forceinline__ void lat_xform(cplx_t<R>* s, int TC, int nx, const Radix& rad, const LatFFT<R>& tw,
+                                          const void* chirp, const void* bhat) {
+  if (chirp)
+    lat_bluestein<R, INV>(s, TC, nx, rad, tw, static_cast<const cplx_t<R>*>(chirp),
+                          static_cast<const cplx_t<R>*>(bhat));
+  else
+    lat_fft<R, INV, DIT>(s, TC, rad, tw);
 }
 
 __device__ __forceinline__ bool al(const void* p, unsigned bytes) {
@@ -338,7 +413,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   using V = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s = reinterpret_cast<V*>(smem_raw);
-  V* tws = s + nx * TC;
+  V* tws = s + rad.n * TC;   // rad.n = nx, or the Bluestein length
   const int tid = threadIdx.x;
   const LatFFT<R> tw = lat_twiddles<R>(tws, twg, rad);
   // digit-reversal table in shared memory: the read-out and the middle epilogue
@@ -393,7 +468,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   if constexpr (kMid) {
     // inverse as a forward dif of conj S, the epilogue in place on the
     // digit-reversed tile, then the forward dit
-    lat_fft<R, false, false>(s, TC, rad, tw);
+    lat_xform<R, false, false>(s, TC, nx, rad, tw, a.chirp, a.bhat);
     constexpr int UM = 2;
     for (int p = p0; p < nx; p += UM * pstep) {
       EpOps<R> oa[UM], ob[UM];
@@ -427,14 +502,14 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
       }
     }
     __syncthreads();
-    lat_fft<R, false, true>(s, TC, rad, tw);
+    lat_xform<R, false, true>(s, TC, nx, rad, tw, a.chirp, a.bhat);
     for (int p = p0; p < nx; p += pstep) {
       V xa, xb;
       lds2(s, p * TC + b, xa, xb);
       st2(reinterpret_cast<V*>(a.out), (size_t)p * C + c, v2, ok0, ok1, cscale(xa, a.scale), cscale(xb, a.scale));
     }
   } else {
-    lat_fft<R, INV, false>(s, TC, rad, tw);
+    lat_xform<R, INV, false>(s, TC, nx, rad, tw, a.chirp, a.bhat);
     constexpr int UE = 4;
     for (int p = p0; p < nx; p += UE * pstep) {
       EpOps<R> oa[UE], ob[UE];
@@ -488,6 +563,8 @@ lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>>
     e.z2 = A.z2;
     e.vout = A.vout;
     e.scal = A.scal;
+    e.chirp = A.chirp;
+    e.bhat = A.bhat;
     e.scale = A.scale;
     e.mu = B.set_mu ? R(B.mu) : A.mu;
     e.delta = A.delta;
@@ -495,6 +572,32 @@ lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>>
     __syncthreads();
     lateral_body<R, MODE>(e, rad, A.nx, A.tc, A.cols, blk, A.tw, A.perm, A.partial);
   }
+}
+
+// The y-axis transform of a volume: lateral_body over the ny rows of every px slab
+// (blockIdx.y) of an [nx][ny][cols] array, in place or not (each CTA stages its
+// whole tile before it writes).  Complex transforms only.
+template <class R, int MODE>
+__global__ void __launch_bounds__(kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
+lateral_slab_kernel(const __grid_constant__ LatArgs<R> a0, long long slab) {
+  static_assert(MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV, "complex slab transforms only");
+  const size_t off = (size_t)blockIdx.y * (size_t)slab;
+  LatEp<R> e;
+  e.in = static_cast<const cplx_t<R>*>(a0.in) + off;
+  e.out = static_cast<cplx_t<R>*>(a0.out) + off;
+  e.mask = nullptr;
+  e.y = nullptr;
+  e.pz = nullptr;
+  e.r = nullptr;
+  e.z1 = nullptr;
+  e.z2 = nullptr;
+  e.vout = nullptr;
+  e.scal = nullptr;
+  e.chirp = a0.chirp;
+  e.bhat = a0.bhat;
+  e.scale = a0.scale;
+  e.mu = e.delta = e.tau = R(0);
+  lateral_body<R, MODE>(e, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, nullptr);
 }
 
 // ------------------------------------------------------------- KB weights
@@ -555,6 +658,16 @@ struct DotAcc {
 
 // --------------------------------------------------------- row kernels (NUFFT)
 
+// Table row of lateral-frequency row l: |l~| for a B-scan; (|lx|, |ly|) with
+// (lx, ly) = (l / ny, l % ny) for a volume.
+template <class A>
+__device__ __forceinline__ int table_row(const A& a, int l) {
+  if (a.ny == 1) return l <= a.nx - l ? l : a.nx - l;
+  const int lx = l / a.ny, ly = l - lx * a.ny;
+  const int ix = lx <= a.nx - lx ? lx : a.nx - lx, iy = ly <= a.ny - ly ? ly : a.ny - ly;
+  return ix * (a.ny / 2 + 1) + iy;
+}
+
 template <class R, int J, bool COMP>
 __device__ __forceinline__ void row_forward_body(const RowArgs<R>& a, const Radix& rad, int blk, const RowArgs<R>& a0) {
   using V = cplx_t<R>;
@@ -563,7 +676,7 @@ __device__ __forceinline__ void row_forward_body(const RowArgs<R>& a, const Radi
   V* buf = reinterpret_cast<V*>(smem_raw);
   V* tws = buf + a.K;
   const int l = blk;
-  const int lp = l <= a.nx - l ? l : a.nx - l;
+  const int lp = table_row(a, l);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
   const bool sw = (K & 15) == 0;
@@ -646,7 +759,7 @@ __device__ __forceinline__ void row_adjoint_body(const RowArgs<R>& a, const Radi
   V* buf = reinterpret_cast<V*>(smem_raw);
   V* tws = buf + a.K;
   const int l = blk;
-  const int lp = l <= a.nx - l ? l : a.nx - l;
+  const int lp = table_row(a, l);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
   const bool sw = (K & 15) == 0;
@@ -737,7 +850,7 @@ __device__ __forceinline__ void row_adjoint_gather_body(const RowArgs<R>& a, con
   uint16_t* su = reinterpret_cast<uint16_t*>(spoly + J * (kKbDeg + 1));   // [M]
   uint16_t* sfirst = su + M + (M & 1);                              // [span + 1]
   const int l = blk;
-  const int lp = l <= a.nx - l ? l : a.nx - l;
+  const int lp = table_row(a, l);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool sw = (K & 15) == 0;
   const int* perm = a.perm;
@@ -871,7 +984,14 @@ __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, c
   const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
   const int K8 = (K + 7) & ~7;
   float4* buf = reinterpret_cast<float4*>(smem_raw);   // [K8], swizzled
-  const int la = lp, lb = pair_row_b(lp, a.nx), lbr = lb < 0 ? la : lb;
+  int la = lp, lb = pair_row_b(lp, a.nx);
+  if (a.rowmap) {   // a volume: the CTA's rows and table row from the plan's map
+    const int4 rm = a.rowmap[lp];
+    la = rm.x;
+    lb = rm.y;
+    lp = rm.z;
+  }
+  const int lbr = lb < 0 ? la : lb;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const TwP tw = load_twiddles_p(buf + K8, reinterpret_cast<const float2*>(a.tw), rad);
   const float2* Xa = reinterpret_cast<const float2*>(a.in) + (size_t)la * nz;
@@ -969,7 +1089,14 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
   float* sw = reinterpret_cast<float*>(sv + M);              // [M][J] weights
   uint16_t* su = reinterpret_cast<uint16_t*>(sw + M * J);    // [M]
   uint16_t* sfirst = su + M + (M & 1);                       // [span + 1]
-  const int la = lp, lb = pair_row_b(lp, a.nx), lbr = lb < 0 ? la : lb;
+  int la = lp, lb = pair_row_b(lp, a.nx);
+  if (a.rowmap) {   // a volume: the CTA's rows and table row from the plan's map
+    const int4 rm = a.rowmap[lp];
+    la = rm.x;
+    lb = rm.y;
+    lp = rm.z;
+  }
+  const int lbr = lb < 0 ? la : lb;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const TwP tw = load_twiddles_p(tws, reinterpret_cast<const float2*>(a.tw), rad);
   const int4 meta = a.rowmeta[lp];
@@ -1066,6 +1193,139 @@ row_gather_pair_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef
   }
 }
 
+// The paired gather without per-pixel weight and cell arrays, so that two CTAs
+// fit an SM (about 110 KB at K = 4096, M = 2048 instead of 162 KB).  Staging keeps
+// conj(f) R of both rows and the fractional position of each pixel in
+// increasing-u order, and first[v] = min{s : u_s >= v}, built directly from the
+// table (pixel s writes the entries (u_{s-1}, u_s]).  Cell c then sums, tap by tap,
+// the run of pixels whose first-tap cell is v = c - j, [first[v], first[v+1]),
+// with the tap's weight evaluated from the pixel's fractional position by its
+// polynomial.  The order of the terms of a cell is fixed (taps in order, pixels
+// in order), so the result is deterministic; it differs from the other gathers
+// only in rounding order.
+template <int J>
+__device__ __forceinline__ float kb_tap_weight(float frac, const RowArgs<float>& a0, int j) {
+  const float x = frac - 0.5f;
+  float t = a0.kbpoly[j][kKbDeg];
+#pragma unroll
+  for (int d = kKbDeg - 1; d >= 0; --d) t = fmaf(t, x, a0.kbpoly[j][d]);
+  return t;
+}
+
+template <int J>
+__device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& a, const Radix& rad, int lp,
+                                                          const RowArgs<float>& a0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  const int K8 = (K + 7) & ~7;
+  float4* buf = reinterpret_cast<float4*>(smem_raw);         // [K8], swizzled
+  float4* tws = buf + K8;
+  float4* sv = tws + rad.tw_lo + rad.tw_hi;                  // [M] conj(f) R of both rows, split
+  float* sfrac = reinterpret_cast<float*>(sv + M);           // [M]
+  uint16_t* sfirst = reinterpret_cast<uint16_t*>(sfrac + M); // [span - J + 2]
+  int la = lp, lb = pair_row_b(lp, a.nx);
+  if (a.rowmap) {   // a volume: the CTA's rows and table row from the plan's map
+    const int4 rm = a.rowmap[lp];
+    la = rm.x;
+    lb = rm.y;
+    lp = rm.z;
+  }
+  const int lbr = lb < 0 ? la : lb;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const TwP tw = load_twiddles_p(tws, reinterpret_cast<const float2*>(a.tw), rad);
+  const int4 meta = a.rowmeta[lp];
+  const int base = meta.x, span = meta.y, dir = meta.z;
+  const int vmax = span - J;                                 // largest u of the row
+  const TabF* tab = reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M;
+  const float2* Ra = reinterpret_cast<const float2*>(a.in) + (size_t)la * M;
+  const float2* Rb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * M;
+  pdl_wait_release();
+  constexpr int UM = 2;
+  for (int m0 = tid; m0 < M; m0 += UM * nthr) {
+    TabF e[UM];
+    float2 ra[UM], rb[UM];
+    int uprev[UM];
+#pragma unroll
+    for (int q = 0; q < UM; ++q) {
+      const int mm = m0 + q * nthr;
+      uprev[q] = -1;
+      if (mm < M) {
+        e[q] = tab[mm];
+        ra[q] = Ra[mm];
+        rb[q] = Rb[mm];
+        // the previous pixel in increasing-u order
+        const int mp = dir > 0 ? mm - 1 : mm + 1;
+        if (mp >= 0 && mp < M) uprev[q] = (int)((unsigned)tab[mp].cell >> 16);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < UM; ++q) {
+      const int mm = m0 + q * nthr;
+      if (mm >= M) continue;
+      const int sidx = dir > 0 ? mm : M - 1 - mm;
+      const float2 f = make_float2(e[q].fre, e[q].fim);
+      const float2 va = cmulc(ra[q], f), vb = cmulc(rb[q], f);
+      sv[sidx] = make_float4(va.x, vb.x, va.y, vb.y);
+      sfrac[sidx] = e[q].frac;
+      const int u = (int)((unsigned)e[q].cell >> 16);
+      for (int v = uprev[q] + 1; v <= u; ++v) sfirst[v] = (uint16_t)sidx;
+      if (sidx == M - 1)
+        for (int v = u + 1; v <= vmax + 1; ++v) sfirst[v] = (uint16_t)M;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < K; i += nthr) {
+    int c = i - base;
+    if (c < 0) c += K;
+    float2 ar = make_float2(0.f, 0.f), ai = ar;
+    if (c < span) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int v = c - j;
+        if (v < 0 || v > vmax) continue;
+        const int s1 = sfirst[v + 1];
+        for (int sidx = sfirst[v]; sidx < s1; ++sidx) {
+          const float w = kb_tap_weight<J>(sfrac[sidx], a0, j);
+          const float4 t = sv[sidx];
+          const float2 ww = make_float2(w, w);
+          ar = fma2(make_float2(t.x, t.y), ww, ar);
+          ai = fma2(make_float2(t.z, t.w), ww, ai);
+        }
+      }
+    }
+    buf[swz8(i)] = make_float4(ar.x, ar.y, ai.x, ai.y);
+  }
+  __syncthreads();
+  fft_p_dif<true, true>(buf, 1, rad, tw);
+  const float* cdep = reinterpret_cast<const float*>(a.cdep);
+  const int* perm = a.perm;
+  float2* Wa = reinterpret_cast<float2*>(a.out) + (size_t)la * nz;
+  float2* Wb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * nz;
+  for (int n = tid; n < nz; n += nthr) {
+    int i = n - n0;
+    if (i < 0) i += K;
+    const float4 t = buf[swz8(perm[i])];
+    const float cn = cdep[n];
+    Wa[n] = make_float2(t.x * cn, t.z * cn);
+    if (lb >= 0) Wb[n] = make_float2(t.y * cn, t.w * cn);
+  }
+}
+
+template <int J, bool BAT>
+__global__ void __launch_bounds__(kGatherLeanThreads, kGatherLeanMinBlocks)
+row_gather_pair_lean_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
+  if constexpr (!BAT) {
+    row_gather_pair_lean_body<J>(a0, a0.rad, (int)blockIdx.x, a0);
+  } else {
+    int blk;
+    const RowArgs<float>& A = *resolve_args(&a0, B, blk);
+    __shared__ Radix rad;
+    copy_radix(&rad, &A.rad);
+    __syncthreads();
+    row_gather_pair_lean_body<J>(A, rad, blk, a0);
+  }
+}
+
 // ------------------------------------------------------------------ launch
 
 int lateral_grid(mbir_plan p, int cols) { return (cols + p->tile_c - 1) / p->tile_c; }
@@ -1090,6 +1350,9 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
   a.rad = p->rad_x;
   a.tw = p->tw_x;
   a.perm = p->perm_x;
+  a.nxl = p->nxl;
+  a.chirp = p->chirp;
+  a.bhat = p->bhat;
   a.scale = scale;
   a.y = nullptr;
   a.pz = nullptr;
@@ -1107,7 +1370,7 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
 // the digit-reversal table
 template <class R>
 size_t lat_smem(mbir_plan p) {
-  return sizeof(cplx_t<R>) * (size_t)p->nx * p->tile_c + 16 * (size_t)(p->rad_x.tw_lo + p->rad_x.tw_hi) +
+  return sizeof(cplx_t<R>) * (size_t)p->nxl * p->tile_c + 16 * (size_t)(p->rad_x.tw_lo + p->rad_x.tw_hi) +
          sizeof(int) * (size_t)p->nx;
 }
 
@@ -1144,6 +1407,8 @@ RowArgs<R> row_args(mbir_plan p, const void* in, void* out) {
   a.K = p->K;
   a.n0 = p->n0;
   a.rowmeta = p->rowmeta;
+  a.rowmap = p->rowmap;
+  a.ny = p->ny;
   a.alpha = p->alpha;
   a.inv_i0a = 1.0 / host_bessel_i0(p->alpha);
   for (int j = 0; j < kMaxJ; ++j)
@@ -1174,6 +1439,10 @@ size_t row_gather_pair_smem(mbir_plan p) {
   const size_t M = p->m;
   return row_pair_smem(p) + 16 * M + sizeof(float) * M * p->J + sizeof(uint16_t) * (M + (M & 1) + p->K + 2);
 }
+size_t row_gather_pair_lean_smem(mbir_plan p) {
+  const size_t M = p->m;
+  return row_pair_smem(p) + 16 * M + sizeof(float) * M + sizeof(uint16_t) * (size_t)(p->max_span - p->J + 2);
+}
 
 size_t row_smem_bytes(mbir_plan p, int adjoint_gather);
 
@@ -1181,6 +1450,8 @@ bool row_kind_fits(mbir_plan p, int kind) {
   switch (kind) {
     case ROW_GATHER_PAIR:
       return p->precision == MBIR_FP32 && p->gather_ok && row_gather_pair_smem(p) <= (size_t)kMaxDynSmem;
+    case ROW_GATHER_PAIR_LEAN:
+      return p->precision == MBIR_FP32 && p->gather_ok && row_gather_pair_lean_smem(p) <= (size_t)kMaxDynSmem;
     case ROW_GATHER: return p->gather_ok && row_smem_bytes(p, 1) <= (size_t)kMaxDynSmem;
     case ROW_ATOMIC: return true;
     default: return false;
@@ -1192,17 +1463,19 @@ int row_kind(mbir_plan p, bool adjoint) {
   if (!adjoint) return pair ? ROW_FWD_PAIR : ROW_FWD;
   if (p->adj_kind >= 0 && row_kind_fits(p, p->adj_kind)) return p->adj_kind;
   if (kAdjAtomic || !p->gather_ok) return ROW_ATOMIC;
+  if (pair && kGatherLeanDefault && row_kind_fits(p, ROW_GATHER_PAIR_LEAN)) return ROW_GATHER_PAIR_LEAN;
   if (pair && row_gather_pair_smem(p) <= (size_t)kMaxDynSmem) return ROW_GATHER_PAIR;
   if (row_smem_bytes(p, 1) <= (size_t)kMaxDynSmem) return ROW_GATHER;
   return ROW_ATOMIC;
 }
 
-int row_ctas(mbir_plan p, int kind) { return kind >= ROW_FWD_PAIR ? p->nlh : p->nx; }
+int row_ctas(mbir_plan p, int kind) { return kind >= ROW_FWD_PAIR ? p->npair : p->nx * p->ny; }
 
 size_t row_kind_smem(mbir_plan p, int kind) {
   switch (kind) {
     case ROW_FWD_PAIR: return row_pair_smem(p);
     case ROW_GATHER_PAIR: return row_gather_pair_smem(p);
+    case ROW_GATHER_PAIR_LEAN: return row_gather_pair_lean_smem(p);
     case ROW_GATHER: return row_smem_bytes(p, 1);
     default: return row_smem_bytes(p, 0);
   }
@@ -1218,6 +1491,10 @@ static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R
     }
     if (kind == ROW_GATHER_PAIR) {
       launch(row_gather_pair_kernel<J, BAT>, dim3(grid), dim3(kGatherPairThreads), smem, st, a, B);
+      return;
+    }
+    if (kind == ROW_GATHER_PAIR_LEAN) {
+      launch(row_gather_pair_lean_kernel<J, BAT>, dim3(grid), dim3(kGatherLeanThreads), smem, st, a, B);
       return;
     }
   }
@@ -1413,12 +1690,81 @@ int power_step_hilbert_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, 
                                    : power_step_hilbert_t<float>(p, mask, w, v, r, scal, part, st);
 }
 
+// ------------------------------------------------------------------ volumes
+//
+// Phi of a volume x[px][py][n] (Sec. 2.1 with both lateral axes): the 2-D lateral
+// transform as the x pass (nx rows, columns (py, n)) and the y pass (ny rows on
+// every px slab), the row kernels over the nx * ny rows (lx, ly) with |q|^2 =
+// qx^2 + qy^2, then the inverse y pass and the inverse x pass with 1/(nx ny), the
+// real part and the mask.  Phi^H is the transpose of each pass in reverse order.
+
+template <class R>
+LatArgs<R> lat_args_y(mbir_plan p, const void* in, void* out, int cols) {
+  LatArgs<R> a = lat_args<R>(p, in, out, nullptr, cols, R(1));
+  a.nx = p->ny;
+  a.tc = p->tile_y;
+  a.rad = p->rad_y;
+  a.tw = p->tw_y;
+  a.perm = p->perm_y;
+  a.nxl = p->nyl;
+  a.chirp = p->chirp_y;
+  a.bhat = p->bhat_y;
+  return a;
+}
+
+template <class R>
+size_t lat_smem_y(mbir_plan p) {
+  return sizeof(cplx_t<R>) * (size_t)p->nyl * p->tile_y + 16 * (size_t)(p->rad_y.tw_lo + p->rad_y.tw_hi) +
+         sizeof(int) * (size_t)p->ny;
+}
+
+// in-place y pass of an [nx][ny][cols] complex array
+template <class R, int MODE>
+int launch_slab(mbir_plan p, void* buf, int cols, cudaStream_t st) {
+  const LatArgs<R> a = lat_args_y<R>(p, buf, buf, cols);
+  {
+    ProfScope ps_(p, MODE == LAT_C2C_FWD ? PC_LAT_FWD : PC_LAT_ADJ, st);
+    launch(lateral_slab_kernel<R, MODE>, dim3((cols + p->tile_y - 1) / p->tile_y, p->nx), dim3(kLatThreads),
+           lat_smem_y<R>(p), st, a, (long long)p->ny * cols);
+  }
+  MBIR_LAUNCH_CHECK();
+  return MBIR_OK;
+}
+
+template <class R>
+int forward_vol_t(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
+  const int ny = p->ny;
+  int rc = launch_lateral<R, LAT_C2C_FWD>(p, x, p->wsA, nullptr, ny * p->nz, R(1), st);
+  if (!rc) rc = launch_slab<R, LAT_C2C_FWD>(p, p->wsA, p->nz, st);
+  if (!rc) rc = launch_row<R>(p, false, p->wsA, p->wsB, st);
+  if (!rc) rc = launch_slab<R, LAT_C2C_INV>(p, p->wsB, p->m, st);
+  if (!rc) rc = launch_lateral<R, LAT_C2R_INV_MASK>(p, p->wsB, y, mask, ny * p->m, R(1) / R(p->nx * ny), st);
+  return rc;
+}
+
+template <class R>
+int adjoint_vol_t(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
+  const int ny = p->ny;
+  int rc = launch_lateral<R, LAT_R2C_MASK>(p, y, p->wsA, mask, ny * p->m, R(1) / R(p->nx * ny), st);
+  if (!rc) rc = launch_slab<R, LAT_C2C_FWD>(p, p->wsA, p->m, st);
+  if (!rc) rc = launch_row<R>(p, true, p->wsA, p->wsB, st);
+  if (!rc) rc = launch_slab<R, LAT_C2C_INV>(p, p->wsB, p->nz, st);
+  if (!rc) rc = launch_lateral<R, LAT_C2C_INV>(p, p->wsB, x, nullptr, ny * p->nz, R(1), st);
+  return rc;
+}
+
 int forward_impl(mbir_plan p, const void* x, const uint8_t* mask, void* y, cudaStream_t st) {
+  if (p->ny > 1)
+    return p->precision == MBIR_FP64 ? forward_vol_t<double>(p, x, mask, y, st)
+                                     : forward_vol_t<float>(p, x, mask, y, st);
   return p->precision == MBIR_FP64 ? forward_t<double>(p, x, mask, y, st)
                                    : forward_t<float>(p, x, mask, y, st);
 }
 
 int adjoint_impl(mbir_plan p, const void* y, const uint8_t* mask, void* x, cudaStream_t st) {
+  if (p->ny > 1)
+    return p->precision == MBIR_FP64 ? adjoint_vol_t<double>(p, y, mask, x, st)
+                                     : adjoint_vol_t<float>(p, y, mask, x, st);
   return p->precision == MBIR_FP64 ? adjoint_t<double>(p, y, mask, x, st)
                                    : adjoint_t<float>(p, y, mask, x, st);
 }
@@ -1471,6 +1817,8 @@ static int configure_t() {
   MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_FWD, true>), lat);
   MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_ADJ, false>), lat);
   MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_ADJ, true>), lat);
+  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_FWD>), lat);
+  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_INV>), lat);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 4, false>), row);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 4, true>), row);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 6, false>), row);
@@ -1514,6 +1862,12 @@ static int configure_t() {
     MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true>), gat);
     MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true>), gat);
     MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, true>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, true>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, true>), gat);
   }
 #undef MBIR_SMEM_ATTR
   return MBIR_OK;
@@ -1547,12 +1901,14 @@ int mbir_adjoint(mbir_plan p, const void* y, const uint8_t* mask, void* x, void*
 }
 
 int mbir_adjoint_hilbert(mbir_plan p, const void* y, const uint8_t* mask, void* x, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_adjoint_hilbert")) return vrc;
   const int rc = check_common(p, y, x);
   if (rc) return rc;
   return adjoint_hilbert_impl(p, y, mask, x, (cudaStream_t)stream);
 }
 
 int mbir_isam_interpolated(mbir_plan p, const void* y, const uint8_t* mask, void* x, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_isam_interpolated")) return vrc;
   const int rc = check_common(p, y, x);
   if (rc) return rc;
   return adjoint_hilbert_impl(p, y, mask, x, (cudaStream_t)stream, true);

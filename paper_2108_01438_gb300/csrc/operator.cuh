@@ -65,6 +65,20 @@ constexpr int kRowPairMinBlocks = MBIR_ROWPAIR_MINB;
 #define MBIR_LAT_UNROLL 4
 #endif
 constexpr int kGatherPairThreads = MBIR_GATHERPAIR_THREADS;
+// the lean paired gather (weights evaluated per term, no per-pixel cell array)
+// fits two CTAs an SM at K = 4096
+#ifndef MBIR_GATHERLEAN_THREADS
+#define MBIR_GATHERLEAN_THREADS 512
+#endif
+#ifndef MBIR_GATHERLEAN_MINB
+#define MBIR_GATHERLEAN_MINB 2
+#endif
+#ifndef MBIR_GATHERLEAN_DEFAULT
+#define MBIR_GATHERLEAN_DEFAULT 0
+#endif
+constexpr int kGatherLeanThreads = MBIR_GATHERLEAN_THREADS;
+constexpr int kGatherLeanMinBlocks = MBIR_GATHERLEAN_MINB;
+constexpr bool kGatherLeanDefault = MBIR_GATHERLEAN_DEFAULT != 0;
 constexpr int kLatUnroll = MBIR_LAT_UNROLL;   // rows of loads in flight per thread when staging a lateral tile
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
@@ -96,7 +110,10 @@ struct LatArgs {
   int nx, cols, tc;
   Radix rad;
   const void* tw;
-  const int* perm;   // digit reversal of the nx-point transform
+  const int* perm;   // [nx] tile row of lateral output p (digit reversal, or the identity)
+  int nxl;           // transform length (rad.n): nx, or the Bluestein length
+  const void* chirp; // Bluestein: [nx] chirp e^{-j pi p^2/nx}, else null
+  const void* bhat;  // Bluestein: [nxl] transformed conjugate chirp / nxl, digit-reversed
   R scale;
   // solver epilogue operands (LAT_SOLVE_*)
   const R* y;          // measurements [nx][m]
@@ -118,9 +135,11 @@ struct RowArgs {
   const void* cdep;
   const void* tw;
   const int* perm;   // digit reversal of the K-point transform
-  const int4* rowmeta;   // per row {base, span, direction, 0} of the unwrapped tap cells
+  const int4* rowmeta;   // per table row {base, span, direction, 0} of the unwrapped tap cells
+  const int4* rowmap;    // volumes: per paired CTA {row a, row b or -1, table row, 0}; null for a B-scan
   Radix rad;
   int nx, nz, m, K, n0;
+  int ny;                // volumes: rows are (lx, ly) = (r / ny, r % ny); 1 for a B-scan
   double alpha, inv_i0a;
   float kbpoly[kMaxJ][kKbDeg + 1];   // FP32 KB weight of tap j: polynomial in (frac - 1/2)
 };

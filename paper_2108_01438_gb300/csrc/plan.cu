@@ -18,6 +18,7 @@
 
 #include <new>
 #include <string>
+#include <complex>
 #include <vector>
 
 #include "common.cuh"
@@ -207,6 +208,18 @@ static void fit_kb_polynomials(int J, double alpha, float out[kMaxJ][kKbDeg + 1]
   }
 }
 
+// Lateral transform length of an nx-point axis: nx itself when it factors into
+// radices 2..8, else the smallest 7-smooth length >= 2 nx - 1 for the Bluestein
+// (chirp-z) form; 0 when that exceeds the largest transform or its tile of two
+// columns exceeds the lateral shared-memory tile.
+static int lateral_length(int nx) {
+  Radix r;
+  if (factor_radix(nx, &r, 8)) return nx;
+  for (int n = 2 * nx - 1; n <= kMaxFFT && 2 * n <= kLatElems; ++n)
+    if (factor_radix(n, &r, 8)) return n;
+  return 0;
+}
+
 static int validate(const mbir_geometry* g) {
   if (!g || !g->k) return MBIR_ERR_INVALID;
   if (g->nx <= 0 || g->nz <= 0 || g->m <= 0) return MBIR_ERR_INVALID;
@@ -235,7 +248,57 @@ static int validate(const mbir_geometry* g) {
   if ((int64_t)g->nx * g->nz >= (int64_t(1) << 31) || (int64_t)g->nx * g->m >= (int64_t(1) << 31))
     return MBIR_ERR_UNSUPPORTED_SIZE;
   Radix r;
-  if (!factor_radix(g->nx, &r) || !factor_radix(2 * g->nz, &r)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  if (!lateral_length(g->nx) || !factor_radix(2 * g->nz, &r)) return MBIR_ERR_UNSUPPORTED_SIZE;
+  return MBIR_OK;
+}
+
+// Tables of one lateral axis of n pixels whose transform has length nl (rad):
+// twiddles, the tile row of each output (digit reversal, or the identity for the
+// Bluestein form) and, when nl != n, the Bluestein chirp and the transformed
+// conjugate chirp.  Uploaded on st, which is synchronised before returning.
+template <class R>
+static int lateral_axis_tables(int n, const Radix& rad, void** tw, int** perm, void** chirp, void** bhat,
+                               cudaStream_t st) {
+  using V = cplx_t<R>;
+  const int nl = rad.n;
+  const bool blu = nl != n;
+  std::vector<V> twv;
+  make_twiddles(rad, twv);
+  std::vector<int> pv(n);
+  for (int i = 0; i < n; ++i) pv[i] = blu ? i : digit_reverse(i, rad);
+  MBIR_CUDA_TRY(cudaMalloc(tw, sizeof(V) * twv.size()));
+  MBIR_CUDA_TRY(cudaMalloc(perm, sizeof(int) * n));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(*tw, twv.data(), sizeof(V) * twv.size(), cudaMemcpyHostToDevice, st));
+  MBIR_CUDA_TRY(cudaMemcpyAsync(*perm, pv.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  std::vector<V> ch, bh;
+  if (blu) {
+    // Bluestein: X_l = c_l sum_p (x_p c_p) conj(c)_{l-p}, c_k = e^{-j pi k^2 / n}; the
+    // convolution runs through nl-point transforms (nl >= 2 n - 1, no wrap-around)
+    ch.resize(n);
+    bh.resize(nl);
+    std::vector<std::complex<double>> b(nl, 0.0), w(nl);
+    for (int k = 0; k < n; ++k) {
+      const double a = M_PI * double(((int64_t)k * k) % (2 * (int64_t)n)) / n;
+      ch[k].x = R(cos(a));
+      ch[k].y = R(-sin(a));
+      b[k] = std::complex<double>(cos(a), sin(a));
+      if (k) b[nl - k] = b[k];
+    }
+    for (int k = 0; k < nl; ++k) w[k] = std::polar(1.0, -2.0 * M_PI * k / nl);
+    for (int j = 0; j < nl; ++j) {
+      std::complex<double> acc = 0.0;
+      for (int k = 0; k < nl; ++k) acc += b[k] * w[((int64_t)j * k) % nl];
+      acc /= double(nl);
+      V& e = bh[digit_reverse(j, rad)];
+      e.x = R(acc.real());
+      e.y = R(acc.imag());
+    }
+    MBIR_CUDA_TRY(cudaMalloc(chirp, sizeof(V) * n));
+    MBIR_CUDA_TRY(cudaMalloc(bhat, sizeof(V) * nl));
+    MBIR_CUDA_TRY(cudaMemcpyAsync(*chirp, ch.data(), sizeof(V) * n, cudaMemcpyHostToDevice, st));
+    MBIR_CUDA_TRY(cudaMemcpyAsync(*bhat, bh.data(), sizeof(V) * nl, cudaMemcpyHostToDevice, st));
+  }
+  MBIR_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors die here
   return MBIR_OK;
 }
 
@@ -244,9 +307,14 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
   using V = cplx_t<R>;
   using Tab = typename TabOf<R>::T;
   const int nx = p->nx, nz = p->nz, m = p->m, K = p->K, J = p->J;
-  std::vector<V> twx, twk;
-  make_twiddles(p->rad_x, twx);
+  std::vector<V> twk;
   make_twiddles(p->rad_k, twk);
+  int rc = lateral_axis_tables<R>(nx, p->rad_x, &p->tw_x, &p->perm_x, &p->chirp, &p->bhat, st);
+  if (rc) return rc;
+  if (p->ny > 1) {
+    rc = lateral_axis_tables<R>(p->ny, p->rad_y, &p->tw_y, &p->perm_y, &p->chirp_y, &p->bhat_y, st);
+    if (rc) return rc;
+  }
   std::vector<R> cdep(nz);
   for (int n = 0; n < nz; ++n) {
     const double z = n * p->dz;
@@ -260,18 +328,22 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
   // beta mapping is monotone in k); u = U_m - min U is packed above pc.  Rows whose
   // unwrapped cells are not monotone or span more than K cells make the plan use
   // shared-memory atomics in the adjoint instead.
-  std::vector<Tab> tab((size_t)p->nlh * m);
-  std::vector<int4> meta(p->nlh);
+  std::vector<Tab> tab((size_t)p->ntab * m);
+  std::vector<int4> meta(p->ntab);
+  const int nyh = p->ny / 2 + 1;
   const int h = J / 2;
   bool gather_ok = m <= 65535 && K <= 32768;
   std::vector<int> pc(m), valid(m);
   std::vector<double> fr(m);
   std::vector<long long> U(m);
-  for (int lp = 0; lp < p->nlh; ++lp) {
-    const double q = 2.0 * M_PI * lp / (nx * p->dx);
+  for (int lp = 0; lp < p->ntab; ++lp) {
+    // table row lp: lateral frequency (|lx|, |ly|) = (lp / nyh, lp % nyh); |ly| = 0 for a B-scan
+    const double qx = 2.0 * M_PI * (lp / nyh) / (nx * p->dx);
+    const double qy = p->ny > 1 ? 2.0 * M_PI * (lp % nyh) / (p->ny * p->dy) : 0.0;
+    const double q2 = qx * qx + qy * qy;
     for (int mm = 0; mm < m; ++mm) {
       const double k = g->k[mm];
-      const double b2 = 4.0 * k * k - q * q;
+      const double b2 = 4.0 * k * k - q2;
       Tab e;
       memset(&e, 0, sizeof(e));
       valid[mm] = b2 > 0;
@@ -287,7 +359,7 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
         if (first < 0) first += K;
         pc[mm] = (int)first;
         const double A = g->source ? g->source[mm] : 1.0;
-        const double G = g->na > 0 ? exp(-q * q / (2.0 * k * k * g->na * g->na)) : 1.0;
+        const double G = g->na > 0 ? exp(-q2 / (2.0 * k * k * g->na * g->na)) : 1.0;
         const double dk = k - g->k0;
         const double omega = g->disp_a * dk * dk + g->disp_b * dk * dk * dk;
         const double phase = fmod(omega - 2.0 * k * g->z_focus_um, 2.0 * M_PI) +
@@ -336,6 +408,7 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
     }
     const long long span = umax - umin + J;
     if (!mono || span > K) gather_ok = false;
+    if (span > p->max_span) p->max_span = (int)span;
     long long base = umin % K;
     if (base < 0) base += K;
     meta[lp] = make_int4((int)base, (int)span, dir >= 0 ? 1 : -1, 0);
@@ -349,20 +422,15 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
   p->gather_ok = gather_ok ? 1 : 0;
   MBIR_CUDA_TRY(cudaMalloc(&p->rowmeta, sizeof(int4) * meta.size()));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->rowmeta, meta.data(), sizeof(int4) * meta.size(), cudaMemcpyHostToDevice, st));
-  MBIR_CUDA_TRY(cudaMalloc(&p->tw_x, sizeof(V) * twx.size()));
   MBIR_CUDA_TRY(cudaMalloc(&p->tw_k, sizeof(V) * twk.size()));
   MBIR_CUDA_TRY(cudaMalloc(&p->cdep, sizeof(R) * nz));
   MBIR_CUDA_TRY(cudaMalloc(&p->tab, sizeof(Tab) * tab.size()));
-  MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_x, twx.data(), sizeof(V) * twx.size(), cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_k, twk.data(), sizeof(V) * twk.size(), cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->cdep, cdep.data(), sizeof(R) * nz, cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->tab, tab.data(), sizeof(Tab) * tab.size(), cudaMemcpyHostToDevice, st));
-  std::vector<int> px(nx), pk(K);
-  for (int i = 0; i < nx; ++i) px[i] = digit_reverse(i, p->rad_x);
+  std::vector<int> pk(K);
   for (int i = 0; i < K; ++i) pk[i] = digit_reverse(i, p->rad_k);
-  MBIR_CUDA_TRY(cudaMalloc(&p->perm_x, sizeof(int) * nx));
   MBIR_CUDA_TRY(cudaMalloc(&p->perm_k, sizeof(int) * K));
-  MBIR_CUDA_TRY(cudaMemcpyAsync(p->perm_x, px.data(), sizeof(int) * nx, cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->perm_k, pk.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaStreamSynchronize(st));
   return MBIR_OK;
@@ -576,6 +644,13 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaFree(p->tw_x);
   cudaFree(p->tw_k);
   cudaFree(p->perm_x);
+  cudaFree(p->chirp);
+  cudaFree(p->bhat);
+  cudaFree(p->rowmap);
+  cudaFree(p->tw_y);
+  cudaFree(p->perm_y);
+  cudaFree(p->chirp_y);
+  cudaFree(p->bhat_y);
   cudaFree(p->rowmeta);
   cudaFree(p->perm_k);
   cudaFree(p->cdep);
@@ -596,11 +671,20 @@ void mbir_plan_destroy(mbir_plan p) {
   delete p;
 }
 
-int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
+}  // extern "C"
+
+// A B-scan plan (ny = 1) or a volume plan with a second lateral axis of ny pixels
+// spaced dy.
+static int plan_create(const mbir_geometry* g, int ny, double dy, void* stream, mbir_plan* out) {
   if (!out) return MBIR_ERR_INVALID;
   *out = nullptr;
   const int v = validate(g);
   if (v != MBIR_OK) return v;
+  if (ny < 1 || (ny > 1 && !(dy > 0 && isfinite(dy)))) return MBIR_ERR_INVALID;
+  if (ny > 4096) return MBIR_ERR_UNSUPPORTED_SIZE;
+  if (ny > 1 && ((int64_t)g->nx * ny * g->nz >= (int64_t(1) << 31) ||
+                 (int64_t)g->nx * ny * g->m >= (int64_t(1) << 31) || !lateral_length(ny)))
+    return MBIR_ERR_UNSUPPORTED_SIZE;
   cudaStream_t st = (cudaStream_t)stream;
 
   mbir_plan p = new (std::nothrow) mbir_plan_s;
@@ -613,6 +697,10 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   p->J = g->kb_width;
   p->n0 = g->nz / 2;
   p->nlh = g->nx / 2 + 1;
+  p->ny = ny;
+  p->dy = ny > 1 ? dy : 0.0;
+  p->ntab = p->nlh * (ny / 2 + 1);
+  p->npair = p->nlh;
   p->precision = g->precision;
   p->dx = g->dx_um;
   if (g->dz_um > 0) {
@@ -624,18 +712,47 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   }
   p->alpha = g->kb_alpha > 0 ? g->kb_alpha : 2.34 * g->kb_width;
   p->k_ascending = g->m < 2 || g->k[g->m - 1] > g->k[0];
-  factor_radix(p->nx, &p->rad_x, 8);
+  p->nxl = lateral_length(p->nx);
+  factor_radix(p->nxl, &p->rad_x, 8);
   factor_radix(p->K, &p->rad_k, 8);
-  // lateral tile: keep nx * tile_c <= kLatElems elements, at most 16 columns
-  int tc = kLatElems / p->nx;
+  // lateral tile: keep nxl * tile_c <= kLatElems elements, at most 16 columns
+  int tc = kLatElems / p->nxl;
   if (tc > 16) tc = 16;
   int pw = 1;
   while (pw * 2 <= tc) pw *= 2;
   p->tile_c = pw;
+  if (ny > 1) {
+    p->nyl = lateral_length(ny);
+    factor_radix(p->nyl, &p->rad_y, 8);
+    int ty = kLatElems / p->nyl;
+    if (ty > 16) ty = 16;
+    int py = 1;
+    while (py * 2 <= ty) py *= 2;
+    p->tile_y = py;
+  }
 
   int rc = MBIR_OK;
   auto fail = [&](int code) { mbir_plan_destroy(p); return code; };
   if (cudaGetDevice(&p->device) != cudaSuccess) return fail(set_cuda_error(cudaGetLastError(), "cudaGetDevice"));
+  if (ny > 1) {
+    // row pairs of the 2-D lateral spectrum [lx][ly]: a row and its point reflection
+    // (-lx, -ly) share |q| and so the table row (|lx|, |ly|); a row that is its own
+    // reflection runs alone
+    const int nx = p->nx, nyh = ny / 2 + 1;
+    std::vector<int4> map;
+    for (int lx = 0; lx < nx; ++lx)
+      for (int ly = 0; ly < ny; ++ly) {
+        const int r = lx * ny + ly, mr = ((nx - lx) % nx) * ny + (ny - ly) % ny;
+        if (mr < r) continue;
+        const int ix = lx <= nx - lx ? lx : nx - lx, iy = ly <= ny - ly ? ly : ny - ly;
+        map.push_back(make_int4(r, mr == r ? -1 : mr, ix * nyh + iy, 0));
+      }
+    p->npair = (int)map.size();
+    cudaError_t e = cudaMalloc(&p->rowmap, sizeof(int4) * map.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->rowmap, map.data(), sizeof(int4) * map.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "volume row map"));
+  }
 
   rc = (p->precision == MBIR_FP64) ? upload_tables<double>(p, g, st) : upload_tables<float>(p, g, st);
   if (rc != MBIR_OK) return fail(rc);
@@ -656,7 +773,7 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   }
   {
     const size_t cols = (size_t)(p->nz > p->m ? p->nz : p->m);
-    p->ws_elems = (size_t)p->nx * cols;
+    p->ws_elems = (size_t)p->nx * p->ny * cols;
     const size_t esz = (p->precision == MBIR_FP64) ? sizeof(double2) : sizeof(float2);
     cudaError_t e = cudaMalloc(&p->wsA, esz * p->ws_elems);
     if (e == cudaSuccess) e = cudaMalloc(&p->wsB, esz * p->ws_elems);
@@ -668,9 +785,28 @@ int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
   rc = configure_wavelet_kernels(p);
   if (rc != MBIR_OK) return fail(rc);
   p->adj_kind = -1;
-  rc = apply_class_tuning(p);
-  if (rc != MBIR_OK) return fail(rc);
+  if (ny == 1) {
+    rc = apply_class_tuning(p);
+    if (rc != MBIR_OK) return fail(rc);
+  }
   *out = p;
+  return MBIR_OK;
+}
+
+extern "C" {
+
+int mbir_plan_create(const mbir_geometry* g, void* stream, mbir_plan* out) {
+  return plan_create(g, 1, 0.0, stream, out);
+}
+
+int mbir_volume_plan_create(const mbir_geometry* g, int32_t ny, double dy_um, void* stream, mbir_plan* out) {
+  if (ny < 2 || !isfinite(dy_um)) return MBIR_ERR_INVALID;
+  return plan_create(g, ny, dy_um > 0 ? dy_um : (g ? g->dx_um : 0.0), stream, out);
+}
+
+int mbir_volume_dims(mbir_plan p, int32_t* ny) {
+  if (!p || !ny) return MBIR_ERR_INVALID;
+  *ny = p->ny;
   return MBIR_OK;
 }
 

@@ -173,6 +173,7 @@ void mbir_server_destroy(mbir_server srv) {
 int mbir_server_submit(mbir_server srv, mbir_plan plan, const void* y, const uint8_t* mask,
                        const mbir_solve_opts* o, void* x, int64_t* ticket) {
   if (!srv || !plan || !y || !o || !x || !ticket) return MBIR_ERR_INVALID;
+  if (const int vrc = bscan_only(plan, "mbir_server_submit")) return vrc;
   if (o->max_iter < 1 || o->min_iter < 0 || o->penalty < MBIR_PENALTY_L1 || o->penalty > MBIR_PENALTY_DB4)
     return MBIR_ERR_INVALID;
   if (o->backprojection != MBIR_BACKPROJ_TRANSPOSE) return MBIR_ERR_INVALID;
@@ -235,6 +236,7 @@ int mbir_server_stats(mbir_server srv, size_t* bytes_in_use, size_t* peak_bytes,
 
 int mbir_server_request_bytes(mbir_plan plan, int32_t penalty, int32_t max_iter, size_t* bytes) {
   if (!plan || !bytes || max_iter < 1) return MBIR_ERR_INVALID;
+  if (const int vrc = bscan_only(plan, "mbir_server_request_bytes")) return vrc;
   *bytes = ctx_bytes(plan, penalty, max_iter);
   return MBIR_OK;
 }

@@ -460,6 +460,7 @@ using namespace mbir;
 extern "C" {
 
 int mbir_lipschitz(mbir_plan p, const uint8_t* mask, int32_t iters, double* out, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_lipschitz")) return vrc;
   if (!p || !out || iters < 1) return MBIR_ERR_INVALID;
   int rc = ensure_state(p, 1);
   if (rc) return rc;
@@ -471,6 +472,7 @@ int mbir_lipschitz(mbir_plan p, const uint8_t* mask, int32_t iters, double* out,
 int mbir_solve(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
                mbir_solve_info* info, void* stream) {
   if (!p || !y || !o || !x) return MBIR_ERR_INVALID;
+  if (const int vrc = bscan_only(p, "mbir_solve")) return vrc;
   if (o->max_iter < 1 || o->min_iter < 0) return MBIR_ERR_INVALID;
   if (o->penalty != MBIR_PENALTY_L1 && o->penalty != MBIR_PENALTY_DB4 && o->penalty != MBIR_PENALTY_TV)
     return MBIR_ERR_INVALID;

@@ -30,7 +30,7 @@ ClassKey class_key(mbir_plan p) { return ClassKey(p->nx, p->nz, p->m, p->J, p->p
 constexpr double kTuneMargin = 0.98;   // a new choice must be at least 2 % faster
 
 bool tile_ok(mbir_plan p, int tc) {
-  return tc >= 2 && tc <= 16 && (tc & (tc - 1)) == 0 && (size_t)p->nx * tc <= (size_t)kLatElems;
+  return tc >= 2 && tc <= 16 && (tc & (tc - 1)) == 0 && (size_t)p->nxl * tc <= (size_t)kLatElems;
 }
 
 // Apply a launch choice.  A new tile width drops the plan's solver state (its
@@ -44,6 +44,9 @@ int apply_tuning(mbir_plan p, int tile_c, int order, int adj) {
     p->tile_c = tile_c;
   }
   if (order != p->lat_order) {
+    // a Bluestein plan keeps its radix order: its filter table is stored in that order's
+    // digit reversal
+    if (p->nxl != p->nx) return MBIR_ERR_INVALID;
     Radix r;
     if (!plan_factor_radix(p->nx, &r, 8)) return MBIR_ERR_INVALID;
     if (order == 1) {
@@ -53,6 +56,7 @@ int apply_tuning(mbir_plan p, int tile_c, int order, int adj) {
     std::vector<int> px(p->nx);
     for (int i = 0; i < p->nx; ++i) px[i] = digit_reverse(i, r);
     MBIR_CUDA_TRY(cudaMemcpy(p->perm_x, px.data(), sizeof(int) * p->nx, cudaMemcpyHostToDevice));
+    MBIR_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));   // a pageable copy: let it land
     p->rad_x = r;
     p->lat_order = order;
   }
@@ -90,11 +94,13 @@ int mbir_plan_get_tuning(mbir_plan p, mbir_tuning* out) {
 }
 
 int mbir_plan_set_tuning(mbir_plan p, const mbir_tuning* t) {
+  if (const int vrc = bscan_only(p, "mbir_plan_set_tuning")) return vrc;
   if (!p || !t) return MBIR_ERR_INVALID;
   return apply_tuning(p, t->tile_c, t->lateral_order, t->adjoint_kernel);
 }
 
 int mbir_plan_autotune(mbir_plan p, int32_t reps, mbir_tuning* best, int32_t* n_tried, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_plan_autotune")) return vrc;
   if (!p || reps < 1 || reps > 1000) return MBIR_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t esz = p->precision == MBIR_FP64 ? sizeof(double2) : sizeof(float2);
@@ -150,8 +156,8 @@ int mbir_plan_autotune(mbir_plan p, int32_t reps, mbir_tuning* best, int32_t* n_
     if ((rc = time_cfg(orig.tile_c, orig.lateral_order, orig.adjoint_kernel))) break;
     // 1. lateral tile width and radix order, automatic adjoint kernel
     Radix r;
-    plan_factor_radix(p->nx, &r, 8);
-    const int orders = r.npass > 1 ? 2 : 1;
+    plan_factor_radix(p->nxl, &r, 8);
+    const int orders = (r.npass > 1 && p->nxl == p->nx) ? 2 : 1;
     for (int tc = 2; tc <= 16 && rc == MBIR_OK; tc *= 2) {
       if (!tile_ok(p, tc)) continue;
       for (int ord = 0; ord < orders && rc == MBIR_OK; ++ord)
@@ -160,7 +166,7 @@ int mbir_plan_autotune(mbir_plan p, int32_t reps, mbir_tuning* best, int32_t* n_
     if (rc) break;
     // 2. row adjoint kernel at the best lateral choice
     const int tc = top.tile_c, ord = top.lateral_order;
-    for (int adj : {(int)ROW_GATHER_PAIR, (int)ROW_GATHER, (int)ROW_ATOMIC}) {
+    for (int adj : {(int)ROW_GATHER_PAIR_LEAN, (int)ROW_GATHER_PAIR, (int)ROW_GATHER, (int)ROW_ATOMIC}) {
       if (!row_kind_fits(p, adj)) continue;
       if ((rc = time_cfg(tc, ord, adj))) break;
     }

@@ -443,6 +443,7 @@ using namespace mbir;
 extern "C" {
 
 int mbir_prox_tv(mbir_plan p, const void* v, double tau, int32_t iters, void* z, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_prox_tv")) return vrc;
   if (!p || !v || !z || v == z || !(tau >= 0) || !isfinite(tau)) return MBIR_ERR_INVALID;
   return tv_prox_impl(p, v, tau, iters, z, nullptr, (cudaStream_t)stream);
 }

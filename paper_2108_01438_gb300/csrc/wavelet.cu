@@ -682,12 +682,14 @@ int mbir_wavelet_static(int32_t nx, int32_t nz, int32_t inverse, const void* in,
 }
 
 int mbir_prox(mbir_plan p, int32_t penalty, const void* v, double tau, void* z, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_prox")) return vrc;
   if (!p || !v || !z || !(tau >= 0) || !isfinite(tau)) return MBIR_ERR_INVALID;
   if (penalty != MBIR_PENALTY_L1 && penalty != MBIR_PENALTY_DB4 && penalty != MBIR_PENALTY_TV) return MBIR_ERR_INVALID;
   return prox_partial_impl(p, penalty, v, tau, z, nullptr, (cudaStream_t)stream);
 }
 
 int mbir_wavelet(mbir_plan p, int32_t inverse, const void* in, void* out, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_wavelet")) return vrc;
   if (!p || !in || !out || in == out) return MBIR_ERR_INVALID;
   return wavelet_impl(p, inverse, in, out, (cudaStream_t)stream);
 }

@@ -86,6 +86,9 @@ _lib = None
 _SIGNATURES = {
     "mbir_plan_create": (C.c_int, [C.POINTER(Geometry), C.c_void_p, C.POINTER(C.c_void_p)]),
     "mbir_plan_destroy": (None, [C.c_void_p]),
+    "mbir_volume_plan_create": (C.c_int, [C.POINTER(Geometry), C.c_int32, C.c_double, C.c_void_p,
+                                          C.POINTER(C.c_void_p)]),
+    "mbir_volume_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "mbir_plan_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mbir_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -435,6 +438,60 @@ class Plan:
         if trace:
             d["trace"] = np.array(tr[: info.iters])
         return out, d
+
+
+class VolumePlan:
+    """One 3-D volume geometry (mbir_volume_plan_create): the B-scan geometry plus a
+    second lateral axis of ny pixels.  Image [nx, ny, nz], measurements and mask
+    [nx, ny, m]; forward and adjoint only."""
+
+    def __init__(self, geometry: dict, ny: int, dy_um: float = 0.0, precision: int = FP32, stream=None):
+        import torch
+        self.geometry = geometry
+        self.precision = precision
+        self.nx, self.nz, self.m = int(geometry["nx"]), int(geometry["nz"]), int(geometry["m"])
+        self.ny = int(ny)
+        self.real_dtype = torch.float64 if precision == FP64 else torch.float32
+        self.complex_dtype = torch.complex128 if precision == FP64 else torch.complex64
+        g, keep = make_geometry(geometry, precision)
+        h = C.c_void_p()
+        _check(lib().mbir_volume_plan_create(C.byref(g), self.ny, float(dy_um), _stream_handle(stream),
+                                             C.byref(h)), "mbir_volume_plan_create")
+        self._h = h
+        del keep
+
+    handle = Plan.handle
+    close = Plan.close
+    __del__ = Plan.__del__
+
+    def _check_t(self, t, name, dtype, last):
+        shape = (self.nx, self.ny, last)
+        if t.dtype != dtype or tuple(t.shape) != shape or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of shape {shape}")
+
+    def forward(self, x, mask=None, out=None, stream=None):
+        import torch
+        self._check_t(x, "x", self.complex_dtype, self.nz)
+        if mask is not None:
+            self._check_t(mask, "mask", torch.uint8, self.m)
+        if out is None:
+            out = torch.empty((self.nx, self.ny, self.m), dtype=self.real_dtype, device=x.device)
+        self._check_t(out, "out", self.real_dtype, self.m)
+        _check(lib().mbir_forward(self._h, _ptr(x), _ptr(mask), _ptr(out), _stream_handle(stream)),
+               "mbir_forward")
+        return out
+
+    def adjoint(self, y, mask=None, out=None, stream=None):
+        import torch
+        self._check_t(y, "y", self.real_dtype, self.m)
+        if mask is not None:
+            self._check_t(mask, "mask", torch.uint8, self.m)
+        if out is None:
+            out = torch.empty((self.nx, self.ny, self.nz), dtype=self.complex_dtype, device=y.device)
+        self._check_t(out, "out", self.complex_dtype, self.nz)
+        _check(lib().mbir_adjoint(self._h, _ptr(y), _ptr(mask), _ptr(out), _stream_handle(stream)),
+               "mbir_adjoint")
+        return out
 
 
 def solve_batch(plans, ys, masks=None, *, penalties="l1", lams=0.01, relative=True, iters=100,

@@ -58,12 +58,28 @@ def _create(lib, d, **over):
 @pytest.mark.parametrize("field,value,code", [
     ("nx", 0, -1), ("nz", -3, -1), ("m", 0, -1), ("dx_um", 0.0, -1), ("dz_um", -1.0, -1),
     ("precision", 7, -1), ("kb_width", 5, -2), ("kb_width", 10, -2), ("kb_oversamp", 1.5, -2),
-    ("nx", 11, -2), ("nx", 8192, -2), ("nz", 4, -2), ("nz", 11 * 8, -2), ("na", float("nan"), -1),
+    ("nx", 2053, -2), ("nx", 8192, -2), ("nz", 4, -2), ("nz", 11 * 8, -2), ("na", float("nan"), -1),
 ])
 def test_plan_rejects_bad_geometry_on_host(lib, field, value, code):
     d = workloads.geometry(16, 32, 24)
     rc, h = _create(lib, d, **{field: value})
     assert rc == code and not h.value
+
+
+@pytest.mark.parametrize("ny,dy,over,code", [
+    (1, 2.0, {}, -1), (0, 2.0, {}, -1), (4, float("nan"), {}, -1), (2053, 2.0, {}, -2), (5000, 2.0, {}, -2),
+    (2048, 2.0, {"size": (1024, 1024, 1024)}, -2), (8, 2.0, {"kb_width": 5}, -2),
+])
+def test_volume_plan_rejects_bad_sizes_on_host(lib, ny, dy, over, code):
+    """A second lateral axis: ny >= 2 with the width rule of nx, the volume below
+    2^31 elements; checked before any device work."""
+    over = dict(over)
+    g, keep = mbir.make_geometry(workloads.geometry(*over.pop("size", (16, 32, 24))))
+    for k, v in over.items():
+        setattr(g, k, v)
+    h = C.c_void_p()
+    assert lib.mbir_volume_plan_create(C.byref(g), ny, dy, None, C.byref(h)) == code
+    assert not h.value
 
 
 def test_plan_rejects_non_monotone_wavenumbers(lib):
