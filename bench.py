@@ -783,15 +783,22 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
     # sub-sampling schemes (half of the spectrometer samples each): the
     # interpolated-ISAM baseline, and MBIR (db4, TV) at the lambda a golden-section
     # search finds best, as in the paper's NCC table
+    # The phantom is the 500 beads without the random-phase background: a background
+    # whose phase changes from pixel to pixel is white across the whole band, which
+    # the band-limited, sub-sampled system cannot represent, and its speckle then
+    # dominates every magnitude NCC and flattens the search.
     eval_res = None
     if not args.no_eval:
-        eval_res = {"workload": "bscan-1024x2048 beads, 25 dB, half of the spectrometer samples per scheme",
+        eval_res = {"workload": "bscan-1024x2048, 500 beads on a zero background, 25 dB, half of the "
+                                "spectrometer samples per scheme",
                     "search": {"log10_bracket": [EVAL_LO, EVAL_HI], "evaluations": EVAL_N, "iters": ITERS}}
+        x_eval = torch.from_numpy(workloads.beads(nx, nz, 500, workloads.BASE_SEED + 1, background=0.0)
+                                  .astype(np.complex64)).to(dev)
         schemes = {"random": workloads.mask_bernoulli(nx, m, 0.5, 4242),
                    "equispaced": workloads.mask_equispaced(nx, m), "partial": workloads.mask_partial(nx, m)}
         for scheme, mk in schemes.items():
             mask_r = torch.from_numpy(mk).to(dev)
-            clean_r = plan.forward(x_true, mask_r)
+            clean_r = plan.forward(x_eval, mask_r)
             sig_r = torch.sqrt(torch.mean(clean_r[mask_r == 1].double() ** 2)).item()
             y_r = (clean_r + float(sig_r * 10 ** (-wl["snr_db"] / 20)) * noise * mask_r).contiguous()
             base = plan.isam_interpolated(y_r, mask_r)
@@ -802,10 +809,10 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                 plan.isam_interpolated(y_r, mask_r, out=base)
             t1.record(stream)
             torch.cuda.synchronize()
-            row = {"isam_interpolated": {"ncc": plan.ncc(base, x_true), "ms": t0.elapsed_time(t1) / 10}}
+            row = {"isam_interpolated": {"ncc": plan.ncc(base, x_eval), "ms": t0.elapsed_time(t1) / 10}}
             for pen in ("db4", "tv"):
                 t_start = time.perf_counter()
-                _, info = plan.lambda_search(y_r, mask_r, x_true, lo=EVAL_LO, hi=EVAL_HI, n_eval=EVAL_N,
+                _, info = plan.lambda_search(y_r, mask_r, x_eval, lo=EVAL_LO, hi=EVAL_HI, n_eval=EVAL_N,
                                              penalty=pen, iters=ITERS, power_iters=POWER_ITERS, tv_iters=TV_ITERS)
                 row["mbir_" + pen] = {"ncc": info["ncc"], "lambda_rel": info["lambda_rel"],
                                       "search_s": time.perf_counter() - t_start,

@@ -20,8 +20,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmbir.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# --split-compile spreads the device-code optimisation of a translation unit over
+# the host's cores (operator.cu instantiates most of the kernels)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-         "--expt-relaxed-constexpr", "-I", INCLUDE]
+         "--expt-relaxed-constexpr", "--split-compile=0", "-I", INCLUDE]
 
 
 def nvcc() -> str:

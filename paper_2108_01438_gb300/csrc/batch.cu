@@ -395,14 +395,16 @@ int Engine::add_lateral(std::vector<Stage>& out, int mode, const std::vector<BSc
   std::vector<unsigned char> blocks(ab * idx.size());
   std::vector<int> off(idx.size() + 1, 0);
   size_t smem = 0;
+  int blu = 0;
   for (size_t i = 0; i < idx.size(); ++i) {
     BScan& s = *idx[i];
     LatFill f = make(s);
     fill_lat_args(s.p, f, blocks.data() + i * ab);
     off[i + 1] = off[i] + lateral_grid(s.p, f.cols);
     smem = std::max(smem, lat_smem_bytes(s.p));
+    if (s.p->chirp) blu = 1;
   }
-  Stage g{0, mode, 0, 0, (int)idx.size(), off.back(), smem, uses_mu ? 1 : 0};
+  Stage g{0, mode, 0, 0, (int)idx.size(), off.back(), smem, uses_mu ? 1 : 0, blu};
   g.arg_off = push(blocks.data(), blocks.size());
   g.off_off = push(off.data(), off.size() * sizeof(int));
   out.push_back(g);
@@ -485,6 +487,7 @@ int Engine::run(const Stage& g, double mu) {
   L.host0 = hbuf_ + g.arg_off;
   L.set_mu = g.uses_mu;
   L.mu = mu;
+  L.blu = g.blu;
   switch (g.kind) {
     case 0: return batch_lateral(g.mode, prec_, L, st_);
     case 1: return batch_row(g.mode, prec_, J_, L, st_);

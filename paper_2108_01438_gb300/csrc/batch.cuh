@@ -81,6 +81,7 @@ class Engine {
     int n, total;
     size_t smem;
     int uses_mu;
+    int blu;    // lateral stages: some scan's plan uses the Bluestein form
   };
   size_t push(const void* data, size_t bytes);
   void grow(size_t need);

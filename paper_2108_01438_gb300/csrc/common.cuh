@@ -60,6 +60,9 @@ struct Radix {
 // and u its unwrapped offset within the row (see the plan), the fractional part
 // of t and the complex filter.
 struct TabF { int cell; float frac; float fre, fim; };
+// The same grid position without the filter (FP32 plans whose row kernels form
+// the filter from per-pixel and per-row constants, see RowArgs::otf).
+struct TabP { int cell; float frac; };
 struct TabD { int cell; int pad; double frac; double fre, fim; };
 
 template <class R> struct TabOf;
@@ -156,6 +159,14 @@ struct mbir_plan_s {
   int* perm_k;                // digit reversal of the K-point transform
   void* cdep;                 // [nz] falloff / KB deapodisation
   void* tab;                  // [ntab][m] TabF or TabD
+  // FP32 plans, filter formed in the row kernels (otf != 0): the grid positions
+  // [ntab][m] TabP, per pixel {Re, Im of A e^{j(Omega - 2k z_f + 2k (z_f - z_c))},
+  // 1/(2 k^2 NA^2), 2k} and per table row q^2; z_f - z_c
+  int otf;
+  mbir::TabP* tabp;
+  float4* fpix;
+  float* q2row;
+  float dzf;
   int4* rowmeta;              // [ntab] {base cell of u = 0, span of u + J, direction, 0}
   int gather_ok;              // every row monotone with span <= K: deterministic adjoint gather
   int max_span;               // largest row span (rowmeta .y) of the plan
@@ -281,6 +292,7 @@ struct BatchLaunch {
   const void* host0;
   int set_mu;
   double mu;
+  int blu;   // a scan of the launch runs its lateral transform in the Bluestein form
 };
 
 // Operands of one lateral stage for one scan (batch.cu fills these).

@@ -452,6 +452,14 @@ __device__ __forceinline__ void ct_pass_p_odd(float4* s, int N, int batch, int b
   __syncthreads();
 }
 
+#ifndef MBIR_FFT_ILP
+#define MBIR_FFT_ILP 1
+#endif
+// Butterflies a thread keeps in flight per pass of the paired transform: 2 loads
+// both butterflies' inputs before computing either, so that the shared-memory
+// latency of one overlaps the arithmetic of the other (twice the registers).
+constexpr int kFftIlp = MBIR_FFT_ILP;
+
 template <int R, bool INV, bool DIT, bool SW>
 __device__ __forceinline__ void ct_pass_p(float4* s, int N, int batch, int bshift, int L, const TwP& tw, int tid,
                                           int nthr) {
@@ -459,19 +467,52 @@ __device__ __forceinline__ void ct_pass_p(float4* s, int N, int batch, int bshif
   const int mshift = log2_if_pow2(M);
   const int nb = batch * (N / R);
   const int tstep = N / L;
-  for (int idx = tid; idx < nb; idx += nthr) {
-    int t, b, blk, j;
-    divmod_u(idx, batch, bshift, t, b);
-    divmod_u(t, M, mshift, blk, j);
-    const int i0 = (blk * L + j) * batch + b, di = M * batch;
-    PC v[R];
+  if constexpr (kFftIlp >= 2) {
+    for (int idx = tid; idx < nb; idx += 2 * nthr) {
+      const bool two = idx + nthr < nb;
+      int ia[2], ja[2];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = ld_pc(s, psw<SW>(i0 + r * di));
-    if (DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
-    dft_small_p<R, INV>(v, tw, N);
-    if (!DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
+      for (int q = 0; q < 2; ++q) {
+        int t, b, blk, j;
+        divmod_u(q && two ? idx + nthr : idx, batch, bshift, t, b);
+        divmod_u(t, M, mshift, blk, j);
+        ia[q] = (blk * L + j) * batch + b;
+        ja[q] = j;
+      }
+      const int di = M * batch;
+      PC v[2][R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) st_pc(s, psw<SW>(i0 + r * di), v[r]);
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = ld_pc(s, psw<SW>(ia[q] + r * di));
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (DIT && ja[q] != 0) apply_twiddles_p<R, INV>(v[q], tw, ja[q] * tstep);
+        dft_small_p<R, INV>(v[q], tw, N);
+        if (!DIT && ja[q] != 0) apply_twiddles_p<R, INV>(v[q], tw, ja[q] * tstep);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) st_pc(s, psw<SW>(ia[0] + r * di), v[0][r]);
+      if (two) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) st_pc(s, psw<SW>(ia[1] + r * di), v[1][r]);
+      }
+    }
+  } else {
+    for (int idx = tid; idx < nb; idx += nthr) {
+      int t, b, blk, j;
+      divmod_u(idx, batch, bshift, t, b);
+      divmod_u(t, M, mshift, blk, j);
+      const int i0 = (blk * L + j) * batch + b, di = M * batch;
+      PC v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = ld_pc(s, psw<SW>(i0 + r * di));
+      if (DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
+      dft_small_p<R, INV>(v, tw, N);
+      if (!DIT && j != 0) apply_twiddles_p<R, INV>(v, tw, j * tstep);
+#pragma unroll
+      for (int r = 0; r < R; ++r) st_pc(s, psw<SW>(i0 + r * di), v[r]);
+    }
   }
   __syncthreads();
 }

@@ -241,14 +241,19 @@ __device__ __noinline__ void lat_bluestein(cplx_t<R>* s, int TC, int nx, const R
 // The lateral transform of a tile: the plan's mixed-radix FFT (dif: digit-reversed
 // out; dit: digit-reversed in, natural out), or the Bluestein form when the plan
 // has a chirp (natural order in and out either way).
-template <class R, bool INV, bool DIT>
+// Kernels instantiated with BLU = false never contain the Bluestein code (it
+// would raise their register pressure); BLU = true kernels check per plan.
+template <class R, bool INV, bool DIT, bool BLU>
 __device__ __forceinline__ void lat_xform(cplx_t<R>* s, int TC, int nx, const Radix& rad, const LatFFT<R>& tw,
                                           const void* chirp, const void* bhat) {
-  if (chirp)
-    lat_bluestein<R, INV>(s, TC, nx, rad, tw, static_cast<const cplx_t<R>*>(chirp),
-                          static_cast<const cplx_t<R>*>(bhat));
-  else
-    lat_fft<R, INV, DIT>(s, TC, rad, tw);
+  if constexpr (BLU) {
+    if (chirp) {
+      lat_bluestein<R, INV>(s, TC, nx, rad, tw, static_cast<const cplx_t<R>*>(chirp),
+                            static_cast<const cplx_t<R>*>(bhat));
+      return;
+    }
+  }
+  lat_fft<R, INV, DIT>(s, TC, rad, tw);
 }
 
 __device__ __forceinline__ bool al(const void* p, unsigned bytes) {
@@ -407,7 +412,7 @@ constexpr bool lat_is_mid() {
 // FFT, epilogue on the digit-reversed result.  Mid modes (the measurement side of
 // Phi^H Phi): inverse FFT (dif), the measurement epilogue in place on the
 // digit-reversed tile, forward FFT (dit, digit-reversed in, natural out).
-template <class R, int MODE, class A>
+template <class R, int MODE, bool BLU, class A>
 __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int nx, int TC, int C, int blk,
                                              const void* twg, const int* perm, double* partial) {
   using V = cplx_t<R>;
@@ -468,7 +473,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   if constexpr (kMid) {
     // inverse as a forward dif of conj S, the epilogue in place on the
     // digit-reversed tile, then the forward dit
-    lat_xform<R, false, false>(s, TC, nx, rad, tw, a.chirp, a.bhat);
+    lat_xform<R, false, false, BLU>(s, TC, nx, rad, tw, a.chirp, a.bhat);
     constexpr int UM = 2;
     for (int p = p0; p < nx; p += UM * pstep) {
       EpOps<R> oa[UM], ob[UM];
@@ -502,14 +507,14 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
       }
     }
     __syncthreads();
-    lat_xform<R, false, true>(s, TC, nx, rad, tw, a.chirp, a.bhat);
+    lat_xform<R, false, true, BLU>(s, TC, nx, rad, tw, a.chirp, a.bhat);
     for (int p = p0; p < nx; p += pstep) {
       V xa, xb;
       lds2(s, p * TC + b, xa, xb);
       st2(reinterpret_cast<V*>(a.out), (size_t)p * C + c, v2, ok0, ok1, cscale(xa, a.scale), cscale(xb, a.scale));
     }
   } else {
-    lat_xform<R, INV, false>(s, TC, nx, rad, tw, a.chirp, a.bhat);
+    lat_xform<R, INV, false, BLU>(s, TC, nx, rad, tw, a.chirp, a.bhat);
     constexpr int UE = 4;
     for (int p = p0; p < nx; p += UE * pstep) {
       EpOps<R> oa[UE], ob[UE];
@@ -542,43 +547,48 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   }
 }
 
-template <class R, int MODE, bool BAT>
-__global__ void __launch_bounds__(kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
+template <class R, int MODE, bool BAT, bool BLU>
+__global__ void __launch_bounds__(BAT ? kLatThreadsBatch : kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
 lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>> B) {
   if constexpr (!BAT) {
-    lateral_body<R, MODE>(a0, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, a0.partial);
+    lateral_body<R, MODE, BLU>(a0, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, a0.partial);
   } else {
     int blk;
     const LatArgs<R>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
-    LatEp<R> e;
-    e.in = A.in;
-    e.out = A.out;
-    e.mask = A.mask;
-    e.y = A.y;
-    e.pz = A.pz;
-    e.r = A.r;
-    e.z1 = A.z1;
-    e.z2 = A.z2;
-    e.vout = A.vout;
-    e.scal = A.scal;
-    e.chirp = A.chirp;
-    e.bhat = A.bhat;
-    e.scale = A.scale;
-    e.mu = B.set_mu ? R(B.mu) : A.mu;
-    e.delta = A.delta;
-    e.tau = A.tau;
+    // the scan's operands in shared memory, where the body reads them as it needs
+    // them (a register copy of all of them made the kernel spill)
+    __shared__ LatEp<R> e;
+    if (threadIdx.x == 0) {
+      e.in = A.in;
+      e.out = A.out;
+      e.mask = A.mask;
+      e.y = A.y;
+      e.pz = A.pz;
+      e.r = A.r;
+      e.z1 = A.z1;
+      e.z2 = A.z2;
+      e.vout = A.vout;
+      e.scal = A.scal;
+      e.chirp = A.chirp;
+      e.bhat = A.bhat;
+      e.scale = A.scale;
+      e.mu = B.set_mu ? R(B.mu) : A.mu;
+      e.delta = A.delta;
+      e.tau = A.tau;
+    }
     __syncthreads();
-    lateral_body<R, MODE>(e, rad, A.nx, A.tc, A.cols, blk, A.tw, A.perm, A.partial);
+    lateral_body<R, MODE, BLU>(e, rad, A.nx, A.tc, A.cols, blk, A.tw, A.perm, A.partial);
   }
 }
 
 // The y-axis transform of a volume: lateral_body over the ny rows of every px slab
 // (blockIdx.y) of an [nx][ny][cols] array, in place or not (each CTA stages its
-// whole tile before it writes).  Complex transforms only.
-template <class R, int MODE>
-__global__ void __launch_bounds__(kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
+// whole tile before it writes).  Complex transforms only.  Like the batched
+// kernels it works from a register copy of its operands, in 256-thread CTAs.
+template <class R, int MODE, bool BLU>
+__global__ void __launch_bounds__(kLatThreadsBatch, sizeof(R) == 4 ? kLatMinBlocks : 1)
 lateral_slab_kernel(const __grid_constant__ LatArgs<R> a0, long long slab) {
   static_assert(MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV, "complex slab transforms only");
   const size_t off = (size_t)blockIdx.y * (size_t)slab;
@@ -597,7 +607,7 @@ lateral_slab_kernel(const __grid_constant__ LatArgs<R> a0, long long slab) {
   e.bhat = a0.bhat;
   e.scale = a0.scale;
   e.mu = e.delta = e.tau = R(0);
-  lateral_body<R, MODE>(e, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, nullptr);
+  lateral_body<R, MODE, BLU>(e, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, nullptr);
 }
 
 // ------------------------------------------------------------- KB weights
@@ -972,12 +982,46 @@ row_adjoint_gather_kernel(const __grid_constant__ RowArgs<R> a0, const BatchRef<
 // (0 <= lp <= nx/2) takes rows lp and nx - lp; rows 0 and nx/2 are their own
 // mirror and run alone (lane b repeats lane a and is not stored).
 
+// The filter of pixel m on table row lp formed from its factors (plan otf):
+// fp = {Re, Im of A e^{j(Omega - 2k z_f + 2k (z_f - z_c))}, 1/(2 k^2 NA^2), 2k},
+// times exp(-q^2 / (2 k^2 NA^2)) e^{-j (2k - beta)(z_f - z_c)}, with
+// 2k - beta = q^2 / (beta + 2k) (no cancellation in FP32); 0 where 4k^2 <= q^2.
+__device__ __forceinline__ float2 otf_filter(const float4& fp, float q2, float dzf) {
+  const float b2 = fp.w * fp.w - q2;
+  if (!(b2 > 0.f)) return make_float2(0.f, 0.f);
+  const float d = q2 / (sqrtf(b2) + fp.w);
+  const float G = expf(-q2 * fp.z);
+  float sn, cs;
+  sincosf(-d * dzf, &sn, &cs);
+  return make_float2(G * (fp.x * cs - fp.y * sn), G * (fp.x * sn + fp.y * cs));
+}
+
+// Table entry of pixel mm on table row lp: grid position and filter, read whole
+// (OTF = false) or position read and filter formed (OTF = true).
+template <bool OTF>
+__device__ __forceinline__ void row_entry_load(const RowArgs<float>& a, int lp, int mm, TabF& e, float4& fp) {
+  if constexpr (OTF) {
+    const TabP t = a.tabp[(size_t)lp * a.m + mm];
+    e.cell = t.cell;
+    e.frac = t.frac;
+    fp = a.fpix[mm];
+  } else {
+    e = reinterpret_cast<const TabF*>(a.tab)[(size_t)lp * a.m + mm];
+  }
+}
+
+template <bool OTF>
+__device__ __forceinline__ float2 row_entry_filter(const RowArgs<float>& a, const TabF& e, const float4& fp, float q2) {
+  if constexpr (OTF) return otf_filter(fp, q2, a.dzf);
+  else return make_float2(e.fre, e.fim);
+}
+
 __device__ __forceinline__ int pair_row_b(int lp, int nx) {
   const int lb = nx - lp;
   return (lp == 0 || lb == lp) ? -1 : lb;
 }
 
-template <int J>
+template <int J, bool OTF>
 __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, const Radix& rad, int lp,
                                                       const RowArgs<float>& a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1024,16 +1068,17 @@ __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, c
   }
   __syncthreads();
   fft_p_dit<false, true>(buf, 1, rad, tw);
-  const TabF* tab = reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M;
   float2* Sa = reinterpret_cast<float2*>(a.out) + (size_t)la * M;
   float2* Sb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * M;
+  const float q2 = OTF ? a.q2row[lp] : 0.f;
   constexpr int UM = 2;
   for (int m0 = tid; m0 < M; m0 += UM * nthr) {
     TabF e[UM];
+    float4 fp[UM];
 #pragma unroll
     for (int u = 0; u < UM; ++u) {
       const int mm = m0 + u * nthr;
-      if (mm < M) e[u] = tab[mm];
+      if (mm < M) row_entry_load<OTF>(a, lp, mm, e[u], fp[u]);
     }
 #pragma unroll
     for (int u = 0; u < UM; ++u) {
@@ -1052,32 +1097,32 @@ __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, c
         ar = fma2(make_float2(t.x, t.y), ww, ar);
         ai = fma2(make_float2(t.z, t.w), ww, ai);
       }
-      const float2 f = make_float2(e[u].fre, e[u].fim);
+      const float2 f = row_entry_filter<OTF>(a, e[u], fp[u], q2);
       Sa[mm] = cmul(make_float2(ar.x, ai.x), f);
       if (lb >= 0) Sb[mm] = cmul(make_float2(ar.y, ai.y), f);
     }
   }
 }
 
-template <int J, bool BAT>
+template <int J, bool BAT, bool OTF>
 __global__ void __launch_bounds__(kRowPairThreads, kRowPairMinBlocks)
 row_forward_pair_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
   if constexpr (!BAT) {
-    row_forward_pair_body<J>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_forward_pair_body<J, OTF>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<float>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_forward_pair_body<J>(A, rad, blk, a0);
+    row_forward_pair_body<J, OTF>(A, rad, blk, a0);
   }
 }
 
 // The adjoint gather of row_adjoint_gather_body for a row pair: the pixels' KB
 // weights, unwrapped cells and run boundaries are built once, each cell sums its
 // run for both rows in the two lanes of split pairs.
-template <int J>
+template <int J, bool OTF>
 __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, const Radix& rad, int lp,
                                                      const RowArgs<float>& a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1101,7 +1146,7 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
   const TwP tw = load_twiddles_p(tws, reinterpret_cast<const float2*>(a.tw), rad);
   const int4 meta = a.rowmeta[lp];
   const int base = meta.x, span = meta.y, dir = meta.z;
-  const TabF* tab = reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M;
+  const float q2 = OTF ? a.q2row[lp] : 0.f;
   const float2* Ra = reinterpret_cast<const float2*>(a.in) + (size_t)la * M;
   const float2* Rb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * M;
   pdl_wait_release();
@@ -1109,12 +1154,13 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
   constexpr int UM = 2;
   for (int m0 = tid; m0 < M; m0 += UM * nthr) {
     TabF e[UM];
+    float4 fp[UM];
     float2 ra[UM], rb[UM];
 #pragma unroll
     for (int q = 0; q < UM; ++q) {
       const int mm = m0 + q * nthr;
       if (mm < M) {
-        e[q] = tab[mm];
+        row_entry_load<OTF>(a, lp, mm, e[q], fp[q]);
         ra[q] = Ra[mm];
         rb[q] = Rb[mm];
       }
@@ -1124,7 +1170,7 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
       const int mm = m0 + q * nthr;
       if (mm >= M) continue;
       const int sidx = dir > 0 ? mm : M - 1 - mm;
-      const float2 f = make_float2(e[q].fre, e[q].fim);
+      const float2 f = row_entry_filter<OTF>(a, e[q], fp[q], q2);
       const float2 va = cmulc(ra[q], f), vb = cmulc(rb[q], f);
       sv[sidx] = make_float4(va.x, vb.x, va.y, vb.y);
       float w[J];
@@ -1178,18 +1224,18 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
   }
 }
 
-template <int J, bool BAT>
+template <int J, bool BAT, bool OTF>
 __global__ void __launch_bounds__(kGatherPairThreads, 1)
 row_gather_pair_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
   if constexpr (!BAT) {
-    row_gather_pair_body<J>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_gather_pair_body<J, OTF>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<float>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_gather_pair_body<J>(A, rad, blk, a0);
+    row_gather_pair_body<J, OTF>(A, rad, blk, a0);
   }
 }
 
@@ -1212,7 +1258,7 @@ __device__ __forceinline__ float kb_tap_weight(float frac, const RowArgs<float>&
   return t;
 }
 
-template <int J>
+template <int J, bool OTF>
 __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& a, const Radix& rad, int lp,
                                                           const RowArgs<float>& a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1236,13 +1282,14 @@ __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& 
   const int4 meta = a.rowmeta[lp];
   const int base = meta.x, span = meta.y, dir = meta.z;
   const int vmax = span - J;                                 // largest u of the row
-  const TabF* tab = reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M;
+  const float q2 = OTF ? a.q2row[lp] : 0.f;
   const float2* Ra = reinterpret_cast<const float2*>(a.in) + (size_t)la * M;
   const float2* Rb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * M;
   pdl_wait_release();
   constexpr int UM = 2;
   for (int m0 = tid; m0 < M; m0 += UM * nthr) {
     TabF e[UM];
+    float4 fp[UM];
     float2 ra[UM], rb[UM];
     int uprev[UM];
 #pragma unroll
@@ -1250,12 +1297,16 @@ __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& 
       const int mm = m0 + q * nthr;
       uprev[q] = -1;
       if (mm < M) {
-        e[q] = tab[mm];
+        row_entry_load<OTF>(a, lp, mm, e[q], fp[q]);
         ra[q] = Ra[mm];
         rb[q] = Rb[mm];
         // the previous pixel in increasing-u order
         const int mp = dir > 0 ? mm - 1 : mm + 1;
-        if (mp >= 0 && mp < M) uprev[q] = (int)((unsigned)tab[mp].cell >> 16);
+        if (mp >= 0 && mp < M) {
+          const int cp = OTF ? a.tabp[(size_t)lp * M + mp].cell
+                             : reinterpret_cast<const TabF*>(a.tab)[(size_t)lp * M + mp].cell;
+          uprev[q] = (int)((unsigned)cp >> 16);
+        }
       }
     }
 #pragma unroll
@@ -1263,7 +1314,7 @@ __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& 
       const int mm = m0 + q * nthr;
       if (mm >= M) continue;
       const int sidx = dir > 0 ? mm : M - 1 - mm;
-      const float2 f = make_float2(e[q].fre, e[q].fim);
+      const float2 f = row_entry_filter<OTF>(a, e[q], fp[q], q2);
       const float2 va = cmulc(ra[q], f), vb = cmulc(rb[q], f);
       sv[sidx] = make_float4(va.x, vb.x, va.y, vb.y);
       sfrac[sidx] = e[q].frac;
@@ -1311,18 +1362,18 @@ __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& 
   }
 }
 
-template <int J, bool BAT>
+template <int J, bool BAT, bool OTF>
 __global__ void __launch_bounds__(kGatherLeanThreads, kGatherLeanMinBlocks)
 row_gather_pair_lean_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
   if constexpr (!BAT) {
-    row_gather_pair_lean_body<J>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_gather_pair_lean_body<J, OTF>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<float>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_gather_pair_lean_body<J>(A, rad, blk, a0);
+    row_gather_pair_lean_body<J, OTF>(A, rad, blk, a0);
   }
 }
 
@@ -1378,8 +1429,12 @@ template <class R, int MODE>
 int launch_lateral_args(mbir_plan p, const LatArgs<R>& a, int cols, cudaStream_t st) {
   {
     ProfScope ps_(p, lat_class(MODE), st);
-    launch(lateral_kernel<R, MODE, false>, dim3(lateral_grid(p, cols)), dim3(kLatThreads), lat_smem<R>(p), st, a,
-           no_batch<LatArgs<R>>());
+    if (p->chirp)
+      launch(lateral_kernel<R, MODE, false, true>, dim3(lateral_grid(p, cols)), dim3(kLatThreads), lat_smem<R>(p), st,
+             a, no_batch<LatArgs<R>>());
+    else
+      launch(lateral_kernel<R, MODE, false, false>, dim3(lateral_grid(p, cols)), dim3(kLatThreads), lat_smem<R>(p),
+             st, a, no_batch<LatArgs<R>>());
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -1409,6 +1464,11 @@ RowArgs<R> row_args(mbir_plan p, const void* in, void* out) {
   a.rowmeta = p->rowmeta;
   a.rowmap = p->rowmap;
   a.ny = p->ny;
+  a.otf = p->otf;
+  a.tabp = p->tabp;
+  a.fpix = p->fpix;
+  a.q2row = p->q2row;
+  a.dzf = p->dzf;
   a.alpha = p->alpha;
   a.inv_i0a = 1.0 / host_bessel_i0(p->alpha);
   for (int j = 0; j < kMaxJ; ++j)
@@ -1485,16 +1545,35 @@ template <class R, int J, bool BAT, bool COMP>
 static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid, size_t smem,
                          cudaStream_t st) {
   if constexpr (sizeof(R) == 4 && !COMP) {
+    const bool otf = a.otf != 0;
     if (kind == ROW_FWD_PAIR) {
-      launch(row_forward_pair_kernel<J, BAT>, dim3(grid), dim3(kRowPairThreads), smem, st, a, B);
+      if constexpr (kFilterOtf) {
+        if (otf) {
+          launch(row_forward_pair_kernel<J, BAT, true>, dim3(grid), dim3(kRowPairThreads), smem, st, a, B);
+          return;
+        }
+      }
+      launch(row_forward_pair_kernel<J, BAT, false>, dim3(grid), dim3(kRowPairThreads), smem, st, a, B);
       return;
     }
     if (kind == ROW_GATHER_PAIR) {
-      launch(row_gather_pair_kernel<J, BAT>, dim3(grid), dim3(kGatherPairThreads), smem, st, a, B);
+      if constexpr (kFilterOtf) {
+        if (otf) {
+          launch(row_gather_pair_kernel<J, BAT, true>, dim3(grid), dim3(kGatherPairThreads), smem, st, a, B);
+          return;
+        }
+      }
+      launch(row_gather_pair_kernel<J, BAT, false>, dim3(grid), dim3(kGatherPairThreads), smem, st, a, B);
       return;
     }
     if (kind == ROW_GATHER_PAIR_LEAN) {
-      launch(row_gather_pair_lean_kernel<J, BAT>, dim3(grid), dim3(kGatherLeanThreads), smem, st, a, B);
+      if constexpr (kFilterOtf) {
+        if (otf) {
+          launch(row_gather_pair_lean_kernel<J, BAT, true>, dim3(grid), dim3(kGatherLeanThreads), smem, st, a, B);
+          return;
+        }
+      }
+      launch(row_gather_pair_lean_kernel<J, BAT, false>, dim3(grid), dim3(kGatherLeanThreads), smem, st, a, B);
       return;
     }
   }
@@ -1724,8 +1803,13 @@ int launch_slab(mbir_plan p, void* buf, int cols, cudaStream_t st) {
   const LatArgs<R> a = lat_args_y<R>(p, buf, buf, cols);
   {
     ProfScope ps_(p, MODE == LAT_C2C_FWD ? PC_LAT_FWD : PC_LAT_ADJ, st);
-    launch(lateral_slab_kernel<R, MODE>, dim3((cols + p->tile_y - 1) / p->tile_y, p->nx), dim3(kLatThreads),
-           lat_smem_y<R>(p), st, a, (long long)p->ny * cols);
+    const dim3 grid((cols + p->tile_y - 1) / p->tile_y, p->nx);
+    if (p->chirp_y)
+      launch(lateral_slab_kernel<R, MODE, true>, grid, dim3(kLatThreadsBatch), lat_smem_y<R>(p), st, a,
+             (long long)p->ny * cols);
+    else
+      launch(lateral_slab_kernel<R, MODE, false>, grid, dim3(kLatThreadsBatch), lat_smem_y<R>(p), st, a,
+             (long long)p->ny * cols);
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -1795,30 +1879,26 @@ static int configure_t() {
 #define MBIR_SMEM_ATTR(fn, bytes)                                                                  \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));    \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_FWD, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_FWD, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_INV, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2C_INV, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_R2C_MASK, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_R2C_MASK, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2R_INV_MASK, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_C2R_INV_MASK, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_FWD, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_FWD, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_L1, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_L1, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_ADJ_V, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_MID, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_SOLVE_MID, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_MID, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_MID, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_FWD, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_FWD, true>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_ADJ, false>), lat);
-  MBIR_SMEM_ATTR((lateral_kernel<R, LAT_POWER_ADJ, true>), lat);
-  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_FWD>), lat);
-  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_INV>), lat);
+#define MBIR_LAT_ATTRS(M)                                       \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, false, false>), lat);    \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, true, false>), lat);     \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, false, true>), lat);     \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, true, true>), lat)
+  MBIR_LAT_ATTRS(LAT_C2C_FWD);
+  MBIR_LAT_ATTRS(LAT_C2C_INV);
+  MBIR_LAT_ATTRS(LAT_R2C_MASK);
+  MBIR_LAT_ATTRS(LAT_C2R_INV_MASK);
+  MBIR_LAT_ATTRS(LAT_SOLVE_FWD);
+  MBIR_LAT_ATTRS(LAT_SOLVE_ADJ_L1);
+  MBIR_LAT_ATTRS(LAT_SOLVE_ADJ_V);
+  MBIR_LAT_ATTRS(LAT_SOLVE_MID);
+  MBIR_LAT_ATTRS(LAT_POWER_MID);
+  MBIR_LAT_ATTRS(LAT_POWER_FWD);
+  MBIR_LAT_ATTRS(LAT_POWER_ADJ);
+  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_FWD, false>), lat);
+  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_INV, false>), lat);
+  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_FWD, true>), lat);
+  MBIR_SMEM_ATTR((lateral_slab_kernel<R, LAT_C2C_INV, true>), lat);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 4, false>), row);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 4, true>), row);
   MBIR_SMEM_ATTR((row_forward_kernel<R, 6, false>), row);
@@ -1850,25 +1930,44 @@ static int configure_t() {
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 6, true, true>), gat);
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, true, true>), gat);
   if constexpr (sizeof(R) == 4) {
-    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, false>), gat);
-    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, false>), gat);
-    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, false>), gat);
-    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, true>), gat);
-    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, true>), gat);
-    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, true>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, false>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, false>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, false>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, false>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, false>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, false>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, true>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, true>), gat);
-    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, true>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<4, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<4, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<6, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<6, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<8, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<8, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<4, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<6, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<8, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, true, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, false, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, false, true>), gat); }
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, true, false>), gat);
+    if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, true, true>), gat); }
   }
+#undef MBIR_LAT_ATTRS
 #undef MBIR_SMEM_ATTR
   return MBIR_OK;
 }
@@ -1979,7 +2078,10 @@ static void lat_batch_t(const BatchLaunch& L, cudaStream_t st) {
   B.mu = L.mu;
   LatArgs<R> a0;
   memcpy(&a0, L.host0, sizeof(a0));
-  launch(lateral_kernel<R, MODE, true>, dim3(L.total), dim3(kLatThreads), L.smem, st, a0, B);
+  if (L.blu)
+    launch(lateral_kernel<R, MODE, true, true>, dim3(L.total), dim3(kLatThreadsBatch), L.smem, st, a0, B);
+  else
+    launch(lateral_kernel<R, MODE, true, false>, dim3(L.total), dim3(kLatThreadsBatch), L.smem, st, a0, B);
 }
 
 int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st) {

@@ -36,6 +36,14 @@ namespace mbir {
 #define MBIR_LAT_MINB 2
 #endif
 constexpr int kLatThreads = MBIR_LAT_THREADS;   // lateral FFT block size
+// Batched lateral kernels read their scan's argument block from device memory
+// and keep a register copy of its operands; at 512 threads and 64 registers they
+// spilled 130-400 bytes a thread, so they run 256-thread CTAs with up to 128
+// registers (two an SM, the same tiles).
+#ifndef MBIR_LAT_THREADS_BATCH
+#define MBIR_LAT_THREADS_BATCH 256
+#endif
+constexpr int kLatThreadsBatch = MBIR_LAT_THREADS_BATCH;
 constexpr int kLatElems = MBIR_LAT_ELEMS;       // nx * columns staged per lateral CTA (max)
 constexpr int kRowThreads = MBIR_ROW_THREADS;   // row (NUFFT) block size
 constexpr int kRowMinBlocks = MBIR_ROW_MINB;    // resident CTAs per SM the register budget targets
@@ -73,6 +81,12 @@ constexpr int kGatherPairThreads = MBIR_GATHERPAIR_THREADS;
 #ifndef MBIR_GATHERLEAN_MINB
 #define MBIR_GATHERLEAN_MINB 2
 #endif
+// FP32 plans form the filter in the row kernels from per-pixel and per-row
+// constants (8-byte table entries) instead of reading it (16-byte entries)
+#ifndef MBIR_FILTER_OTF
+#define MBIR_FILTER_OTF 0
+#endif
+constexpr bool kFilterOtf = MBIR_FILTER_OTF != 0;
 #ifndef MBIR_GATHERLEAN_DEFAULT
 #define MBIR_GATHERLEAN_DEFAULT 0
 #endif
@@ -140,6 +154,13 @@ struct RowArgs {
   Radix rad;
   int nx, nz, m, K, n0;
   int ny;                // volumes: rows are (lx, ly) = (r / ny, r % ny); 1 for a B-scan
+  // FP32 pair kernels with the filter formed per (row, pixel) instead of read
+  // from the table (the plan's otf): tab then points at TabP entries
+  int otf;
+  const TabP* tabp;
+  const float4* fpix;
+  const float* q2row;
+  float dzf;
   double alpha, inv_i0a;
   float kbpoly[kMaxJ][kKbDeg + 1];   // FP32 KB weight of tap j: polynomial in (frac - 1/2)
 };

@@ -425,6 +425,43 @@ static int upload_tables(mbir_plan p, const mbir_geometry* g, cudaStream_t st) {
   MBIR_CUDA_TRY(cudaMalloc(&p->tw_k, sizeof(V) * twk.size()));
   MBIR_CUDA_TRY(cudaMalloc(&p->cdep, sizeof(R) * nz));
   MBIR_CUDA_TRY(cudaMalloc(&p->tab, sizeof(Tab) * tab.size()));
+  if (sizeof(R) == 4 && kFilterOtf) {
+    // the filter's factors: per pixel A e^{j(Omega - 2k z_f + 2k (z_f - z_c))}, the beam
+    // filter's 1/(2 k^2 NA^2) and 2k; per table row q^2; the row kernels form
+    // A G(q, k) e^{j(Omega - 2k z_f + beta (z_f - z_c))} as that times
+    // exp(-q^2 / (2 k^2 NA^2)) e^{-j (2k - beta)(z_f - z_c)}, 2k - beta = q^2 / (beta + 2k)
+    std::vector<TabP> tp(tab.size());
+    for (size_t i = 0; i < tab.size(); ++i) {
+      tp[i].cell = tab[i].cell;
+      tp[i].frac = (float)tab[i].frac;
+    }
+    std::vector<float4> fp(m);
+    const double zc = p->n0 * p->dz, dzf = g->z_focus_um - zc;
+    for (int mm = 0; mm < m; ++mm) {
+      const double k = g->k[mm];
+      const double A = g->source ? g->source[mm] : 1.0;
+      const double dk = k - g->k0;
+      const double omega = g->disp_a * dk * dk + g->disp_b * dk * dk * dk;
+      const double ph = fmod(omega - 2.0 * k * g->z_focus_um, 2.0 * M_PI) + fmod(2.0 * k * dzf, 2.0 * M_PI);
+      fp[mm] = make_float4((float)(A * cos(ph)), (float)(A * sin(ph)),
+                           g->na > 0 ? (float)(1.0 / (2.0 * k * k * g->na * g->na)) : 0.0f, (float)(2.0 * k));
+    }
+    std::vector<float> q2v(p->ntab);
+    for (int lp = 0; lp < p->ntab; ++lp) {
+      const double qx = 2.0 * M_PI * (lp / nyh) / (nx * p->dx);
+      const double qy = p->ny > 1 ? 2.0 * M_PI * (lp % nyh) / (p->ny * p->dy) : 0.0;
+      q2v[lp] = (float)(qx * qx + qy * qy);
+    }
+    p->otf = 1;
+    p->dzf = (float)dzf;
+    MBIR_CUDA_TRY(cudaMalloc(&p->tabp, sizeof(TabP) * tp.size()));
+    MBIR_CUDA_TRY(cudaMalloc(&p->fpix, sizeof(float4) * fp.size()));
+    MBIR_CUDA_TRY(cudaMalloc(&p->q2row, sizeof(float) * q2v.size()));
+    MBIR_CUDA_TRY(cudaMemcpyAsync(p->tabp, tp.data(), sizeof(TabP) * tp.size(), cudaMemcpyHostToDevice, st));
+    MBIR_CUDA_TRY(cudaMemcpyAsync(p->fpix, fp.data(), sizeof(float4) * fp.size(), cudaMemcpyHostToDevice, st));
+    MBIR_CUDA_TRY(cudaMemcpyAsync(p->q2row, q2v.data(), sizeof(float) * q2v.size(), cudaMemcpyHostToDevice, st));
+    MBIR_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors die here
+  }
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->tw_k, twk.data(), sizeof(V) * twk.size(), cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->cdep, cdep.data(), sizeof(R) * nz, cudaMemcpyHostToDevice, st));
   MBIR_CUDA_TRY(cudaMemcpyAsync(p->tab, tab.data(), sizeof(Tab) * tab.size(), cudaMemcpyHostToDevice, st));
@@ -647,6 +684,9 @@ void mbir_plan_destroy(mbir_plan p) {
   cudaFree(p->chirp);
   cudaFree(p->bhat);
   cudaFree(p->rowmap);
+  cudaFree(p->tabp);
+  cudaFree(p->fpix);
+  cudaFree(p->q2row);
   cudaFree(p->tw_y);
   cudaFree(p->perm_y);
   cudaFree(p->chirp_y);
