@@ -534,24 +534,34 @@ __device__ __forceinline__ void ct_dispatch_p(int R, float4* s, int N, int batch
 
 // `batch` interleaved pair-sequences, element i of pair-sequence b at
 // s[psw<SW>(i * batch + b)] (SW only with batch = 1).
+// Passes [first, end) (end < 0: to the last): a caller that runs pass 0 on its
+// way in from global memory starts at 1, one that runs the last pass on its way
+// out ends before it.
 template <bool INV, bool SW = false>
-__device__ void fft_p_dif(float4* s, int batch, const Radix& rad, const TwP& tw) {
+__device__ void fft_p_dif(float4* s, int batch, const Radix& rad, const TwP& tw, int first = 0, int end = -1) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int bshift = log2_if_pow2(batch);
+  if (end < 0) end = rad.npass;
   int L = rad.n;
-  for (int p = 0; p < rad.npass; ++p) {
+  for (int p = 0; p < first; ++p) L /= rad.r[p];
+  for (int p = first; p < end; ++p) {
     const int R = rad.r[p];
     ct_dispatch_p<INV, false, SW>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);
     L /= R;
   }
 }
 
+// Passes top, top - 1, ..., last (top < 0: from the first dit pass, npass - 1): a
+// caller that runs pass 0 on its way out to global memory stops at 1, one that
+// ran pass npass - 1 itself starts at npass - 2.
 template <bool INV, bool SW = false>
-__device__ void fft_p_dit(float4* s, int batch, const Radix& rad, const TwP& tw) {
+__device__ void fft_p_dit(float4* s, int batch, const Radix& rad, const TwP& tw, int last = 0, int top = -1) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int bshift = log2_if_pow2(batch);
+  if (top < 0) top = rad.npass - 1;
   int L = 1;
-  for (int p = rad.npass - 1; p >= 0; --p) {
+  for (int p = rad.npass - 1; p > top; --p) L *= rad.r[p];
+  for (int p = top; p >= last; --p) {
     const int R = rad.r[p];
     L *= R;
     ct_dispatch_p<INV, true, SW>(R, s, rad.n, batch, bshift, L, tw, tid, nthr);

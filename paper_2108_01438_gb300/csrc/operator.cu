@@ -403,6 +403,137 @@ constexpr bool lat_is_mid() {
   return MODE == LAT_SOLVE_MID || MODE == LAT_POWER_MID;
 }
 
+// The input pair (p, c), (p, c + 1) of a lateral tile as the transform takes it:
+// loaded (masked for R2C), scaled by 1/||w|| and written out as v for the power
+// iteration's first pass, conjugated for the middle passes (their inverse
+// transform runs as a forward transform of conj S).
+template <class R, int MODE, class A>
+__device__ __forceinline__ void lat_in2(const A& a, size_t off, bool v2, bool ok0, bool ok1, R fscale,
+                                        cplx_t<R>& va, cplx_t<R>& vb) {
+  using V = cplx_t<R>;
+  va = vb = cmk<V>(R(0), R(0));
+  lat_load2<R, MODE>(a, off, v2, ok0, ok1, va, vb);
+  if constexpr (MODE == LAT_POWER_FWD) {
+    va = cscale(va, fscale);
+    vb = cscale(vb, fscale);
+    st2(reinterpret_cast<V*>(a.vout), off, v2, ok0, ok1, va, vb);
+  }
+  if constexpr (lat_is_mid<MODE>()) {
+    va.y = -va.y;
+    vb.y = -vb.y;
+  }
+}
+
+// Pass 0 of the FP32 dif transform (radix RR, span N/RR) run on the way in from
+// global memory: each thread loads the RR rows of its butterflies straight into
+// registers, so the tile is written to shared memory once, already through that
+// pass (staging would write it, and the pass read and write it again).
+template <int RR, bool INV, int MODE, class A>
+__device__ __forceinline__ void lat_first_pass_p(const A& a, float4* s4, int N, int half, int hs, int C, int c,
+                                                 bool v2, bool ok0, bool ok1, float fscale, const TwP& tw) {
+  const int M = N / RR, q = threadIdx.x & (half - 1);
+  for (int j = threadIdx.x >> hs; j < M; j += (int)blockDim.x >> hs) {
+    PC v[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      float2 va, vb;
+      lat_in2<float, MODE>(a, (size_t)(j + r * M) * C + c, v2, ok0, ok1, fscale, va, vb);
+      v[r] = PC{make_float2(va.x, vb.x), make_float2(va.y, vb.y)};
+    }
+    dft_small_p<RR, INV>(v, tw, N);
+    if (j != 0) apply_twiddles_p<RR, INV>(v, tw, j);
+#pragma unroll
+    for (int r = 0; r < RR; ++r) st_pc(s4, (j + r * M) * half + q, v[r]);
+  }
+}
+
+// The last pass (pass 0, span N/RR) of the FP32 forward dit transform run on the
+// way out: its outputs are in natural row order, so each thread writes the RR rows
+// of its butterflies, scaled, straight to global memory.
+template <int RR, class A>
+__device__ __forceinline__ void lat_last_pass_store_p(const A& a, const float4* s4, int N, int half, int hs, int C,
+                                                      int c, bool v2, bool ok0, bool ok1, const TwP& tw) {
+  const int M = N / RR, q = threadIdx.x & (half - 1);
+  const float sc = a.scale;
+  for (int j = threadIdx.x >> hs; j < M; j += (int)blockDim.x >> hs) {
+    PC v[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) v[r] = ld_pc(s4, (j + r * M) * half + q);
+    if (j != 0) apply_twiddles_p<RR, false>(v, tw, j);
+    dft_small_p<RR, false>(v, tw, N);
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+      st2(reinterpret_cast<float2*>(a.out), (size_t)(j + r * M) * C + c, v2, ok0, ok1,
+          make_float2(v[r].re.x * sc, v[r].im.x * sc), make_float2(v[r].re.y * sc, v[r].im.y * sc));
+  }
+}
+
+// The last pass (span 1, radix RL) of an FP32 dif transform run on the way out:
+// its outputs sit at positions blk RL + r, natural row siperm[pos]; the mode's
+// epilogue runs there and writes straight to global memory (a read-out would
+// read the tile back after that pass wrote it).
+template <int RL, bool INV, int MODE, class A>
+__device__ __forceinline__ void lat_last_pass_epi_p(const A& a, const float4* s4, int N, int half, int hs, int C,
+                                                    int c, bool v2, bool ok0, bool ok1, const int* siperm,
+                                                    const TwP& tw, float& part, float& part2) {
+  const int q = threadIdx.x & (half - 1);
+  for (int blk = threadIdx.x >> hs; blk < N / RL; blk += (int)blockDim.x >> hs) {
+    PC v[RL];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) v[r] = ld_pc(s4, (blk * RL + r) * half + q);
+    dft_small_p<RL, INV>(v, tw, N);
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const size_t off = (size_t)siperm[blk * RL + r] * C + c;
+      EpOps<float> o0, o1;
+      lat_prefetch2<float, MODE>(a, off, v2, ok0, ok1, o0, o1);
+      lat_store2<float, MODE>(a, off, v2, ok0, ok1, make_float2(v[r].re.x, v[r].im.x),
+                              make_float2(v[r].re.y, v[r].im.y), o0, o1, part, part2);
+    }
+  }
+}
+
+// The middle of the measurement pass in registers: the last dif pass of the
+// inverse transform (span 1, radix RL), the measurement epilogue at the natural
+// rows of its outputs, and the first dit pass of the forward transform, which
+// works on the same RL positions (span 1, no twiddles).  The tile is read and
+// written once for the three.
+template <int RL, int MODE, class A>
+__device__ __forceinline__ void lat_mid_center_p(const A& a, float4* s4, int N, int half, int hs, int C, int c,
+                                                 bool v2, bool ok0, bool ok1, const int* siperm, const TwP& tw,
+                                                 float& part) {
+  const int q = threadIdx.x & (half - 1);
+  for (int blk = threadIdx.x >> hs; blk < N / RL; blk += (int)blockDim.x >> hs) {
+    PC v[RL];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) v[r] = ld_pc(s4, (blk * RL + r) * half + q);
+    dft_small_p<RL, false>(v, tw, N);
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const size_t off = (size_t)siperm[blk * RL + r] * C + c;
+      EpOps<float> o0, o1;
+      lat_prefetch2<float, MODE>(a, off, v2, ok0, ok1, o0, o1);
+      float ra, rb;
+      if constexpr (MODE == LAT_SOLVE_MID) {
+        float pa, pb, qa = 0.f, qb = 0.f;
+        ra = solve_meas<float>(a, v[r].re.x, o0, pa, qa);
+        rb = solve_meas<float>(a, v[r].re.y, o1, pb, qb);
+        if (ok0) part += qa;
+        if (ok1) part += qb;
+        st2(a.pz, off, v2, ok0, ok1, pa, pb);
+      } else {
+        ra = o0.meas ? v[r].re.x * a.scale : 0.f;
+        rb = o1.meas ? v[r].re.y * a.scale : 0.f;
+      }
+      v[r] = PC{make_float2(ok0 ? ra : 0.f, ok1 ? rb : 0.f), make_float2(0.f, 0.f)};
+    }
+    dft_small_p<RL, false>(v, tw, N);
+#pragma unroll
+    for (int r = 0; r < RL; ++r) st_pc(s4, (blk * RL + r) * half + q, v[r]);
+  }
+  __syncthreads();
+}
+
 // One lateral tile: `a` supplies the operands (the launch's argument block, or a
 // register copy of a batched scan's block), `rad` the nx-point radix plan.
 // Thread t owns the column pair b = 2 (t mod TC/2) of rows p0 = t / (TC/2),
@@ -412,7 +543,10 @@ constexpr bool lat_is_mid() {
 // FFT, epilogue on the digit-reversed result.  Mid modes (the measurement side of
 // Phi^H Phi): inverse FFT (dif), the measurement epilogue in place on the
 // digit-reversed tile, forward FFT (dit, digit-reversed in, natural out).
-template <class R, int MODE, bool BLU, class A>
+// FZ: 0 the plain staging, transform and read-out; 1 the fused first and last
+// passes only (the launch checked that the plan's radices allow them); 2 either,
+// chosen per tile (batched launches, whose scans may differ).
+template <class R, int MODE, bool BLU, int FZ, class A>
 __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int nx, int TC, int C, int blk,
                                              const void* twg, const int* perm, double* partial) {
   using V = cplx_t<R>;
@@ -425,7 +559,13 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   // index the tile with it once per row, and a global load there would stall
   // the dependent shared-memory read (first read after the transform's barriers)
   int* sperm = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(tws) + 16 * (rad.tw_lo + rad.tw_hi));
-  for (int i = tid; i < nx; i += blockDim.x) sperm[i] = perm[i];
+  // and its inverse, the natural row of each tile position (the fused last passes)
+  int* siperm = sperm + nx;
+  for (int i = tid; i < nx; i += blockDim.x) {
+    const int pi = perm[i];
+    sperm[i] = pi;
+    siperm[pi] = i;
+  }
   const int half = TC >> 1, hs = __ffs(half) - 1;
   const int b = 2 * (tid & (half - 1));
   const int p0 = tid >> hs, pstep = (int)blockDim.x >> hs;
@@ -433,44 +573,97 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   const bool ok0 = c < C, ok1 = c + 1 < C;
   const bool v2 = ok1 && (C & 1) == 0 && lat_pairs_aligned<R, MODE>(a);
   constexpr int U = kLatUnroll;
-  const V zero = cmk<V>(R(0), R(0));
+  constexpr bool kMid = lat_is_mid<MODE>();
+  constexpr bool INV = !(MODE == LAT_C2C_FWD || MODE == LAT_R2C_MASK || MODE == LAT_POWER_FWD);
+  // FP32 mixed-radix tiles whose first radix is 2, 4 or 8 run the transform's
+  // pass 0 on the way in (and the middle passes' last dit pass on the way out)
+  static_assert(FZ == 0 || (sizeof(R) == 4 && !BLU), "fused passes: FP32 mixed-radix tiles only");
+  int r0 = 0;
+  if constexpr (FZ == 1) {
+    r0 = rad.r[0];
+  } else if constexpr (FZ == 2) {
+    const int rl = rad.r[rad.npass - 1];
+    if (rad.npass >= 2 && (rad.r[0] == 8 || rad.r[0] == 4 || rad.r[0] == 2) && (rl == 8 || rl == 4 || rl == 2))
+      r0 = rad.r[0];
+  }
   pdl_wait_release();
   R fscale = R(1);
   if constexpr (MODE == LAT_POWER_FWD) fscale = R(a.scal[1]);
-  for (int p = p0; p < nx; p += U * pstep) {
-    V va[U], vb[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      va[u] = vb[u] = zero;
-      const int pp = p + u * pstep;
-      if (pp < nx) lat_load2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, va[u], vb[u]);
+  if constexpr (FZ != 0) {
+    if (r0) {
+      float4* s4 = reinterpret_cast<float4*>(s);
+      constexpr bool INV0 = kMid ? false : INV;
+      if (r0 == 8) lat_first_pass_p<8, INV0, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, fscale, tw.twp);
+      else if (r0 == 4) lat_first_pass_p<4, INV0, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, fscale, tw.twp);
+      else lat_first_pass_p<2, INV0, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, fscale, tw.twp);
     }
+  }
+  if (FZ != 1 && !r0) {
+    const V zero = cmk<V>(R(0), R(0));
+    for (int p = p0; p < nx; p += U * pstep) {
+      V va[U], vb[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int pp = p + u * pstep;
-      if (pp < nx) {
-        if constexpr (MODE == LAT_POWER_FWD) {
-          va[u] = cscale(va[u], fscale);
-          vb[u] = cscale(vb[u], fscale);
-          st2(reinterpret_cast<V*>(a.vout), (size_t)pp * C + c, v2, ok0, ok1, va[u], vb[u]);
+      for (int u = 0; u < U; ++u) {
+        va[u] = vb[u] = zero;
+        const int pp = p + u * pstep;
+        if (pp < nx) lat_load2<R, MODE>(a, (size_t)pp * C + c, v2, ok0, ok1, va[u], vb[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int pp = p + u * pstep;
+        if (pp < nx) {
+          if constexpr (MODE == LAT_POWER_FWD) {
+            va[u] = cscale(va[u], fscale);
+            vb[u] = cscale(vb[u], fscale);
+            st2(reinterpret_cast<V*>(a.vout), (size_t)pp * C + c, v2, ok0, ok1, va[u], vb[u]);
+          }
+          if constexpr (kMid) {
+            // inverse transform as conj(FFT(conj S)); the epilogue reads only its real part
+            va[u].y = -va[u].y;
+            vb[u].y = -vb[u].y;
+          }
+          sts2(s, pp * TC + b, va[u], vb[u]);
         }
-        if constexpr (lat_is_mid<MODE>()) {
-          // inverse transform as conj(FFT(conj S)); the epilogue reads only its real part
-          va[u].y = -va[u].y;
-          vb[u].y = -vb[u].y;
-        }
-        sts2(s, pp * TC + b, va[u], vb[u]);
       }
     }
   }
   __syncthreads();
-  constexpr bool kMid = lat_is_mid<MODE>();
-  constexpr bool INV = !(MODE == LAT_C2C_FWD || MODE == LAT_R2C_MASK || MODE == LAT_POWER_FWD);
+
   // per-thread partial sums in the working precision (a thread adds a few dozen
   // terms; FP64 arithmetic is a small fraction of FP32 throughput on this GPU),
   // the block and grid reductions in FP64
   R part = R(0), part2 = R(0);
-  if constexpr (kMid) {
+  bool fused = false;
+  if constexpr (FZ != 0) {
+    if (r0) {
+      // pass 0 ran on the way in; the last pass runs on the way out (and, in the
+      // middle passes, together with the epilogue and the forward transform's first)
+      float4* s4 = reinterpret_cast<float4*>(s);
+      const int rl = rad.r[rad.npass - 1];
+      if constexpr (kMid) {
+        fft_p_dif<false>(s4, half, rad, tw.twp, 1, rad.npass - 1);
+        if (rl == 8) lat_mid_center_p<8, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, siperm, tw.twp, part);
+        else if (rl == 4) lat_mid_center_p<4, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, siperm, tw.twp, part);
+        else lat_mid_center_p<2, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, siperm, tw.twp, part);
+        fft_p_dit<false>(s4, half, rad, tw.twp, 1, rad.npass - 2);
+        if (r0 == 8) lat_last_pass_store_p<8>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, tw.twp);
+        else if (r0 == 4) lat_last_pass_store_p<4>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, tw.twp);
+        else lat_last_pass_store_p<2>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, tw.twp);
+      } else {
+        fft_p_dif<INV>(s4, half, rad, tw.twp, 1, rad.npass - 1);
+        if (rl == 8)
+          lat_last_pass_epi_p<8, INV, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, siperm, tw.twp, part, part2);
+        else if (rl == 4)
+          lat_last_pass_epi_p<4, INV, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, siperm, tw.twp, part, part2);
+        else
+          lat_last_pass_epi_p<2, INV, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, siperm, tw.twp, part, part2);
+      }
+      fused = true;
+    }
+  }
+  if (FZ == 1 || fused) {
+    // done
+  } else if constexpr (kMid) {
     // inverse as a forward dif of conj S, the epilogue in place on the
     // digit-reversed tile, then the forward dit
     lat_xform<R, false, false, BLU>(s, TC, nx, rad, tw, a.chirp, a.bhat);
@@ -547,11 +740,11 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   }
 }
 
-template <class R, int MODE, bool BAT, bool BLU>
+template <class R, int MODE, bool BAT, bool BLU, int FZ = 0>
 __global__ void __launch_bounds__(BAT ? kLatThreadsBatch : kLatThreads, sizeof(R) == 4 ? kLatMinBlocks : 1)
 lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>> B) {
   if constexpr (!BAT) {
-    lateral_body<R, MODE, BLU>(a0, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, a0.partial);
+    lateral_body<R, MODE, BLU, FZ>(a0, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, a0.partial);
   } else {
     int blk;
     const LatArgs<R>& A = *resolve_args(&a0, B, blk);
@@ -579,7 +772,7 @@ lateral_kernel(const __grid_constant__ LatArgs<R> a0, const BatchRef<LatArgs<R>>
       e.tau = A.tau;
     }
     __syncthreads();
-    lateral_body<R, MODE, BLU>(e, rad, A.nx, A.tc, A.cols, blk, A.tw, A.perm, A.partial);
+    lateral_body<R, MODE, BLU, FZ>(e, rad, A.nx, A.tc, A.cols, blk, A.tw, A.perm, A.partial);
   }
 }
 
@@ -607,7 +800,7 @@ lateral_slab_kernel(const __grid_constant__ LatArgs<R> a0, long long slab) {
   e.bhat = a0.bhat;
   e.scale = a0.scale;
   e.mu = e.delta = e.tau = R(0);
-  lateral_body<R, MODE, BLU>(e, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, nullptr);
+  lateral_body<R, MODE, BLU, 0>(e, a0.rad, a0.nx, a0.tc, a0.cols, (int)blockIdx.x, a0.tw, a0.perm, nullptr);
 }
 
 // ------------------------------------------------------------- KB weights
@@ -1422,19 +1615,35 @@ LatArgs<R> lat_args(mbir_plan p, const void* in, void* out, const uint8_t* mask,
 template <class R>
 size_t lat_smem(mbir_plan p) {
   return sizeof(cplx_t<R>) * (size_t)p->nxl * p->tile_c + 16 * (size_t)(p->rad_x.tw_lo + p->rad_x.tw_hi) +
-         sizeof(int) * (size_t)p->nx;
+         2 * sizeof(int) * (size_t)p->nx;
+}
+
+// The fused first and last passes apply to FP32 mixed-radix plans whose first and
+// last radices are 2, 4 or 8 (at least two passes).
+static bool lat_fusable(mbir_plan p) {
+  const Radix& r = p->rad_x;
+  auto ok = [](int x) { return x == 2 || x == 4 || x == 8; };
+  return kLatFuse && p->precision != MBIR_FP64 && !p->chirp && r.npass >= 2 && ok(r.r[0]) && ok(r.r[r.npass - 1]);
 }
 
 template <class R, int MODE>
 int launch_lateral_args(mbir_plan p, const LatArgs<R>& a, int cols, cudaStream_t st) {
   {
     ProfScope ps_(p, lat_class(MODE), st);
-    if (p->chirp)
-      launch(lateral_kernel<R, MODE, false, true>, dim3(lateral_grid(p, cols)), dim3(kLatThreads), lat_smem<R>(p), st,
-             a, no_batch<LatArgs<R>>());
-    else
-      launch(lateral_kernel<R, MODE, false, false>, dim3(lateral_grid(p, cols)), dim3(kLatThreads), lat_smem<R>(p),
-             st, a, no_batch<LatArgs<R>>());
+    const dim3 grid(lateral_grid(p, cols)), block(kLatThreads);
+    if (p->chirp) {
+      launch(lateral_kernel<R, MODE, false, true>, grid, block, lat_smem<R>(p), st, a, no_batch<LatArgs<R>>());
+    } else {
+      bool fused = false;
+      if constexpr (sizeof(R) == 4) {
+        if (lat_fusable(p)) {
+          launch(lateral_kernel<R, MODE, false, false, 1>, grid, block, lat_smem<R>(p), st, a, no_batch<LatArgs<R>>());
+          fused = true;
+        }
+      }
+      if (!fused)
+        launch(lateral_kernel<R, MODE, false, false>, grid, block, lat_smem<R>(p), st, a, no_batch<LatArgs<R>>());
+    }
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -1794,7 +2003,7 @@ LatArgs<R> lat_args_y(mbir_plan p, const void* in, void* out, int cols) {
 template <class R>
 size_t lat_smem_y(mbir_plan p) {
   return sizeof(cplx_t<R>) * (size_t)p->nyl * p->tile_y + 16 * (size_t)(p->rad_y.tw_lo + p->rad_y.tw_hi) +
-         sizeof(int) * (size_t)p->ny;
+         2 * sizeof(int) * (size_t)p->ny;
 }
 
 // in-place y pass of an [nx][ny][cols] complex array
@@ -1873,17 +2082,21 @@ int power_step_impl(mbir_plan p, const uint8_t* mask, void* w, void* v, const do
 
 template <class R>
 static int configure_t() {
-  const int lat = (int)(sizeof(cplx_t<R>) * kLatElems + 16 * 512 + sizeof(int) * 4096);
+  const int lat = (int)(sizeof(cplx_t<R>) * kLatElems + 16 * 512 + 2 * sizeof(int) * 4096);
   const int row = (int)(sizeof(cplx_t<R>) * (kMaxFFT + 512));
   const int gat = kMaxDynSmem;
 #define MBIR_SMEM_ATTR(fn, bytes)                                                                  \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));    \
   MBIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
-#define MBIR_LAT_ATTRS(M)                                       \
-  MBIR_SMEM_ATTR((lateral_kernel<R, M, false, false>), lat);    \
-  MBIR_SMEM_ATTR((lateral_kernel<R, M, true, false>), lat);     \
-  MBIR_SMEM_ATTR((lateral_kernel<R, M, false, true>), lat);     \
-  MBIR_SMEM_ATTR((lateral_kernel<R, M, true, true>), lat)
+#define MBIR_LAT_ATTRS(M)                                                                   \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, false, false>), lat);                                \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, true, false>), lat);                                 \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, false, true>), lat);                                 \
+  MBIR_SMEM_ATTR((lateral_kernel<R, M, true, true>), lat);                                  \
+  if constexpr (sizeof(R) == 4 && kLatFuse) {                                               \
+    MBIR_SMEM_ATTR((lateral_kernel<R, M, false, false, sizeof(R) == 4 ? 1 : 0>), lat);     \
+    MBIR_SMEM_ATTR((lateral_kernel<R, M, true, false, sizeof(R) == 4 ? 2 : 0>), lat);      \
+  }
   MBIR_LAT_ATTRS(LAT_C2C_FWD);
   MBIR_LAT_ATTRS(LAT_C2C_INV);
   MBIR_LAT_ATTRS(LAT_R2C_MASK);
@@ -2080,6 +2293,9 @@ static void lat_batch_t(const BatchLaunch& L, cudaStream_t st) {
   memcpy(&a0, L.host0, sizeof(a0));
   if (L.blu)
     launch(lateral_kernel<R, MODE, true, true>, dim3(L.total), dim3(kLatThreadsBatch), L.smem, st, a0, B);
+  else if (sizeof(R) == 4 && kLatFuse)
+    launch(lateral_kernel<R, MODE, true, false, sizeof(R) == 4 ? 2 : 0>, dim3(L.total), dim3(kLatThreadsBatch), L.smem,
+           st, a0, B);
   else
     launch(lateral_kernel<R, MODE, true, false>, dim3(L.total), dim3(kLatThreadsBatch), L.smem, st, a0, B);
 }

@@ -94,6 +94,12 @@ constexpr int kGatherLeanThreads = MBIR_GATHERLEAN_THREADS;
 constexpr int kGatherLeanMinBlocks = MBIR_GATHERLEAN_MINB;
 constexpr bool kGatherLeanDefault = MBIR_GATHERLEAN_DEFAULT != 0;
 constexpr int kLatUnroll = MBIR_LAT_UNROLL;   // rows of loads in flight per thread when staging a lateral tile
+// FP32 lateral tiles run the transform's first pass on the way in from global
+// memory and the middle passes' last pass on the way out
+#ifndef MBIR_LAT_FUSE
+#define MBIR_LAT_FUSE 1
+#endif
+constexpr bool kLatFuse = MBIR_LAT_FUSE != 0;
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
 constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics

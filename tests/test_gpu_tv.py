@@ -40,7 +40,8 @@ def _img(shape, seed):
                                              (2, 40, 0.5, 20), (48, 64, 2.0, 50), (35, 50, 0.8, 21),
                                              (20, 70, 0.4, 3), (9, 35, 0.4, 1), (18, 126, 0.6, 2)])
 def test_prox_tv_matches_oracle(mbir, nx, nz, tau, iters):
-    """Tiles of 16 x 64 with ragged edges in both directions, a two-row image, a
+    """Tiles of 8 x 64 (two-step passes) and 16 x 64 (one-step passes) with ragged
+    edges in both directions, a two-row image, a
     strong and a weak tau; odd step counts (two-step passes, then one one-step
     pass), a single step, a single two-step pass."""
     plan = mbir.Plan(W.geometry(nx, nz, 16))
