@@ -60,6 +60,9 @@ def parse():
                     help="skip the evaluation loop (interpolated ISAM, NCC, lambda search)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch choices (no mbir_plan_autotune before timing)")
+    ap.add_argument("--tuning", default=None, metavar="TILE,ORDER,KIND",
+                    help="fix the full-size plan's launch choices (lateral tile, radix order, adjoint "
+                         "kernel) instead of tuning them, e.g. to reproduce a tuned run under a profiler")
     return ap.parse_args()
 
 
@@ -604,7 +607,12 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
     nx, nz, m = d["nx"], d["nz"], d["m"]
     plan = mbir.Plan(d)
     # launch choices for this shape class, timed before anything else (not in the timed region)
-    tuning = None if args.no_autotune else plan.autotune(reps=5)
+    if args.tuning:
+        t, o, k = (int(v) for v in args.tuning.split(","))
+        plan.set_tuning(t, o, k)
+        tuning = {"tile_c": t, "lateral_order": o, "adjoint_kernel": k}
+    else:
+        tuning = None if args.no_autotune else plan.autotune(reps=5)
     stream = torch.cuda.current_stream()
     x_true = torch.from_numpy(wl["x_true"].astype(np.complex64)).to(dev)
     mask = torch.from_numpy(wl["mask"]).to(dev)

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <tuple>
 #include <vector>
 
 #include "batch.cuh"
@@ -411,16 +412,17 @@ int Engine::add_lateral(std::vector<Stage>& out, int mode, const std::vector<BSc
   return grow_failed_ ? MBIR_ERR_OOM : MBIR_OK;
 }
 
-// One launch per (row kernel, shared-memory size) among the scans: each scan runs
-// the kernel its own plan chooses (tuned or automatic), and scans with shorter
-// rows keep the occupancy of their own footprint.
+// One launch per (row kernel, shared-memory size, fused passes or not) among the
+// scans: each scan runs the kernel its own plan chooses (tuned or automatic), and
+// scans with shorter rows keep the occupancy of their own footprint.
 int Engine::add_row(std::vector<Stage>& out, bool adjoint, const std::vector<BScan*>& idx) {
   if (idx.empty()) return MBIR_OK;
   const size_t ab = row_args_bytes(prec_);
-  using Key = std::pair<int, size_t>;
+  using Key = std::tuple<int, size_t, bool>;
   auto key_of = [&](BScan* s) {
     const int k = row_kind(s->p, adjoint);
-    return Key(k, row_kind_smem(s->p, k));
+    // batched lean gathers keep the plain passes (their fused form spills)
+    return Key(k, row_kind_smem(s->p, k), row_fusable(s->p) && k != ROW_GATHER_PAIR_LEAN);
   };
   std::vector<Key> keys;
   for (BScan* s : idx) {
@@ -428,7 +430,7 @@ int Engine::add_row(std::vector<Stage>& out, bool adjoint, const std::vector<BSc
     if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
   }
   for (const Key& key : keys) {
-    const int kind = key.first;
+    const int kind = std::get<0>(key);
     std::vector<BScan*> grp;
     for (BScan* s : idx)
       if (key_of(s) == key) grp.push_back(s);
@@ -441,7 +443,7 @@ int Engine::add_row(std::vector<Stage>& out, bool adjoint, const std::vector<BSc
       off[i + 1] = off[i] + row_ctas(s.p, kind);
       smem = std::max(smem, row_kind_smem(s.p, kind));
     }
-    Stage g{1, kind, 0, 0, (int)grp.size(), off.back(), smem, 0};
+    Stage g{1, kind, 0, 0, (int)grp.size(), off.back(), smem, 0, 0, std::get<2>(key) ? 1 : 0};
     g.arg_off = push(blocks.data(), blocks.size());
     g.off_off = push(off.data(), off.size() * sizeof(int));
     out.push_back(g);
@@ -488,6 +490,7 @@ int Engine::run(const Stage& g, double mu) {
   L.set_mu = g.uses_mu;
   L.mu = mu;
   L.blu = g.blu;
+  L.fz = g.fz;
   switch (g.kind) {
     case 0: return batch_lateral(g.mode, prec_, L, st_);
     case 1: return batch_row(g.mode, prec_, J_, L, st_);

@@ -82,6 +82,7 @@ class Engine {
     size_t smem;
     int uses_mu;
     int blu;    // lateral stages: some scan's plan uses the Bluestein form
+    int fz;     // row stages: every scan's row transform takes the fused passes
   };
   size_t push(const void* data, size_t bytes);
   void grow(size_t need);

@@ -293,6 +293,7 @@ struct BatchLaunch {
   int set_mu;
   double mu;
   int blu;   // a scan of the launch runs its lateral transform in the Bluestein form
+  int fz;    // row launches: every scan's K-point transform takes the fused first and last passes
 };
 
 // Operands of one lateral stage for one scan (batch.cu fills these).
@@ -329,6 +330,8 @@ void fill_lat_args(mbir_plan p, const LatFill& f, void* dst);
 void fill_row_args(mbir_plan p, const void* in, void* out, void* dst);
 int batch_lateral(int mode, int precision, const BatchLaunch& L, cudaStream_t st);
 int batch_row(int kind, int precision, int J, const BatchLaunch& L, cudaStream_t st);
+// FP32 plan whose paired row kernels run the fused first and last transform passes
+bool row_fusable(mbir_plan p);
 
 // wavelet.cu (batch helpers)
 size_t dwt_args_bytes(int precision);

@@ -591,6 +591,8 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
   if constexpr (MODE == LAT_POWER_FWD) fscale = R(a.scal[1]);
   if constexpr (FZ != 0) {
     if (r0) {
+      // the pass's twiddles come from the table the CTA's threads just staged
+      __syncthreads();
       float4* s4 = reinterpret_cast<float4*>(s);
       constexpr bool INV0 = kMid ? false : INV;
       if (r0 == 8) lat_first_pass_p<8, INV0, MODE>(a, s4, nx, half, hs, C, c, v2, ok0, ok1, fscale, tw.twp);
@@ -1214,7 +1216,73 @@ __device__ __forceinline__ int pair_row_b(int lp, int nx) {
   return (lp == 0 || lb == lp) ? -1 : lb;
 }
 
-template <int J, bool OTF>
+// Fused first and last passes of the K-point row transforms (the pair kernels'
+// FZ = 1; the host launches them for plans whose transform starts and ends with a
+// radix 2, 4 or 8, and batches only when every scan of the launch qualifies).  With R the radix of
+// the last dif pass (the first dit pass), the positions b' R + r of a
+// digit-reversed row hold the natural elements b + r K/R, where perm[b] = b' R
+// (b < K/R: the last digit of k is its most significant one).  So a butterfly of
+// that pass is addressed from its natural base b with one table read.
+
+// The first dit pass (span 1, no twiddles) run on the way in: load(i) gives the
+// natural element i of the row.
+template <int R, class F>
+__device__ __forceinline__ void row_first_pass_dit(float4* buf, int K, const int* perm, const TwP& tw, F&& load) {
+  const int B = K / R;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int p0 = perm[b];
+    PC v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = load(b + r * B);
+    dft_small_p<R, false>(v, tw, K);
+#pragma unroll
+    for (int r = 0; r < R; ++r) st_pc(buf, swz8(p0 + r), v[r]);
+  }
+}
+
+// The first dif pass (span K/R, twiddles after the butterfly) with its inputs,
+// the natural cells j + r K/R, computed in registers by cell(i).
+template <int R, class F>
+__device__ __forceinline__ void row_first_pass_dif(float4* buf, int K, const TwP& tw, F&& cell) {
+  const int B = K / R;
+  for (int j = threadIdx.x; j < B; j += blockDim.x) {
+    PC v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = cell(j + r * B);
+    dft_small_p<R, true>(v, tw, K);
+    if (j != 0) apply_twiddles_p<R, true>(v, tw, j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) st_pc(buf, swz8(j + r * B), v[r]);
+  }
+}
+
+// The last dif pass (span 1, no twiddles) run on the way out: out(i, v) takes the
+// natural output i.
+template <int R, class F>
+__device__ __forceinline__ void row_last_pass_dif(const float4* buf, int K, const int* perm, const TwP& tw,
+                                                  F&& out) {
+  const int B = K / R;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int p0 = perm[b];
+    PC v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = ld_pc(buf, swz8(p0 + r));
+    dft_small_p<R, true>(v, tw, K);
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(b + r * B, v[r]);
+  }
+}
+
+// f(RadixC<r>()) for a radix r in {2, 4, 8}
+template <int N> struct RadixC { static constexpr int value = N; };
+template <class F>
+__device__ __forceinline__ void with_radix248(int r, F&& f) {
+  if (r == 8) f(RadixC<8>());
+  else if (r == 4) f(RadixC<4>());
+  else f(RadixC<2>());
+}
+
+template <int J, bool OTF, int FZ>
 __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, const Radix& rad, int lp,
                                                       const RowArgs<float>& a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1238,29 +1306,48 @@ __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, c
   pdl_wait_release();
   // centred zero-padded rows, element i = (n - n0) mod K holding c_n X[l][n],
   // placed digit-reversed for the decimation-in-time transform
-  constexpr int U = 4;
-  for (int i0 = tid; i0 < K; i0 += U * nthr) {
-    float4 v[U];
+  if constexpr (FZ != 0) {
+    // the first dit pass on the way in (its butterflies read no twiddles)
+    with_radix248(rad.r[rad.npass - 1], [&](auto rc) {
+      row_first_pass_dit<decltype(rc)::value>(buf, K, perm, tw, [&](int i) {
+        int n = i + n0;
+        if (n >= K) n -= K;
+        PC v{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (n < nz) {
+          const float c = cdep[n];
+          const float2 xa = Xa[n], xb = Xb[n];
+          v = PC{make_float2(xa.x * c, xb.x * c), make_float2(xa.y * c, xb.y * c)};
+        }
+        return v;
+      });
+    });
+    __syncthreads();
+    fft_p_dit<false, true>(buf, 1, rad, tw, 0, rad.npass - 2);
+  } else {
+    constexpr int U = 4;
+    for (int i0 = tid; i0 < K; i0 += U * nthr) {
+      float4 v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * nthr;
-      int n = i + n0;
-      if (n >= K) n -= K;
-      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < K && n < nz) {
-        const float c = cdep[n];
-        const float2 xa = Xa[n], xb = Xb[n];
-        v[u] = make_float4(xa.x * c, xb.x * c, xa.y * c, xb.y * c);
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * nthr;
+        int n = i + n0;
+        if (n >= K) n -= K;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < K && n < nz) {
+          const float c = cdep[n];
+          const float2 xa = Xa[n], xb = Xb[n];
+          v[u] = make_float4(xa.x * c, xb.x * c, xa.y * c, xb.y * c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * nthr;
+        if (i < K) buf[swz8(perm[i])] = v[u];
       }
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * nthr;
-      if (i < K) buf[swz8(perm[i])] = v[u];
-    }
+    __syncthreads();
+    fft_p_dit<false, true>(buf, 1, rad, tw);
   }
-  __syncthreads();
-  fft_p_dit<false, true>(buf, 1, rad, tw);
   float2* Sa = reinterpret_cast<float2*>(a.out) + (size_t)la * M;
   float2* Sb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * M;
   const float q2 = OTF ? a.q2row[lp] : 0.f;
@@ -1297,29 +1384,75 @@ __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, c
   }
 }
 
-template <int J, bool BAT, bool OTF>
+template <int J, bool BAT, bool OTF, int FZ = 0>
 __global__ void __launch_bounds__(kRowPairThreads, kRowPairMinBlocks)
 row_forward_pair_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
   if constexpr (!BAT) {
-    row_forward_pair_body<J, OTF>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_forward_pair_body<J, OTF, FZ>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<float>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_forward_pair_body<J, OTF>(A, rad, blk, a0);
+    row_forward_pair_body<J, OTF, FZ>(A, rad, blk, a0);
   }
 }
 
 // The adjoint gather of row_adjoint_gather_body for a row pair: the pixels' KB
 // weights, unwrapped cells and run boundaries are built once, each cell sums its
 // run for both rows in the two lanes of split pairs.
-template <int J, bool OTF>
+// The end of a paired gather once its pixels are staged: the K grid cells of both
+// rows (cell(i), after a barrier), the inverse K-point dif transform and the
+// read-out of the nz depth samples n (natural output (n - n0) mod K, times c_n).
+// FZ: the cells feed the first pass's butterflies in registers and the last pass
+// writes the read-out, so the row crosses shared memory two times fewer.
+template <int FZ, class F>
+__device__ __forceinline__ void row_gather_pair_finish(const RowArgs<float>& a, const Radix& rad, const TwP& tw,
+                                                       float4* buf, int la, int lb, int lbr, F&& cell) {
+  const int K = a.K, nz = a.nz, n0 = a.n0;
+  const float* cdep = reinterpret_cast<const float*>(a.cdep);
+  const int* perm = a.perm;
+  float2* Wa = reinterpret_cast<float2*>(a.out) + (size_t)la * nz;
+  float2* Wb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * nz;
+  if constexpr (FZ != 0) {
+    with_radix248(rad.r[0], [&](auto rc) { row_first_pass_dif<decltype(rc)::value>(buf, K, tw, cell); });
+    __syncthreads();
+    fft_p_dif<true, true>(buf, 1, rad, tw, 1, rad.npass - 1);
+    with_radix248(rad.r[rad.npass - 1], [&](auto rc) {
+      row_last_pass_dif<decltype(rc)::value>(buf, K, perm, tw, [&](int i, const PC& v) {
+        int n = i + n0;
+        if (n >= K) n -= K;
+        if (n < nz) {
+          const float cn = cdep[n];
+          Wa[n] = make_float2(v.re.x * cn, v.im.x * cn);
+          if (lb >= 0) Wb[n] = make_float2(v.re.y * cn, v.im.y * cn);
+        }
+      });
+    });
+  } else {
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      const PC v = cell(i);
+      buf[swz8(i)] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y);
+    }
+    __syncthreads();
+    fft_p_dif<true, true>(buf, 1, rad, tw);
+    for (int n = threadIdx.x; n < nz; n += blockDim.x) {
+      int i = n - n0;
+      if (i < 0) i += K;
+      const float4 t = buf[swz8(perm[i])];
+      const float cn = cdep[n];
+      Wa[n] = make_float2(t.x * cn, t.z * cn);
+      if (lb >= 0) Wb[n] = make_float2(t.y * cn, t.w * cn);
+    }
+  }
+}
+
+template <int J, bool OTF, int FZ>
 __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, const Radix& rad, int lp,
                                                      const RowArgs<float>& a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  const int K = a.K, M = a.m;
   const int K8 = (K + 7) & ~7;
   float4* buf = reinterpret_cast<float4*>(smem_raw);         // [K8], swizzled
   float4* tws = buf + K8;
@@ -1383,7 +1516,7 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
       for (int c = hi + 1; c <= span; ++c) sfirst[c] = (uint16_t)M;
   }
   __syncthreads();
-  for (int i = tid; i < K; i += nthr) {
+  auto cell = [&](int i) {
     int c = i - base;
     if (c < 0) c += K;
     float2 ar = make_float2(0.f, 0.f), ai = ar;
@@ -1399,36 +1532,23 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
         ai = fma2(make_float2(t.z, t.w), ww, ai);
       }
     }
-    buf[swz8(i)] = make_float4(ar.x, ar.y, ai.x, ai.y);
-  }
-  __syncthreads();
-  fft_p_dif<true, true>(buf, 1, rad, tw);
-  const float* cdep = reinterpret_cast<const float*>(a.cdep);
-  const int* perm = a.perm;
-  float2* Wa = reinterpret_cast<float2*>(a.out) + (size_t)la * nz;
-  float2* Wb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * nz;
-  for (int n = tid; n < nz; n += nthr) {
-    int i = n - n0;
-    if (i < 0) i += K;
-    const float4 t = buf[swz8(perm[i])];
-    const float cn = cdep[n];
-    Wa[n] = make_float2(t.x * cn, t.z * cn);
-    if (lb >= 0) Wb[n] = make_float2(t.y * cn, t.w * cn);
-  }
+    return PC{ar, ai};
+  };
+  row_gather_pair_finish<FZ>(a, rad, tw, buf, la, lb, lbr, cell);
 }
 
-template <int J, bool BAT, bool OTF>
+template <int J, bool BAT, bool OTF, int FZ = 0>
 __global__ void __launch_bounds__(kGatherPairThreads, 1)
 row_gather_pair_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
   if constexpr (!BAT) {
-    row_gather_pair_body<J, OTF>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_gather_pair_body<J, OTF, FZ>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<float>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_gather_pair_body<J, OTF>(A, rad, blk, a0);
+    row_gather_pair_body<J, OTF, FZ>(A, rad, blk, a0);
   }
 }
 
@@ -1451,11 +1571,11 @@ __device__ __forceinline__ float kb_tap_weight(float frac, const RowArgs<float>&
   return t;
 }
 
-template <int J, bool OTF>
+template <int J, bool OTF, int FZ>
 __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& a, const Radix& rad, int lp,
                                                           const RowArgs<float>& a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = a.K, nz = a.nz, n0 = a.n0, M = a.m;
+  const int K = a.K, M = a.m;
   const int K8 = (K + 7) & ~7;
   float4* buf = reinterpret_cast<float4*>(smem_raw);         // [K8], swizzled
   float4* tws = buf + K8;
@@ -1518,7 +1638,8 @@ __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& 
     }
   }
   __syncthreads();
-  for (int i = tid; i < K; i += nthr) {
+  // grid cell i of both rows
+  auto cell = [&](int i) {
     int c = i - base;
     if (c < 0) c += K;
     float2 ar = make_float2(0.f, 0.f), ai = ar;
@@ -1537,36 +1658,23 @@ __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& 
         }
       }
     }
-    buf[swz8(i)] = make_float4(ar.x, ar.y, ai.x, ai.y);
-  }
-  __syncthreads();
-  fft_p_dif<true, true>(buf, 1, rad, tw);
-  const float* cdep = reinterpret_cast<const float*>(a.cdep);
-  const int* perm = a.perm;
-  float2* Wa = reinterpret_cast<float2*>(a.out) + (size_t)la * nz;
-  float2* Wb = reinterpret_cast<float2*>(a.out) + (size_t)lbr * nz;
-  for (int n = tid; n < nz; n += nthr) {
-    int i = n - n0;
-    if (i < 0) i += K;
-    const float4 t = buf[swz8(perm[i])];
-    const float cn = cdep[n];
-    Wa[n] = make_float2(t.x * cn, t.z * cn);
-    if (lb >= 0) Wb[n] = make_float2(t.y * cn, t.w * cn);
-  }
+    return PC{ar, ai};
+  };
+  row_gather_pair_finish<FZ>(a, rad, tw, buf, la, lb, lbr, cell);
 }
 
-template <int J, bool BAT, bool OTF>
+template <int J, bool BAT, bool OTF, int FZ = 0>
 __global__ void __launch_bounds__(kGatherLeanThreads, kGatherLeanMinBlocks)
 row_gather_pair_lean_kernel(const __grid_constant__ RowArgs<float> a0, const BatchRef<RowArgs<float>> B) {
   if constexpr (!BAT) {
-    row_gather_pair_lean_body<J, OTF>(a0, a0.rad, (int)blockIdx.x, a0);
+    row_gather_pair_lean_body<J, OTF, FZ>(a0, a0.rad, (int)blockIdx.x, a0);
   } else {
     int blk;
     const RowArgs<float>& A = *resolve_args(&a0, B, blk);
     __shared__ Radix rad;
     copy_radix(&rad, &A.rad);
     __syncthreads();
-    row_gather_pair_lean_body<J, OTF>(A, rad, blk, a0);
+    row_gather_pair_lean_body<J, OTF, FZ>(A, rad, blk, a0);
   }
 }
 
@@ -1624,6 +1732,14 @@ static bool lat_fusable(mbir_plan p) {
   const Radix& r = p->rad_x;
   auto ok = [](int x) { return x == 2 || x == 4 || x == 8; };
   return kLatFuse && p->precision != MBIR_FP64 && !p->chirp && r.npass >= 2 && ok(r.r[0]) && ok(r.r[r.npass - 1]);
+}
+
+// The fused row passes apply to FP32 plans whose K-point transform starts and
+// ends with a radix 2, 4 or 8 (at least two passes).
+bool row_fusable(mbir_plan p) {
+  const Radix& r = p->rad_k;
+  auto ok = [](int x) { return x == 2 || x == 4 || x == 8; };
+  return kRowFuse && p->precision == MBIR_FP32 && !p->otf && r.npass >= 2 && ok(r.r[0]) && ok(r.r[r.npass - 1]);
 }
 
 template <class R, int MODE>
@@ -1752,7 +1868,27 @@ size_t row_kind_smem(mbir_plan p, int kind) {
 
 template <class R, int J, bool BAT, bool COMP>
 static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid, size_t smem,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool fz) {
+  if constexpr (sizeof(R) == 4 && !COMP) {
+    // FP32 pair kernels with the fused first and last transform passes
+    if (fz && a.otf == 0) {
+      if (kind == ROW_FWD_PAIR) {
+        launch(row_forward_pair_kernel<J, BAT, false, 1>, dim3(grid), dim3(kRowPairThreads), smem, st, a, B);
+        return;
+      }
+      if (kind == ROW_GATHER_PAIR) {
+        launch(row_gather_pair_kernel<J, BAT, false, 1>, dim3(grid), dim3(kGatherPairThreads), smem, st, a, B);
+        return;
+      }
+      if constexpr (!BAT) {   // batched: the lean gather keeps its plain passes (it would spill)
+        if (kind == ROW_GATHER_PAIR_LEAN) {
+          launch(row_gather_pair_lean_kernel<J, false, false, 1>, dim3(grid), dim3(kGatherLeanThreads), smem, st, a,
+                 B);
+          return;
+        }
+      }
+    }
+  }
   if constexpr (sizeof(R) == 4 && !COMP) {
     const bool otf = a.otf != 0;
     if (kind == ROW_FWD_PAIR) {
@@ -1794,18 +1930,18 @@ static void row_launch_j(int kind, const RowArgs<R>& a, const BatchRef<RowArgs<R
 
 template <class R, bool BAT>
 static void row_launch(int kind, int J, bool comp, const RowArgs<R>& a, const BatchRef<RowArgs<R>>& B, int grid,
-                       size_t smem, cudaStream_t st) {
+                       size_t smem, cudaStream_t st, bool fz = false) {
   if (comp && sizeof(R) == 4) {
     switch (J) {
-      case 4: row_launch_j<R, 4, BAT, true>(kind, a, B, grid, smem, st); break;
-      case 6: row_launch_j<R, 6, BAT, true>(kind, a, B, grid, smem, st); break;
-      default: row_launch_j<R, 8, BAT, true>(kind, a, B, grid, smem, st); break;
+      case 4: row_launch_j<R, 4, BAT, true>(kind, a, B, grid, smem, st, fz); break;
+      case 6: row_launch_j<R, 6, BAT, true>(kind, a, B, grid, smem, st, fz); break;
+      default: row_launch_j<R, 8, BAT, true>(kind, a, B, grid, smem, st, fz); break;
     }
   } else {
     switch (J) {
-      case 4: row_launch_j<R, 4, BAT, false>(kind, a, B, grid, smem, st); break;
-      case 6: row_launch_j<R, 6, BAT, false>(kind, a, B, grid, smem, st); break;
-      default: row_launch_j<R, 8, BAT, false>(kind, a, B, grid, smem, st); break;
+      case 4: row_launch_j<R, 4, BAT, false>(kind, a, B, grid, smem, st, fz); break;
+      case 6: row_launch_j<R, 6, BAT, false>(kind, a, B, grid, smem, st, fz); break;
+      default: row_launch_j<R, 8, BAT, false>(kind, a, B, grid, smem, st, fz); break;
     }
   }
 }
@@ -1817,7 +1953,7 @@ int launch_row(mbir_plan p, bool adjoint, const void* in, void* out, cudaStream_
   {
     ProfScope ps_(p, adjoint ? PC_ROW_ADJ : PC_ROW_FWD, st);
     row_launch<R, false>(kind, p->J, p->precision == MBIR_FP32_COMPENSATED, a, no_batch<RowArgs<R>>(),
-                         row_ctas(p, kind), row_kind_smem(p, kind), st);
+                         row_ctas(p, kind), row_kind_smem(p, kind), st, row_fusable(p));
   }
   MBIR_LAUNCH_CHECK();
   return MBIR_OK;
@@ -2144,38 +2280,53 @@ static int configure_t() {
   MBIR_SMEM_ATTR((row_adjoint_gather_kernel<R, 8, true, true>), gat);
   if constexpr (sizeof(R) == 4) {
     MBIR_SMEM_ATTR((row_forward_pair_kernel<4, false, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<4, false, true>), gat); }
     MBIR_SMEM_ATTR((row_forward_pair_kernel<4, true, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<4, true, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<4, true, true>), gat); }
     MBIR_SMEM_ATTR((row_forward_pair_kernel<6, false, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<6, false, true>), gat); }
     MBIR_SMEM_ATTR((row_forward_pair_kernel<6, true, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<6, true, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<6, true, true>), gat); }
     MBIR_SMEM_ATTR((row_forward_pair_kernel<8, false, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<8, false, true>), gat); }
     MBIR_SMEM_ATTR((row_forward_pair_kernel<8, true, false>), gat);
+    MBIR_SMEM_ATTR((row_forward_pair_kernel<8, true, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_forward_pair_kernel<8, true, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_kernel<4, false, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<4, false, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<4, true, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_kernel<6, false, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<6, false, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<6, true, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_kernel<8, false, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<8, false, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_kernel<8, true, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, false, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, false, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, true, false>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<4, true, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, false, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, false, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, true, false>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<6, true, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, false, false>), gat);
+    MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, false, false, 1>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, false, true>), gat); }
     MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, true, false>), gat);
     if constexpr (kFilterOtf) { MBIR_SMEM_ATTR((row_gather_pair_lean_kernel<8, true, true>), gat); }
@@ -2336,7 +2487,7 @@ static void row_batch_t(int kind, int J, bool comp, const BatchLaunch& L, cudaSt
   B.mu = 0.0;
   RowArgs<R> a0;
   memcpy(&a0, L.host0, sizeof(a0));
-  row_launch<R, true>(kind, J, comp, a0, B, L.total, L.smem, st);
+  row_launch<R, true>(kind, J, comp, a0, B, L.total, L.smem, st, L.fz != 0);
 }
 
 int batch_row(int kind, int precision, int J, const BatchLaunch& L, cudaStream_t st) {

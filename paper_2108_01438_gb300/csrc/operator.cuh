@@ -100,6 +100,13 @@ constexpr int kLatUnroll = MBIR_LAT_UNROLL;   // rows of loads in flight per thr
 #define MBIR_LAT_FUSE 1
 #endif
 constexpr bool kLatFuse = MBIR_LAT_FUSE != 0;
+// FP32 paired row kernels: the forward runs its first transform pass on the way in
+// from global memory; the gathers sum the cells of the first pass's butterflies in
+// registers and run the last pass on the way out
+#ifndef MBIR_ROW_FUSE
+#define MBIR_ROW_FUSE 1
+#endif
+constexpr bool kRowFuse = MBIR_ROW_FUSE != 0;
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
 constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics
