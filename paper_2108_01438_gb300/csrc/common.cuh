@@ -233,6 +233,38 @@ __device__ __forceinline__ void pdl_wait_release() {
   asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Before its dependency wait a kernel may pull into L2 the operands that no
+// kernel still in flight writes (measurements, masks, tables, iterates of earlier
+// iterations): its CTAs that start while the previous grid drains then find them
+// there.  A prefetch is a hint: it returns no data, leaves L1 alone and cannot
+// expose a stale value, since L2 is the point of coherence.
+#ifndef MBIR_L2_PREFETCH
+#define MBIR_L2_PREFETCH 1
+#endif
+constexpr bool kL2Prefetch = MBIR_L2_PREFETCH != 0;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// The 128-byte lines of bytes [0, len) from base, spread over the CTA's threads.
+__device__ __forceinline__ void prefetch_l2_range(const void* base, size_t len) {
+  if (!kL2Prefetch || base == nullptr) return;
+  const uintptr_t s = reinterpret_cast<uintptr_t>(base) & ~uintptr_t(127);
+  const uintptr_t e = reinterpret_cast<uintptr_t>(base) + len;
+  for (uintptr_t l = s + 128 * (uintptr_t)threadIdx.x; l < e; l += 128 * (uintptr_t)blockDim.x)
+    prefetch_l2(reinterpret_cast<const void*>(l));
+}
+
+// The 128-byte lines of rows [0, rows) of a row-major array (row pitch `pitch`
+// bytes), bytes [off, off + len) of each row; the CTA's threads share the rows.
+__device__ __forceinline__ void prefetch_l2_rows(const void* base, int rows, size_t pitch, size_t off, int len) {
+  if (!kL2Prefetch || base == nullptr || len <= 0) return;
+  const char* b = static_cast<const char*>(base) + off;
+  for (int p = threadIdx.x; p < rows; p += blockDim.x) {
+    const uintptr_t s = reinterpret_cast<uintptr_t>(b + (size_t)p * pitch);
+    for (uintptr_t l = s & ~uintptr_t(127); l < s + len; l += 128) prefetch_l2(reinterpret_cast<const void*>(l));
+  }
+}
+
 template <class... KArgs, class... Args>
 inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                    const Args&... args) {

@@ -328,6 +328,27 @@ __device__ __forceinline__ void lat_prefetch2(const A& a, size_t off, bool v2, b
   }
 }
 
+// The epilogue operands of the CTA's columns [c0, c0 + TC) that the kernel just
+// before this one does not write -- the measurements, the mask, Phi z^{k-2}, the
+// iterates z^{k-1}, z^{k-2} -- pulled into L2 ahead of the dependency wait.
+template <class R, int MODE, class A>
+__device__ __forceinline__ void lat_prefetch_l2(const A& a, int nx, int C, int c0, int TC) {
+  using V = cplx_t<R>;
+  const int ncol = C - c0 < TC ? C - c0 : TC;
+  if (ncol <= 0) return;
+  if constexpr (MODE == LAT_C2R_INV_MASK || MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_MID ||
+                MODE == LAT_POWER_MID)
+    prefetch_l2_rows(a.mask, nx, (size_t)C, (size_t)c0, ncol);
+  if constexpr (MODE == LAT_SOLVE_FWD || MODE == LAT_SOLVE_MID) {
+    prefetch_l2_rows(a.y, nx, sizeof(R) * C, sizeof(R) * c0, (int)sizeof(R) * ncol);
+    prefetch_l2_rows(a.pz, nx, sizeof(R) * C, sizeof(R) * c0, (int)sizeof(R) * ncol);
+  }
+  if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V || MODE == LAT_POWER_ADJ)
+    prefetch_l2_rows(a.z1, nx, sizeof(V) * C, sizeof(V) * c0, (int)sizeof(V) * ncol);
+  if constexpr (MODE == LAT_SOLVE_ADJ_L1 || MODE == LAT_SOLVE_ADJ_V)
+    prefetch_l2_rows(a.z2, nx, sizeof(V) * C, sizeof(V) * c0, (int)sizeof(V) * ncol);
+}
+
 // Measurement-side FISTA epilogue of one element (Eq. alg): pz = s Re{S}/nx,
 // r = (1 + mu) pz - mu pz_prev - s y; accumulates (pz - s y)^2.
 template <class R, class A>
@@ -586,6 +607,7 @@ __device__ __forceinline__ void lateral_body(const A& a, const Radix& rad, int n
     if (rad.npass >= 2 && (rad.r[0] == 8 || rad.r[0] == 4 || rad.r[0] == 2) && (rl == 8 || rl == 4 || rl == 2))
       r0 = rad.r[0];
   }
+  lat_prefetch_l2<R, MODE>(a, nx, C, blk * TC, TC);
   pdl_wait_release();
   R fscale = R(1);
   if constexpr (MODE == LAT_POWER_FWD) fscale = R(a.scal[1]);
@@ -1303,6 +1325,7 @@ __device__ __forceinline__ void row_forward_pair_body(const RowArgs<float>& a, c
   const float2* Xb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * nz;
   const float* cdep = reinterpret_cast<const float*>(a.cdep);
   const int* perm = a.perm;
+  if (!OTF) prefetch_l2_range(reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M, sizeof(TabF) * M);
   pdl_wait_release();
   // centred zero-padded rows, element i = (n - n0) mod K holding c_n X[l][n],
   // placed digit-reversed for the decimation-in-time transform
@@ -1475,6 +1498,7 @@ __device__ __forceinline__ void row_gather_pair_body(const RowArgs<float>& a, co
   const float q2 = OTF ? a.q2row[lp] : 0.f;
   const float2* Ra = reinterpret_cast<const float2*>(a.in) + (size_t)la * M;
   const float2* Rb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * M;
+  if (!OTF) prefetch_l2_range(reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M, sizeof(TabF) * M);
   pdl_wait_release();
   // stage both rows in increasing-u order
   constexpr int UM = 2;
@@ -1598,6 +1622,7 @@ __device__ __forceinline__ void row_gather_pair_lean_body(const RowArgs<float>& 
   const float q2 = OTF ? a.q2row[lp] : 0.f;
   const float2* Ra = reinterpret_cast<const float2*>(a.in) + (size_t)la * M;
   const float2* Rb = reinterpret_cast<const float2*>(a.in) + (size_t)lbr * M;
+  if (!OTF) prefetch_l2_range(reinterpret_cast<const TabF*>(a.tab) + (size_t)lp * M, sizeof(TabF) * M);
   pdl_wait_release();
   constexpr int UM = 2;
   for (int m0 = tid; m0 < M; m0 += UM * nthr) {
