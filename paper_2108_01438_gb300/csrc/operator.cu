@@ -498,7 +498,16 @@ __device__ __forceinline__ void lat_last_pass_epi_p(const A& a, const float4* s4
                                                     int c, bool v2, bool ok0, bool ok1, const int* siperm,
                                                     const TwP& tw, float& part, float& part2) {
   const int q = threadIdx.x & (half - 1);
+  constexpr bool kHoist = RL <= kEpHoistMax;
   for (int blk = threadIdx.x >> hs; blk < N / RL; blk += (int)blockDim.x >> hs) {
+    // with a small radix the epilogue operands are loaded first, so that their
+    // latency overlaps the shared-memory reads and the butterfly
+    EpOps<float> o0[kHoist ? RL : 1], o1[kHoist ? RL : 1];
+    if constexpr (kHoist) {
+#pragma unroll
+      for (int r = 0; r < RL; ++r)
+        lat_prefetch2<float, MODE>(a, (size_t)siperm[blk * RL + r] * C + c, v2, ok0, ok1, o0[r], o1[r]);
+    }
     PC v[RL];
 #pragma unroll
     for (int r = 0; r < RL; ++r) v[r] = ld_pc(s4, (blk * RL + r) * half + q);
@@ -506,10 +515,10 @@ __device__ __forceinline__ void lat_last_pass_epi_p(const A& a, const float4* s4
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       const size_t off = (size_t)siperm[blk * RL + r] * C + c;
-      EpOps<float> o0, o1;
-      lat_prefetch2<float, MODE>(a, off, v2, ok0, ok1, o0, o1);
+      const int k = kHoist ? r : 0;
+      if constexpr (!kHoist) lat_prefetch2<float, MODE>(a, off, v2, ok0, ok1, o0[0], o1[0]);
       lat_store2<float, MODE>(a, off, v2, ok0, ok1, make_float2(v[r].re.x, v[r].im.x),
-                              make_float2(v[r].re.y, v[r].im.y), o0, o1, part, part2);
+                              make_float2(v[r].re.y, v[r].im.y), o0[k], o1[k], part, part2);
     }
   }
 }
@@ -524,7 +533,14 @@ __device__ __forceinline__ void lat_mid_center_p(const A& a, float4* s4, int N, 
                                                  bool v2, bool ok0, bool ok1, const int* siperm, const TwP& tw,
                                                  float& part) {
   const int q = threadIdx.x & (half - 1);
+  constexpr bool kHoist = RL <= kEpHoistMax;
   for (int blk = threadIdx.x >> hs; blk < N / RL; blk += (int)blockDim.x >> hs) {
+    EpOps<float> e0[kHoist ? RL : 1], e1[kHoist ? RL : 1];
+    if constexpr (kHoist) {
+#pragma unroll
+      for (int r = 0; r < RL; ++r)
+        lat_prefetch2<float, MODE>(a, (size_t)siperm[blk * RL + r] * C + c, v2, ok0, ok1, e0[r], e1[r]);
+    }
     PC v[RL];
 #pragma unroll
     for (int r = 0; r < RL; ++r) v[r] = ld_pc(s4, (blk * RL + r) * half + q);
@@ -532,8 +548,10 @@ __device__ __forceinline__ void lat_mid_center_p(const A& a, float4* s4, int N, 
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       const size_t off = (size_t)siperm[blk * RL + r] * C + c;
-      EpOps<float> o0, o1;
-      lat_prefetch2<float, MODE>(a, off, v2, ok0, ok1, o0, o1);
+      const int k = kHoist ? r : 0;
+      if constexpr (!kHoist) lat_prefetch2<float, MODE>(a, off, v2, ok0, ok1, e0[0], e1[0]);
+      const EpOps<float>& o0 = e0[k];
+      const EpOps<float>& o1 = e1[k];
       float ra, rb;
       if constexpr (MODE == LAT_SOLVE_MID) {
         float pa, pb, qa = 0.f, qb = 0.f;

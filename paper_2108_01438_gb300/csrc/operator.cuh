@@ -107,6 +107,12 @@ constexpr bool kLatFuse = MBIR_LAT_FUSE != 0;
 #define MBIR_ROW_FUSE 1
 #endif
 constexpr bool kRowFuse = MBIR_ROW_FUSE != 0;
+// fused last lateral passes of radix <= this load their epilogue operands before
+// the butterfly (more radix means more registers held across it)
+#ifndef MBIR_EP_HOIST
+#define MBIR_EP_HOIST 4
+#endif
+constexpr int kEpHoistMax = MBIR_EP_HOIST;
 constexpr int kMaxDynSmem = 200 * 1024;   // dynamic shared memory cap (static use stays below the rest)
 constexpr bool kGatherPrecomp = MBIR_GATHER_PRECOMP != 0;   // adjoint gather keeps per-pixel weights
 constexpr bool kAdjAtomic = MBIR_ADJ_ATOMIC != 0;           // adjoint spreads with atomics
