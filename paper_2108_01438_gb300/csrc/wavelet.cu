@@ -143,7 +143,9 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const V* in = reinterpret_cast<const V*>(a.in);
   pdl_wait_release();
   // stage the input tile with every load of a thread in flight at once; the
-  // periodic wrap is a conditional subtraction (2 a0 + i < 2 P)
+  // periodic wrap subtracts P (N) as often as needed: once at most when the block
+  // is larger than the tile's window, more often at the coarse levels of small
+  // images, whose window can span the block several times
   constexpr int kFwdPer = (kRows * kCols + wav_threads<SMALL>() - 1) / wav_threads<SMALL>();
   {
     V vv[kFwdPer];
@@ -153,8 +155,8 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
       if (e < kRows * kCols) {
         const int i = e / kCols, j = e - i * kCols;
         int row = 2 * a0 + i, col = 2 * b0 + j;
-        if (row >= P) row -= P;
-        if (col >= N) col -= N;
+        while (row >= P) row -= P;
+        while (col >= N) col -= N;
         vv[q] = in[(size_t)row * a.istride + col];
       }
     }
@@ -267,12 +269,13 @@ dwt_inv_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
       const int e = tid + q * nthr;
       if (e < kRows * kCols) {
         const int ia = e / kCols, ib = e - ia * kCols;
-        // r0/2 - 3 + ia lies in [-3, Ph + kRows): one conditional wrap each way
+        // r0/2 - 3 + ia lies in [-3, Ph + kRows): one wrap up (Ph, Nh >= 4), and
+        // as many down as the window spans the block
         int A = r0 / 2 - 3 + ia, Bc = c0 / 2 - 3 + ib;
         if (A < 0) A += Ph;
-        if (A >= Ph) A -= Ph;
+        while (A >= Ph) A -= Ph;
         if (Bc < 0) Bc += Nh;
-        if (Bc >= Nh) Bc -= Nh;
+        while (Bc >= Nh) Bc -= Nh;
         v0[q] = ll[(size_t)A * a.istride + Bc];
         v1[q] = coef[(size_t)A * a.cstride + Nh + Bc];
         v2[q] = coef[(size_t)(Ph + A) * a.cstride + Bc];
