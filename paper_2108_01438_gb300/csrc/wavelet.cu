@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -142,12 +143,13 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
   const int a0 = by * kTA, b0 = bx * kTB;
   const V* in = reinterpret_cast<const V*>(a.in);
   pdl_wait_release();
-  // stage the input tile with every load of a thread in flight at once; the
-  // periodic wrap subtracts P (N) as often as needed: once at most when the block
-  // is larger than the tile's window, more often at the coarse levels of small
-  // images, whose window can span the block several times
+  // stage the input tile with every load of a thread in flight at once.  The
+  // window starts inside the block, so one subtraction of P (N) wraps it when the
+  // block is at least as large as the window; the coarse levels of small images,
+  // whose window can span the block several times, take the remainder as well
+  // (a branch that is the same for the whole grid)
   constexpr int kFwdPer = (kRows * kCols + wav_threads<SMALL>() - 1) / wav_threads<SMALL>();
-  {
+  auto stage = [&](auto small_block) {
     V vv[kFwdPer];
 #pragma unroll
     for (int q = 0; q < kFwdPer; ++q) {
@@ -155,8 +157,12 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
       if (e < kRows * kCols) {
         const int i = e / kCols, j = e - i * kCols;
         int row = 2 * a0 + i, col = 2 * b0 + j;
-        while (row >= P) row -= P;
-        while (col >= N) col -= N;
+        if (row >= P) row -= P;
+        if (col >= N) col -= N;
+        if constexpr (decltype(small_block)::value) {
+          row %= P;
+          col %= N;
+        }
         vv[q] = in[(size_t)row * a.istride + col];
       }
     }
@@ -165,7 +171,9 @@ dwt_fwd_kernel(const __grid_constant__ WArgs<R> arg0, const BatchRef<WArgs<R>> B
       const int e = tid + q * nthr;
       if (e < kRows * kCols) tin[e] = vv[q];
     }
-  }
+  };
+  if (P < kRows || N < kCols) stage(std::true_type());
+  else stage(std::false_type());
   __syncthreads();
   // along depth: outputs b, b + 1 of row i from inputs 2b .. 2b + 9
   for (int e = tid; e < kRows * (kTB / 2); e += nthr) {

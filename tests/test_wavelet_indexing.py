@@ -32,18 +32,28 @@ def _wrap_down(v, n):
     return v
 
 
+def _analysis_wrap(v, n, small_block):
+    """The analysis kernel's wrap: one subtraction, and the remainder when the
+    block is smaller than the window."""
+    if v >= n:
+        v -= n
+    return v % n if small_block else v
+
+
 def _analysis_ok(P, N, small):
     """dwt_fwd_kernel: a tile of TA x TB coefficients per band stages the
     (2 TA + 6) x (2 TB + 6) input window at (2 a0, 2 b0)."""
     ta, tb = FWD[small]
     rows, cols = 2 * ta + 6, 2 * tb + 6
     Ph, Nh = P // 2, N // 2
+    small_block = P < rows or N < cols
     for a0 in range(0, Ph, ta):
         for b0 in range(0, Nh, tb):
             staged = {}
             for i in range(rows):
                 for j in range(cols):
-                    r, c = _wrap_down(2 * a0 + i, P), _wrap_down(2 * b0 + j, N)
+                    r = _analysis_wrap(2 * a0 + i, P, small_block)
+                    c = _analysis_wrap(2 * b0 + j, N, small_block)
                     assert 0 <= r < P and 0 <= c < N
                     staged[(i, j)] = (r, c)
             # kept outputs (A < Ph, B < Nh) read window rows 2(A - a0) + t, t < 8
@@ -94,16 +104,17 @@ def test_wavelet_windows_stay_inside_their_blocks(nx, nz):
         _synthesis_ok(P, N, small)
 
 
-def test_kernels_use_the_repeated_wrap():
+def test_kernels_use_the_emulated_wrap():
     s = open(SRC).read()
-    for stmt in ("while (row >= P) row -= P;", "while (col >= N) col -= N;", "while (A >= Ph) A -= Ph;",
-                 "while (Bc >= Nh) Bc -= Nh;"):
+    for stmt in ("if (row >= P) row -= P;", "if (col >= N) col -= N;", "row %= P;", "col %= N;",
+                 "if (P < kRows || N < kCols) stage(std::true_type());",
+                 "while (A >= Ph) A -= Ph;", "while (Bc >= Nh) Bc -= Nh;"):
         assert stmt in s, stmt
 
 
 def test_single_wrap_would_leave_the_block_at_small_sizes():
-    """The case the repeated wrap exists for: level 3 of a 32-row image has an
-    8-row block and a 38-row window."""
+    """The case the remainder exists for: level 3 of a 32-row image has an 8-row
+    block and a 38-row window."""
     ta, _ = FWD[True]
     rows, P = 2 * ta + 6, 32 >> 2
     once = [(i - P if i >= P else i) for i in range(rows)]
