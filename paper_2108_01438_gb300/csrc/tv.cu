@@ -214,7 +214,9 @@ __device__ __forceinline__ Dual<R> project_step(Dual<R> q, cplx_t<R> g1, cplx_t<
   q.p2 = cmk<V>(q.p2.x + step * g2.x, q.p2.y + step * g2.y);
   const R n2 = q.p1.x * q.p1.x + q.p1.y * q.p1.y + q.p2.x * q.p2.x + q.p2.y * q.p2.y;
   if (n2 > R(1)) {
-    const R s = R(1) / sqrt(n2);
+    // 1/|q| by the library's reciprocal square root (a few ulp) rather than a
+    // rounded square root and a division: the pass is bound by instruction issue
+    const R s = rsqrt(n2);
     q.p1 = cscale(q.p1, s);
     q.p2 = cscale(q.p2, s);
   }
