@@ -67,6 +67,27 @@ def test_prox_matches_oracle(mbir, penalty):
     plan.close()
 
 
+@pytest.mark.parametrize("nx,nz", [(32, 32), (40, 72), (96, 160), (136, 64)])
+@pytest.mark.parametrize("precision", [0, 2])
+def test_db4_prox_small_ragged_and_fp64(mbir, nx, nz, precision):
+    """The db4 prox at sizes whose coarse-level tile windows span their block
+    several times (nx = 32: an 8-row level-3 block), with ragged tiles
+    (136 x 64, 40 x 72), and on FP64 plans."""
+    plan = mbir.Plan(W.geometry(nx, nz, 16), precision=precision)
+    rng = np.random.default_rng(nx * 7 + nz)
+    v = rng.standard_normal((nx, nz)) + 1j * rng.standard_normal((nx, nz))
+    tau = 0.7
+    if precision == 2:
+        vt = torch.from_numpy(v).cuda()
+        z = plan.prox(vt, tau, "db4").cpu().numpy()
+        assert _rel(z, fista.prox_wavelet(v, tau, H)) <= 1e-11
+    else:
+        v32 = v.astype(np.complex64).astype(np.complex128)
+        z = plan.prox(_c64(v), tau, "db4").cpu().numpy()
+        assert _rel(z, fista.prox_wavelet(v32, tau, H)) <= 1e-6
+    plan.close()
+
+
 def _tiny_problem(penalty="l1"):
     wl = W.tiny_workload()
     d = wl["geom"]
