@@ -300,12 +300,17 @@ int mbir_solve(mbir_plan plan, const void* y, const uint8_t* mask, const mbir_so
 /*
  * FISTA on n B-scans at once (the uneven-size batch): plans[i] (each plan at most
  * once, all with the same precision, KB width and shape), y[i], mask[i] (mask may
- * be NULL, or mask[i] NULL), opts[i] and x[i] as for mbir_solve.  Every stage of
- * the path -- power iteration, lambda rule, the operator passes, the FISTA
- * epilogues and the wavelet levels -- is one launch over all scans; the iteration
- * loop is captured into a CUDA graph and replayed when `stream` is a created
- * stream (not the legacy or per-thread default).  Each scan's result does not
- * depend on what it is batched with.  All opts[i].max_iter must be equal,
+ * be NULL, or mask[i] NULL), opts[i] and x[i] as for mbir_solve.  Scans whose row
+ * kernels alone give every SM at least three CTAs (nx/2 + 1 >= 3 x the SM count)
+ * run the single-scan path of mbir_solve; for the others every stage of the path
+ * -- power iteration, lambda rule, the operator passes, the FISTA epilogues and
+ * the wavelet levels -- is one launch over all of them, and their iteration loop
+ * is captured into a CUDA graph and replayed.  When `stream` is a created stream
+ * (not the legacy or per-thread default) and both kinds are present, the wide
+ * scans run on a high-priority stream and the shared stages on a second stream,
+ * both forked from `stream` and joined back to it, so that the shared stages fill
+ * the SMs the wide scans' launches leave idle.  Each scan's result does not
+ * depend on what it is batched with (a wide scan's equals its mbir_solve result).  All opts[i].max_iter must be equal,
  * rel_tol must be 0 (fixed iteration count), the penalty l1 or db4 and the
  * back-projection the transpose.  info (NULL or n entries) receives
  * iters, lipschitz, step and lambda_used; objective is not evaluated (NaN).

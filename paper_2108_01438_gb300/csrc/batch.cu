@@ -820,6 +820,14 @@ int Engine::finish(BScan* s) {
 
 }  // namespace mbir
 
+namespace mbir {
+
+// A scan runs its own stages inside a batch when its row kernels alone give every
+// SM at least three CTAs (nx/2 + 1 row pairs).
+static bool runs_alone(mbir_plan p, int sms) { return p->nx / 2 + 1 >= 3 * sms; }
+
+}  // namespace mbir
+
 using namespace mbir;
 
 extern "C" {
@@ -850,16 +858,80 @@ int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const ui
     ptrs[i] = &s;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  Engine eng(st);
-  int rc = eng.setup(ptrs);
+  // Scans whose own row stage fills every SM several times run the single-scan
+  // path: batching them only adds the batched kernels' per-CTA cost (argument
+  // blocks in device memory, fewer resident warps), which outweighs the wave tails
+  // it fills.  The other scans share batched stages on a second stream, where they
+  // fill the idle SMs of the large scans' launches.  A scan's path depends on its
+  // own size only, so its result does not depend on the rest of the batch.
+  int dev = 0, sms = 0;
+  MBIR_CUDA_TRY(cudaGetDevice(&dev));
+  MBIR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  std::vector<BScan*> shared;
+  std::vector<int> alone;
+  for (int i = 0; i < n; ++i) {
+    if (runs_alone(plans[i], sms)) alone.push_back(i);
+    else shared.push_back(ptrs[i]);
+  }
+  // two created streams forked from `stream`: the large scans on a high-priority
+  // one, the shared batch on another; the legacy and per-thread default streams
+  // run everything on `stream`, one after the other
+  const bool fork = !alone.empty() && !shared.empty() && st != nullptr && st != cudaStreamLegacy &&
+                    st != cudaStreamPerThread;
+  cudaStream_t sa = st, sb = st;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  auto release = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (sa != st) cudaStreamDestroy(sa);
+    if (sb != st) cudaStreamDestroy(sb);
+  };
+  if (fork) {
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sa, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sa, ev[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sb, ev[0], 0);
+    if (e != cudaSuccess) {
+      release();
+      return set_cuda_error(e, "mbir_solve_batch: streams");
+    }
+  }
+  int rc = MBIR_OK;
+  std::vector<mbir_solve_info> solo_info(alone.size());
+  {
+    Engine eng(sb);
+    if (!shared.empty()) {
+      // set-up (one read-back), then the captured iteration loop, queued on sb
+      rc = eng.setup(shared);
+      if (!rc) rc = eng.solve_fixed(shared);
+      for (size_t i = 0; !rc && i < shared.size(); ++i) rc = eng.finish(shared[i]);
+    }
+    // the large scans on sa while the shared batch runs
+    for (size_t j = 0; !rc && j < alone.size(); ++j) {
+      const int i = alone[j];
+      memset(&solo_info[j], 0, sizeof(mbir_solve_info));
+      rc = solve_plan(plans[i], y[i], mask ? mask[i] : nullptr, &opts[i], x[i], info ? &solo_info[j] : nullptr, sa,
+                      false);
+    }
+    if (fork) {
+      cudaError_t e = cudaEventRecord(ev[1], sa);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2], sb);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[2], 0);
+      if (e != cudaSuccess && !rc) rc = set_cuda_error(e, "mbir_solve_batch: join");
+    }
+    if (!rc && info) {
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = set_cuda_error(e, "cudaStreamSynchronize");
+    }
+  }
+  release();
   if (rc) return rc;
-  rc = eng.solve_fixed(ptrs);
-  if (rc) return rc;
-  for (BScan* s : ptrs)
-    if ((rc = eng.finish(s))) return rc;
   if (info) {
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamSynchronize");
     for (int i = 0; i < n; ++i) {
       info[i].iters = scans[i].k;
       info[i].status = MBIR_OK;
@@ -867,6 +939,16 @@ int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const ui
       info[i].lipschitz = scans[i].L;
       info[i].step = scans[i].delta;
       info[i].lambda_used = scans[i].lam;
+    }
+    for (size_t j = 0; j < alone.size(); ++j) {
+      mbir_solve_info& d = info[alone[j]];
+      const mbir_solve_info& s = solo_info[j];
+      d.iters = s.iters;
+      d.status = s.status;
+      d.objective = NAN;
+      d.lipschitz = s.lipschitz;
+      d.step = s.step;
+      d.lambda_used = s.lambda_used;
     }
   }
   return MBIR_OK;

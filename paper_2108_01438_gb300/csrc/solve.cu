@@ -340,7 +340,7 @@ static int reg_count(mbir_plan p, int penalty) {
 
 template <class R>
 static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
-                   mbir_solve_info* info, cudaStream_t st) {
+                   mbir_solve_info* info, cudaStream_t st, bool final_objective) {
   SolveState* s = p->solve;
   const size_t es = elem_size(p);
   const bool hil = o->backprojection == MBIR_BACKPROJ_HILBERT;
@@ -428,15 +428,17 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
   const int iters = k > o->max_iter ? o->max_iter : k;
   MBIR_CUDA_TRY(cudaMemcpyAsync(x, z1, es * s->nimg, cudaMemcpyDeviceToDevice, st));
   if (info) {
-    // F(z^iters): one more forward pass for the data term
-    int rc = forward_impl(p, z1, mask, s->r, st);
-    if (rc) return rc;
-    const int gb = grid_for(s->nmeas);
-    { ProfScope ps_(p, PC_REDUCE, st); launch(resid_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, (const R*)s->r, (const R*)y, mask, s->nmeas, s->part_tmp); }
-    { ProfScope ps_(p, PC_REDUCE, st); launch(combine_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, gb, 0.5, s->part_reg, nreg, lam, s->scal + 6); }
-    MBIR_LAUNCH_CHECK();
-    double fin = 0.0;
-    MBIR_CUDA_TRY(cudaMemcpyAsync(&fin, s->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double fin = NAN;
+    if (final_objective) {
+      // F(z^iters): one more forward pass for the data term
+      int rc = forward_impl(p, z1, mask, s->r, st);
+      if (rc) return rc;
+      const int gb = grid_for(s->nmeas);
+      { ProfScope ps_(p, PC_REDUCE, st); launch(resid_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, (const R*)s->r, (const R*)y, mask, s->nmeas, s->part_tmp); }
+      { ProfScope ps_(p, PC_REDUCE, st); launch(combine_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, gb, 0.5, s->part_reg, nreg, lam, s->scal + 6); }
+      MBIR_LAUNCH_CHECK();
+      MBIR_CUDA_TRY(cudaMemcpyAsync(&fin, s->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     if (info->objective_trace && info->trace_len > 0) {
       const int n = info->trace_len < iters ? info->trace_len : iters;
       MBIR_CUDA_TRY(cudaMemcpyAsync(info->objective_trace, s->objtrace, sizeof(double) * n,
@@ -453,24 +455,9 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
   return status;
 }
 
-}  // namespace mbir
-
-using namespace mbir;
-
-extern "C" {
-
-int mbir_lipschitz(mbir_plan p, const uint8_t* mask, int32_t iters, double* out, void* stream) {
-  if (const int vrc = bscan_only(p, "mbir_lipschitz")) return vrc;
-  if (!p || !out || iters < 1) return MBIR_ERR_INVALID;
-  int rc = ensure_state(p, 1);
-  if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
-  return p->precision == MBIR_FP64 ? lipschitz_t<double>(p, mask, iters, out, st)
-                                   : lipschitz_t<float>(p, mask, iters, out, st);
-}
-
-int mbir_solve(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
-               mbir_solve_info* info, void* stream) {
+// mbir_solve; final_objective = false leaves info->objective NaN (no extra forward pass).
+int solve_plan(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
+               mbir_solve_info* info, cudaStream_t st, bool final_objective) {
   if (!p || !y || !o || !x) return MBIR_ERR_INVALID;
   if (const int vrc = bscan_only(p, "mbir_solve")) return vrc;
   if (o->max_iter < 1 || o->min_iter < 0) return MBIR_ERR_INVALID;
@@ -491,9 +478,29 @@ int mbir_solve(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve
     rc = ensure_wavelet_scratch(p);
     if (rc) return rc;
   }
+  return p->precision == MBIR_FP64 ? solve_t<double>(p, y, mask, o, x, info, st, final_objective)
+                                   : solve_t<float>(p, y, mask, o, x, info, st, final_objective);
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
+extern "C" {
+
+int mbir_lipschitz(mbir_plan p, const uint8_t* mask, int32_t iters, double* out, void* stream) {
+  if (const int vrc = bscan_only(p, "mbir_lipschitz")) return vrc;
+  if (!p || !out || iters < 1) return MBIR_ERR_INVALID;
+  int rc = ensure_state(p, 1);
+  if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  return p->precision == MBIR_FP64 ? solve_t<double>(p, y, mask, o, x, info, st)
-                                   : solve_t<float>(p, y, mask, o, x, info, st);
+  return p->precision == MBIR_FP64 ? lipschitz_t<double>(p, mask, iters, out, st)
+                                   : lipschitz_t<float>(p, mask, iters, out, st);
+}
+
+int mbir_solve(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
+               mbir_solve_info* info, void* stream) {
+  return solve_plan(p, y, mask, o, x, info, (cudaStream_t)stream, true);
 }
 
 }  // extern "C"

@@ -24,5 +24,9 @@ struct SolveState {
 int ensure_state(mbir_plan p, int trace_cap);
 int wavelet_partial_count(int nx, int nz);
 int ensure_wavelet_scratch(mbir_plan p);
+// mbir_solve on a cudaStream_t; final_objective = false skips the extra forward
+// pass that evaluates F(z^iters) for info (info->objective stays NaN).
+int solve_plan(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
+               mbir_solve_info* info, cudaStream_t st, bool final_objective);
 
 }  // namespace mbir

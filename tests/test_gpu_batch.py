@@ -90,3 +90,32 @@ def test_batch_rejects_bad_arguments(mbir, batch_case):
     scans, plans, ys, ms, pens, xs, infos = batch_case
     with pytest.raises(mbir.MbirError):
         mbir.solve_batch([plans[0], plans[0]], [ys[0], ys[0]], iters=5)
+
+
+def test_batch_runs_wide_scans_alone_and_overlaps_the_rest(mbir, batch_case):
+    """A scan whose row kernels alone fill every SM three times (nx/2 + 1 >= 3 SMs)
+    takes the single-scan path inside the batch, on a stream of its own, while the
+    small scans share batched stages on another: the wide scan's result equals its
+    solo solve bit for bit, the small scans' results equal those of the batch
+    without it, and every result matches the oracle's iterates."""
+    scans, plans, ys, ms, pens, xs, infos = batch_case
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nx = min(w for w in W.smooth_widths(8, 4096) if w // 2 + 1 >= 3 * sms)   # mixed-radix width
+    assert nx <= 2048
+    d, g, mask, y = _scan(7, nx, 64, 64)
+    wide = mbir.Plan(d)
+    yw, mw = torch.from_numpy(y).cuda(), torch.from_numpy(mask).cuda()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        out, inf = mbir.solve_batch([plans[0], wide, plans[1]], [ys[0], yw, ys[1]], [ms[0], mw, ms[1]],
+                                    penalties=[pens[0], "l1", pens[1]], lams=0.02, iters=40, stream=stream)
+        z, zi = wide.solve(yw, mw, penalty="l1", lam=0.02, relative=True, iters=40, stream=stream)
+    stream.synchronize()
+    assert np.array_equal(out[1].cpu().numpy(), z.cpu().numpy())
+    assert inf[1]["step"] == zi["step"] and inf[1]["lambda_used"] == zi["lambda_used"] and inf[1]["iters"] == 40
+    assert np.array_equal(out[0].cpu().numpy(), xs[0]) and np.array_equal(out[2].cpu().numpy(), xs[1])
+    y64 = y.astype(np.float64)
+    ref = fista.fista(lambda v: isam.phi_nufft(v, mask, g), lambda r: isam.phi_adj_nufft(r, mask, g), y64, mask,
+                      fista.prox_l1, inf[1]["lambda_used"], inf[1]["step"], 40, (g.nx, g.nz))
+    assert _rel(out[1].cpu().numpy(), ref) <= 1e-3
+    wide.close()
