@@ -72,6 +72,21 @@ def test_odd_radix_and_ragged_sizes(mbir, nx, nz, m):
     assert_parity(xg, isam.phi_adj_nufft(y32, mask, g), OP_TOL, what=f"Phi^H {nx}x{nz}x{m}")
 
 
+@pytest.mark.parametrize("nx,nz,m", [(4096, 16, 16), (8, 4096, 4096), (6, 4096, 3000)])
+def test_maximum_sizes(mbir, nx, nz, m):
+    """The largest sizes a plan takes: 4096 A-scans (a 4096-point lateral transform
+    on two-column tiles) and 4096 depth pixels (K = 8192, the largest row transform,
+    where the row kernels fall back from the paired gather by footprint), also with
+    a spectrometer length that is not the depth."""
+    d, x, y, mask = _case(nx, nz, m, 7 + nx + nz)
+    g = isam.make_geom(d)
+    yg, xg = _run(mbir, d, x, y, mask)
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    y32 = y.astype(np.float32).astype(np.float64)
+    assert_parity(yg, isam.phi_nufft(x32, mask, g), OP_TOL, what=f"Phi {nx}x{nz}x{m}")
+    assert_parity(xg, isam.phi_adj_nufft(y32, mask, g), OP_TOL, what=f"Phi^H {nx}x{nz}x{m}")
+
+
 def test_gpu_adjoint_identity(mbir):
     d, x, y, mask = _case(64, 256, 256, 3)
     yg, xg = _run(mbir, d, x, y, mask)
