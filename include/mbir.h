@@ -193,8 +193,8 @@ int mbir_plan_dims(mbir_plan plan, int32_t* nx, int32_t* nz, int32_t* m, int32_t
  * beam filter see |q|^2 = q_x^2 + q_y^2 with q_y = 2 pi l~_y / (ny dy).
  * Layouts: image x [nx][ny][nz] complex, measurements y and mask [nx][ny][m],
  * depth / spectrum contiguous.  A volume plan runs mbir_forward and mbir_adjoint
- * (same arguments, these layouts); the other calls that take a plan return
- * MBIR_ERR_UNSUPPORTED_SIZE for it.  Sizes: ny in [2, 4096] with the same rule as
+ * (same arguments, these layouts) and mbir_solve with the l1 penalty (see there);
+ * the other calls that take a plan return MBIR_ERR_UNSUPPORTED_SIZE for it.  Sizes: ny in [2, 4096] with the same rule as
  * nx (Bluestein beyond 7-smooth), nx * ny * nz and nx * ny * m below 2^31; the
  * other limits as mbir_plan_create.  The resampling table has one row per
  * (|lx|, |ly|): (nx/2 + 1)(ny/2 + 1) m entries of 16 bytes (FP32), built on the
@@ -293,6 +293,11 @@ int mbir_lambda_search(mbir_plan plan, const void* y, const uint8_t* mask, const
  * Allocates the iteration state on the first call for a given plan and keeps it.
  * Synchronous when it has to read a device scalar back (step or lambda derived on
  * the device, rel_tol > 0, or info != NULL); otherwise asynchronous on stream.
+ * On a volume plan (mbir_volume_plan_create) the image and measurements take the
+ * volume layouts and the options are restricted to the l1 penalty, the transpose
+ * back-projection and a fixed iteration count (rel_tol = 0; MBIR_ERR_INVALID
+ * otherwise; the objective trace is not recorded).  Each iteration is one volume
+ * Phi, one volume Phi^H and two elementwise passes (no fused solver passes).
  */
 int mbir_solve(mbir_plan plan, const void* y, const uint8_t* mask, const mbir_solve_opts* opts,
                void* x, mbir_solve_info* info, void* stream);

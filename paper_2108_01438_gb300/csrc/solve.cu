@@ -192,6 +192,33 @@ __global__ void resid_kernel(const R* pz, const R* y, const uint8_t* mask, size_
   if (threadIdx.x == 0) part[blockIdx.x] = S;
 }
 
+
+// Volume FISTA (the operator of both lateral axes has no fused solver passes):
+// r = s (Phi x) - s y; Phi x arrives masked, so r = 0 where s = 0.
+template <class R>
+__global__ void vol_resid_kernel(const R* pz, const R* y, const uint8_t* mask, size_t n, R* r) {
+  pdl_wait_release();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    r[i] = (mask && !mask[i]) ? R(0) : pz[i] - y[i];
+}
+
+// z^k = prox_{tau |.|}(x^k - delta g) (modulus soft threshold), then the momentum
+// point x^{k+1} = z^k + mu (z^k - z^{k-1}) over x in place (Eq. alg).
+template <class R>
+__global__ void vol_fista_kernel(cplx_t<R>* x, const cplx_t<R>* g, const cplx_t<R>* zprev, cplx_t<R>* znew,
+                                 size_t n, R delta, R tau, R mu) {
+  pdl_wait_release();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx_t<R> xi = x[i], gi = g[i], zp = zprev[i];
+    const R ux = xi.x - delta * gi.x, uy = xi.y - delta * gi.y;
+    const R mag = sqrt(ux * ux + uy * uy);
+    const R sh = mag > tau ? R(1) - tau / mag : R(0);
+    const R zx = ux * sh, zy = uy * sh;
+    znew[i] = cmk<cplx_t<R>>(zx, zy);
+    x[i] = cmk<cplx_t<R>>(zx + mu * (zx - zp.x), zy + mu * (zy - zp.y));
+  }
+}
+
 // ------------------------------------------------------------------ state
 
 // doubles in part_tmp / 2: grid-stride reductions and the power iteration's two
@@ -217,6 +244,7 @@ void destroy_solve_state(mbir_plan p) {
   cudaFree(s->part_tmp);
   cudaFree(s->scal);
   cudaFree(s->objtrace);
+  cudaFree(s->g);
   delete s;
   p->solve = nullptr;
 }
@@ -233,8 +261,8 @@ int ensure_state(mbir_plan p, int trace_cap) {
   SolveState* s = new (std::nothrow) SolveState;
   if (!s) return MBIR_ERR_OOM;
   p->solve = s;
-  s->nimg = (size_t)p->nx * p->nz;
-  s->nmeas = (size_t)p->nx * p->m;
+  s->nimg = (size_t)p->nx * p->ny * p->nz;
+  s->nmeas = (size_t)p->nx * p->ny * p->m;
   s->n_data = lateral_grid(p, p->m);
   int nr = lateral_grid(p, p->nz);
   if (wavelet_supported(p->nx, p->nz)) {
@@ -254,6 +282,7 @@ int ensure_state(mbir_plan p, int trace_cap) {
   MBIR_CUDA_TRY(cudaMalloc(&s->part_tmp, sizeof(double) * 2 * part_tmp_count(p)));
   MBIR_CUDA_TRY(cudaMalloc(&s->scal, sizeof(double) * 16));
   MBIR_CUDA_TRY(cudaMalloc(&s->objtrace, sizeof(double) * trace_cap));
+  if (p->ny > 1) MBIR_CUDA_TRY(cudaMalloc(&s->g, elem_size(p) * s->nimg));
   return MBIR_OK;
 }
 
@@ -455,11 +484,125 @@ static int solve_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_s
   return status;
 }
 
+
+// FISTA (Eq. alg) on a volume plan with the l1 penalty, in the oracle's form:
+// z^k = prox(x^k - delta Phi^H(s Phi x^k - s y)), x^{k+1} = z^k + mu_k (z^k - z^{k-1}),
+// x^1 = z^0 = 0 (or the warm start), the step from the power iteration on
+// Phi^H s Phi and the relative lambda from max|Phi^H s y|.  Each iteration is one
+// volume forward, one volume adjoint and two elementwise passes.
+template <class R>
+static int solve_vol_t(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
+                       mbir_solve_info* info, cudaStream_t st, bool final_objective) {
+  using V = cplx_t<R>;
+  SolveState* s = p->solve;
+  const size_t n = s->nimg, nm = s->nmeas;
+  const int gb = grid_for(n), gm = grid_for(nm);
+  const size_t es = elem_size(p);
+  V* G = (V*)s->g;
+  double L = 0.0, delta = o->step;
+  if (!(delta > 0)) {
+    const int pit = o->power_iters > 0 ? o->power_iters : 30;
+    V* w = (V*)s->zA;
+    V* v = (V*)s->v;
+    { ProfScope ps_(p, PC_REDUCE, st); launch(fill_hash_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, w, n); }
+    { ProfScope ps_(p, PC_REDUCE, st); launch(dot_norm_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, w, w, n, s->part_tmp); }
+    { ProfScope ps_(p, PC_REDUCE, st); launch(power_finalize_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, gb, s->scal); }
+    MBIR_LAUNCH_CHECK();
+    for (int it = 0; it < pit; ++it) {
+      { ProfScope ps_(p, PC_REDUCE, st); launch(scale_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, v, (const V*)w, n, (const double*)s->scal); }
+      MBIR_LAUNCH_CHECK();
+      int rc = forward_impl(p, v, mask, s->pz, st);
+      if (!rc) rc = adjoint_impl(p, s->pz, mask, w, st);
+      if (rc) return rc;
+      { ProfScope ps_(p, PC_REDUCE, st); launch(dot_norm_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, (const V*)v, (const V*)w, n, s->part_tmp); }
+      { ProfScope ps_(p, PC_REDUCE, st); launch(power_finalize_kernel, dim3(1), dim3(kRedThreads), 0, st, s->part_tmp, gb, s->scal); }
+      MBIR_LAUNCH_CHECK();
+    }
+    MBIR_CUDA_TRY(cudaMemcpyAsync(&L, s->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(L > 0) || !isfinite(L)) return MBIR_ERR_INVALID;
+    delta = 1.0 / (1.01 * L);
+  }
+  double lam = o->lambda;
+  if (o->lambda_is_relative) {
+    int rc = adjoint_impl(p, y, mask, G, st);
+    if (rc) return rc;
+    { ProfScope ps_(p, PC_REDUCE, st); launch(maxabs_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, (const V*)G, n, s->part_tmp); }
+    { ProfScope ps_(p, PC_REDUCE, st); launch(max_finalize_kernel, dim3(1), dim3(kRedThreads), 0, st, (const double*)s->part_tmp, gb, s->scal + 4); }
+    MBIR_LAUNCH_CHECK();
+    double m = 0.0;
+    MBIR_CUDA_TRY(cudaMemcpyAsync(&m, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+    lam *= m;
+  }
+  const double tau = lam * delta;
+  V* X = (V*)s->v;                       // the momentum point x^k
+  V* Z[2] = {(V*)s->zA, (V*)s->zB};      // z^{k-1}, z^k alternate
+  if (o->warm_start) {
+    MBIR_CUDA_TRY(cudaMemcpyAsync(X, x, es * n, cudaMemcpyDeviceToDevice, st));
+    MBIR_CUDA_TRY(cudaMemcpyAsync(Z[0], x, es * n, cudaMemcpyDeviceToDevice, st));
+  } else {
+    MBIR_CUDA_TRY(cudaMemsetAsync(X, 0, es * n, st));
+    MBIR_CUDA_TRY(cudaMemsetAsync(Z[0], 0, es * n, st));
+  }
+  double t = 1.0;
+  int cur = 0;   // Z[cur] holds z^{k-1}
+  for (int k = 1; k <= o->max_iter; ++k) {
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const double mu = (t - 1.0) / tn;
+    t = tn;
+    int rc = forward_impl(p, X, mask, s->pz, st);
+    if (rc) return rc;
+    { ProfScope ps_(p, PC_REDUCE, st); launch(vol_resid_kernel<R>, dim3(gm), dim3(kRedThreads), 0, st, (const R*)s->pz, (const R*)y, mask, nm, (R*)s->r); }
+    MBIR_LAUNCH_CHECK();
+    if ((rc = adjoint_impl(p, s->r, mask, G, st))) return rc;
+    { ProfScope ps_(p, PC_SOFT, st); launch(vol_fista_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, X, (const V*)G, (const V*)Z[cur], Z[cur ^ 1], n, R(delta), R(tau), R(mu)); }
+    MBIR_LAUNCH_CHECK();
+    cur ^= 1;
+  }
+  MBIR_CUDA_TRY(cudaMemcpyAsync(x, Z[cur], es * n, cudaMemcpyDeviceToDevice, st));
+  if (info) {
+    double fin = NAN;
+    if (final_objective) {
+      // F(z) = 1/2 ||s Phi z - s y||^2 + lambda ||z||_1
+      int rc = forward_impl(p, Z[cur], mask, s->pz, st);
+      if (rc) return rc;
+      double* pd = s->part_tmp;
+      double* pr = s->part_tmp + gm;
+      { ProfScope ps_(p, PC_REDUCE, st); launch(resid_kernel<R>, dim3(gm), dim3(kRedThreads), 0, st, (const R*)s->pz, (const R*)y, mask, nm, pd); }
+      { ProfScope ps_(p, PC_REDUCE, st); launch(abs_sum_kernel<R>, dim3(gb), dim3(kRedThreads), 0, st, (const V*)Z[cur], n, pr); }
+      { ProfScope ps_(p, PC_REDUCE, st); launch(combine_kernel, dim3(1), dim3(kRedThreads), 0, st, (const double*)pd, gm, 0.5, (const double*)pr, gb, lam, s->scal + 6); }
+      MBIR_LAUNCH_CHECK();
+      MBIR_CUDA_TRY(cudaMemcpyAsync(&fin, s->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    MBIR_CUDA_TRY(cudaStreamSynchronize(st));
+    info->iters = o->max_iter;
+    info->status = MBIR_OK;
+    info->objective = fin;
+    info->lipschitz = L;
+    info->step = delta;
+    info->lambda_used = lam;
+  }
+  return MBIR_OK;
+}
+
 // mbir_solve; final_objective = false leaves info->objective NaN (no extra forward pass).
 int solve_plan(mbir_plan p, const void* y, const uint8_t* mask, const mbir_solve_opts* o, void* x,
                mbir_solve_info* info, cudaStream_t st, bool final_objective) {
   if (!p || !y || !o || !x) return MBIR_ERR_INVALID;
-  if (const int vrc = bscan_only(p, "mbir_solve")) return vrc;
+  if (p->ny > 1) {
+    // volume plans: l1 penalty, the transpose back-projection, a fixed iteration count
+    if (o->max_iter < 1 || o->penalty != MBIR_PENALTY_L1 || o->backprojection != MBIR_BACKPROJ_TRANSPOSE ||
+        o->rel_tol != 0.0 || !(o->lambda >= 0) || !isfinite(o->lambda) || !isfinite(o->step)) {
+      set_error_text("mbir_solve: a volume plan takes the l1 penalty, the transpose back-projection and "
+                     "rel_tol = 0");
+      return MBIR_ERR_INVALID;
+    }
+    int rc = ensure_state(p, 1);
+    if (rc) return rc;
+    return p->precision == MBIR_FP64 ? solve_vol_t<double>(p, y, mask, o, x, info, st, final_objective)
+                                     : solve_vol_t<float>(p, y, mask, o, x, info, st, final_objective);
+  }
   if (o->max_iter < 1 || o->min_iter < 0) return MBIR_ERR_INVALID;
   if (o->penalty != MBIR_PENALTY_L1 && o->penalty != MBIR_PENALTY_DB4 && o->penalty != MBIR_PENALTY_TV)
     return MBIR_ERR_INVALID;

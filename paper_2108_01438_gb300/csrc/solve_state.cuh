@@ -18,6 +18,7 @@ struct SolveState {
   double* part_tmp = nullptr;
   double* scal = nullptr;        // device scalars (power iteration, lambda, objective)
   double* objtrace = nullptr;
+  void* g = nullptr;              // volume plans: the gradient image Phi^H (s Phi x - s y)
   int n_data = 0, n_reg = 0, trace_cap = 0;
 };
 

@@ -443,7 +443,7 @@ class Plan:
 class VolumePlan:
     """One 3-D volume geometry (mbir_volume_plan_create): the B-scan geometry plus a
     second lateral axis of ny pixels.  Image [nx, ny, nz], measurements and mask
-    [nx, ny, m]; forward and adjoint only."""
+    [nx, ny, m]; forward, adjoint and the l1 FISTA solve."""
 
     def __init__(self, geometry: dict, ny: int, dy_um: float = 0.0, precision: int = FP32, stream=None):
         import torch
@@ -492,6 +492,28 @@ class VolumePlan:
         _check(lib().mbir_adjoint(self._h, _ptr(y), _ptr(mask), _ptr(out), _stream_handle(stream)),
                "mbir_adjoint")
         return out
+
+
+    def solve(self, y, mask=None, *, lam: float = 0.01, relative: bool = True, iters: int = 100,
+              power_iters: int = 30, step: float = 0.0, x0=None, out=None, stream=None):
+        """FISTA with the l1 penalty on the volume (mbir_solve).  Returns (x, info dict)."""
+        import torch
+        self._check_t(y, "y", self.real_dtype, self.m)
+        if mask is not None:
+            self._check_t(mask, "mask", torch.uint8, self.m)
+        if out is None:
+            out = torch.zeros((self.nx, self.ny, self.nz), dtype=self.complex_dtype, device=y.device) \
+                if x0 is None else x0.clone()
+        elif x0 is not None:
+            out.copy_(x0)
+        self._check_t(out, "out", self.complex_dtype, self.nz)
+        o = SolveOpts(PENALTIES["l1"], float(lam), int(bool(relative)), int(iters), 0, 0.0, int(power_iters),
+                      float(step), int(x0 is not None), 0, BACKPROJECTIONS["transpose"])
+        info = SolveInfo()
+        _check(lib().mbir_solve(self._h, _ptr(y), _ptr(mask), C.byref(o), _ptr(out), C.byref(info),
+                                _stream_handle(stream)), "mbir_solve")
+        return out, dict(iters=info.iters, status=info.status, objective=info.objective,
+                         lipschitz=info.lipschitz, step=info.step, lambda_used=info.lambda_used)
 
 
 def solve_batch(plans, ys, masks=None, *, penalties="l1", lams=0.01, relative=True, iters=100,

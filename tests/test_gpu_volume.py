@@ -139,3 +139,60 @@ def test_volume_plan_refuses_the_b_scan_calls(mbir):
     ny = C.c_int32()
     assert L.mbir_volume_dims(vol.handle, C.byref(ny)) == 0 and ny.value == 4
     vol.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-3), (2, 1e-8)])
+def test_volume_fista_l1_matches_oracle(mbir, precision, tol):
+    """FISTA with the l1 penalty on a volume (mbir_solve on a volume plan) against
+    the oracle's FISTA driven by the volume KB-NUFFT operator from the GPU's step
+    and lambda; the power iteration's L and the relative lambda against the
+    oracle's; the reported objective against the oracle's objective of the
+    returned volume."""
+    from oracle import fista
+    nx, ny, nz, m = 12, 8, 32, 40
+    d = W.geometry(nx, nz, m)
+    v = volume.make_vol_geom(d, ny)
+    rng = np.random.default_rng(91)
+    x_true = np.zeros((nx, ny, nz), dtype=np.complex128)
+    idx = rng.choice(nx * ny * nz, size=12, replace=False)
+    x_true.flat[idx] = np.exp(2j * np.pi * rng.random(12))
+    mask = (rng.random((nx, ny, m)) < 0.6).astype(np.uint8)
+    y = volume.phi3_nufft(x_true, mask, v) + 0.01 * rng.standard_normal((nx, ny, m)) * mask
+    rdt = torch.float64 if precision == 2 else torch.float32
+    yq = y.astype(np.float64 if precision == 2 else np.float32).astype(np.float64)
+    plan = mbir.VolumePlan(d, ny, precision=precision)
+    yt = torch.from_numpy(y).to(rdt).cuda()
+    mt = torch.from_numpy(mask).cuda()
+    z, info = plan.solve(yt, mt, lam=0.02, relative=True, iters=25, power_iters=60)
+    z = z.cpu().numpy().astype(np.complex128)
+    phi = lambda a: volume.phi3_nufft(a, mask, v)
+    phi_adj = lambda r: volume.phi3_adj_nufft(r, mask, v)
+    L_ref = fista.power_iteration(phi, phi_adj, (nx, ny, nz), iters=100)
+    assert abs(info["lipschitz"] - L_ref) <= 1e-3 * L_ref
+    lam_ref = 0.02 * float(np.max(np.abs(phi_adj(yq))))
+    assert abs(info["lambda_used"] - lam_ref) <= 1e-5 * lam_ref
+    assert info["iters"] == 25 and info["status"] == 0
+    ref = fista.fista(phi, phi_adj, yq, mask, fista.prox_l1, info["lambda_used"], info["step"], 25, (nx, ny, nz))
+    assert rel_l2(z, ref) <= tol
+    f_ref = fista.objective(phi, yq, mask, z, info["lambda_used"], fista.penalty_l1)
+    assert abs(info["objective"] - f_ref) <= 1e-4 * f_ref
+    # the same step and absolute lambda given explicitly reproduce the solve exactly
+    z2, info2 = plan.solve(yt, mt, lam=info["lambda_used"], relative=False, iters=25, step=info["step"])
+    assert np.array_equal(z2.cpu().numpy().astype(np.complex128), z)
+    assert info2["lipschitz"] == 0
+    plan.close()
+
+
+def test_volume_solve_refuses_other_options(mbir):
+    d = W.geometry(8, 16, 24)
+    vol = mbir.VolumePlan(d, 4)
+    y = torch.zeros((8, 4, 24), dtype=torch.float32, device="cuda")
+    x = torch.zeros((8, 4, 16), dtype=torch.complex64, device="cuda")
+    import ctypes as C
+    L = mbir.lib()
+    for pen, rel_tol in ((1, 0.0), (2, 0.0), (0, 1e-4)):
+        o = mbir.SolveOpts(pen, 0.01, 1, 5, 0, rel_tol, 5, 0.0, 0, 0, 0)
+        assert L.mbir_solve(vol.handle, C.c_void_p(y.data_ptr()), None, C.byref(o), C.c_void_p(x.data_ptr()),
+                            None, None) == -1
+        assert b"volume plan" in L.mbir_last_error()
+    vol.close()
