@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-tv", action="store_true", help="skip the TV-penalty solve")
     ap.add_argument("--no-hilbert", action="store_true",
                     help="skip the Hilbert-form back-projection (Phi*) measurements")
+    ap.add_argument("--no-shapes", action="store_true",
+                    help="skip the lateral-width (Bluestein) and 3-D volume measurements")
     ap.add_argument("--no-eval", action="store_true",
                     help="skip the evaluation loop (interpolated ISAM, NCC, lambda search)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -583,6 +585,83 @@ def serve_comparison(dev, stream, n_req: int = 2000, rate_hz: float = 200.0, low
 
 # ------------------------------------------------------------ our arm
 
+# ------------------------------------------------------------ other shapes
+
+def shapes_section(dev, stream, peak: float) -> dict:
+    """Shapes beyond the B-scan workload, with the data of Sec. 3.1 in mind (1024 x 1024
+    A-scans): a lateral width with a prime factor above 7, whose lateral transform runs
+    in the Bluestein form (1021), beside the 7-smooth width next to it (1024), both at
+    2048 depth pixels; and a 256 x 256 x 512 volume (a 2-D lateral transform).  Phi +
+    Phi^H pairs per second, back to back, against the algorithmic bytes of a pair,
+    2 (b_x + b_y + bit-packed mask); for the volume also an l1 FISTA solve."""
+    import torch
+
+    from paper_2108_01438_gb300 import mbir, workloads
+
+    def pair_ms(plan, x, mask, yshape, n):
+        y = torch.empty(yshape, dtype=plan.real_dtype, device=dev)
+        xa = torch.empty_like(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plan.forward(x, mask, out=y, stream=stream)
+                plan.adjoint(y, mask, out=xa, stream=stream)
+            e0.record(stream)
+            for _ in range(n):
+                plan.forward(x, mask, out=y, stream=stream)
+                plan.adjoint(y, mask, out=xa, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def entry(ms, nvox, nmeas, extra):
+        alg = 2 * (8 * nvox + 4 * nmeas + nmeas / 8)
+        gbs = alg / (ms * 1e-3) / 1e9
+        return dict(extra, pairs_per_sec=1e3 / ms, ms_per_pair=ms, alg_bytes_per_pair=alg, achieved_gbs=gbs,
+                    frac=gbs / peak)
+
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2108)
+    res = {}
+    for nx in (1021, 1024):
+        d = workloads.geometry(nx, 2048, 2048)
+        plan = mbir.Plan(d)
+        x = torch.randn((nx, 2048), dtype=torch.complex64, device=dev, generator=gen)
+        mask = torch.from_numpy(workloads.mask_ascans(nx, 2048, 0.5, 7)).to(dev)
+        ms = pair_ms(plan, x, mask, (nx, 2048), 100)
+        res[f"bscan_{nx}x2048"] = entry(ms, nx * 2048, nx * 2048, {
+            "lateral_transform": "Bluestein (chirp-z, length 2048)" if nx == 1021 else "mixed radix"})
+        plan.close()
+    nx, ny, nz = 256, 256, 512
+    d = workloads.geometry(nx, nz, nz)
+    vol = mbir.VolumePlan(d, ny)
+    x = torch.randn((nx, ny, nz), dtype=torch.complex64, device=dev, generator=gen)
+    mask = (torch.rand((nx, ny, nz), device=dev, generator=gen) < 0.5).to(torch.uint8)
+    ms = pair_ms(vol, x, mask, (nx, ny, nz), 10)
+    v = entry(ms, nx * ny * nz, nx * ny * nz, {"l2": "image 268 MB, larger than L2"})
+    # l1 FISTA on a sparse volume: 2000 unit scatterers of random phase, half of the samples
+    xt = torch.zeros((nx * ny * nz,), dtype=torch.complex64, device=dev)
+    idx = torch.randperm(nx * ny * nz, device=dev, generator=gen)[:2000]
+    ph = torch.rand((2000,), device=dev, generator=gen) * 6.283185307179586
+    xt[idx] = torch.polar(torch.ones_like(ph), ph)
+    y = vol.forward(xt.view(nx, ny, nz), mask)
+    iters, power = 20, 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        vol.solve(y, mask, lam=0.01, relative=True, iters=2, power_iters=2, stream=stream)
+        e0.record(stream)
+        _, info = vol.solve(y, mask, lam=0.01, relative=True, iters=iters, power_iters=power, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    v["fista_l1"] = {"iters": iters, "power_iters": power, "ms_per_solve": solve_ms,
+                     "voxel_iterations_per_sec": nx * ny * nz * (iters + power) / (solve_ms * 1e-3),
+                     "note": "each FISTA and power step is one volume Phi and one volume Phi^H"}
+    res[f"volume_{nx}x{ny}x{nz}"] = v
+    vol.close()
+    return res
+
+
 def run_ours(args, rank: int, ws: int, local: int) -> None:
     import numpy as np
     import torch
@@ -899,6 +978,14 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
                              POWER_ITERS, ITERS)),
                "pairs_per_sec": 1.0 / ot["t_pair"], "nproc": hc["nproc"], "cpu_model": hc["model"]}
 
+    shapes = None
+    if rank == 0 and not args.no_shapes:
+        # last: these sizes run nowhere else in the bench
+        try:
+            shapes = shapes_section(dev, torch.cuda.Stream(device=dev), peak)
+        except Exception as exc:   # report, keep the line
+            shapes = {"error": str(exc)[:300]}
+
     if rank == 0:
         step_sorted = sorted(step_ms)
         line = {
@@ -919,6 +1006,7 @@ def run_ours(args, rank: int, ws: int, local: int) -> None:
             "tv": tv_res,
             "hilbert": hil_res,
             "evaluation": eval_res,
+            "shapes": shapes,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * 4 + mask.numel(),
