@@ -319,7 +319,8 @@ int mbir_solve(mbir_plan plan, const void* y, const uint8_t* mask, const mbir_so
  * rel_tol must be 0 (fixed iteration count), the penalty l1 or db4 and the
  * back-projection the transpose.  info (NULL or n entries) receives
  * iters, lipschitz, step and lambda_used; objective is not evaluated (NaN).
- * Synchronous at set-up (one read-back for the whole batch) and when info != NULL.
+ * Synchronous at set-up (one read-back for the shared scans, and the read-backs
+ * of mbir_solve for each wide scan) and when info != NULL.
  */
 int mbir_solve_batch(mbir_plan* plans, int32_t n, const void* const* y, const uint8_t* const* mask,
                      const mbir_solve_opts* opts, void* const* x, mbir_solve_info* info, void* stream);
